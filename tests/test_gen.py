@@ -1,0 +1,42 @@
+"""Input generators: valid CSR (sorted, unique columns) with the documented sizes."""
+import numpy as np
+
+import gen
+
+
+def test_lap2d_shape():
+    A = gen.lap2d(64)
+    A.validate()
+    assert A.shape == (4096, 4096) and A.nnz == 20224
+    assert set(np.unique(A.val).tolist()) == {4.0, -1.0}
+
+
+def test_lap3d27_and_aggregation_shapes():
+    A = gen.lap3d27(8)
+    A.validate()
+    assert A.nnz == 22 ** 3                       # (3g-2)^3 entries for a 27-point stencil
+    P = gen.agg_P(8)
+    P.validate()
+    assert P.shape == (512, 64) and P.nnz == 512
+    assert np.all(np.diff(P.row_ptr) == 1)
+    R = gen.transpose(P)
+    R.validate()
+    assert R.shape == (64, 512) and np.all(np.diff(R.row_ptr) == 8)
+
+
+def test_rmat_is_seeded_and_valid():
+    A1 = gen.rmat(12, 16, seed=1)
+    A2 = gen.rmat(12, 16, seed=1)
+    A1.validate()
+    assert np.array_equal(A1.col, A2.col) and np.array_equal(A1.val, A2.val)
+    assert A1.nnz <= 16 * 4096
+    assert np.all(np.abs(A1.val) <= 1.0)
+    # power law: the first row (highest quadrant probability) is far longer than average
+    assert np.diff(A1.row_ptr)[0] > 10 * A1.nnz / A1.nrows
+
+
+def test_families_valid():
+    for fam, param in [("banded", 7), ("blockdiag", 16), ("er", 12), ("rmat", 8)]:
+        M = gen.family_matrix(fam, 1000, param, seed=3)
+        M.validate()
+        assert M.nrows >= 1000
