@@ -1,0 +1,407 @@
+"""Benchmark: FP64 CSR SpGEMM throughput (GFLOP/s = 2 * products / s) on one GB300.
+
+Default workload: C = A*A, A = R-MAT with 2^16 rows/cols, 16 samples/row
+(a,b,c,d = .57,.19,.19,.05, duplicates merged, values U(-1,1), seed 1).  A step is
+one full pass of the four-stage framework (symbolic + numeric: stages 1-4,
+including the size read-backs and allocations the method needs) on inputs that
+are already resident in device memory.  L2 is flushed (a 512 MB write) between
+timed steps, outside the timed events.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle (the reference arm)
+on the same workload.  Under torchrun each rank runs an independent replica (the
+method does not exchange data between problems), and rank 0 reports the
+aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rmat16x16": "C = A*A, A = R-MAT 2^16 x 2^16, 16 samples/row (.57,.19,.19,.05), U(-1,1), seed 1",
+    "lap2d64": "C = A*A, A = 2D 5-point Laplacian on a 64x64 grid",
+    "galerkin64": "Ac = R*(A*P), A = 27-point Laplacian on 64^3, P = 2x2x2 aggregation, R = P^T",
+    "rmat20x8": "C = A*A, A = R-MAT 2^20 x 2^20, 8 samples/row, U(-1,1), seed 1",
+}
+
+
+def make_workload(name):
+    import gen
+    if name == "rmat16x16":
+        A = gen.rmat(16, 16, seed=1)
+        return [(A, A)]
+    if name == "lap2d64":
+        A = gen.lap2d(64)
+        return [(A, A)]
+    if name == "rmat20x8":
+        A = gen.rmat(20, 8, seed=1)
+        return [(A, A)]
+    if name == "galerkin64":
+        A = gen.lap3d27(64)
+        P = gen.agg_P(64)
+        R = gen.transpose(P)
+        return [(A, P), (R, None)]  # second product multiplies R by the first result
+    raise ValueError(name)
+
+
+def src_digest(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "merge": ["paper_1504_05022_gb300/csrc/merge.cu", "paper_1504_05022_gb300/csrc/common.cuh"],
+    "arrange": ["paper_1504_05022_gb300/csrc/arrange.cu", "paper_1504_05022_gb300/csrc/scan.cuh"],
+    "esc": ["paper_1504_05022_gb300/csrc/esc.cu"],
+    "heap": ["paper_1504_05022_gb300/csrc/heap.cu"],
+    "bound": ["paper_1504_05022_gb300/csrc/stage12.cu", "paper_1504_05022_gb300/csrc/scan.cuh"],
+    "bin": ["paper_1504_05022_gb300/csrc/stage12.cu"],
+}
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # median over the samples taken under load (upper half of the clock distribution)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(A, B, u, rows_sel, row_nnz):
+    """Bytes of A (12 B per entry + 16 B B.row_ptr pair per entry), touched B rows (12 B per
+    product) and C~/C rows (12 B per output entry) for the rows in rows_sel."""
+    la = np.diff(A.row_ptr)[rows_sel]
+    return int(la.sum()) * 28 + int(u[rows_sel].sum()) * 12 + int(row_nnz[rows_sel].sum()) * 12
+
+
+def run_ours(args, rank, world, device):
+    import torch
+
+    import paper_1504_05022_gb300 as spg
+
+    spg.load_library()
+    pairs = make_workload(args.workload)
+    dev = torch.device(f"cuda:{device}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    Ad = [spg.CSR.from_host(A, device=dev, rowptr_dtype=torch.int32) for A, _ in pairs]
+    Bd = [spg.CSR.from_host(B, device=dev, rowptr_dtype=torch.int32) if B is not None and B is not A else None
+          for A, B in pairs]
+    opts = dict(alloc_policy=args.policy, record_timing=True)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        prev = None
+        plans = []
+        for i in range(len(pairs)):
+            A_ = Ad[i] if Ad[i] is not None else prev
+            if pairs[i][1] is None:          # chained: R * (previous result)
+                B_ = prev
+            elif pairs[i][1] is pairs[i][0]:  # A*A
+                B_ = A_
+            else:
+                B_ = Bd[i]
+            plan = spg.Plan(A_, B_, stream=stream, **opts)
+            prev = plan.numeric()
+            plans.append(plan)
+        return plans, prev
+
+    for _ in range(args.warmup):
+        plans, C = step()
+        del plans, C
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    times, kms, launches, stats0 = [], {}, 0, None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(device) as clk:
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            plans, C = step()
+            ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            for p in plans:
+                st = p.stats()
+                stats0 = stats0 or st
+                for name, ms in st["kernel_ms"].items():
+                    kms[name] = kms.get(name, 0.0) + ms
+                launches += sum(st["launches"].values())
+            del plans, C
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    times = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    ms_step = float(np.mean(times))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    # products per step (sum over the chained products)
+    plans, C = step()
+    sum_u = sum(p.upper_bound_nnz for p in plans)
+    st_all = [p.stats() for p in plans]
+    arrays = [p.arrays() for p in plans]
+    torch.cuda.synchronize()
+    flops = 2.0 * sum_u
+    value = flops * world / (ms_step * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel class ----
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dom = max(kms, key=lambda k: kms[k]) if kms else "merge"
+    dom_ms = kms.get(dom, 0.0) / args.steps
+    dom_launches = sum(s["launches"].get(dom, 0) for s in st_all)
+    bytes_dom = 0
+    for (A, B), arr in zip(pairs, arrays):
+        if B is None or A is None:
+            continue
+        u = arr["u"]
+        rn = arr["row_nnz"].astype(np.int64)
+        bins = arr["bin"]
+        if dom == "merge":
+            sel = bins == 37
+        elif dom == "esc":
+            sel = (bins >= 33) & (bins <= 36)
+        elif dom == "heap":
+            sel = (bins >= 2) & (bins <= 32)
+        else:
+            sel = np.ones(u.shape[0], dtype=bool)
+        if dom == "arrange":
+            bytes_dom += int(rn.sum()) * 24 + 8 * (u.shape[0] + 1)
+        elif dom in ("bound", "bin", "scan"):
+            bytes_dom += A.nnz * 12 + 16 * u.shape[0]
+        else:
+            bytes_dom += algorithmic_bytes(A, B, u, np.nonzero(sel)[0], rn)
+    achieved = bytes_dom / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
+    traffic = None
+    tj = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tj):
+        try:
+            t = json.load(open(tj))
+            ent = t.get(args.workload, {}).get(dom)
+            if ent and ent.get("source_digest") == src_digest(KERNEL_SOURCES.get(dom, [])):
+                traffic = ent.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
+                "peak_source": peak_src, "algorithmic_bytes_per_step": bytes_dom,
+                "ms_per_step": dom_ms, "launches_per_step": dom_launches}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = run_e2e(args, spg, pairs, dev, stream, opts)
+
+    out = {
+        "metric": "FP64 SpGEMM GFLOP/s (2*products/s)",
+        "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded generator)",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                   "alloc_policy": args.policy, "products_per_step": sum_u,
+                   "nnz_C": int(st_all[-1]["nnz_c"]), "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "wall_s_timed": t_wall,
+        "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "stats": {"merge_rounds": st_all[-1]["merge_rounds"], "rows_relaunched": st_all[-1]["rows_relaunched"],
+                  "rows_level1": st_all[-1]["rows_level1"], "peak_bytes": max(s["peak_bytes"] for s in st_all),
+                  "bytes_ctilde": sum(s["bytes_ctilde"] for s in st_all)},
+        "clocks": clk.summary(),
+    }
+    return out
+
+
+def run_e2e(args, spg, pairs, dev, stream, opts):
+    """Same metric through the public API with host buffers: pinned host -> device copies of
+    the inputs, the product, and a device -> host read of the whole result, all timed."""
+    import torch
+    if len(pairs) != 1 or pairs[0][1] is not pairs[0][0]:
+        return None
+    A = pairs[0][0]
+    hp = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+          for x in (A.row_ptr.astype(np.int32), A.col, A.val)]
+    h2d = sum(t.numel() * t.element_size() for t in hp)
+    reps = max(3, min(args.steps, 10))
+    times, d2h = [], 0
+    out_host = None
+    for k in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rp, col, val = (t.to(dev, non_blocking=True) for t in hp)
+        Ad = spg.CSR(rp, col, val, (A.nrows, A.ncols))
+        C = spg.Plan(Ad, Ad, stream=stream, alloc_policy=opts["alloc_policy"]).numeric()
+        if out_host is None or out_host[1].numel() != C.nnz:
+            out_host = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in (C.row_ptr, C.col, C.val)]
+        for h, d in zip(out_host, (C.row_ptr, C.col, C.val)):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        d2h = sum(t.numel() * t.element_size() for t in out_host)
+        del C, Ad
+        if k > 0:
+            times.append(dt)
+    u_sum = int(_products(A))
+    t = float(np.median(times))
+    return {"value": 2.0 * u_sum / t / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": t * 1e3}
+
+
+def _products(A):
+    blen = np.diff(A.row_ptr)
+    return blen[A.col].sum()
+
+
+def run_cpu_baseline(args, budget_s=20.0):
+    """The oracle, as it stands, on the host cores: repeated full passes over the workload
+    (or a row sample when a pass is too long), median time, GFLOP/s on the products computed."""
+    import oracle
+    pairs = make_workload(args.workload)
+    A, B = pairs[0]
+    B = A if B is None else B
+    nthreads = oracle.num_threads()
+    blen = np.diff(B.row_ptr)
+    u = np.add.reduceat(blen[A.col], A.row_ptr[:-1]) if A.nnz else np.zeros(A.nrows, np.int64)
+    u[np.diff(A.row_ptr) == 0] = 0
+    total_u = int(u.sum())
+    rows = None
+    sample = "full workload"
+    # keep one pass under ~budget/3 seconds assuming >= 20M products/s/thread
+    cap_products = int(20e6 * nthreads * budget_s / 3)
+    if total_u > cap_products:
+        rng = np.random.default_rng(0)
+        perm = rng.permutation(A.nrows)
+        cs = np.cumsum(u[perm])
+        rows = np.sort(perm[: int(np.searchsorted(cs, cap_products)) + 1])
+        sample = f"{rows.size} of {A.nrows} rows (random, seed 0)"
+    prods = total_u if rows is None else int(u[rows].sum())
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < 5 and (time.perf_counter() - t_start) < budget_s:
+        t0 = time.perf_counter()
+        oracle.spgemm_rows(A, B, rows, nthreads=nthreads)
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    return {"value": 2.0 * prods / t / 1e9, "unit": "GFLOP/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"{sample}; {prods} products; median of {len(times)} passes",
+            "ms_per_pass": t * 1e3}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat16x16", choices=list(WORKLOADS))
+    ap.add_argument("--policy", default="hybrid", choices=["hybrid", "upper_bound", "learned"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = run_cpu_baseline(args, budget_s=max(20.0, 6.0 * (args.steps + args.warmup)))
+        out = {"metric": "FP64 SpGEMM GFLOP/s (2*products/s)", "value": cb["value"], "unit": "GFLOP/s",
+               "impl": "reference", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": cb["ms_per_pass"], "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+               "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
+               "cpu_baseline": cb,
+               "e2e": {"value": cb["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world, local)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = run_cpu_baseline(args)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * spgemm.h -- C ABI of a GB300 (sm_103a) CSR SpGEMM library, C = A * B, FP64.
+ *
+ * The library implements the four-stage framework of Liu & Vinter, "A
+ * Framework for General Sparse Matrix-Matrix Multiplication on GPUs and
+ * Heterogeneous Processors" (JPDC 2015), Section 4.1:
+ *   stage 1  per-row upper bound u_i of the intermediate products (Algorithm 2);
+ *   stage 2  binning of rows by u_i into 38 bins and allocation of the
+ *            temporary matrix C~ with the hybrid policy (Algorithm 3) --
+ *            computed on the GPU here, without atomics;
+ *   stage 3  per-bin insert-and-accumulate: heap method (bins u = 2..32),
+ *            bitonic expand-sort-compress (u = 33..512), merge method with
+ *            progressive reallocation and a level-1 sequence (u > 512);
+ *   stage 4  prefix sum of the row sizes and compaction of C~ into C.
+ *
+ * All pointers inside spgemm_csr_in / spgemm_csr_out are DEVICE pointers on the
+ * device that is current when spgemm_symbolic is called.  No function throws;
+ * every function returns an spgemm_status.  A plan is used by one host thread at
+ * a time.  Everything a plan launches is ordered on the stream given to
+ * spgemm_symbolic.
+ */
+#ifndef SPGEMM_H
+#define SPGEMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL means the legacy default stream. */
+typedef struct CUstream_st *spgemm_stream_t;
+
+typedef enum spgemm_status {
+    SPGEMM_OK = 0,
+    SPGEMM_ERR_INVALID_ARG = 1, /* NULL where a pointer is required, negative size, bad option */
+    SPGEMM_ERR_SHAPE = 2,       /* A.ncols != B.nrows, or a dimension beyond the supported range */
+    SPGEMM_ERR_UNSORTED = 3,    /* check_inputs: a row's column indices are not strictly ascending,
+                                   out of range, or row_ptr is not a valid prefix array */
+    SPGEMM_ERR_OOM = 4,         /* a device allocation failed; the plan stays freeable */
+    SPGEMM_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
+    SPGEMM_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    SPGEMM_ERR_INTERNAL = 7     /* an internal consistency check failed */
+} spgemm_status;
+
+/*
+ * Input matrix in CSR format (Section 2.1): row_ptr has nrows+1 entries with
+ * row_ptr[0] = 0 and row_ptr[nrows] = nnz; row i holds col_idx/val entries
+ * row_ptr[i] .. row_ptr[i+1]-1 with column indices strictly ascending (the
+ * sorted-column assumption of Section 3.2; duplicates are not allowed).
+ * row_ptr is int32 (rowptr_bits = 32) or int64 (rowptr_bits = 64).
+ * Requirements: 0 <= nrows, ncols <= 2^31 - 1.  Borrowed: the arrays must stay
+ * valid and unchanged until the work enqueued by spgemm_numeric has completed.
+ * A value stored as 0.0 is still a structural entry.
+ */
+typedef struct spgemm_csr_in {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    const void *row_ptr;
+    int32_t rowptr_bits;
+    const int32_t *col_idx;
+    const double *val;
+} spgemm_csr_in;
+
+/*
+ * Result matrix C in CSR format, owned by the plan: valid from the completion
+ * of spgemm_numeric's work on the plan's stream until spgemm_free.  row_ptr is
+ * always int64 (nrows+1 entries); each row's columns are strictly ascending.
+ * Every (i, j) with a structural a_ik and b_kj is present, also when the sum
+ * cancels to 0.0 (Section 3.1).
+ */
+typedef struct spgemm_csr_out {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    int64_t *row_ptr;
+    int32_t *col_idx;
+    double *val;
+} spgemm_csr_out;
+
+/* Memory pre-allocation policy for the temporary matrix C~ (Section 3.1). */
+typedef enum spgemm_alloc_policy {
+    /* The paper's hybrid method: rows with u_i <= 512 get u_i slots, longer rows
+       start at initial_cap slots and grow x2 per relaunch (Section 4.1). */
+    SPGEMM_ALLOC_HYBRID = 0,
+    /* Every row gets u_i slots (the upper-bound method of Section 3.1); long rows
+       still run in shared memory and use the level-1 sequence when too long. */
+    SPGEMM_ALLOC_UPPER_BOUND = 1,
+    /* Rows are sized from a learned prediction of nnz(c_i) (see
+       spgemm_predictor_*); a row whose result exceeds its prediction falls back
+       to the exact path, so C is unchanged. */
+    SPGEMM_ALLOC_LEARNED = 2
+} spgemm_alloc_policy;
+
+/* Options; initialise with spgemm_opts_init and change fields as needed. */
+typedef struct spgemm_opts {
+    int32_t alloc_policy;    /* spgemm_alloc_policy */
+    int32_t initial_cap;     /* first temporary row size of bin 37 (paper: 256) */
+    int32_t check_inputs;    /* 1: validate A and B on the device (one pass) */
+    int32_t record_timing;   /* 1: time every kernel with CUDA events (spgemm_plan_stats) */
+    int32_t merge_batch;     /* products per batch in the bin-37 merge kernel (0 = auto) */
+    int32_t smem_cap_max;    /* largest result capacity held in shared memory (0 = auto) */
+    int32_t heap_block;      /* threads per block of the heap kernel (0 = auto) */
+    int32_t reserved[9];
+    const void *predictor;   /* spgemm_predictor* for SPGEMM_ALLOC_LEARNED, else NULL */
+    double predictor_margin; /* predicted size is multiplied by this before rounding up */
+} spgemm_opts;
+
+/* Fills *opts with the defaults (hybrid policy, initial_cap 256, no checks). */
+spgemm_status spgemm_opts_init(spgemm_opts *opts);
+
+typedef struct spgemm_plan spgemm_plan;
+
+/*
+ * Stages 1 and 2.  Computes u_i for every row of A (Algorithm 2), bins the
+ * rows (Algorithm 3) and allocates C~.  Enqueues on `stream` and synchronises it
+ * once to read the 38 bin sizes (the host decides which per-bin kernels to
+ * launch, Section 4.1).  On success *plan_out owns the temporaries and, if
+ * upper_bound_nnz_out is not NULL, receives sum_i u_i = nnz(C^) = flops/2.
+ * On error *plan_out is set to NULL and nothing stays allocated.
+ */
+spgemm_status spgemm_symbolic(const spgemm_csr_in *A, const spgemm_csr_in *B,
+                              const spgemm_opts *opts, spgemm_stream_t stream,
+                              spgemm_plan **plan_out, int64_t *upper_bound_nnz_out);
+
+/*
+ * Stages 3 and 4.  Runs the per-bin kernels (including the progressive
+ * relaunches of bin 37), scans the row sizes, allocates C and compacts C~ into
+ * it.  Synchronises the plan's stream when it needs a size on the host (each
+ * progressive round, and nnz(C) before C is allocated).  On success *C_out
+ * describes C, owned by the plan.  Calling it twice returns the same C.
+ */
+spgemm_status spgemm_numeric(spgemm_plan *plan, spgemm_csr_out *C_out);
+
+/* Releases every device buffer of the plan (stream-ordered on its stream) and
+   the plan itself.  NULL is accepted. */
+spgemm_status spgemm_free(spgemm_plan *plan);
+
+/* Static English text for a status code. */
+const char *spgemm_status_string(spgemm_status status);
+
+/* Kernel classes reported by spgemm_plan_stats. */
+typedef enum spgemm_kernel_id {
+    SPGEMM_K_BOUND = 0,     /* stage 1: upper bound (prefix sum of B-row lengths over A) */
+    SPGEMM_K_BIN = 1,       /* stage 2: histogram, scan and scatter of the 38 bins */
+    SPGEMM_K_HEAP = 2,      /* stage 3, bins 2..32 */
+    SPGEMM_K_ESC = 3,       /* stage 3, bins 33..36 */
+    SPGEMM_K_MERGE = 4,     /* stage 3, bin 37 (all progressive rounds and level-1) */
+    SPGEMM_K_SCAN = 5,      /* stage 4: prefix sum of nnz(c_i) */
+    SPGEMM_K_ARRANGE = 6,   /* stage 4: copy of C~ into C (and the u_i = 1 rows) */
+    SPGEMM_K_OTHER = 7,     /* validation, predictor, bookkeeping */
+    SPGEMM_K_COUNT = 8
+} spgemm_kernel_id;
+
+typedef struct spgemm_stats {
+    int64_t bin_count[38];      /* rows per bin (Algorithm 3) */
+    int64_t sum_u;              /* sum of u_i = number of products */
+    int64_t nnz_ctilde;         /* entries allocated for C~ in stage 2 */
+    int64_t nnz_c;              /* nnz(C), after spgemm_numeric */
+    int64_t merge_rounds;       /* launches of the bin-37 kernel (progressive rounds) */
+    int64_t rows_relaunched;    /* bin-37 rows that overflowed at least once */
+    int64_t rows_level1;        /* bin-37 rows finished with a level-1 sequence */
+    int64_t rows_fallback;      /* rows recomputed because a prediction was too small */
+    int64_t bytes_ctilde;       /* device bytes allocated for temporary rows (all rounds) */
+    int64_t peak_bytes;         /* high-water mark of the library's device pool since symbolic */
+    int32_t launches[SPGEMM_K_COUNT];  /* kernels launched per class */
+    float kernel_ms[SPGEMM_K_COUNT];   /* summed event time per class (record_timing = 1) */
+} spgemm_stats;
+
+/* Copies the plan's counters into *out.  Timings are read after synchronising
+   the plan's stream. */
+spgemm_status spgemm_plan_stats(spgemm_plan *plan, spgemm_stats *out);
+
+/*
+ * Read-only views of a plan's intermediate arrays (device pointers owned by the
+ * plan, valid until spgemm_free; bin_start is a host array inside the plan):
+ *   u[m]             upper bound of each row of C (Algorithm 2, stage 1)
+ *   bin[m]           bin of each row, 0..37 (Algorithm 3, stage 2)
+ *   bin_rows[m]      row ids grouped by bin, ascending within each bin
+ *   bin_start[39]    offsets of the 38 bins in bin_rows
+ *   ctilde_row_ptr   m+1 offsets of the rows of C~ as first allocated (stage 2)
+ *   row_nnz[m]       nnz(c_i); complete after spgemm_numeric (stage 3)
+ */
+typedef struct spgemm_plan_arrays {
+    int64_t nrows;
+    const int64_t *u;
+    const uint8_t *bin;
+    const int32_t *bin_rows;
+    const int64_t *bin_start;
+    const int64_t *ctilde_row_ptr;
+    const int32_t *row_nnz;
+} spgemm_plan_arrays;
+
+spgemm_status spgemm_plan_arrays_get(spgemm_plan *plan, spgemm_plan_arrays *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPGEMM_H */

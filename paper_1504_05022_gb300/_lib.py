@@ -1,0 +1,99 @@
+"""ctypes mirror of include/spgemm.h (argument marshalling only).
+
+Loads paper_1504_05022_gb300/_build/libspgemm.so.  If the library is missing the
+import fails loudly: there is no CPU fallback."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+c_i32, c_i64, c_ptr, c_f64, c_f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double, ctypes.c_float
+
+STATUS = {
+    0: "SPGEMM_OK", 1: "SPGEMM_ERR_INVALID_ARG", 2: "SPGEMM_ERR_SHAPE", 3: "SPGEMM_ERR_UNSORTED",
+    4: "SPGEMM_ERR_OOM", 5: "SPGEMM_ERR_CUDA", 6: "SPGEMM_ERR_TIMEOUT", 7: "SPGEMM_ERR_INTERNAL",
+}
+POLICY = {"hybrid": 0, "upper_bound": 1, "learned": 2}
+KERNELS = ["bound", "bin", "heap", "esc", "merge", "scan", "arrange", "other"]
+NUM_BINS = 38
+
+
+class CsrIn(ctypes.Structure):
+    _fields_ = [("nrows", c_i64), ("ncols", c_i64), ("nnz", c_i64), ("row_ptr", c_ptr),
+                ("rowptr_bits", c_i32), ("col_idx", c_ptr), ("val", c_ptr)]
+
+
+class CsrOut(ctypes.Structure):
+    _fields_ = [("nrows", c_i64), ("ncols", c_i64), ("nnz", c_i64), ("row_ptr", c_ptr),
+                ("col_idx", c_ptr), ("val", c_ptr)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("alloc_policy", c_i32), ("initial_cap", c_i32), ("check_inputs", c_i32),
+                ("record_timing", c_i32), ("merge_batch", c_i32), ("smem_cap_max", c_i32),
+                ("heap_block", c_i32), ("reserved", c_i32 * 9), ("predictor", c_ptr),
+                ("predictor_margin", c_f64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("bin_count", c_i64 * NUM_BINS), ("sum_u", c_i64), ("nnz_ctilde", c_i64), ("nnz_c", c_i64),
+                ("merge_rounds", c_i64), ("rows_relaunched", c_i64), ("rows_level1", c_i64),
+                ("rows_fallback", c_i64), ("bytes_ctilde", c_i64), ("peak_bytes", c_i64),
+                ("launches", c_i32 * 8), ("kernel_ms", c_f32 * 8)]
+
+
+class PlanArrays(ctypes.Structure):
+    _fields_ = [("nrows", c_i64), ("u", c_ptr), ("bin", c_ptr), ("bin_rows", c_ptr), ("bin_start", c_ptr),
+                ("ctilde_row_ptr", c_ptr), ("row_nnz", c_ptr)]
+
+
+# Every function declared in include/spgemm.h, with its ctypes signature.
+SIGNATURES = {
+    "spgemm_opts_init": ([ctypes.POINTER(Opts)], c_i32),
+    "spgemm_symbolic": ([ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(Opts), c_ptr,
+                         ctypes.POINTER(c_ptr), ctypes.POINTER(c_i64)], c_i32),
+    "spgemm_numeric": ([c_ptr, ctypes.POINTER(CsrOut)], c_i32),
+    "spgemm_free": ([c_ptr], c_i32),
+    "spgemm_status_string": ([c_i32], ctypes.c_char_p),
+    "spgemm_plan_stats": ([c_ptr, ctypes.POINTER(Stats)], c_i32),
+    "spgemm_plan_arrays_get": ([c_ptr, ctypes.POINTER(PlanArrays)], c_i32),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Returns the loaded library.  Builds it first when missing and a compiler exists."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libspgemm.so not built ({path}); run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+class SpgemmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = load().spgemm_status_string(code).decode()
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({msg})")
+
+
+def check(code: int, where: str) -> None:
+    if code != 0:
+        raise SpgemmError(code, where)

@@ -1,0 +1,99 @@
+// Stage 4 (Section 4.1, "arranging data"): the sizes nnz(c_i) are summed by an
+// exclusive prefix sum into C.row_ptr (int64), C is allocated by the host, and
+// the rows are copied from the temporary matrix C~ into C.  Rows of bin 1 hold a
+// single product, which is computed here directly; rows of bin 0 need nothing.
+// Bins 2..36 are copied by one warp per row, bin 37 by one CTA per row.
+#include "internal.h"
+#include "scan.cuh"
+
+namespace spg {
+
+struct LoadNnzc {
+    const int32_t *nnzc;
+    SPG_DEV int64_t operator()(int64_t i) const { return (int64_t)nnzc[i]; }
+};
+struct StoreRp {
+    int64_t *rp;
+    SPG_DEV void operator()(int64_t i, int64_t v) const { rp[i] = v; }
+};
+
+cudaError_t launch_row_scan(int64_t m, const int32_t *nnzc, int64_t *c_rp, int64_t *partial,
+                            cudaStream_t st) {
+    return device_exclusive_scan(m, LoadNnzc{nnzc}, StoreRp{c_rp}, partial, c_rp + m, st);
+}
+
+constexpr int ARR_NT = 256;
+
+__global__ void __launch_bounds__(ARR_NT)
+k_arrange_short(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows, const uint8_t *__restrict__ bin,
+                const int64_t *__restrict__ c_rp, int32_t *__restrict__ c_col, double *__restrict__ c_val) {
+    const int64_t wg = ((int64_t)blockIdx.x * ARR_NT + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wg >= nrows) return;
+    const int row = rows[wg];
+    const int64_t o = c_rp[row];
+    if (bin[row] == 1) {
+        // exactly one A entry of this row selects a B row of length 1
+        const int64_t a0 = a.A.rp[row], a1 = a.A.rp[row + 1];
+        for (int64_t base = a0; base < a1; base += 32) {
+            const int64_t p = base + lane;
+            int64_t b0 = 0;
+            bool hit = false;
+            if (p < a1) {
+                const int32_t j = a.A.col[p];
+                b0 = a.B.rp[j];
+                hit = (a.B.rp[j + 1] - b0) > 0;
+            }
+            const unsigned m = __ballot_sync(SPG_FULL, hit);
+            if (m) {
+                if (lane == __ffs(m) - 1) {
+                    c_col[o] = a.B.col[b0];
+                    c_val[o] = a.A.val[p] * a.B.val[b0];
+                }
+                break;
+            }
+        }
+        return;
+    }
+    const int64_t n = c_rp[row + 1] - o;
+    const int64_t src = a.ctil_rp[row];
+    for (int64_t t = lane; t < n; t += 32) {
+        c_col[o + t] = a.ctil_col[src + t];
+        c_val[o + t] = a.ctil_val[src + t];
+    }
+}
+
+cudaError_t launch_arrange_short(const StageArgs &a, const int32_t *rows, int64_t nrows,
+                                 const uint8_t *bin, const int64_t *c_rp, int32_t *c_col,
+                                 double *c_val, cudaStream_t st) {
+    if (nrows <= 0) return cudaSuccess;
+    const int64_t threads = nrows * 32;
+    k_arrange_short<<<(unsigned)((threads + ARR_NT - 1) / ARR_NT), ARR_NT, 0, st>>>(a, rows, nrows, bin, c_rp,
+                                                                                   c_col, c_val);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(ARR_NT)
+k_arrange_long(MergeState s, const int32_t *__restrict__ rows37, const int64_t *__restrict__ c_rp,
+               int32_t *__restrict__ c_col, double *__restrict__ c_val) {
+    const int j = blockIdx.x;
+    const int row = rows37[j];
+    const int64_t o = c_rp[row];
+    const int64_t n = s.len[j];
+    const int32_t *sc = s.loc_col[j];
+    const double *sv = s.loc_val[j];
+    for (int64_t t = threadIdx.x; t < n; t += ARR_NT) {
+        c_col[o + t] = sc[t];
+        c_val[o + t] = sv[t];
+    }
+}
+
+cudaError_t launch_arrange_long(const MergeState &s, const int32_t *rows37, int64_t n37,
+                                const int64_t *c_rp, int32_t *c_col, double *c_val,
+                                cudaStream_t st) {
+    if (n37 <= 0) return cudaSuccess;
+    k_arrange_long<<<(unsigned)n37, ARR_NT, 0, st>>>(s, rows37, c_rp, c_col, c_val);
+    return cudaGetLastError();
+}
+
+}  // namespace spg

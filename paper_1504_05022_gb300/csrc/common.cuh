@@ -1,0 +1,190 @@
+// Device helpers shared by the SpGEMM kernels: warp/block scans, merge-path
+// partitioning and the in-place merges used by the bin-37 merge kernel.
+#pragma once
+
+#include <cstdint>
+#include <climits>
+#include <cuda_runtime.h>
+
+#define SPG_DEV __device__ __forceinline__
+#define SPG_FULL 0xffffffffu
+
+namespace spg {
+
+// Sentinel key used to pad sorting networks; real column indices are < ncols <= INT_MAX.
+constexpr int32_t KEY_PAD = INT_MAX;
+
+SPG_DEV int lane_id() { return threadIdx.x & 31; }
+SPG_DEV int warp_id() { return threadIdx.x >> 5; }
+
+template <typename T>
+SPG_DEV T warp_inclusive_scan(T v) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T n = __shfl_up_sync(SPG_FULL, v, d);
+        if (lane_id() >= d) v += n;
+    }
+    return v;
+}
+
+template <typename T>
+SPG_DEV T warp_reduce_sum(T v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(SPG_FULL, v, d);
+    return v;
+}
+
+// Block-wide exclusive scan.  `scratch` needs NT/32 + 1 elements of T.  Every
+// thread of the block must call it.  Returns the exclusive prefix; `total`
+// receives the block sum.  Ends with a barrier so scratch can be reused.
+template <int NT, typename T>
+SPG_DEV T block_exclusive_scan(T v, T *scratch, T &total) {
+    constexpr int NW = NT / 32;
+    const int lane = lane_id(), wid = warp_id();
+    T inc = warp_inclusive_scan(v);
+    if (lane == 31) scratch[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        T w = (lane < NW) ? scratch[lane] : T(0);
+        T winc = warp_inclusive_scan(w);
+        if (lane < NW) scratch[lane] = winc - w;
+        if (lane == NW - 1) scratch[NW] = winc;
+    }
+    __syncthreads();
+    T res = scratch[wid] + inc - v;
+    total = scratch[NW];
+    __syncthreads();
+    return res;
+}
+
+template <int NT, typename T>
+SPG_DEV T block_reduce_sum(T v, T *scratch) {
+    constexpr int NW = NT / 32;
+    v = warp_reduce_sum(v);
+    if (lane_id() == 0) scratch[warp_id()] = v;
+    __syncthreads();
+    T s = T(0);
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < NW; ++w) s += scratch[w];
+        scratch[NW] = s;
+    }
+    __syncthreads();
+    s = scratch[NW];
+    __syncthreads();
+    return s;
+}
+
+// Number of elements of the sorted array a[0..n) that are < key.
+SPG_DEV int lower_bound_i32(const int32_t *a, int n, int32_t key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Number of elements of the sorted array a[0..n) that are <= key.
+SPG_DEV int upper_bound_i32(const int32_t *a, int n, int32_t key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Largest t in [0, n) with s[t] <= x, for a non-decreasing s with s[0] <= x.
+SPG_DEV int find_segment_i64(const int64_t *s, int n, int64_t x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+SPG_DEV int find_segment_i32(const int32_t *s, int n, int32_t x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Merge path (Green, McColl & Bader): for the stable merge of a[0..na) and
+// b[0..nb) in which a's element goes first on equal keys, returns how many of
+// the first `diag` outputs come from a.
+SPG_DEV int merge_path(const int32_t *a, int na, const int32_t *b, int nb, int diag) {
+    int lo = diag > nb ? diag - nb : 0;
+    int hi = diag < na ? diag : na;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] <= b[diag - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// In-place merge of two disjoint sorted sequences: x (keys xk, values xv,
+// length nx) lives at the front of an array with room for nx + ny entries; y
+// (yk, yv, length ny) lives elsewhere.  Afterwards xk/xv[0 .. nx+ny) hold the
+// merged sequence.  The output is produced in chunks of NT*IPT entries from the
+// right end: an x entry only moves right, so a chunk never overwrites an x entry
+// that a chunk to its left still has to read.  Every thread of the block must
+// call it; it ends with a barrier.
+template <int NT, int IPT>
+SPG_DEV void merge_inplace_rtl(int32_t *xk, double *xv, int nx, const int32_t *yk, const double *yv,
+                               int ny) {
+    if (ny == 0) return;
+    const int n = nx + ny;
+    constexpr int CH = NT * IPT;
+    for (int hi = n; hi > 0; hi -= CH) {
+        const int lo = hi > CH ? hi - CH : 0;
+        int32_t rk[IPT];
+        double rv[IPT];
+        const int d0 = lo + threadIdx.x * IPT;
+        int cnt = 0;
+        if (d0 < hi) {
+            int i = merge_path(xk, nx, yk, ny, d0);
+            int j = d0 - i;
+            cnt = min(IPT, hi - d0);
+#pragma unroll
+            for (int t = 0; t < IPT; ++t) {
+                if (t < cnt) {
+                    bool takex = (i < nx) && (j >= ny || xk[i] <= yk[j]);
+                    if (takex) { rk[t] = xk[i]; rv[t] = xv[i]; ++i; }
+                    else { rk[t] = yk[j]; rv[t] = yv[j]; ++j; }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < IPT; ++t) {
+            if (t < cnt) { xk[d0 + t] = rk[t]; xv[d0 + t] = rv[t]; }
+        }
+        __syncthreads();
+    }
+}
+
+// Out-of-place stable merge of a and b into out (na + nb entries).  All threads call.
+template <int NT>
+SPG_DEV void merge_into(const int32_t *ak, const double *av, int na, const int32_t *bk,
+                        const double *bv, int nb, int32_t *ok, double *ov) {
+    const int n = na + nb;
+    const int ipt = (n + NT - 1) / NT;
+    const int d0 = threadIdx.x * ipt;
+    if (d0 < n) {
+        const int d1 = min(n, d0 + ipt);
+        int i = merge_path(ak, na, bk, nb, d0);
+        int j = d0 - i;
+        for (int d = d0; d < d1; ++d) {
+            bool takea = (i < na) && (j >= nb || ak[i] <= bk[j]);
+            if (takea) { ok[d] = ak[i]; ov[d] = av[i]; ++i; }
+            else { ok[d] = bk[j]; ov[d] = bv[j]; ++j; }
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace spg

@@ -1,0 +1,117 @@
+// Internal interfaces between the host orchestrator (spgemm_api.cu) and the
+// kernel translation units.  Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spg {
+
+constexpr int NUM_BINS = 38;
+constexpr int BIN_HEAP_LO = 2, BIN_HEAP_HI = 32;  // bin group 3 (Section 4.1)
+constexpr int BIN_ESC_LO = 33, BIN_ESC_HI = 36;   // bin group 4
+constexpr int BIN_MERGE = 37;                     // bin group 5
+
+enum AllocPolicy { POLICY_HYBRID = 0, POLICY_UPPER_BOUND = 1, POLICY_LEARNED = 2 };
+
+// CSR with int64 row pointers (int32 inputs are widened once per call).
+struct DevCSR {
+    int64_t nrows, ncols, nnz;
+    const int64_t *rp;
+    const int32_t *col;
+    const double *val;
+};
+
+// Host-visible summary written by stage 2 (copied back in one transfer).
+struct BinSummary {
+    int64_t bin_count[NUM_BINS];
+    int64_t sum_cap;   // nnz(C~) of the initial allocation
+    int64_t sum_u;     // sum u_i
+    int64_t status;    // validation result (0 = ok)
+    int64_t pad;
+};
+
+struct CapPolicy {
+    int policy;
+    int64_t initial_cap;
+    const int32_t *pred_cap;  // learned per-row temporary row sizes (POLICY_LEARNED), may be null
+};
+
+// ---- stage 0/1/2 (stage12.cu) ----
+cudaError_t launch_widen_rowptr(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st);
+cudaError_t launch_validate(const DevCSR &M, int64_t *status, cudaStream_t st);
+// S[j] = sum_{t<j} nnz(b_{A.col[t]*}), S[nnzA] = sum u (Algorithm 2 as a prefix sum).
+cudaError_t launch_bound(const DevCSR &A, const DevCSR &B, int64_t *S, int64_t *partial,
+                         cudaStream_t st);
+int64_t bound_partial_size(int64_t nnzA);
+// Binning scratch sizes for m rows.
+int64_t bin_blocks(int64_t m);
+cudaError_t launch_binning(int64_t m, const int64_t *arp, const int64_t *S,
+                           const int64_t *sum_u_ptr, CapPolicy P, int64_t *u, uint8_t *bin, int32_t *nnzc, int32_t *bin_rows,
+                           int64_t *ctil_rp, int32_t *hist, int64_t *cap_partial,
+                           BinSummary *summary, cudaStream_t st);
+
+// ---- stage 3 ----
+struct StageArgs {
+    DevCSR A, B;
+    const int64_t *ctil_rp;
+    int32_t *ctil_col;
+    double *ctil_val;
+    int32_t *nnzc;
+};
+
+cudaError_t launch_heap(const StageArgs &a, const int32_t *rows, int64_t nrows, int slots, int nt,
+                        cudaStream_t st);
+cudaError_t launch_esc(const StageArgs &a, const int32_t *rows, int64_t nrows, int bin,
+                       cudaStream_t st);
+
+// Bin-37 per-row state (indexed by position j in the bin-37 row list).
+struct MergeState {
+    int32_t **loc_col;   // current global home of the row's sequence
+    double **loc_val;
+    int64_t *loc_cap;    // capacity of that home
+    int32_t *len;        // entries stored there
+    int64_t *ck_entry;   // checkpoint: A-entry index relative to the row start
+    int64_t *ck_off;     // checkpoint: offset inside that B row
+    int32_t *done;       // 1 once the row is final
+};
+
+struct MergeLaunch {
+    const int32_t *rows37;   // bin-37 row list (row ids)
+    const int32_t *work;     // positions j to process (nullptr: j = 0..nwork-1)
+    int64_t nwork;
+    int cap;                 // shared-memory result capacity for this launch
+    int batch;               // products per batch
+    int level1;              // 1: level-1 mode (global result + shared level-1 sequence)
+    int32_t *pool_col;       // per-work-item homes of capacity pool_cap (may be null)
+    double *pool_val;
+    int64_t pool_cap;
+    const int64_t *g_off;    // level-1: per-work-item offset of two global buffers
+    const int64_t *g_cap;    //          and their capacity
+    int32_t *g_col;
+    double *g_val;
+    int32_t *ovf_list;       // rows that overflowed (positions j)
+    int32_t *ovf_count;
+    int64_t *err;            // device error word
+};
+
+int merge_smem_bytes(int cap, int batch);
+int merge_max_cap(int batch, int smem_limit);
+cudaError_t launch_merge(const StageArgs &a, const MergeState &s, const MergeLaunch &L,
+                         const int64_t *u, cudaStream_t st);
+// level-1 buffer sizing: per work item cap = min(u_row, ncols_B) (two buffers each)
+cudaError_t launch_level1_sizes(const int32_t *rows37, const int32_t *work, int64_t nwork,
+                                const int64_t *u, int64_t ncols, int64_t *g_cap, int64_t *g_off,
+                                int64_t *partial, int64_t *total, cudaStream_t st);
+
+// ---- stage 4 (arrange.cu) ----
+cudaError_t launch_row_scan(int64_t m, const int32_t *nnzc, int64_t *c_rp, int64_t *partial,
+                            cudaStream_t st);
+cudaError_t launch_arrange_short(const StageArgs &a, const int32_t *rows, int64_t nrows,
+                                 const uint8_t *bin, const int64_t *c_rp, int32_t *c_col,
+                                 double *c_val, cudaStream_t st);
+cudaError_t launch_arrange_long(const MergeState &s, const int32_t *rows37, int64_t n37,
+                                const int64_t *c_rp, int32_t *c_col, double *c_val,
+                                cudaStream_t st);
+
+}  // namespace spg

@@ -1,0 +1,586 @@
+// C ABI and host orchestration of the four-stage SpGEMM framework (Section 4.1).
+//
+// The host side decides which per-bin kernels run (only non-empty bins), sizes
+// and allocates the temporary matrix C~ and the result C, and drives the
+// progressive relaunch loop of bin 37.  Device memory comes from a
+// library-owned stream-ordered pool (cudaMallocAsync), so every buffer is
+// ordered on the plan's stream and its high-water mark is the peak memory of
+// a call.
+#include "spgemm.h"
+#include "internal.h"
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+using namespace spg;
+
+namespace {
+
+struct DevicePool {
+    int device;
+    cudaMemPool_t pool;
+};
+
+std::mutex g_pool_mu;
+std::vector<DevicePool> g_pools;
+
+cudaError_t get_pool(int device, cudaMemPool_t *out) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto &p : g_pools)
+        if (p.device == device) {
+            *out = p.pool;
+            return cudaSuccess;
+        }
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t thr = UINT64_MAX;  // keep freed blocks for reuse by later calls
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (e != cudaSuccess) return e;
+    g_pools.push_back({device, pool});
+    *out = pool;
+    return cudaSuccess;
+}
+
+// Small pinned host blocks for the few device->host size reads of a call.
+std::mutex g_pin_mu;
+std::vector<void *> g_pinned_free;
+constexpr size_t PIN_BYTES = 4096;
+
+void *get_pinned() {
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (!g_pinned_free.empty()) {
+            void *p = g_pinned_free.back();
+            g_pinned_free.pop_back();
+            return p;
+        }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, PIN_BYTES) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void put_pinned(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pinned_free.push_back(p);
+}
+
+spgemm_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return SPGEMM_OK;
+    if (e == cudaErrorMemoryAllocation) return SPGEMM_ERR_OOM;
+    return SPGEMM_ERR_CUDA;
+}
+
+struct Timer {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+// Heap-kernel launches: bins 2..32 split into ranges sized to their widest heap.
+const int kHeapRanges[][2] = {{2, 8}, {9, 16}, {17, 24}, {25, 32}};
+
+}  // namespace
+
+struct spgemm_plan {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    spgemm_opts opts{};
+    cudaMemPool_t pool = nullptr;
+    DevCSR A{}, B{};
+    std::vector<void *> allocs;
+    int64_t bytes_ctilde = 0;
+    // stage 1-2 buffers
+    int64_t *S = nullptr, *u = nullptr, *ctil_rp = nullptr, *scan_partial = nullptr;
+    uint8_t *bin = nullptr;
+    int32_t *bin_rows = nullptr, *nnzc = nullptr, *ctil_col_i = nullptr;
+    int32_t *ctil_col = nullptr;
+    double *ctil_val = nullptr;
+    BinSummary *d_summary = nullptr;
+    int64_t *d_err = nullptr;
+    BinSummary h_summary{};
+    int64_t bin_start[NUM_BINS + 1] = {0};
+    // bin 37
+    MergeState ms{};
+    // result
+    bool numeric_done = false;
+    spgemm_csr_out C{};
+    spgemm_stats stats{};
+    std::vector<Timer> timers;
+    void *pinned = nullptr;
+    int smem_optin = 0;
+
+    cudaError_t alloc(void **p, size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            cudaGetLastError();
+            return e;
+        }
+        allocs.push_back(*p);
+        return cudaSuccess;
+    }
+    template <typename T>
+    cudaError_t alloc_n(T **p, int64_t n) {
+        return alloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+    }
+    void time_begin(int kind) {
+        if (!opts.record_timing) return;
+        Timer t{kind, nullptr, nullptr};
+        cudaEventCreate(&t.a);
+        cudaEventCreate(&t.b);
+        cudaEventRecord(t.a, st);
+        timers.push_back(t);
+    }
+    void time_end() {
+        if (!opts.record_timing || timers.empty()) return;
+        cudaEventRecord(timers.back().b, st);
+    }
+    void count(int kind, int n = 1) { stats.launches[kind] += n; }
+    cudaError_t d2h(void *dst, const void *src, size_t bytes) {
+        cudaError_t e = cudaMemcpyAsync(pinned, src, bytes, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        std::memcpy(dst, pinned, bytes);
+        return cudaSuccess;
+    }
+    void release() {
+        for (auto &t : timers) {
+            if (t.a) cudaEventDestroy(t.a);
+            if (t.b) cudaEventDestroy(t.b);
+        }
+        timers.clear();
+        for (void *p : allocs) cudaFreeAsync(p, st);
+        allocs.clear();
+        put_pinned(pinned);
+        pinned = nullptr;
+    }
+};
+
+extern "C" {
+
+spgemm_status spgemm_opts_init(spgemm_opts *o) {
+    if (!o) return SPGEMM_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->alloc_policy = SPGEMM_ALLOC_HYBRID;
+    o->initial_cap = 256;
+    o->predictor_margin = 1.0;
+    return SPGEMM_OK;
+}
+
+const char *spgemm_status_string(spgemm_status s) {
+    switch (s) {
+        case SPGEMM_OK: return "success";
+        case SPGEMM_ERR_INVALID_ARG: return "invalid argument";
+        case SPGEMM_ERR_SHAPE: return "shape mismatch or unsupported dimension";
+        case SPGEMM_ERR_UNSORTED: return "input CSR is malformed (unsorted/duplicate/out-of-range columns)";
+        case SPGEMM_ERR_OOM: return "device out of memory";
+        case SPGEMM_ERR_CUDA: return "CUDA error";
+        case SPGEMM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SPGEMM_ERR_INTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"
+
+namespace {
+
+spgemm_status check_in(const spgemm_csr_in *M) {
+    if (!M) return SPGEMM_ERR_INVALID_ARG;
+    if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0) return SPGEMM_ERR_INVALID_ARG;
+    if (M->nrows > INT32_MAX || M->ncols > INT32_MAX) return SPGEMM_ERR_SHAPE;
+    if (M->rowptr_bits != 32 && M->rowptr_bits != 64) return SPGEMM_ERR_INVALID_ARG;
+    if (M->rowptr_bits == 32 && M->nnz > INT32_MAX) return SPGEMM_ERR_INVALID_ARG;
+    if (!M->row_ptr) return SPGEMM_ERR_INVALID_ARG;
+    if (M->nnz > 0 && (!M->col_idx || !M->val)) return SPGEMM_ERR_INVALID_ARG;
+    return SPGEMM_OK;
+}
+
+#define SPG_TRY(expr)                                  \
+    do {                                               \
+        cudaError_t _e = (expr);                       \
+        if (_e != cudaSuccess) {                       \
+            status = from_cuda(_e);                    \
+            goto fail;                                 \
+        }                                              \
+    } while (0)
+
+StageArgs stage_args(spgemm_plan *p) {
+    StageArgs a;
+    a.A = p->A;
+    a.B = p->B;
+    a.ctil_rp = p->ctil_rp;
+    a.ctil_col = p->ctil_col;
+    a.ctil_val = p->ctil_val;
+    a.nnzc = p->nnzc;
+    return a;
+}
+
+__global__ void k_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
+                             double *ctil_val, MergeState s) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n37) return;
+    const int row = rows37[j];
+    const int64_t o = ctil_rp[row];
+    s.loc_col[j] = ctil_col + o;
+    s.loc_val[j] = ctil_val + o;
+    s.loc_cap[j] = ctil_rp[row + 1] - o;
+    s.len[j] = 0;
+    s.ck_entry[j] = 0;
+    s.ck_off[j] = 0;
+    s.done[j] = 0;
+}
+
+}  // namespace
+
+extern "C" spgemm_status spgemm_symbolic(const spgemm_csr_in *A_in, const spgemm_csr_in *B_in,
+                                         const spgemm_opts *opts, spgemm_stream_t stream,
+                                         spgemm_plan **plan_out, int64_t *upper_bound_nnz_out) {
+    if (!plan_out) return SPGEMM_ERR_INVALID_ARG;
+    *plan_out = nullptr;
+    spgemm_status status = check_in(A_in);
+    if (status != SPGEMM_OK) return status;
+    status = check_in(B_in);
+    if (status != SPGEMM_OK) return status;
+    if (A_in->ncols != B_in->nrows) return SPGEMM_ERR_SHAPE;
+    spgemm_opts o;
+    if (opts) o = *opts; else spgemm_opts_init(&o);
+    if (o.alloc_policy < 0 || o.alloc_policy > 2 || o.initial_cap < 1) return SPGEMM_ERR_INVALID_ARG;
+    if (o.alloc_policy == SPGEMM_ALLOC_LEARNED && o.predictor == nullptr) return SPGEMM_ERR_INVALID_ARG;
+
+    spgemm_plan *p = new (std::nothrow) spgemm_plan();
+    if (!p) return SPGEMM_ERR_OOM;
+    p->opts = o;
+    p->st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t m = A_in->nrows, nnzA = A_in->nnz;
+    int64_t nblk;
+    CapPolicy pol{};
+    {
+        SPG_TRY(cudaGetDevice(&p->device));
+        SPG_TRY(get_pool(p->device, &p->pool));
+        SPG_TRY(cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+        p->pinned = get_pinned();
+        if (!p->pinned) {
+            status = SPGEMM_ERR_OOM;
+            goto fail;
+        }
+        {
+            size_t used = 0;
+            cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemCurrent, &used);
+            uint64_t reset = 0;
+            cudaMemPoolSetAttribute(p->pool, cudaMemPoolAttrUsedMemHigh, &reset);
+        }
+        // int64 row pointers everywhere on the device
+        auto widen = [&](const spgemm_csr_in *M, DevCSR &D) -> cudaError_t {
+            D.nrows = M->nrows;
+            D.ncols = M->ncols;
+            D.nnz = M->nnz;
+            D.col = M->col_idx;
+            D.val = M->val;
+            if (M->rowptr_bits == 64) {
+                D.rp = static_cast<const int64_t *>(M->row_ptr);
+                return cudaSuccess;
+            }
+            int64_t *rp = nullptr;
+            cudaError_t e = p->alloc_n(&rp, M->nrows + 1);
+            if (e != cudaSuccess) return e;
+            e = launch_widen_rowptr(static_cast<const int32_t *>(M->row_ptr), rp, M->nrows + 1, p->st);
+            p->count(SPGEMM_K_OTHER);
+            D.rp = rp;
+            return e;
+        };
+        SPG_TRY(widen(A_in, p->A));
+        SPG_TRY(widen(B_in, p->B));
+        SPG_TRY(p->alloc_n(&p->d_summary, 1));
+        SPG_TRY(p->alloc_n(&p->d_err, 1));
+        SPG_TRY(cudaMemsetAsync(p->d_summary, 0, sizeof(BinSummary), p->st));
+        SPG_TRY(cudaMemsetAsync(p->d_err, 0, sizeof(int64_t), p->st));
+        if (o.check_inputs) {
+            // the verdict is read before any kernel indexes B through A's columns
+            p->time_begin(SPGEMM_K_OTHER);
+            SPG_TRY(launch_validate(p->A, &p->d_summary->status, p->st));
+            SPG_TRY(launch_validate(p->B, &p->d_summary->status, p->st));
+            p->time_end();
+            p->count(SPGEMM_K_OTHER, 2);
+            int64_t bad = 0;
+            SPG_TRY(p->d2h(&bad, &p->d_summary->status, sizeof(int64_t)));
+            if (bad != 0) {
+                status = SPGEMM_ERR_UNSORTED;
+                goto fail;
+            }
+        }
+        // ---- stage 1: upper bound ----
+        SPG_TRY(p->alloc_n(&p->S, nnzA + 1));
+        {
+            int64_t nb = std::max<int64_t>(bound_partial_size(nnzA), bin_blocks(m) + 1);
+            SPG_TRY(p->alloc_n(&p->scan_partial, nb + 1));
+        }
+        p->time_begin(SPGEMM_K_BOUND);
+        SPG_TRY(launch_bound(p->A, p->B, p->S, p->scan_partial, p->st));
+        p->time_end();
+        p->count(SPGEMM_K_BOUND, 3);
+        // ---- stage 2: binning ----
+        nblk = bin_blocks(m);
+        SPG_TRY(p->alloc_n(&p->u, m));
+        SPG_TRY(p->alloc_n(&p->bin, m));
+        SPG_TRY(p->alloc_n(&p->nnzc, m));
+        SPG_TRY(p->alloc_n(&p->bin_rows, m));
+        SPG_TRY(p->alloc_n(&p->ctil_rp, m + 1));
+        {
+            int32_t *hist = nullptr;
+            int64_t *capp = nullptr;
+            SPG_TRY(p->alloc_n(&hist, (int64_t)NUM_BINS * nblk));
+            SPG_TRY(p->alloc_n(&capp, nblk));
+            pol.policy = o.alloc_policy;
+            pol.initial_cap = o.initial_cap;
+            pol.pred_cap = nullptr;
+            p->time_begin(SPGEMM_K_BIN);
+            SPG_TRY(launch_binning(m, p->A.rp, p->S, p->S + nnzA, pol, p->u, p->bin, p->nnzc, p->bin_rows,
+                                   p->ctil_rp, hist, capp, p->d_summary, p->st));
+            p->time_end();
+            p->count(SPGEMM_K_BIN, nblk > 0 ? 3 : 1);
+        }
+        SPG_TRY(p->d2h(&p->h_summary, p->d_summary, sizeof(BinSummary)));
+        p->bin_start[0] = 0;
+        for (int b = 0; b < NUM_BINS; ++b) p->bin_start[b + 1] = p->bin_start[b] + p->h_summary.bin_count[b];
+        for (int b = 0; b < NUM_BINS; ++b) p->stats.bin_count[b] = p->h_summary.bin_count[b];
+        p->stats.sum_u = p->h_summary.sum_u;
+        p->stats.nnz_ctilde = p->h_summary.sum_cap;
+        // C~ (hybrid: u_i for bins 0..36, 256 for bin 37)
+        SPG_TRY(p->alloc_n(&p->ctil_col, p->h_summary.sum_cap));
+        SPG_TRY(p->alloc_n(&p->ctil_val, p->h_summary.sum_cap));
+        p->bytes_ctilde += p->h_summary.sum_cap * 12;
+    }
+    if (upper_bound_nnz_out) *upper_bound_nnz_out = p->h_summary.sum_u;
+    *plan_out = p;
+    return SPGEMM_OK;
+fail:
+    cudaStreamSynchronize(p->st);
+    p->release();
+    delete p;
+    return status;
+}
+
+namespace {
+
+spgemm_status run_bin37(spgemm_plan *p) {
+    spgemm_status status = SPGEMM_OK;
+    const int64_t n37 = p->h_summary.bin_count[BIN_MERGE];
+    if (n37 == 0) return SPGEMM_OK;
+    const int32_t *rows37 = p->bin_rows + p->bin_start[BIN_MERGE];
+    StageArgs a = stage_args(p);
+    MergeState &s = p->ms;
+    int32_t *list[2] = {nullptr, nullptr};
+    int32_t *ovf_count = nullptr;
+    int64_t *g_cap = nullptr, *g_off = nullptr, *g_partial = nullptr, *g_total = nullptr;
+    // leave room for the kernel's static shared memory
+    const int smem_limit = (p->smem_optin > 0 ? p->smem_optin : 227 * 1024) - 1024;
+    int batch = p->opts.merge_batch > 0 ? p->opts.merge_batch : 1024;
+    batch = std::max(32, std::min(batch, 2048));
+    int capmax = merge_max_cap(batch, smem_limit);
+    if (p->opts.smem_cap_max > 0) capmax = std::min(capmax, std::max(256, p->opts.smem_cap_max));
+    int cap;
+    if (p->opts.alloc_policy == SPGEMM_ALLOC_UPPER_BOUND) cap = capmax;
+    else cap = std::min(capmax, std::max(32, (int)p->opts.initial_cap));
+    const int32_t *work = nullptr;
+    int64_t nwork = n37;
+    int which = 0;
+    {
+        SPG_TRY(p->alloc_n(&s.loc_col, n37));
+        SPG_TRY(p->alloc_n(&s.loc_val, n37));
+        SPG_TRY(p->alloc_n(&s.loc_cap, n37));
+        SPG_TRY(p->alloc_n(&s.len, n37));
+        SPG_TRY(p->alloc_n(&s.ck_entry, n37));
+        SPG_TRY(p->alloc_n(&s.ck_off, n37));
+        SPG_TRY(p->alloc_n(&s.done, n37));
+        SPG_TRY(p->alloc_n(&list[0], n37));
+        SPG_TRY(p->alloc_n(&list[1], n37));
+        SPG_TRY(p->alloc_n(&ovf_count, 1));
+        k_merge_init<<<(unsigned)((n37 + 255) / 256), 256, 0, p->st>>>(rows37, n37, p->ctil_rp, p->ctil_col,
+                                                                        p->ctil_val, s);
+        SPG_TRY(cudaGetLastError());
+        p->count(SPGEMM_K_OTHER);
+        bool level1 = false;
+        while (nwork > 0) {
+            MergeLaunch L{};
+            L.rows37 = rows37;
+            L.work = work;
+            L.nwork = nwork;
+            L.cap = cap;
+            L.batch = std::min(batch, cap);
+            L.level1 = level1 ? 1 : 0;
+            L.ovf_list = list[which];
+            L.ovf_count = ovf_count;
+            L.err = p->d_err;
+            if (!level1 && p->opts.alloc_policy != SPGEMM_ALLOC_UPPER_BOUND &&
+                (work != nullptr || cap > p->opts.initial_cap)) {
+                SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap));
+                SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap));
+                L.pool_cap = cap;
+                p->bytes_ctilde += nwork * (int64_t)cap * 12;
+            }
+            if (level1) {
+                SPG_TRY(p->alloc_n(&g_cap, nwork));
+                SPG_TRY(p->alloc_n(&g_off, nwork));
+                SPG_TRY(p->alloc_n(&g_partial, nwork / 2048 + 2));
+                SPG_TRY(p->alloc_n(&g_total, 1));
+                SPG_TRY(launch_level1_sizes(rows37, work, nwork, p->u, p->B.ncols, g_cap, g_off, g_partial,
+                                            g_total, p->st));
+                p->count(SPGEMM_K_OTHER, 4);
+                int64_t gtot = 0;
+                SPG_TRY(p->d2h(&gtot, g_total, sizeof(int64_t)));
+                SPG_TRY(p->alloc_n(&L.g_col, gtot));
+                SPG_TRY(p->alloc_n(&L.g_val, gtot));
+                p->bytes_ctilde += gtot * 12;
+                L.g_cap = g_cap;
+                L.g_off = g_off;
+                p->stats.rows_level1 += nwork;
+            }
+            SPG_TRY(cudaMemsetAsync(ovf_count, 0, sizeof(int32_t), p->st));
+            p->time_begin(SPGEMM_K_MERGE);
+            SPG_TRY(launch_merge(a, s, L, p->u, p->st));
+            p->time_end();
+            p->count(SPGEMM_K_MERGE);
+            p->stats.merge_rounds += 1;
+            int32_t novf = 0;
+            SPG_TRY(p->d2h(&novf, ovf_count, sizeof(int32_t)));
+            if (novf > 0 && level1) {
+                status = SPGEMM_ERR_INTERNAL;
+                goto fail;
+            }
+            if (work == nullptr) p->stats.rows_relaunched = novf;
+            work = list[which];
+            which ^= 1;
+            nwork = novf;
+            if (cap >= capmax) level1 = true;
+            else cap = std::min(capmax, cap * 2);
+        }
+        int64_t err = 0;
+        SPG_TRY(p->d2h(&err, p->d_err, sizeof(int64_t)));
+        if (err != 0) status = SPGEMM_ERR_INTERNAL;
+    }
+    return status;
+fail:
+    return status;
+}
+
+}  // namespace
+
+extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
+    if (!p || !C_out) return SPGEMM_ERR_INVALID_ARG;
+    if (p->numeric_done) {
+        *C_out = p->C;
+        return SPGEMM_OK;
+    }
+    spgemm_status status = SPGEMM_OK;
+    const int64_t m = p->A.nrows;
+    StageArgs a = stage_args(p);
+    {
+        // ---- stage 3: bin groups 3 (heap) and 4 (bitonic ESC) ----
+        const int heap_nt = p->opts.heap_block > 0 ? p->opts.heap_block : 128;
+        for (auto &r : kHeapRanges) {
+            const int64_t s0 = p->bin_start[r[0]], s1 = p->bin_start[r[1] + 1];
+            if (s1 > s0) {
+                const int slots = r[1];
+                p->time_begin(SPGEMM_K_HEAP);
+                SPG_TRY(launch_heap(a, p->bin_rows + s0, s1 - s0, slots, heap_nt, p->st));
+                p->time_end();
+                p->count(SPGEMM_K_HEAP);
+            }
+        }
+        for (int b = BIN_ESC_LO; b <= BIN_ESC_HI; ++b) {
+            const int64_t s0 = p->bin_start[b], s1 = p->bin_start[b + 1];
+            if (s1 > s0) {
+                p->time_begin(SPGEMM_K_ESC);
+                SPG_TRY(launch_esc(a, p->bin_rows + s0, s1 - s0, b, p->st));
+                p->time_end();
+                p->count(SPGEMM_K_ESC);
+            }
+        }
+        // ---- stage 3: bin group 5 (merge, progressive) ----
+        status = run_bin37(p);
+        if (status != SPGEMM_OK) goto fail;
+        // ---- stage 4: arrange ----
+        SPG_TRY(p->alloc_n(&p->C.row_ptr, m + 1));
+        p->time_begin(SPGEMM_K_SCAN);
+        SPG_TRY(launch_row_scan(m, p->nnzc, p->C.row_ptr, p->scan_partial, p->st));
+        p->time_end();
+        p->count(SPGEMM_K_SCAN, 3);
+        int64_t nnzC = 0;
+        SPG_TRY(p->d2h(&nnzC, p->C.row_ptr + m, sizeof(int64_t)));
+        SPG_TRY(p->alloc_n(&p->C.col_idx, nnzC));
+        SPG_TRY(p->alloc_n(&p->C.val, nnzC));
+        p->time_begin(SPGEMM_K_ARRANGE);
+        {
+            const int64_t s0 = p->bin_start[1], s1 = p->bin_start[BIN_MERGE];
+            SPG_TRY(launch_arrange_short(a, p->bin_rows + s0, s1 - s0, p->bin, p->C.row_ptr, p->C.col_idx,
+                                         p->C.val, p->st));
+            if (s1 > s0) p->count(SPGEMM_K_ARRANGE);
+            const int64_t n37 = p->h_summary.bin_count[BIN_MERGE];
+            SPG_TRY(launch_arrange_long(p->ms, p->bin_rows + p->bin_start[BIN_MERGE], n37, p->C.row_ptr,
+                                        p->C.col_idx, p->C.val, p->st));
+            if (n37 > 0) p->count(SPGEMM_K_ARRANGE);
+        }
+        p->time_end();
+        p->C.nrows = m;
+        p->C.ncols = p->B.ncols;
+        p->C.nnz = nnzC;
+        p->stats.nnz_c = nnzC;
+        p->stats.bytes_ctilde = p->bytes_ctilde;
+        p->numeric_done = true;
+        *C_out = p->C;
+    }
+    return SPGEMM_OK;
+fail:
+    return status;
+}
+
+extern "C" spgemm_status spgemm_free(spgemm_plan *p) {
+    if (!p) return SPGEMM_OK;
+    p->release();
+    delete p;
+    return SPGEMM_OK;
+}
+
+extern "C" spgemm_status spgemm_plan_stats(spgemm_plan *p, spgemm_stats *out) {
+    if (!p || !out) return SPGEMM_ERR_INVALID_ARG;
+    if (!p->timers.empty()) {
+        cudaError_t e = cudaStreamSynchronize(p->st);
+        if (e != cudaSuccess) return from_cuda(e);
+        for (int k = 0; k < SPGEMM_K_COUNT; ++k) p->stats.kernel_ms[k] = 0.f;
+        for (auto &t : p->timers) {
+            float ms = 0.f;
+            if (t.a && t.b && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) p->stats.kernel_ms[t.kind] += ms;
+        }
+    }
+    size_t hi = 0;
+    if (cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemHigh, &hi) == cudaSuccess)
+        p->stats.peak_bytes = (int64_t)hi;
+    *out = p->stats;
+    return SPGEMM_OK;
+}
+
+extern "C" spgemm_status spgemm_plan_arrays_get(spgemm_plan *p, spgemm_plan_arrays *out) {
+    if (!p || !out) return SPGEMM_ERR_INVALID_ARG;
+    out->nrows = p->A.nrows;
+    out->u = p->u;
+    out->bin = p->bin;
+    out->bin_rows = p->bin_rows;
+    out->bin_start = p->bin_start;
+    out->ctilde_row_ptr = p->ctil_rp;
+    out->row_nnz = p->nnzc;
+    return SPGEMM_OK;
+}

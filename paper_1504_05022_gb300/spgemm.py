@@ -1,0 +1,210 @@
+"""Python binding of the C ABI: device CSR matrices as torch tensors, and
+C = A*B through spgemm_symbolic / spgemm_numeric / spgemm_free.
+
+torch is used only for device memory, streams and as the tensor container; every
+step of the product runs in the library's CUDA kernels."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+@dataclass
+class CSR:
+    """A CSR matrix whose arrays are torch tensors on one CUDA device.
+
+    row_ptr: int32 or int64 (nrows+1), col: int32 (nnz), val: float64 (nnz); columns of a row
+    strictly ascending."""
+
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor
+    shape: tuple
+
+    @property
+    def nrows(self) -> int:
+        return int(self.shape[0])
+
+    @property
+    def ncols(self) -> int:
+        return int(self.shape[1])
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    @classmethod
+    def from_host(cls, M, device="cuda", rowptr_dtype=torch.int64, pin: bool = False) -> "CSR":
+        """Copies a host CSR (anything with row_ptr/col/val numpy arrays and nrows/ncols)."""
+        rp = torch.from_numpy(np.ascontiguousarray(M.row_ptr)).to(rowptr_dtype)
+        col = torch.from_numpy(np.ascontiguousarray(M.col, dtype=np.int32))
+        val = torch.from_numpy(np.ascontiguousarray(M.val, dtype=np.float64))
+        if pin:
+            rp, col, val = rp.pin_memory(), col.pin_memory(), val.pin_memory()
+        return cls(rp.to(device, non_blocking=pin), col.to(device, non_blocking=pin),
+                   val.to(device, non_blocking=pin), (int(M.nrows), int(M.ncols)))
+
+    def to_host(self):
+        """(row_ptr int64, col int32, val float64) numpy arrays."""
+        return (self.row_ptr.to("cpu", torch.int64).numpy(), self.col.cpu().numpy(), self.val.cpu().numpy())
+
+    def _c_in(self) -> _lib.CsrIn:
+        for t in (self.row_ptr, self.col, self.val):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("CSR arrays must be contiguous CUDA tensors")
+        if self.col.dtype != torch.int32 or self.val.dtype != torch.float64:
+            raise TypeError("col must be int32 and val float64")
+        if self.row_ptr.dtype not in (torch.int32, torch.int64):
+            raise TypeError("row_ptr must be int32 or int64")
+        if self.row_ptr.numel() != self.nrows + 1 or self.val.numel() != self.col.numel():
+            raise ValueError("inconsistent CSR array sizes")
+        return _lib.CsrIn(self.nrows, self.ncols, self.nnz, self.row_ptr.data_ptr(),
+                          32 if self.row_ptr.dtype == torch.int32 else 64,
+                          self.col.data_ptr() if self.nnz else None,
+                          self.val.data_ptr() if self.nnz else None)
+
+
+class _PlanHandle:
+    """Owns an spgemm_plan*; freed (stream-ordered) when the last reference goes."""
+
+    def __init__(self, ptr: int, stream: torch.cuda.Stream):
+        self.ptr = ptr
+        self.stream = stream
+
+    def free(self):
+        if self.ptr:
+            _lib.load().spgemm_free(ctypes.c_void_p(self.ptr))
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class _PlanArray:
+    """Exposes one plan-owned device array through __cuda_array_interface__ and keeps the
+    plan alive while a tensor views it."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner: _PlanHandle, device: int):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None, "stream": None}
+        self._device = device
+
+
+def _wrap(ptr: int, n: int, dtype: torch.dtype, owner: _PlanHandle, device: int) -> torch.Tensor:
+    typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.float64: "<f8"}[dtype]
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device=f"cuda:{device}")
+    return torch.as_tensor(_PlanArray(ptr, n, typestr, owner, device), device=f"cuda:{device}")
+
+
+def _wrap_u8(ptr: int, n: int, owner: _PlanHandle, device: int) -> torch.Tensor:
+    if n == 0:
+        return torch.empty(0, dtype=torch.uint8, device=f"cuda:{device}")
+    return torch.as_tensor(_PlanArray(ptr, n, "|u1", owner, device), device=f"cuda:{device}")
+
+
+def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs: bool = False,
+              record_timing: bool = False, merge_batch: int = 0, smem_cap_max: int = 0,
+              heap_block: int = 0, predictor=None, predictor_margin: float = 1.0) -> _lib.Opts:
+    L = _lib.load()
+    o = _lib.Opts()
+    _lib.check(L.spgemm_opts_init(ctypes.byref(o)), "spgemm_opts_init")
+    o.alloc_policy = _lib.POLICY[alloc_policy]
+    o.initial_cap = int(initial_cap)
+    o.check_inputs = int(bool(check_inputs))
+    o.record_timing = int(bool(record_timing))
+    o.merge_batch = int(merge_batch)
+    o.smem_cap_max = int(smem_cap_max)
+    o.heap_block = int(heap_block)
+    o.predictor = predictor
+    o.predictor_margin = float(predictor_margin)
+    return o
+
+
+class Plan:
+    """C = A*B split into the symbolic part (stages 1-2) and the numeric part (stages 3-4)."""
+
+    def __init__(self, A: CSR, B: CSR, stream: torch.cuda.Stream | None = None, **opts):
+        L = _lib.load()
+        self.A, self.B = A, B  # keep inputs alive until numeric work completes
+        self.device = A.val.device.index if A.val.is_cuda else torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.opts = make_opts(**opts)
+        a_in, b_in = A._c_in(), B._c_in()
+        plan = ctypes.c_void_p()
+        ub = ctypes.c_int64()
+        with torch.cuda.device(self.device):
+            _lib.check(L.spgemm_symbolic(ctypes.byref(a_in), ctypes.byref(b_in), ctypes.byref(self.opts),
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(plan),
+                                         ctypes.byref(ub)), "spgemm_symbolic")
+        self.handle = _PlanHandle(plan.value, self.stream)
+        self.upper_bound_nnz = int(ub.value)
+        self._C = None
+
+    def numeric(self) -> CSR:
+        if self._C is not None:
+            return self._C
+        L = _lib.load()
+        out = _lib.CsrOut()
+        with torch.cuda.device(self.device):
+            _lib.check(L.spgemm_numeric(ctypes.c_void_p(self.handle.ptr), ctypes.byref(out)), "spgemm_numeric")
+        h = self.handle
+        rp = _wrap(out.row_ptr, out.nrows + 1, torch.int64, h, self.device)
+        col = _wrap(out.col_idx, out.nnz, torch.int32, h, self.device)
+        val = _wrap(out.val, out.nnz, torch.float64, h, self.device)
+        self._C = CSR(rp, col, val, (int(out.nrows), int(out.ncols)))
+        return self._C
+
+    def stats(self) -> dict:
+        L = _lib.load()
+        s = _lib.Stats()
+        _lib.check(L.spgemm_plan_stats(ctypes.c_void_p(self.handle.ptr), ctypes.byref(s)), "spgemm_plan_stats")
+        return {
+            "bin_count": list(s.bin_count), "sum_u": s.sum_u, "nnz_ctilde": s.nnz_ctilde, "nnz_c": s.nnz_c,
+            "merge_rounds": s.merge_rounds, "rows_relaunched": s.rows_relaunched, "rows_level1": s.rows_level1,
+            "rows_fallback": s.rows_fallback, "bytes_ctilde": s.bytes_ctilde, "peak_bytes": s.peak_bytes,
+            "launches": dict(zip(_lib.KERNELS, list(s.launches))),
+            "kernel_ms": dict(zip(_lib.KERNELS, [float(x) for x in s.kernel_ms])),
+        }
+
+    def arrays(self) -> dict:
+        """Copies of the plan's intermediate arrays to host numpy (for inspection and tests):
+        u, bin, bin_rows, bin_start, ctilde_row_ptr, row_nnz."""
+        L = _lib.load()
+        a = _lib.PlanArrays()
+        _lib.check(L.spgemm_plan_arrays_get(ctypes.c_void_p(self.handle.ptr), ctypes.byref(a)),
+                   "spgemm_plan_arrays_get")
+        self.stream.synchronize()
+        m = int(a.nrows)
+        h = self.handle
+        out = {
+            "u": _wrap(a.u, m, torch.int64, h, self.device).cpu().numpy(),
+            "bin": _wrap_u8(a.bin, m, h, self.device).cpu().numpy(),
+            "bin_rows": _wrap(a.bin_rows, m, torch.int32, h, self.device).cpu().numpy(),
+            "bin_start": np.ctypeslib.as_array(ctypes.cast(a.bin_start, ctypes.POINTER(ctypes.c_int64)),
+                                               shape=(39,)).copy(),
+            "ctilde_row_ptr": _wrap(a.ctilde_row_ptr, m + 1, torch.int64, h, self.device).cpu().numpy(),
+            "row_nnz": _wrap(a.row_nnz, m, torch.int32, h, self.device).cpu().numpy(),
+        }
+        return out
+
+    def free(self) -> None:
+        """Releases the plan now; tensors of C obtained from numeric() become invalid."""
+        self._C = None
+        self.handle.free()
+
+
+def spgemm(A: CSR, B: CSR, stream: torch.cuda.Stream | None = None, **opts) -> CSR:
+    """C = A*B on the GPU (four-stage framework).  The returned tensors keep the plan alive."""
+    if A.ncols != B.nrows:
+        raise ValueError(f"shape mismatch: {A.shape} x {B.shape}")
+    return Plan(A, B, stream=stream, **opts).numeric()

@@ -1,0 +1,83 @@
+"""The C-ABI library builds, loads without a GPU and exports every function that
+include/*.h declares; the ctypes structures match the header's layout."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*([a-z_][a-z0-9_]*)\s*\(",
+                             src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1504_05022_gb300 import _build, _lib
+    _build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ["spgemm_symbolic", "spgemm_numeric", "spgemm_free", "spgemm_status_string",
+                     "spgemm_opts_init", "spgemm_plan_stats"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1504_05022_gb300 import _lib
+    so = _lib.lib_path()
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in _declared_functions() if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    for n in _declared_functions():
+        assert hasattr(lib, n)
+    # the ctypes signature table covers every declared function
+    assert set(_lib.SIGNATURES) == _declared_functions()
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_1504_05022_gb300 import _lib
+    for code in range(8):
+        s = lib.spgemm_status_string(code)
+        assert isinstance(s, bytes) and len(s) > 3
+    o = _lib.Opts()
+    assert lib.spgemm_opts_init(ctypes.byref(o)) == 0
+    assert o.alloc_policy == 0 and o.initial_cap == 256 and o.check_inputs == 0
+    assert lib.spgemm_opts_init(None) == 1
+
+
+def test_struct_layout_matches_header():
+    from paper_1504_05022_gb300 import _lib
+    assert ctypes.sizeof(_lib.CsrIn) == 56
+    assert ctypes.sizeof(_lib.CsrOut) == 48
+    assert _lib.Opts.predictor.offset == 64 and ctypes.sizeof(_lib.Opts) == 80
+    assert _lib.Stats.launches.offset == 38 * 8 + 9 * 8
+
+
+def test_argument_errors_without_gpu(lib):
+    """Invalid arguments are rejected before any CUDA call, so this runs on CPU."""
+    from paper_1504_05022_gb300 import _lib
+    plan = ctypes.c_void_p()
+    A = _lib.CsrIn(4, 5, 0, ctypes.c_void_p(1), 32, None, None)
+    B = _lib.CsrIn(6, 3, 0, ctypes.c_void_p(1), 32, None, None)
+    assert lib.spgemm_symbolic(ctypes.byref(A), ctypes.byref(B), None, None, ctypes.byref(plan), None) == 2
+    B.nrows = 5
+    B.rowptr_bits = 16
+    assert lib.spgemm_symbolic(ctypes.byref(A), ctypes.byref(B), None, None, ctypes.byref(plan), None) == 1
+    assert lib.spgemm_symbolic(ctypes.byref(A), ctypes.byref(B), None, None, None, None) == 1
+    assert lib.spgemm_numeric(None, None) == 1
+    assert lib.spgemm_free(None) == 0

@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Structure (row_ptr, col) must match bit-exactly; values within
+|c - ref| <= 1e-12 * sum_k |a_ik b_kj|, or bit-exactly where all values are
+small integers.  Stage 1 and stage 2 outputs are integers and must match the
+oracle's restatements of Algorithms 2 and 3 exactly."""
+import numpy as np
+import pytest
+
+import gen
+from tests.helpers import REL_TOL, assert_csr_equal
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def spg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1504_05022_gb300 as spg
+    spg.load_library()
+    return spg
+
+
+def run(spg, A, B, rowptr_dtype=torch.int64, **opts):
+    Ad = spg.CSR.from_host(A, rowptr_dtype=rowptr_dtype)
+    Bd = Ad if B is A else spg.CSR.from_host(B, rowptr_dtype=rowptr_dtype)
+    plan = spg.Plan(Ad, Bd, **opts)
+    C = plan.numeric()
+    torch.cuda.synchronize()
+    return plan, C
+
+
+def check(oracle_mod, A, B, C, exact=False, label=""):
+    ref = oracle_mod.spgemm(A, B)
+    rp, col, val = C.to_host()
+    assert C.shape == (A.nrows, B.ncols)
+    assert_csr_equal(rp, col, val, ref.row_ptr, ref.col, ref.val, ref.den, exact=exact, label=label)
+    return ref
+
+
+def test_lap2d_64_bit_exact(spg, oracle_mod):
+    A = gen.lap2d(64)
+    plan, C = run(spg, A, A, rowptr_dtype=torch.int32, check_inputs=True)
+    assert C.nnz == 51972
+    check(oracle_mod, A, A, C, exact=True, label="lap2d64")
+    assert plan.upper_bound_nnz == 100104
+
+
+@pytest.mark.parametrize("policy", ["hybrid", "upper_bound"])
+@pytest.mark.parametrize("scale,avg", [(8, 4), (10, 16), (12, 8), (12, 32)])
+def test_rmat_small(spg, oracle_mod, policy, scale, avg):
+    A = gen.rmat(scale, avg, seed=scale + avg)
+    plan, C = run(spg, A, A, alloc_policy=policy)
+    check(oracle_mod, A, A, C, label=f"rmat{scale}x{avg}/{policy}")
+
+
+@pytest.mark.parametrize("name,mk", [
+    ("lap2d", lambda: (gen.lap2d(40), None)),
+    ("rmat", lambda: (gen.rmat(11, 16, seed=4), None)),
+    ("er_rect", lambda: (gen.erdos_renyi(700, 9, seed=2, ncols=900), gen.erdos_renyi(900, 30, seed=3, ncols=500))),
+    ("blockdiag", lambda: (gen.blockdiag(1000, 40, seed=1), None)),
+])
+def test_stage1_stage2_bit_exact(spg, oracle_mod, name, mk):
+    A, B = mk()
+    B = A if B is None else B
+    for policy in ("hybrid", "upper_bound"):
+        plan, _ = run(spg, A, B, alloc_policy=policy)
+        arr = plan.arrays()
+        u = oracle_mod.upper_bound(A, B)
+        assert np.array_equal(arr["u"], u), name
+        b, sz, cnt, rows, total = oracle_mod.binning(u)
+        assert np.array_equal(arr["bin"].astype(np.int32), b)
+        assert np.array_equal(arr["bin_rows"], rows)           # stable order inside each bin
+        assert np.array_equal(np.diff(arr["bin_start"]), cnt)
+        caps = np.diff(arr["ctilde_row_ptr"])
+        if policy == "hybrid":
+            assert np.array_equal(caps, sz)                     # Algorithm 3 sizes
+            assert int(arr["ctilde_row_ptr"][-1]) == total
+        else:
+            assert np.array_equal(caps, u)
+        assert plan.upper_bound_nnz == int(u.sum())
+        st = plan.stats()
+        assert st["sum_u"] == int(u.sum()) and st["bin_count"] == cnt.tolist()
+        ref = oracle_mod.spgemm(A, B)
+        assert np.array_equal(arr["row_nnz"].astype(np.int64), np.diff(ref.row_ptr))
+
+
+@pytest.mark.parametrize("initial_cap,smem_cap_max,batch", [
+    (32, 256, 32), (64, 512, 64), (256, 1024, 256), (256, 0, 2048), (128, 2048, 512)])
+def test_progressive_and_level1_paths(spg, oracle_mod, initial_cap, smem_cap_max, batch):
+    """Small capacities force every long row through several relaunches and, past
+    smem_cap_max, through the level-1 sequence."""
+    A = gen.rmat(12, 16, seed=7)
+    plan, C = run(spg, A, A, initial_cap=initial_cap, smem_cap_max=smem_cap_max, merge_batch=batch)
+    check(oracle_mod, A, A, C, label=f"cap{initial_cap}/{smem_cap_max}/{batch}")
+    st = plan.stats()
+    assert st["merge_rounds"] >= 2 and st["rows_relaunched"] > 0
+    if smem_cap_max and smem_cap_max <= 1024:
+        assert st["rows_level1"] > 0
+
+
+def _rows_with_u(targets, ncols_b, seed, dup=False):
+    """A (len(targets) rows) and B such that row i of A*B has exactly targets[i] products.
+    B row k has length k+1 (k < 600); dup=True makes every B row use the same columns, so many
+    products collide (all-duplicates rows)."""
+    rng = np.random.default_rng(seed)
+    nb = 600
+    rows, cols = [], []
+    for k in range(nb):
+        L = k + 1
+        c = np.arange(L) if dup else np.sort(rng.choice(ncols_b, size=L, replace=False))
+        rows.append(np.full(L, k))
+        cols.append(c)
+    B = gen.from_coo(nb, ncols_b, np.concatenate(rows), np.concatenate(cols), None)
+    B.val = rng.uniform(-1, 1, B.nnz)
+    ar, ac = [], []
+    for i, t in enumerate(targets):
+        # greedy: pick distinct B rows whose lengths sum to t
+        left, k = t, nb - 1
+        picked = []
+        while left > 0:
+            k = min(k, left - 1)
+            picked.append(k)
+            left -= k + 1
+            k -= 1
+        ar += [i] * len(picked)
+        ac += picked
+    A = gen.from_coo(len(targets), nb, np.array(ar, dtype=np.int64), np.array(ac, dtype=np.int64), None)
+    A.val = rng.uniform(-1, 1, A.nnz)
+    return A, B
+
+
+@pytest.mark.parametrize("dup", [False, True])
+def test_bin_edges(spg, oracle_mod, dup):
+    targets = [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513,
+               1000, 4096, 20000, 70000]
+    A, B = _rows_with_u(targets, 3000, seed=11, dup=dup)
+    u = oracle_mod.upper_bound(A, B)
+    assert u.tolist() == targets
+    for policy in ("hybrid", "upper_bound"):
+        plan, C = run(spg, A, B, alloc_policy=policy)
+        check(oracle_mod, A, B, C, label=f"edges dup={dup} {policy}")
+
+
+def test_rectangular_empty_and_degenerate(spg, oracle_mod):
+    cases = [
+        (gen.random_sparse(50, 70, 0.1, 1, empty_rows=0.3), gen.random_sparse(70, 40, 0.1, 2, empty_rows=0.3)),
+        (gen.random_sparse(1, 1, 1.0, 3), gen.random_sparse(1, 1, 1.0, 4)),
+        (gen.random_sparse(30, 20, 0.0, 5), gen.random_sparse(20, 30, 0.2, 6)),     # A empty
+        (gen.random_sparse(30, 20, 0.2, 7), gen.random_sparse(20, 30, 0.0, 8)),     # B empty
+        (gen.random_sparse(0, 20, 0.2, 9), gen.random_sparse(20, 30, 0.2, 10)),     # no rows
+        (gen.random_sparse(25, 0, 0.2, 11), gen.random_sparse(0, 30, 0.2, 12)),     # inner dim 0
+        (gen.random_sparse(25, 20, 0.3, 13), gen.random_sparse(20, 0, 0.2, 14)),    # no columns
+        (gen.random_sparse(300, 5000, 0.01, 15), gen.random_sparse(5000, 3, 0.5, 16)),  # long A rows
+    ]
+    for i, (A, B) in enumerate(cases):
+        for rdt in (torch.int32, torch.int64):
+            plan, C = run(spg, A, B, rowptr_dtype=rdt)
+            check(oracle_mod, A, B, C, label=f"case{i}")
+
+
+def test_integer_values_bit_exact(spg, oracle_mod):
+    A = gen.random_sparse(400, 300, 0.05, 21, integer_values=True)
+    B = gen.random_sparse(300, 500, 0.08, 22, integer_values=True)
+    _, C = run(spg, A, B)
+    check(oracle_mod, A, B, C, exact=True, label="int")
+
+
+def test_cancellation_keeps_structural_zeros(spg, oracle_mod):
+    # row 0 of A*B: 1*2 + 1*(-2) = 0 at column 0 stays a structural entry
+    A = gen.from_coo(2, 2, np.array([0, 0, 1]), np.array([0, 1, 1]), np.array([1.0, 1.0, 3.0]))
+    B = gen.from_coo(2, 2, np.array([0, 1, 1]), np.array([0, 0, 1]), np.array([2.0, -2.0, 1.0]))
+    _, C = run(spg, A, B)
+    rp, col, val = C.to_host()
+    assert rp.tolist() == [0, 1, 3] and col.tolist() == [0, 0, 1]
+    assert val.tolist() == [0.0, -6.0, 3.0]
+
+
+def test_check_inputs_rejects_malformed(spg):
+    good = gen.random_sparse(20, 20, 0.2, 1)
+    for mutate in ("unsorted", "duplicate", "out_of_range"):
+        bad = gen.HostCSR(good.nrows, good.ncols, good.row_ptr.copy(), good.col.copy(), good.val.copy())
+        r = int(np.argmax(np.diff(bad.row_ptr) >= 2))
+        s = int(bad.row_ptr[r])
+        if mutate == "unsorted":
+            bad.col[s], bad.col[s + 1] = bad.col[s + 1], bad.col[s]
+        elif mutate == "duplicate":
+            bad.col[s + 1] = bad.col[s]
+        else:
+            bad.col[s] = 20 + 5
+        Ad = spg.CSR.from_host(bad)
+        Bd = spg.CSR.from_host(good)
+        with pytest.raises(spg.SpgemmError) as ei:
+            spg.Plan(Ad, Bd, check_inputs=True)
+        assert ei.value.code == 3
+    with pytest.raises(ValueError):
+        spg.spgemm(spg.CSR.from_host(good), spg.CSR.from_host(gen.random_sparse(21, 20, 0.2, 2)))
+
+
+def test_repeat_is_structurally_identical(spg, oracle_mod):
+    A = gen.rmat(11, 16, seed=9)
+    _, C1 = run(spg, A, A)
+    _, C2 = run(spg, A, A)
+    r1, c1, v1 = C1.to_host()
+    r2, c2, v2 = C2.to_host()
+    assert np.array_equal(r1, r2) and np.array_equal(c1, c2)
+    ref = oracle_mod.spgemm(A, A)
+    assert np.all(np.abs(v1 - v2) <= 2 * REL_TOL * ref.den)
+
+
+def test_config2_rmat16_full(spg, oracle_mod):
+    """R-MAT 2^16 rows, 16 samples/row, A*A: every bin group, progressive rounds, level-1."""
+    A = gen.rmat(16, 16, seed=1)
+    plan, C = run(spg, A, A, rowptr_dtype=torch.int32, record_timing=True)
+    check(oracle_mod, A, A, C, label="cfg2")
+    st = plan.stats()
+    assert st["merge_rounds"] >= 3 and st["rows_level1"] > 0
+    assert all(st["bin_count"][b] > 0 for b in (0, 1, 2, 33, 34, 35, 36, 37))
+
+
+def test_config3_galerkin_closed_form(spg, oracle_mod):
+    g = 64
+    A = gen.lap3d27(g)
+    P = gen.agg_P(g)
+    R = gen.transpose(P)
+    Ad, Pd, Rd = (spg.CSR.from_host(M, rowptr_dtype=torch.int32) for M in (A, P, R))
+    AP = spg.spgemm(Ad, Pd)
+    assert AP.nnz == 126 ** 3
+    Ac = spg.spgemm(Rd, AP)
+    torch.cuda.synchronize()
+    assert Ac.nnz == 94 ** 3
+    rp, col, val = Ac.to_host()
+    assert set(np.unique(val).tolist()) == {152.0, -16.0, -4.0, -1.0}
+    RA = spg.spgemm(Rd, Ad)
+    Ac2 = spg.spgemm(RA, Pd)
+    rp2, col2, val2 = Ac2.to_host()
+    assert np.array_equal(rp, rp2) and np.array_equal(col, col2) and np.array_equal(val, val2)
+    # exact against the oracle too
+    APh = oracle_mod.spgemm(A, P)
+    ref = oracle_mod.spgemm(R, gen.HostCSR(APh.nrows, APh.ncols, APh.row_ptr, APh.col, APh.val))
+    assert np.array_equal(rp, ref.row_ptr) and np.array_equal(col, ref.col) and np.array_equal(val, ref.val)
