@@ -333,8 +333,8 @@ def run_cpu_baseline(args, budget_s=20.0):
     B = A if B is None else B
     nthreads = oracle.num_threads()
     blen = np.diff(B.row_ptr)
-    u = np.add.reduceat(blen[A.col], A.row_ptr[:-1]) if A.nnz else np.zeros(A.nrows, np.int64)
-    u[np.diff(A.row_ptr) == 0] = 0
+    cs = np.concatenate([[0], np.cumsum(blen[A.col])])
+    u = cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]
     total_u = int(u.sum())
     rows = None
     sample = "full workload"

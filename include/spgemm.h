@@ -93,6 +93,16 @@ typedef enum spgemm_alloc_policy {
     SPGEMM_ALLOC_LEARNED = 2
 } spgemm_alloc_policy;
 
+/* Rows whose result outgrows the largest shared-memory capacity (bin 37). */
+typedef enum spgemm_long_rows {
+    /* Split the row at the median column of its merged sequence into two column
+       slices that resume independently (default; slices run on separate SMs). */
+    SPGEMM_LONG_ROWS_SPLIT = 0,
+    /* The paper's level-1 sequence (Section 4.1): shared memory holds a level-1
+       sequence that is merged into a global sequence whenever it fills up. */
+    SPGEMM_LONG_ROWS_LEVEL1 = 1
+} spgemm_long_rows;
+
 /* Options; initialise with spgemm_opts_init and change fields as needed. */
 typedef struct spgemm_opts {
     int32_t alloc_policy;    /* spgemm_alloc_policy */
@@ -102,7 +112,8 @@ typedef struct spgemm_opts {
     int32_t merge_batch;     /* products per batch in the bin-37 merge kernel (0 = auto) */
     int32_t smem_cap_max;    /* largest result capacity held in shared memory (0 = auto) */
     int32_t heap_block;      /* threads per block of the heap kernel (0 = auto) */
-    int32_t reserved[9];
+    int32_t long_rows;       /* spgemm_long_rows: handling of rows beyond shared memory */
+    int32_t reserved[8];
     const void *predictor;   /* spgemm_predictor* for SPGEMM_ALLOC_LEARNED, else NULL */
     double predictor_margin; /* predicted size is multiplied by this before rounding up */
 } spgemm_opts;
@@ -161,6 +172,7 @@ typedef struct spgemm_stats {
     int64_t merge_rounds;       /* launches of the bin-37 kernel (progressive rounds) */
     int64_t rows_relaunched;    /* bin-37 rows that overflowed at least once */
     int64_t rows_level1;        /* bin-37 rows finished with a level-1 sequence */
+    int64_t rows_split;         /* column splits of long rows (SPGEMM_LONG_ROWS_SPLIT) */
     int64_t rows_fallback;      /* rows recomputed because a prediction was too small */
     int64_t bytes_ctilde;       /* device bytes allocated for temporary rows (all rounds) */
     int64_t peak_bytes;         /* high-water mark of the library's device pool since symbolic */

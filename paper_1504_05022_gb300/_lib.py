@@ -16,6 +16,7 @@ STATUS = {
     4: "SPGEMM_ERR_OOM", 5: "SPGEMM_ERR_CUDA", 6: "SPGEMM_ERR_TIMEOUT", 7: "SPGEMM_ERR_INTERNAL",
 }
 POLICY = {"hybrid": 0, "upper_bound": 1, "learned": 2}
+LONG_ROWS = {"split": 0, "level1": 1}
 KERNELS = ["bound", "bin", "heap", "esc", "merge", "scan", "arrange", "other"]
 NUM_BINS = 38
 
@@ -33,13 +34,13 @@ class CsrOut(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("alloc_policy", c_i32), ("initial_cap", c_i32), ("check_inputs", c_i32),
                 ("record_timing", c_i32), ("merge_batch", c_i32), ("smem_cap_max", c_i32),
-                ("heap_block", c_i32), ("reserved", c_i32 * 9), ("predictor", c_ptr),
+                ("heap_block", c_i32), ("long_rows", c_i32), ("reserved", c_i32 * 8), ("predictor", c_ptr),
                 ("predictor_margin", c_f64)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("bin_count", c_i64 * NUM_BINS), ("sum_u", c_i64), ("nnz_ctilde", c_i64), ("nnz_c", c_i64),
-                ("merge_rounds", c_i64), ("rows_relaunched", c_i64), ("rows_level1", c_i64),
+                ("merge_rounds", c_i64), ("rows_relaunched", c_i64), ("rows_level1", c_i64), ("rows_split", c_i64),
                 ("rows_fallback", c_i64), ("bytes_ctilde", c_i64), ("peak_bytes", c_i64),
                 ("launches", c_i32 * 8), ("kernel_ms", c_f32 * 8)]
 

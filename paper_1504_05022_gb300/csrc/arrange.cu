@@ -2,7 +2,8 @@
 // exclusive prefix sum into C.row_ptr (int64), C is allocated by the host, and
 // the rows are copied from the temporary matrix C~ into C.  Rows of bin 1 hold a
 // single product, which is computed here directly; rows of bin 0 need nothing.
-// Bins 2..36 are copied by one warp per row, bin 37 by one CTA per row.
+// Bins 2..36 are copied by one warp per row, bin 37 by one CTA per row (all
+// column slices of a split row, in column order).
 #include "internal.h"
 #include "scan.cuh"
 
@@ -73,26 +74,59 @@ cudaError_t launch_arrange_short(const StageArgs &a, const int32_t *rows, int64_
     return cudaGetLastError();
 }
 
+// One CTA per bin-37 row: its leaves (column slices) are visited in column order
+// by a depth-first walk of the split tree (left child first) and copied back to back.
 __global__ void __launch_bounds__(ARR_NT)
-k_arrange_long(MergeState s, const int32_t *__restrict__ rows37, const int64_t *__restrict__ c_rp,
-               int32_t *__restrict__ c_col, double *__restrict__ c_val) {
+k_arrange_long(MergeItems it, const int64_t *__restrict__ c_rp, int32_t *__restrict__ c_col,
+               double *__restrict__ c_val) {
+    constexpr int LEAF_BUF = 128, STACK = 64;
+    __shared__ int leaves[LEAF_BUF];
+    __shared__ int stack[STACK];
+    __shared__ int sp, nleaves;
     const int j = blockIdx.x;
-    const int row = rows37[j];
-    const int64_t o = c_rp[row];
-    const int64_t n = s.len[j];
-    const int32_t *sc = s.loc_col[j];
-    const double *sv = s.loc_val[j];
-    for (int64_t t = threadIdx.x; t < n; t += ARR_NT) {
-        c_col[o + t] = sc[t];
-        c_val[o + t] = sv[t];
+    int64_t o = c_rp[it.row[j]];
+    if (threadIdx.x == 0) {
+        sp = 0;
+        stack[sp++] = j;
+    }
+    __syncthreads();
+    while (true) {
+        if (threadIdx.x == 0) {
+            int n = 0;
+            while (sp > 0 && n < LEAF_BUF) {
+                const int x = stack[--sp];
+                const int c = it.child[x];
+                if (c < 0) {
+                    leaves[n++] = x;
+                } else if (sp + 2 <= STACK) {
+                    stack[sp++] = c + 1;
+                    stack[sp++] = c;
+                }
+            }
+            nleaves = n;
+        }
+        __syncthreads();
+        const int nl = nleaves;
+        if (nl == 0) break;
+        for (int l = 0; l < nl; ++l) {
+            const int x = leaves[l];
+            const int64_t n = it.len[x];
+            const int32_t *sc = it.home_col[x];
+            const double *sv = it.home_val[x];
+            for (int64_t t = threadIdx.x; t < n; t += ARR_NT) {
+                c_col[o + t] = sc[t];
+                c_val[o + t] = sv[t];
+            }
+            o += n;
+        }
+        __syncthreads();
     }
 }
 
-cudaError_t launch_arrange_long(const MergeState &s, const int32_t *rows37, int64_t n37,
-                                const int64_t *c_rp, int32_t *c_col, double *c_val,
-                                cudaStream_t st) {
+cudaError_t launch_arrange_long(const MergeItems &it, int64_t n37, const int64_t *c_rp, int32_t *c_col,
+                                double *c_val, cudaStream_t st) {
     if (n37 <= 0) return cudaSuccess;
-    k_arrange_long<<<(unsigned)n37, ARR_NT, 0, st>>>(s, rows37, c_rp, c_col, c_val);
+    k_arrange_long<<<(unsigned)n37, ARR_NT, 0, st>>>(it, c_rp, c_col, c_val);
     return cudaGetLastError();
 }
 

@@ -65,20 +65,30 @@ cudaError_t launch_heap(const StageArgs &a, const int32_t *rows, int64_t nrows, 
 cudaError_t launch_esc(const StageArgs &a, const int32_t *rows, int64_t nrows, int bin,
                        cudaStream_t st);
 
-// Bin-37 per-row state (indexed by position j in the bin-37 row list).
-struct MergeState {
-    int32_t **loc_col;   // current global home of the row's sequence
-    double **loc_val;
-    int64_t *loc_cap;    // capacity of that home
-    int32_t *len;        // entries stored there
+// Bin-37 work items.  Item j < n37 is the j-th row of bin 37 with the full
+// column range.  An item whose sequence outgrows the largest shared-memory
+// capacity is split at the median column of that sequence into two child items
+// with column ranges [clo, mkey) and [mkey, chi); the leaves of a row, read in
+// column order, concatenate to the row of C.
+struct MergeItems {
+    int32_t *row;        // row of C
+    int32_t *clo;        // first column of the item's range
+    int32_t *chi;        // end of the range (exclusive); INT32_MAX = unbounded
+    int32_t **src_col;   // sorted sequence to reload when the item (re)starts
+    double **src_val;
+    int32_t *src_len;
+    int32_t **home_col;  // where the item's sequence is written
+    double **home_val;
+    int64_t *home_cap;
+    int32_t *len;        // final length (leaves)
     int64_t *ck_entry;   // checkpoint: A-entry index relative to the row start
-    int64_t *ck_off;     // checkpoint: offset inside that B row
-    int32_t *done;       // 1 once the row is final
+    int64_t *ck_off;     //             and offset inside that entry's full B row
+    int32_t *child;      // -1 for a leaf, else the left child (the right one is child + 1)
 };
 
 struct MergeLaunch {
-    const int32_t *rows37;   // bin-37 row list (row ids)
-    const int32_t *work;     // positions j to process (nullptr: j = 0..nwork-1)
+    const int32_t *work;     // items to process (nullptr: items work_base .. work_base + nwork - 1)
+    int64_t work_base;
     int64_t nwork;
     int cap;                 // shared-memory result capacity for this launch
     int batch;               // products per batch
@@ -90,17 +100,24 @@ struct MergeLaunch {
     const int64_t *g_cap;    //          and their capacity
     int32_t *g_col;
     double *g_val;
-    int32_t *ovf_list;       // rows that overflowed (positions j)
+    int32_t *ovf_list;       // items that overflowed
     int32_t *ovf_count;
     int64_t *err;            // device error word
 };
 
 int merge_smem_bytes(int cap, int batch);
+int merge_batch_limit(int cap);
 int merge_max_cap(int batch, int smem_limit);
-cudaError_t launch_merge(const StageArgs &a, const MergeState &s, const MergeLaunch &L,
-                         const int64_t *u, cudaStream_t st);
+cudaError_t launch_merge(const StageArgs &a, const MergeItems &it, const MergeLaunch &L, cudaStream_t st);
+cudaError_t launch_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
+                              double *ctil_val, const MergeItems &it, cudaStream_t st);
+// splits the items listed in ovf (count n) into children first_new + 2i, first_new + 2i + 1
+cudaError_t launch_split(const int32_t *ovf, int64_t n, int64_t first_new, const MergeItems &it,
+                         cudaStream_t st);
+// nnz(c_i) of every bin-37 row = summed lengths of its leaves
+cudaError_t launch_finalize37(int64_t n37, const MergeItems &it, int32_t *nnzc, int64_t *err, cudaStream_t st);
 // level-1 buffer sizing: per work item cap = min(u_row, ncols_B) (two buffers each)
-cudaError_t launch_level1_sizes(const int32_t *rows37, const int32_t *work, int64_t nwork,
+cudaError_t launch_level1_sizes(const MergeItems &it, const int32_t *work, int64_t nwork,
                                 const int64_t *u, int64_t ncols, int64_t *g_cap, int64_t *g_off,
                                 int64_t *partial, int64_t *total, cudaStream_t st);
 
@@ -110,8 +127,7 @@ cudaError_t launch_row_scan(int64_t m, const int32_t *nnzc, int64_t *c_rp, int64
 cudaError_t launch_arrange_short(const StageArgs &a, const int32_t *rows, int64_t nrows,
                                  const uint8_t *bin, const int64_t *c_rp, int32_t *c_col,
                                  double *c_val, cudaStream_t st);
-cudaError_t launch_arrange_long(const MergeState &s, const int32_t *rows37, int64_t n37,
-                                const int64_t *c_rp, int32_t *c_col, double *c_val,
-                                cudaStream_t st);
+cudaError_t launch_arrange_long(const MergeItems &it, int64_t n37, const int64_t *c_rp, int32_t *c_col,
+                                double *c_val, cudaStream_t st);
 
 }  // namespace spg

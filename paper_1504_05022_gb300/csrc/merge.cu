@@ -29,11 +29,11 @@
 #include "common.cuh"
 #include "scan.cuh"
 
+#include <algorithm>
+
 namespace spg {
 
-constexpr int MERGE_NT = 256;
-constexpr int MERGE_W = 256;       // A entries per window (one per thread)
-constexpr int MERGE_MAX_IPT = 8;   // batch <= MERGE_NT * MERGE_MAX_IPT
+constexpr int MERGE_MAX_IPT = 4;   // products per thread per batch: batch <= NT * 4
 constexpr int MERGE_TN_MAX = 1024; // pending-set capacity
 
 struct MergeSmem {
@@ -42,11 +42,11 @@ struct MergeSmem {
     int32_t *Rk, *Nk, *Sak, *Sbk, *pf, *runoff;
 };
 
-SPG_DEV size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
 __host__ __device__ inline int merge_tn(int cap) { return cap < MERGE_TN_MAX ? cap : MERGE_TN_MAX; }
 
-__host__ __device__ inline size_t merge_layout(int cap, int kb, unsigned char *base, MergeSmem *s) {
+// Shared-memory layout of one CTA: result R (cap), pending set N, two batch
+// buffers, the compaction prefix, and the window of W A entries (W = threads).
+__host__ __device__ inline size_t merge_layout(int cap, int kb, int W, unsigned char *base, MergeSmem *s) {
     const int tn = merge_tn(cap);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -55,28 +55,55 @@ __host__ __device__ inline size_t merge_layout(int cap, int kb, unsigned char *b
         return base ? base + o : nullptr;
     };
     unsigned char *p;
-    p = take(sizeof(double) * cap);           if (s) s->Rv = (double *)p;
-    p = take(sizeof(double) * tn);            if (s) s->Nv = (double *)p;
-    p = take(sizeof(double) * kb);            if (s) s->Sav = (double *)p;
-    p = take(sizeof(double) * kb);            if (s) s->Sbv = (double *)p;
-    p = take(sizeof(double) * MERGE_W);       if (s) s->wa = (double *)p;
-    p = take(sizeof(int64_t) * MERGE_W);      if (s) s->wbs = (int64_t *)p;
-    p = take(sizeof(int64_t) * (MERGE_W + 1)); if (s) s->wscan = (int64_t *)p;
-    p = take(sizeof(int32_t) * cap);          if (s) s->Rk = (int32_t *)p;
-    p = take(sizeof(int32_t) * tn);           if (s) s->Nk = (int32_t *)p;
-    p = take(sizeof(int32_t) * kb);           if (s) s->Sak = (int32_t *)p;
-    p = take(sizeof(int32_t) * kb);           if (s) s->Sbk = (int32_t *)p;
-    p = take(sizeof(int32_t) * (kb + 1));     if (s) s->pf = (int32_t *)p;
-    p = take(sizeof(int32_t) * (MERGE_W + 2)); if (s) s->runoff = (int32_t *)p;
+    p = take(sizeof(double) * cap);       if (s) s->Rv = (double *)p;
+    p = take(sizeof(double) * tn);        if (s) s->Nv = (double *)p;
+    p = take(sizeof(double) * kb);        if (s) s->Sav = (double *)p;
+    p = take(sizeof(double) * kb);        if (s) s->Sbv = (double *)p;
+    p = take(sizeof(double) * W);         if (s) s->wa = (double *)p;
+    p = take(sizeof(int64_t) * W);        if (s) s->wbs = (int64_t *)p;
+    p = take(sizeof(int64_t) * (W + 1));  if (s) s->wscan = (int64_t *)p;
+    p = take(sizeof(int32_t) * cap);      if (s) s->Rk = (int32_t *)p;
+    p = take(sizeof(int32_t) * tn);       if (s) s->Nk = (int32_t *)p;
+    p = take(sizeof(int32_t) * kb);       if (s) s->Sak = (int32_t *)p;
+    p = take(sizeof(int32_t) * kb);       if (s) s->Sbk = (int32_t *)p;
+    p = take(sizeof(int32_t) * (kb + 1)); if (s) s->pf = (int32_t *)p;
+    p = take(sizeof(int32_t) * (W + 2));  if (s) s->runoff = (int32_t *)p;
     return off;
 }
 
-int merge_smem_bytes(int cap, int batch) { return (int)merge_layout(cap, batch, nullptr, nullptr); }
+// Threads per CTA for a launch with result capacity `cap`.
+inline int merge_threads(int cap) { return cap <= 512 ? 128 : (cap <= 2048 ? 256 : 512); }
+
+int merge_smem_bytes(int cap, int batch) {
+    return (int)merge_layout(cap, batch, merge_threads(cap), nullptr, nullptr);
+}
 
 int merge_max_cap(int batch, int smem_limit) {
     int cap = 256;
-    while (merge_smem_bytes(cap + 256, batch) <= smem_limit) cap += 256;
+    while (merge_smem_bytes(cap + 256, std::min(batch, 4 * merge_threads(cap + 256))) <= smem_limit) cap += 256;
     return cap;
+}
+
+// Lockstep lower_bound of up to IPT keys in the sorted array a[0..n): pos[k]
+// receives the number of entries < key[k].  The IPT searches are independent,
+// so their shared-memory loads overlap.
+template <int IPT>
+SPG_DEV void lower_bound_multi(const int32_t *a, int n, const int32_t (&key)[IPT], int cnt, int (&pos)[IPT]) {
+    int hi[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        pos[k] = 0;
+        hi[k] = (k < cnt) ? n : 0;
+    }
+    for (int step = 32 - __clz(n); step > 0; --step) {
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            if (pos[k] < hi[k]) {
+                const int mid = (pos[k] + hi[k]) >> 1;
+                if (a[mid] < key[k]) pos[k] = mid + 1; else hi[k] = mid;
+            }
+        }
+    }
 }
 
 // One level of the pairwise merge of `nruns` sorted runs: run r occupies
@@ -175,74 +202,83 @@ SPG_DEV int64_t union_stream(const int32_t *xk, const double *xv, int64_t nx, co
     return zo;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT, 1)
-k_merge(StageArgs a, MergeState st, MergeLaunch L, const int64_t *__restrict__ u) {
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
     extern __shared__ __align__(16) unsigned char merge_smem[];
     __shared__ int64_t scan64[NT / 32 + 1];
     __shared__ int32_t scan32[NT / 32 + 1];
+    constexpr int W = NT;
     MergeSmem s;
     const int cap = L.cap;
     const int kb = L.batch;
     const int tn = merge_tn(cap);
-    merge_layout(cap, kb, merge_smem, &s);
+    merge_layout(cap, kb, W, merge_smem, &s);
 
     const int64_t w = blockIdx.x;
-    const int j = L.work ? L.work[w] : (int)w;
-    const int row = L.rows37[j];
+    const int j = L.work ? L.work[w] : (int)(L.work_base + w);
+    const int row = it.row[j];
+    const int32_t clo = it.clo[j], chi = it.chi[j];
+    const bool filtered = (clo > 0) || (chi < INT32_MAX);
     const int64_t a0 = a.A.rp[row], a1 = a.A.rp[row + 1];
-    int32_t *home_col = st.loc_col[j];
-    double *home_val = st.loc_val[j];
-    const int64_t home_cap = st.loc_cap[j];
-    int rlen = st.len[j];
-    int64_t e = a0 + st.ck_entry[j];
-    int64_t off = st.ck_off[j];
+    int rlen = it.src_len[j];
+    int64_t e = a0 + it.ck_entry[j];
+    int64_t off = it.ck_off[j];
 
-    // reload the dumped sequence (empty for a fresh row)
-    for (int t = threadIdx.x; t < rlen; t += NT) {
-        s.Rk[t] = home_col[t];
-        s.Rv[t] = home_val[t];
+    // reload the item's sequence (empty for a fresh row; half of the parent's for a split child)
+    {
+        const int32_t *sc = it.src_col[j];
+        const double *sv = it.src_val[j];
+        for (int t = threadIdx.x; t < rlen; t += NT) {
+            s.Rk[t] = sc[t];
+            s.Rv[t] = sv[t];
+        }
     }
-    // where this launch writes the row: its home if large enough, else a fresh slot
-    int32_t *dst_col = home_col;
-    double *dst_val = home_val;
-    int64_t dst_cap = home_cap;
-    if (!L.level1 && home_cap < cap && L.pool_col != nullptr) {
+    // where this launch writes the item: its home if large enough, else a fresh slot
+    int32_t *dst_col = it.home_col[j];
+    double *dst_val = it.home_val[j];
+    int64_t dst_cap = it.home_cap[j];
+    if (!L.level1 && dst_cap < cap && L.pool_col != nullptr) {
         dst_col = L.pool_col + w * L.pool_cap;
         dst_val = L.pool_val + w * L.pool_cap;
         dst_cap = L.pool_cap;
     }
-    // level-1 global sequence (ping-pong)
-    int32_t *gk[2] = {nullptr, nullptr};
-    double *gv[2] = {nullptr, nullptr};
-    int gcur = 0;
+    // level-1 global sequence: ping-pong between g0 and g1
+    int32_t *g0k = nullptr, *g1k = nullptr;
+    double *g0v = nullptr, *g1v = nullptr;
     int64_t glen = 0;
     if (L.level1) {
         const int64_t go = L.g_off[w], gc = L.g_cap[w];
-        gk[0] = L.g_col + go;
-        gv[0] = L.g_val + go;
-        gk[1] = L.g_col + go + gc;
-        gv[1] = L.g_val + go + gc;
+        g0k = L.g_col + go;
+        g0v = L.g_val + go;
+        g1k = L.g_col + go + gc;
+        g1v = L.g_val + go + gc;
     }
     int nlen = 0;
     __syncthreads();
 
     bool overflow = false;
     while (e < a1 && !overflow) {
-        const int nW = (int)min((int64_t)MERGE_W, a1 - e);
+        // ---- window: the next W entries of the A row and their (column-filtered) B-row ranges ----
+        const int nW = (int)min((int64_t)W, a1 - e);
         int64_t len = 0;
         if (threadIdx.x < nW) {
             const int64_t idx = e + threadIdx.x;
             const int32_t kk = a.A.col[idx];
-            int64_t bs = a.B.rp[kk];
-            int64_t bl = a.B.rp[kk + 1] - bs;
-            if (threadIdx.x == 0) {
-                bs += off;
-                bl -= off;
+            const int64_t rs = a.B.rp[kk];
+            int64_t be = a.B.rp[kk + 1];
+            int64_t bs = rs + (threadIdx.x == 0 ? off : 0);
+            if (filtered) {
+                const int n = (int)(be - rs);
+                if (clo > 0) {
+                    const int64_t lo = rs + lower_bound_i32(a.B.col + rs, n, clo);
+                    bs = bs > lo ? bs : lo;
+                }
+                if (chi < INT32_MAX) be = rs + lower_bound_i32(a.B.col + rs, n, chi);
             }
             s.wbs[threadIdx.x] = bs;
             s.wa[threadIdx.x] = a.A.val[idx];
-            len = bl;
+            len = be > bs ? be - bs : 0;
         }
         int64_t total;
         const int64_t ex = block_exclusive_scan<NT>(len, scan64, total);
@@ -262,84 +298,97 @@ k_merge(StageArgs a, MergeState st, MergeLaunch L, const int64_t *__restrict__ u
                         rlen += nlen;
                         nlen = 0;
                     }
-                    glen = union_stream<NT>(gk[gcur], gv[gcur], glen, s.Rk, s.Rv, rlen, gk[gcur ^ 1],
-                                            gv[gcur ^ 1], s, kb, scan32);
-                    gcur ^= 1;
+                    glen = union_stream<NT>(g0k, g0v, glen, s.Rk, s.Rv, rlen, g1k, g1v, s, kb, scan32);
+                    int32_t *tk = g0k; g0k = g1k; g1k = tk;
+                    double *tv = g0v; g0v = g1v; g1v = tv;
                     rlen = 0;
                     avail = cap;
                 } else if (avail < (kb >> 2) || avail <= 0) {
-                    // checkpoint at product p0 of this window
+                    // checkpoint at product p0 of this window (offset counted in the full B row)
                     const int t = find_segment_i64(s.wscan, nW, p0);
                     if (threadIdx.x == 0) {
-                        st.ck_entry[j] = (e + t) - a0;
-                        st.ck_off[j] = (t == 0 ? off : 0) + (p0 - s.wscan[t]);
+                        const int32_t kk = a.A.col[e + t];
+                        it.ck_entry[j] = (e + t) - a0;
+                        it.ck_off[j] = s.wbs[t] + (p0 - s.wscan[t]) - a.B.rp[kk];
                     }
                     overflow = true;
                     break;
                 }
             }
             const int nb = min(need, avail);
-            // (0) expand the batch [p0, p0 + nb) into Sa, one run per B row
             const int tf = find_segment_i64(s.wscan, nW, p0);
             const int tl = find_segment_i64(s.wscan, nW, p0 + nb - 1);
             const int nruns = tl - tf + 1;
-            for (int q = threadIdx.x; q < nb; q += NT) {
-                const int64_t pos = p0 + q;
-                const int t = tf + find_segment_i64(s.wscan + tf, nruns, pos);
-                const int64_t bidx = s.wbs[t] + (pos - s.wscan[t]);
-                s.Sak[q] = a.B.col[bidx];
-                s.Sav[q] = s.wa[t] * a.B.val[bidx];
-            }
-            for (int r = threadIdx.x; r <= nruns; r += NT)
-                s.runoff[r] = (r == 0) ? 0 : (r == nruns ? nb : (int)(s.wscan[tf + r] - p0));
-            __syncthreads();
-            // (1) fuse products whose column is already in R or N
+            // (0) each thread expands IPT consecutive products of the batch into registers
             const int ipt = (nb + NT - 1) / NT;
             const int q0 = threadIdx.x * ipt;
-            unsigned newmask = 0;
-            int cntnew = 0;
-            for (int k = 0; k < MERGE_MAX_IPT; ++k) {
-                const int q = q0 + k;
-                if (k < ipt && q < nb) {
-                    const int32_t key = s.Sak[q];
-                    bool found = false;
-                    if (rlen > 0) {
-                        const int pos = lower_bound_i32(s.Rk, rlen, key);
-                        if (pos < rlen && s.Rk[pos] == key) {
-                            atomicAdd(&s.Rv[pos], s.Sav[q]);
-                            found = true;
-                        }
+            const int cnt = max(0, min(ipt, nb - q0));
+            int32_t key[MERGE_MAX_IPT];
+            double val[MERGE_MAX_IPT];
+            if (cnt > 0) {
+                int64_t pos = p0 + q0;
+                int t = tf + find_segment_i64(s.wscan + tf, nruns, pos);
+#pragma unroll
+                for (int k = 0; k < MERGE_MAX_IPT; ++k) {
+                    if (k < cnt) {
+                        while (t + 1 < nW && s.wscan[t + 1] <= pos) ++t;
+                        const int64_t bidx = s.wbs[t] + (pos - s.wscan[t]);
+                        key[k] = a.B.col[bidx];
+                        val[k] = s.wa[t] * a.B.val[bidx];
+                        ++pos;
                     }
-                    if (!found && nlen > 0) {
-                        const int pos = lower_bound_i32(s.Nk, nlen, key);
-                        if (pos < nlen && s.Nk[pos] == key) {
-                            atomicAdd(&s.Nv[pos], s.Sav[q]);
-                            found = true;
-                        }
+                }
+            }
+            // (1) fuse products whose column is already in R or N (lockstep binary searches)
+            unsigned miss = 0;
+            int pos[MERGE_MAX_IPT];
+            if (rlen > 0) {
+                lower_bound_multi<MERGE_MAX_IPT>(s.Rk, rlen, key, cnt, pos);
+#pragma unroll
+                for (int k = 0; k < MERGE_MAX_IPT; ++k) {
+                    if (k < cnt) {
+                        if (pos[k] < rlen && s.Rk[pos[k]] == key[k]) atomicAdd(&s.Rv[pos[k]], val[k]);
+                        else miss |= 1u << k;
                     }
-                    if (!found) {
-                        newmask |= 1u << k;
-                        ++cntnew;
+                }
+            } else {
+                miss = (1u << cnt) - 1u;
+            }
+            if (nlen > 0 && miss != 0) {
+                int32_t k2[MERGE_MAX_IPT];
+#pragma unroll
+                for (int k = 0; k < MERGE_MAX_IPT; ++k) k2[k] = (miss >> k) & 1u ? key[k] : INT_MIN;
+                lower_bound_multi<MERGE_MAX_IPT>(s.Nk, nlen, k2, cnt, pos);
+#pragma unroll
+                for (int k = 0; k < MERGE_MAX_IPT; ++k) {
+                    if ((miss >> k) & 1u) {
+                        if (pos[k] < nlen && s.Nk[pos[k]] == key[k]) {
+                            atomicAdd(&s.Nv[pos[k]], val[k]);
+                            miss &= ~(1u << k);
+                        }
                     }
                 }
             }
             // (2) compact the misses into Sb, keeping one run per B row
             int nnew;
-            int o = block_exclusive_scan<NT>(cntnew, scan32, nnew);
+            int o = block_exclusive_scan<NT>(__popc(miss), scan32, nnew);
+#pragma unroll
             for (int k = 0; k < MERGE_MAX_IPT; ++k) {
-                const int q = q0 + k;
-                if (k < ipt && q < nb) {
-                    s.pf[q] = o;
-                    if (newmask & (1u << k)) {
-                        s.Sbk[o] = s.Sak[q];
-                        s.Sbv[o] = s.Sav[q];
+                if (k < cnt) {
+                    s.pf[q0 + k] = o;
+                    if ((miss >> k) & 1u) {
+                        s.Sbk[o] = key[k];
+                        s.Sbv[o] = val[k];
                         ++o;
                     }
                 }
             }
             if (threadIdx.x == 0) s.pf[nb] = nnew;
             __syncthreads();
-            for (int r = threadIdx.x; r <= nruns; r += NT) s.runoff[r] = s.pf[s.runoff[r]];
+            for (int r = threadIdx.x; r <= nruns; r += NT) {
+                const int q = (r == 0) ? 0 : (r == nruns ? nb : (int)(s.wscan[tf + r] - p0));
+                s.runoff[r] = s.pf[q];
+            }
             __syncthreads();
             if (nnew > 0) {
                 // (3) pairwise merge-path merges of the runs, then fuse equal columns
@@ -400,12 +449,10 @@ k_merge(StageArgs a, MergeState st, MergeLaunch L, const int64_t *__restrict__ u
     double *fin_val;
     int64_t fin_cap;
     if (L.level1) {
-        glen = union_stream<NT>(gk[gcur], gv[gcur], glen, s.Rk, s.Rv, rlen, gk[gcur ^ 1], gv[gcur ^ 1], s,
-                                kb, scan32);
-        gcur ^= 1;
+        glen = union_stream<NT>(g0k, g0v, glen, s.Rk, s.Rv, rlen, g1k, g1v, s, kb, scan32);
         final_len = glen;
-        fin_col = gk[gcur];
-        fin_val = gv[gcur];
+        fin_col = g1k;
+        fin_val = g1v;
         fin_cap = L.g_cap[w];
     } else {
         if (rlen > dst_cap) {  // cannot happen: dst_cap >= cap >= rlen
@@ -422,26 +469,129 @@ k_merge(StageArgs a, MergeState st, MergeLaunch L, const int64_t *__restrict__ u
         fin_cap = dst_cap;
     }
     if (threadIdx.x == 0) {
-        st.loc_col[j] = fin_col;
-        st.loc_val[j] = fin_val;
-        st.loc_cap[j] = fin_cap;
-        st.len[j] = (int32_t)final_len;
+        it.home_col[j] = fin_col;
+        it.home_val[j] = fin_val;
+        it.home_cap[j] = fin_cap;
         if (overflow) {
+            it.src_col[j] = fin_col;
+            it.src_val[j] = fin_val;
+            it.src_len[j] = (int32_t)final_len;
             const int slot = atomicAdd(L.ovf_count, 1);
             L.ovf_list[slot] = j;
         } else {
-            st.done[j] = 1;
-            a.nnzc[row] = (int32_t)final_len;
+            it.len[j] = (int32_t)final_len;
         }
     }
 }
 
-__global__ void k_level1_caps(const int32_t *rows37, const int32_t *work, int64_t nwork,
-                              const int64_t *u, int64_t ncols, int64_t *g_cap) {
+__global__ void k_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
+                             double *ctil_val, MergeItems it) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n37) return;
+    const int row = rows37[j];
+    const int64_t o = ctil_rp[row];
+    it.row[j] = row;
+    it.clo[j] = 0;
+    it.chi[j] = INT32_MAX;
+    it.src_col[j] = ctil_col + o;
+    it.src_val[j] = ctil_val + o;
+    it.src_len[j] = 0;
+    it.home_col[j] = ctil_col + o;
+    it.home_val[j] = ctil_val + o;
+    it.home_cap[j] = ctil_rp[row + 1] - o;
+    it.len[j] = 0;
+    it.ck_entry[j] = 0;
+    it.ck_off[j] = 0;
+    it.child[j] = -1;
+}
+
+cudaError_t launch_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
+                              double *ctil_val, const MergeItems &it, cudaStream_t st) {
+    if (n37 <= 0) return cudaSuccess;
+    k_merge_init<<<(unsigned)((n37 + 255) / 256), 256, 0, st>>>(rows37, n37, ctil_rp, ctil_col, ctil_val, it);
+    return cudaGetLastError();
+}
+
+// Splits an overflowed item at the median column of its dumped sequence.  Both
+// children resume from the parent's checkpoint; each reloads its half of the
+// parent's sequence and only takes products inside its column range.
+__global__ void k_split(const int32_t *ovf, int64_t n, int64_t first_new, MergeItems it) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = ovf[i];
+    const int plen = it.src_len[p];
+    const int mid = plen / 2;
+    const int32_t mkey = it.src_col[p][mid];
+    const int64_t l = first_new + 2 * i, r = l + 1;
+    for (int c = 0; c < 2; ++c) {
+        const int64_t q = c == 0 ? l : r;
+        it.row[q] = it.row[p];
+        it.clo[q] = c == 0 ? it.clo[p] : mkey;
+        it.chi[q] = c == 0 ? mkey : it.chi[p];
+        it.src_col[q] = it.src_col[p] + (c == 0 ? 0 : mid);
+        it.src_val[q] = it.src_val[p] + (c == 0 ? 0 : mid);
+        it.src_len[q] = c == 0 ? mid : plen - mid;
+        it.home_col[q] = nullptr;
+        it.home_val[q] = nullptr;
+        it.home_cap[q] = 0;
+        it.len[q] = 0;
+        it.ck_entry[q] = it.ck_entry[p];
+        it.ck_off[q] = it.ck_off[p];
+        it.child[q] = -1;
+    }
+    it.child[p] = (int32_t)l;
+    it.len[p] = 0;
+}
+
+cudaError_t launch_split(const int32_t *ovf, int64_t n, int64_t first_new, const MergeItems &it,
+                         cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ovf, n, first_new, it);
+    return cudaGetLastError();
+}
+
+// Sum of the leaf lengths under item j (its column slices); -1 if the split
+// tree is deeper than the walk's stack (a split tree is at most ~31 deep).
+SPG_DEV int64_t leaf_total(const MergeItems &it, int j) {
+    constexpr int STACK = 64;
+    int stack[STACK];
+    int sp = 0;
+    int64_t tot = 0;
+    stack[sp++] = j;
+    while (sp > 0) {
+        const int x = stack[--sp];
+        const int c = it.child[x];
+        if (c < 0) {
+            tot += it.len[x];
+        } else {
+            if (sp + 2 > STACK) return -1;
+            stack[sp++] = c + 1;
+            stack[sp++] = c;
+        }
+    }
+    return tot;
+}
+
+__global__ void k_finalize37(int64_t n37, MergeItems it, int32_t *nnzc, int64_t *err) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n37) return;
+    const int64_t tot = leaf_total(it, (int)j);
+    if (tot < 0 || tot > INT32_MAX) atomicExch((unsigned long long *)err, 2ull);
+    nnzc[it.row[j]] = tot < 0 ? 0 : (int32_t)tot;
+}
+
+cudaError_t launch_finalize37(int64_t n37, const MergeItems &it, int32_t *nnzc, int64_t *err, cudaStream_t st) {
+    if (n37 <= 0) return cudaSuccess;
+    k_finalize37<<<(unsigned)((n37 + 127) / 128), 128, 0, st>>>(n37, it, nnzc, err);
+    return cudaGetLastError();
+}
+
+__global__ void k_level1_caps(MergeItems it, const int32_t *work, int64_t nwork, const int64_t *u,
+                              int64_t ncols, int64_t *g_cap) {
     int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nwork) return;
-    const int j = work ? work[w] : (int)w;
-    int64_t c = u[rows37[j]];
+    const int j = work[w];
+    int64_t c = u[it.row[j]];
     if (c > ncols) c = ncols;
     g_cap[w] = c < 1 ? 1 : c;
 }
@@ -455,24 +605,37 @@ struct StoreOff {
     SPG_DEV void operator()(int64_t i, int64_t v) const { out[i] = v; }
 };
 
-cudaError_t launch_level1_sizes(const int32_t *rows37, const int32_t *work, int64_t nwork,
+cudaError_t launch_level1_sizes(const MergeItems &it, const int32_t *work, int64_t nwork,
                                 const int64_t *u, int64_t ncols, int64_t *g_cap, int64_t *g_off,
                                 int64_t *partial, int64_t *total, cudaStream_t st) {
     if (nwork > 0)
-        k_level1_caps<<<(unsigned)((nwork + 255) / 256), 256, 0, st>>>(rows37, work, nwork, u, ncols, g_cap);
+        k_level1_caps<<<(unsigned)((nwork + 255) / 256), 256, 0, st>>>(it, work, nwork, u, ncols, g_cap);
     return device_exclusive_scan(nwork, LoadCap2{g_cap}, StoreOff{g_off}, partial, total, st);
 }
 
-cudaError_t launch_merge(const StageArgs &a, const MergeState &s, const MergeLaunch &L,
-                         const int64_t *u, cudaStream_t st) {
-    if (L.nwork <= 0) return cudaSuccess;
-    // batch >= 32 keeps every loop of the kernel progressing (the level-1 stream takes batch/2 per step)
-    if (L.batch > MERGE_NT * MERGE_MAX_IPT || L.batch < 32 || L.batch > L.cap) return cudaErrorInvalidValue;
-    const int smem = merge_smem_bytes(L.cap, L.batch);
-    cudaError_t e = cudaFuncSetAttribute(k_merge<MERGE_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <int NT, int MINB>
+static cudaError_t launch_merge_nt(const StageArgs &a, const MergeItems &s, const MergeLaunch &L, int smem,
+                                  cudaStream_t st) {
+    auto kern = k_merge<NT, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_merge<MERGE_NT><<<(unsigned)L.nwork, MERGE_NT, smem, st>>>(a, s, L, u);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)L.nwork, NT, smem, st>>>(a, s, L);
     return cudaGetLastError();
 }
+
+cudaError_t launch_merge(const StageArgs &a, const MergeItems &s, const MergeLaunch &L, cudaStream_t st) {
+    if (L.nwork <= 0) return cudaSuccess;
+    const int nt = merge_threads(L.cap);
+    // batch >= 32 keeps every loop of the kernel progressing (the level-1 stream takes batch/2 per step)
+    if (L.batch > nt * MERGE_MAX_IPT || L.batch < 32 || L.batch > L.cap) return cudaErrorInvalidValue;
+    const int smem = merge_smem_bytes(L.cap, L.batch);
+    if (nt == 128) return launch_merge_nt<128, 4>(a, s, L, smem, st);
+    if (nt == 256) return launch_merge_nt<256, 2>(a, s, L, smem, st);
+    return launch_merge_nt<512, 1>(a, s, L, smem, st);
+}
+
+int merge_batch_limit(int cap) { return MERGE_MAX_IPT * merge_threads(cap); }
 
 }  // namespace spg

@@ -110,8 +110,9 @@ struct spgemm_plan {
     int64_t *d_err = nullptr;
     BinSummary h_summary{};
     int64_t bin_start[NUM_BINS + 1] = {0};
-    // bin 37
-    MergeState ms{};
+    // bin 37 work items
+    MergeItems items{};
+    int64_t n_items = 0, items_cap = 0;
     // result
     bool numeric_done = false;
     spgemm_csr_out C{};
@@ -227,21 +228,6 @@ StageArgs stage_args(spgemm_plan *p) {
     a.ctil_val = p->ctil_val;
     a.nnzc = p->nnzc;
     return a;
-}
-
-__global__ void k_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
-                             double *ctil_val, MergeState s) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n37) return;
-    const int row = rows37[j];
-    const int64_t o = ctil_rp[row];
-    s.loc_col[j] = ctil_col + o;
-    s.loc_val[j] = ctil_val + o;
-    s.loc_cap[j] = ctil_rp[row + 1] - o;
-    s.len[j] = 0;
-    s.ck_entry[j] = 0;
-    s.ck_off[j] = 0;
-    s.done[j] = 0;
 }
 
 }  // namespace
@@ -376,57 +362,105 @@ fail:
 
 namespace {
 
+template <typename T>
+cudaError_t grow_array(spgemm_plan *p, T **arr, int64_t old_n, int64_t new_cap) {
+    T *n = nullptr;
+    cudaError_t e = p->alloc_n(&n, new_cap);
+    if (e != cudaSuccess) return e;
+    if (old_n > 0 && *arr) {
+        e = cudaMemcpyAsync(n, *arr, sizeof(T) * old_n, cudaMemcpyDeviceToDevice, p->st);
+        if (e != cudaSuccess) return e;
+    }
+    *arr = n;
+    return cudaSuccess;
+}
+
+// Makes room for `need` work items (keeps the first n_items).
+cudaError_t reserve_items(spgemm_plan *p, int64_t need) {
+    if (need <= p->items_cap) return cudaSuccess;
+    const int64_t nc = std::max(need, p->items_cap + p->items_cap / 2);
+    MergeItems &it = p->items;
+    const int64_t n = p->n_items;
+    cudaError_t e;
+    if ((e = grow_array(p, &it.row, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.clo, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.chi, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.src_col, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.src_val, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.src_len, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.home_col, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.home_val, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.home_cap, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.len, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.ck_entry, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.ck_off, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.child, n, nc)) != cudaSuccess) return e;
+    p->items_cap = nc;
+    return cudaSuccess;
+}
+
+// Bin group 5: the merge kernel over all bin-37 rows, then the progressive
+// rounds: items that overflowed are relaunched with twice the capacity (and a
+// twice as large home); at the largest shared-memory capacity an overflowing
+// item is split by column (default) or finished with a level-1 sequence.
 spgemm_status run_bin37(spgemm_plan *p) {
     spgemm_status status = SPGEMM_OK;
     const int64_t n37 = p->h_summary.bin_count[BIN_MERGE];
     if (n37 == 0) return SPGEMM_OK;
     const int32_t *rows37 = p->bin_rows + p->bin_start[BIN_MERGE];
     StageArgs a = stage_args(p);
-    MergeState &s = p->ms;
     int32_t *list[2] = {nullptr, nullptr};
+    int64_t list_cap = 0;
     int32_t *ovf_count = nullptr;
     int64_t *g_cap = nullptr, *g_off = nullptr, *g_partial = nullptr, *g_total = nullptr;
     // leave room for the kernel's static shared memory
     const int smem_limit = (p->smem_optin > 0 ? p->smem_optin : 227 * 1024) - 1024;
-    int batch = p->opts.merge_batch > 0 ? p->opts.merge_batch : 1024;
+    int batch = p->opts.merge_batch > 0 ? p->opts.merge_batch : 2048;
     batch = std::max(32, std::min(batch, 2048));
     int capmax = merge_max_cap(batch, smem_limit);
     if (p->opts.smem_cap_max > 0) capmax = std::min(capmax, std::max(256, p->opts.smem_cap_max));
+    const bool use_level1 = p->opts.long_rows == SPGEMM_LONG_ROWS_LEVEL1;
     int cap;
     if (p->opts.alloc_policy == SPGEMM_ALLOC_UPPER_BOUND) cap = capmax;
     else cap = std::min(capmax, std::max(32, (int)p->opts.initial_cap));
     const int32_t *work = nullptr;
+    int64_t work_base = 0;
     int64_t nwork = n37;
     int which = 0;
+    bool level1 = false;
     {
-        SPG_TRY(p->alloc_n(&s.loc_col, n37));
-        SPG_TRY(p->alloc_n(&s.loc_val, n37));
-        SPG_TRY(p->alloc_n(&s.loc_cap, n37));
-        SPG_TRY(p->alloc_n(&s.len, n37));
-        SPG_TRY(p->alloc_n(&s.ck_entry, n37));
-        SPG_TRY(p->alloc_n(&s.ck_off, n37));
-        SPG_TRY(p->alloc_n(&s.done, n37));
-        SPG_TRY(p->alloc_n(&list[0], n37));
-        SPG_TRY(p->alloc_n(&list[1], n37));
+        SPG_TRY(reserve_items(p, n37));
+        p->n_items = n37;
         SPG_TRY(p->alloc_n(&ovf_count, 1));
-        k_merge_init<<<(unsigned)((n37 + 255) / 256), 256, 0, p->st>>>(rows37, n37, p->ctil_rp, p->ctil_col,
-                                                                        p->ctil_val, s);
-        SPG_TRY(cudaGetLastError());
+        list_cap = n37;
+        SPG_TRY(p->alloc_n(&list[0], list_cap));
+        SPG_TRY(p->alloc_n(&list[1], list_cap));
+        SPG_TRY(launch_merge_init(rows37, n37, p->ctil_rp, p->ctil_col, p->ctil_val, p->items, p->st));
         p->count(SPGEMM_K_OTHER);
-        bool level1 = false;
         while (nwork > 0) {
+            if (nwork > list_cap) {  // more work items than the overflow lists can hold
+                list_cap = nwork;
+                SPG_TRY(p->alloc_n(&list[which], list_cap));
+                SPG_TRY(p->alloc_n(&list[which ^ 1], list_cap));
+            }
             MergeLaunch L{};
-            L.rows37 = rows37;
             L.work = work;
+            L.work_base = work_base;
             L.nwork = nwork;
             L.cap = cap;
-            L.batch = std::min(batch, cap);
+            L.batch = std::min(std::min(batch, cap), merge_batch_limit(cap));
             L.level1 = level1 ? 1 : 0;
             L.ovf_list = list[which];
             L.ovf_count = ovf_count;
             L.err = p->d_err;
             if (!level1 && p->opts.alloc_policy != SPGEMM_ALLOC_UPPER_BOUND &&
-                (work != nullptr || cap > p->opts.initial_cap)) {
+                (work != nullptr || work_base > 0 || cap > p->opts.initial_cap)) {
+                SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap));
+                SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap));
+                L.pool_cap = cap;
+                p->bytes_ctilde += nwork * (int64_t)cap * 12;
+            } else if (!level1 && (work_base > 0)) {
+                // split children have no home yet
                 SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap));
                 SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap));
                 L.pool_cap = cap;
@@ -437,7 +471,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 SPG_TRY(p->alloc_n(&g_off, nwork));
                 SPG_TRY(p->alloc_n(&g_partial, nwork / 2048 + 2));
                 SPG_TRY(p->alloc_n(&g_total, 1));
-                SPG_TRY(launch_level1_sizes(rows37, work, nwork, p->u, p->B.ncols, g_cap, g_off, g_partial,
+                SPG_TRY(launch_level1_sizes(p->items, work, nwork, p->u, p->B.ncols, g_cap, g_off, g_partial,
                                             g_total, p->st));
                 p->count(SPGEMM_K_OTHER, 4);
                 int64_t gtot = 0;
@@ -451,7 +485,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
             }
             SPG_TRY(cudaMemsetAsync(ovf_count, 0, sizeof(int32_t), p->st));
             p->time_begin(SPGEMM_K_MERGE);
-            SPG_TRY(launch_merge(a, s, L, p->u, p->st));
+            SPG_TRY(launch_merge(a, p->items, L, p->st));
             p->time_end();
             p->count(SPGEMM_K_MERGE);
             p->stats.merge_rounds += 1;
@@ -461,13 +495,36 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 status = SPGEMM_ERR_INTERNAL;
                 goto fail;
             }
-            if (work == nullptr) p->stats.rows_relaunched = novf;
-            work = list[which];
-            which ^= 1;
-            nwork = novf;
-            if (cap >= capmax) level1 = true;
-            else cap = std::min(capmax, cap * 2);
+            if (work == nullptr && work_base == 0) p->stats.rows_relaunched = novf;
+            if (novf == 0) break;
+            if (cap < capmax) {
+                cap = std::min(capmax, cap * 2);
+                work = list[which];
+                work_base = 0;
+                nwork = novf;
+                which ^= 1;
+            } else if (use_level1) {
+                level1 = true;
+                work = list[which];
+                work_base = 0;
+                nwork = novf;
+                which ^= 1;
+            } else {
+                // split every overflowed item at the median column of its sequence
+                SPG_TRY(reserve_items(p, p->n_items + 2 * (int64_t)novf));
+                p->time_begin(SPGEMM_K_OTHER);
+                SPG_TRY(launch_split(list[which], novf, p->n_items, p->items, p->st));
+                p->time_end();
+                p->count(SPGEMM_K_OTHER);
+                p->stats.rows_split += novf;
+                work = nullptr;
+                work_base = p->n_items;
+                nwork = 2 * (int64_t)novf;
+                p->n_items += nwork;
+            }
         }
+        SPG_TRY(launch_finalize37(n37, p->items, p->nnzc, p->d_err, p->st));
+        p->count(SPGEMM_K_OTHER);
         int64_t err = 0;
         SPG_TRY(p->d2h(&err, p->d_err, sizeof(int64_t)));
         if (err != 0) status = SPGEMM_ERR_INTERNAL;
@@ -530,8 +587,7 @@ extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
                                          p->C.val, p->st));
             if (s1 > s0) p->count(SPGEMM_K_ARRANGE);
             const int64_t n37 = p->h_summary.bin_count[BIN_MERGE];
-            SPG_TRY(launch_arrange_long(p->ms, p->bin_rows + p->bin_start[BIN_MERGE], n37, p->C.row_ptr,
-                                        p->C.col_idx, p->C.val, p->st));
+            SPG_TRY(launch_arrange_long(p->items, n37, p->C.row_ptr, p->C.col_idx, p->C.val, p->st));
             if (n37 > 0) p->count(SPGEMM_K_ARRANGE);
         }
         p->time_end();

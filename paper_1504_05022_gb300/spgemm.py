@@ -114,7 +114,8 @@ def _wrap_u8(ptr: int, n: int, owner: _PlanHandle, device: int) -> torch.Tensor:
 
 def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs: bool = False,
               record_timing: bool = False, merge_batch: int = 0, smem_cap_max: int = 0,
-              heap_block: int = 0, predictor=None, predictor_margin: float = 1.0) -> _lib.Opts:
+              heap_block: int = 0, long_rows: str = "split", predictor=None,
+              predictor_margin: float = 1.0) -> _lib.Opts:
     L = _lib.load()
     o = _lib.Opts()
     _lib.check(L.spgemm_opts_init(ctypes.byref(o)), "spgemm_opts_init")
@@ -125,6 +126,7 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
     o.merge_batch = int(merge_batch)
     o.smem_cap_max = int(smem_cap_max)
     o.heap_block = int(heap_block)
+    o.long_rows = _lib.LONG_ROWS[long_rows]
     o.predictor = predictor
     o.predictor_margin = float(predictor_margin)
     return o
@@ -171,6 +173,7 @@ class Plan:
         return {
             "bin_count": list(s.bin_count), "sum_u": s.sum_u, "nnz_ctilde": s.nnz_ctilde, "nnz_c": s.nnz_c,
             "merge_rounds": s.merge_rounds, "rows_relaunched": s.rows_relaunched, "rows_level1": s.rows_level1,
+            "rows_split": s.rows_split,
             "rows_fallback": s.rows_fallback, "bytes_ctilde": s.bytes_ctilde, "peak_bytes": s.peak_bytes,
             "launches": dict(zip(_lib.KERNELS, list(s.launches))),
             "kernel_ms": dict(zip(_lib.KERNELS, [float(x) for x in s.kernel_ms])),

@@ -65,7 +65,8 @@ def test_struct_layout_matches_header():
     assert ctypes.sizeof(_lib.CsrIn) == 56
     assert ctypes.sizeof(_lib.CsrOut) == 48
     assert _lib.Opts.predictor.offset == 64 and ctypes.sizeof(_lib.Opts) == 80
-    assert _lib.Stats.launches.offset == 38 * 8 + 9 * 8
+    assert _lib.Stats.launches.offset == 38 * 8 + 10 * 8
+    assert _lib.Opts.long_rows.offset == 7 * 4
 
 
 def test_argument_errors_without_gpu(lib):

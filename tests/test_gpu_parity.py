@@ -87,18 +87,23 @@ def test_stage1_stage2_bit_exact(spg, oracle_mod, name, mk):
         assert np.array_equal(arr["row_nnz"].astype(np.int64), np.diff(ref.row_ptr))
 
 
+@pytest.mark.parametrize("long_rows", ["split", "level1"])
 @pytest.mark.parametrize("initial_cap,smem_cap_max,batch", [
     (32, 256, 32), (64, 512, 64), (256, 1024, 256), (256, 0, 2048), (128, 2048, 512)])
-def test_progressive_and_level1_paths(spg, oracle_mod, initial_cap, smem_cap_max, batch):
+def test_progressive_split_and_level1_paths(spg, oracle_mod, initial_cap, smem_cap_max, batch, long_rows):
     """Small capacities force every long row through several relaunches and, past
-    smem_cap_max, through the level-1 sequence."""
+    smem_cap_max, through column splitting or the level-1 sequence."""
     A = gen.rmat(12, 16, seed=7)
-    plan, C = run(spg, A, A, initial_cap=initial_cap, smem_cap_max=smem_cap_max, merge_batch=batch)
-    check(oracle_mod, A, A, C, label=f"cap{initial_cap}/{smem_cap_max}/{batch}")
+    plan, C = run(spg, A, A, initial_cap=initial_cap, smem_cap_max=smem_cap_max, merge_batch=batch,
+                  long_rows=long_rows)
+    check(oracle_mod, A, A, C, label=f"cap{initial_cap}/{smem_cap_max}/{batch}/{long_rows}")
     st = plan.stats()
     assert st["merge_rounds"] >= 2 and st["rows_relaunched"] > 0
     if smem_cap_max and smem_cap_max <= 1024:
-        assert st["rows_level1"] > 0
+        if long_rows == "split":
+            assert st["rows_split"] > 0 and st["rows_level1"] == 0
+        else:
+            assert st["rows_level1"] > 0 and st["rows_split"] == 0
 
 
 def _rows_with_u(targets, ncols_b, seed, dup=False):
@@ -130,6 +135,13 @@ def _rows_with_u(targets, ncols_b, seed, dup=False):
     A = gen.from_coo(len(targets), nb, np.array(ar, dtype=np.int64), np.array(ac, dtype=np.int64), None)
     A.val = rng.uniform(-1, 1, A.nnz)
     return A, B
+
+
+def test_config2_level1_mode(spg, oracle_mod):
+    A = gen.rmat(16, 16, seed=1)
+    plan, C = run(spg, A, A, rowptr_dtype=torch.int32, long_rows="level1")
+    check(oracle_mod, A, A, C, label="cfg2-level1")
+    assert plan.stats()["rows_level1"] > 0
 
 
 @pytest.mark.parametrize("dup", [False, True])
@@ -169,13 +181,13 @@ def test_integer_values_bit_exact(spg, oracle_mod):
 
 
 def test_cancellation_keeps_structural_zeros(spg, oracle_mod):
-    # row 0 of A*B: 1*2 + 1*(-2) = 0 at column 0 stays a structural entry
+    # A = [[1, 1], [0, 3]], B = [[2, 0], [-2, 1]]: c_00 = 1*2 + 1*(-2) = 0 stays a structural entry
     A = gen.from_coo(2, 2, np.array([0, 0, 1]), np.array([0, 1, 1]), np.array([1.0, 1.0, 3.0]))
     B = gen.from_coo(2, 2, np.array([0, 1, 1]), np.array([0, 0, 1]), np.array([2.0, -2.0, 1.0]))
     _, C = run(spg, A, B)
     rp, col, val = C.to_host()
-    assert rp.tolist() == [0, 1, 3] and col.tolist() == [0, 0, 1]
-    assert val.tolist() == [0.0, -6.0, 3.0]
+    assert rp.tolist() == [0, 2, 4] and col.tolist() == [0, 1, 0, 1]
+    assert val.tolist() == [0.0, 1.0, -6.0, 3.0]
 
 
 def test_check_inputs_rejects_malformed(spg):
@@ -216,7 +228,7 @@ def test_config2_rmat16_full(spg, oracle_mod):
     plan, C = run(spg, A, A, rowptr_dtype=torch.int32, record_timing=True)
     check(oracle_mod, A, A, C, label="cfg2")
     st = plan.stats()
-    assert st["merge_rounds"] >= 3 and st["rows_level1"] > 0
+    assert st["merge_rounds"] >= 3 and st["rows_split"] > 0
     assert all(st["bin_count"][b] > 0 for b in (0, 1, 2, 33, 34, 35, 36, 37))
 
 
