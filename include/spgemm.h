@@ -206,6 +206,38 @@ typedef struct spgemm_plan_arrays {
 
 spgemm_status spgemm_plan_arrays_get(spgemm_plan *plan, spgemm_plan_arrays *out);
 
+/*
+ * Allocation-free row-pointer scan (no counterpart in the paper).
+ *
+ * Computes row_ptr[0..m] from row sizes: row_ptr[i] = row_nnz[0] + ... +
+ * row_nnz[i-1] (int64), row_ptr[m] = the total -- the prefix sum that stage 4
+ * uses to lay out C -- without allocating any device memory.  It is meant for
+ * callers that cannot call cudaMalloc: code whose device memory is owned by an
+ * arena that forbids other allocations, code that must not risk the implicit
+ * device synchronisation an allocation can cause, or code that has a fixed
+ * memory budget decided up front.
+ *
+ * row_nnz: device array of m int32 sizes (each >= 0); row_ptr: device array of
+ * m+1 int64 outputs.  Both are owned by the caller.  The work is enqueued on
+ * `stream`; the call returns without waiting for it.
+ *
+ * The scan keeps its per-tile partial sums in one fixed device array that the
+ * library holds on every GPU that loads it until the process exits (32769
+ * int64 = 256 KiB), which limits m to spgemm_rowptr_scan_noalloc_max_rows()
+ * (67,108,864); a larger m returns SPGEMM_ERR_SHAPE without launching anything.
+ * NULL pointers or m < 0 return SPGEMM_ERR_INVALID_ARG.  The first call on a
+ * device looks up that array's device address (once per device, with that
+ * device current), so make the first call on each device before any stream
+ * capture.  All calls on a device share the one array: calls whose work could
+ * overlap on the GPU (different streams, or concurrent host threads) race and
+ * must be serialised by the caller.  Nothing needs clearing between calls.
+ */
+spgemm_status spgemm_rowptr_scan_noalloc(const int32_t *row_nnz, int64_t m, int64_t *row_ptr,
+                                         spgemm_stream_t stream);
+
+/* Largest m accepted by spgemm_rowptr_scan_noalloc. */
+int64_t spgemm_rowptr_scan_noalloc_max_rows(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,8 @@ SIGNATURES = {
     "spgemm_status_string": ([c_i32], ctypes.c_char_p),
     "spgemm_plan_stats": ([c_ptr, ctypes.POINTER(Stats)], c_i32),
     "spgemm_plan_arrays_get": ([c_ptr, ctypes.POINTER(PlanArrays)], c_i32),
+    "spgemm_rowptr_scan_noalloc": ([c_ptr, c_i64, c_ptr, c_ptr], c_i32),
+    "spgemm_rowptr_scan_noalloc_max_rows": ([], c_i64),
 }
 
 _lib = None
