@@ -238,6 +238,60 @@ spgemm_status spgemm_rowptr_scan_noalloc(const int32_t *row_nnz, int64_t m, int6
 /* Largest m accepted by spgemm_rowptr_scan_noalloc. */
 int64_t spgemm_rowptr_scan_noalloc_max_rows(void);
 
+/*
+ * Learned preallocation (not in the paper; it replaces the fixed 256-entry start
+ * of bin 37's progressive allocation, Section 4.1, by a predicted size).
+ *
+ * A small MLP maps 8 features of a row of C to SPGEMM_MLP_CLASSES size-class
+ * logits (class of nnz(c_i): 0 for nnz <= 1, else ceil(log2 nnz), at most 15)
+ * and a regression of log2(1 + nnz(c_i)).  Parameter vector (float32):
+ *   W1[32x8] b1[32] W2[32x32] b2[32] W3[17x32] b3[17]   (SPGEMM_MLP_NUM_PARAMS)
+ *   mu[8] sigma[8]                                      (input standardisation)
+ * out = W3 relu(W2 relu(W1 (x - mu)/sigma + b1) + b2) + b3.
+ * Features (float32, row-major [m][8]): log2(1+x) of nnz(a_i*), of u_i, the
+ * min, max, mean and standard deviation of log2(1 + nnz(b_k*)) over the stored
+ * a_ik, log2(1 + column span of the selected non-empty B rows), log2(1 + ncols(B)).
+ * With SPGEMM_ALLOC_LEARNED, a bin-37 row gets a temporary row of
+ * max(256, 32*ceil(margin * (2^reg - 1) / 32)) entries (at most u_i) and starts in
+ * the shared-memory class that fits it; a row whose result outgrows that size
+ * continues on the exact progressive path, so C does not depend on the prediction.
+ */
+#define SPGEMM_MLP_FEATURES 8
+#define SPGEMM_MLP_HIDDEN 32
+#define SPGEMM_MLP_CLASSES 16
+#define SPGEMM_MLP_NUM_PARAMS 1905
+#define SPGEMM_MLP_NUM_TOTAL 1921
+
+typedef struct spgemm_predictor spgemm_predictor;
+
+/* Copies SPGEMM_MLP_NUM_TOTAL host floats (n must equal it) to the current device. */
+spgemm_status spgemm_predictor_create(const float *host_params, int64_t n, spgemm_predictor **out);
+spgemm_status spgemm_predictor_free(spgemm_predictor *pred);
+
+/* X[m][8] (device, float32) = the features of every row of C = A*B; enqueued on stream. */
+spgemm_status spgemm_row_features(const spgemm_csr_in *A, const spgemm_csr_in *B, float *X,
+                                  spgemm_stream_t stream);
+
+/* out[n][17] (device) = MLP outputs for X[n][8] with device parameters `params`. */
+spgemm_status spgemm_mlp_forward(const float *params, const float *X, int64_t n, float *out,
+                                 spgemm_stream_t stream);
+
+/* Floats of device workspace spgemm_mlp_loss_grad needs for n samples. */
+int64_t spgemm_mlp_work_floats(int64_t n);
+
+/* Summed loss over n samples, loss = CE(softmax(out[0..15]), cls) + 0.5 (out[16] - y)^2,
+   into *loss (device double), and its gradient w.r.t. the SPGEMM_MLP_NUM_PARAMS
+   trainable values into grad (device float, overwritten).  work: device floats of
+   spgemm_mlp_work_floats(n). */
+spgemm_status spgemm_mlp_loss_grad(const float *params, const float *X, const int32_t *cls,
+                                   const float *y, int64_t n, float *work, float *grad, double *loss,
+                                   spgemm_stream_t stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the trainable values with
+   gradient grad * grad_scale; m and v are device moment buffers; step >= 1. */
+spgemm_status spgemm_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t step,
+                              float lr, float grad_scale, spgemm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libspgemm.so")
 
-SOURCES = ["stage12.cu", "heap.cu", "esc.cu", "merge.cu", "arrange.cu", "spgemm_api.cu", "noalloc.cu"]
+SOURCES = ["stage12.cu", "heap.cu", "esc.cu", "merge.cu", "arrange.cu", "predictor.cu", "spgemm_api.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,7 +42,7 @@ def _digest() -> str:
             h.update(name.encode() + f.read())
     with open(os.path.join(INCLUDE, "spgemm.h"), "rb") as f:
         h.update(f.read())
-    h.update(" ".join(_flags()).encode())
+    h.update(" ".join(_flags() + SOURCES).encode())
     return h.hexdigest()
 
 
@@ -70,7 +71,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

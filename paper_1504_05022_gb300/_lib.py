@@ -62,7 +62,16 @@ SIGNATURES = {
     "spgemm_plan_arrays_get": ([c_ptr, ctypes.POINTER(PlanArrays)], c_i32),
     "spgemm_rowptr_scan_noalloc": ([c_ptr, c_i64, c_ptr, c_ptr], c_i32),
     "spgemm_rowptr_scan_noalloc_max_rows": ([], c_i64),
+    "spgemm_predictor_create": ([c_ptr, c_i64, ctypes.POINTER(c_ptr)], c_i32),
+    "spgemm_predictor_free": ([c_ptr], c_i32),
+    "spgemm_row_features": ([ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_ptr, c_ptr], c_i32),
+    "spgemm_mlp_forward": ([c_ptr, c_ptr, c_i64, c_ptr, c_ptr], c_i32),
+    "spgemm_mlp_work_floats": ([c_i64], c_i64),
+    "spgemm_mlp_loss_grad": ([c_ptr, c_ptr, c_ptr, c_ptr, c_i64, c_ptr, c_ptr, c_ptr, c_ptr], c_i32),
+    "spgemm_mlp_adam": ([c_ptr, c_ptr, c_ptr, c_ptr, c_i64, ctypes.c_float, ctypes.c_float, c_ptr], c_i32),
 }
+
+MLP_FEATURES, MLP_HIDDEN, MLP_CLASSES, MLP_NUM_PARAMS, MLP_NUM_TOTAL = 8, 32, 16, 1905, 1921
 
 _lib = None
 

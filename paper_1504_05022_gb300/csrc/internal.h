@@ -23,12 +23,15 @@ struct DevCSR {
 };
 
 // Host-visible summary written by stage 2 (copied back in one transfer).
+constexpr int NUM_LAUNCH_CLASSES = 8;  // learned: shared-memory classes of bin-37 rows
+
 struct BinSummary {
     int64_t bin_count[NUM_BINS];
     int64_t sum_cap;   // nnz(C~) of the initial allocation
     int64_t sum_u;     // sum u_i
     int64_t status;    // validation result (0 = ok)
     int64_t pad;
+    int64_t class_count[NUM_LAUNCH_CLASSES];  // learned: bin-37 rows per launch class
 };
 
 struct CapPolicy {
@@ -50,6 +53,18 @@ cudaError_t launch_binning(int64_t m, const int64_t *arp, const int64_t *S,
                            const int64_t *sum_u_ptr, CapPolicy P, int64_t *u, uint8_t *bin, int32_t *nnzc, int32_t *bin_rows,
                            int64_t *ctil_rp, int32_t *hist, int64_t *cap_partial,
                            BinSummary *summary, cudaStream_t st);
+
+// ---- learned preallocation (predictor.cu) ----
+cudaError_t launch_row_features(const DevCSR &A, const DevCSR &B, float *X, cudaStream_t st);
+cudaError_t launch_predict_caps(const float *params, const float *X, int64_t m, const int64_t *u, float margin,
+                                int32_t min_cap, int32_t *pred_cap, cudaStream_t st);
+// Groups the bin-37 items (tail of bin_rows, size read from summary) by launch
+// class; scratch: 96 + m int32; order: item indices grouped by class; counts go
+// to summary->class_count.
+cudaError_t launch_class_partition_tail(const int32_t *bin_rows, int64_t m, BinSummary *summary,
+                                        const int32_t *pred_cap, const int32_t *class_cap, int ncls,
+                                        int32_t *scratch, int32_t *order, cudaStream_t st);
+const float *predictor_params(const void *pred);
 
 // ---- stage 3 ----
 struct StageArgs {

@@ -210,10 +210,9 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
     __shared__ int32_t scan32[NT / 32 + 1];
     constexpr int W = NT;
     MergeSmem s;
-    const int cap = L.cap;
     const int kb = L.batch;
-    const int tn = merge_tn(cap);
-    merge_layout(cap, kb, W, merge_smem, &s);
+    const int tn = merge_tn(L.cap);
+    merge_layout(L.cap, kb, W, merge_smem, &s);
 
     const int64_t w = blockIdx.x;
     const int j = L.work ? L.work[w] : (int)(L.work_base + w);
@@ -234,14 +233,20 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
             s.Rv[t] = sv[t];
         }
     }
-    // where this launch writes the item: its home if large enough, else a fresh slot
+    // where this launch writes the item: its home if large enough, else a fresh
+    // slot; without a pool the item's capacity is that of its home
     int32_t *dst_col = it.home_col[j];
     double *dst_val = it.home_val[j];
     int64_t dst_cap = it.home_cap[j];
-    if (!L.level1 && dst_cap < cap && L.pool_col != nullptr) {
-        dst_col = L.pool_col + w * L.pool_cap;
-        dst_val = L.pool_val + w * L.pool_cap;
-        dst_cap = L.pool_cap;
+    int cap = L.cap;
+    if (!L.level1 && dst_cap < cap) {
+        if (L.pool_col != nullptr) {
+            dst_col = L.pool_col + w * L.pool_cap;
+            dst_val = L.pool_val + w * L.pool_cap;
+            dst_cap = L.pool_cap;
+        } else {
+            cap = (int)dst_cap;
+        }
     }
     // level-1 global sequence: ping-pong between g0 and g1
     int32_t *g0k = nullptr, *g1k = nullptr;

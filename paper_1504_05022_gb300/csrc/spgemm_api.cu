@@ -113,6 +113,11 @@ struct spgemm_plan {
     // bin 37 work items
     MergeItems items{};
     int64_t n_items = 0, items_cap = 0;
+    // learned preallocation
+    int32_t *pred_cap = nullptr;      // predicted temporary size per row
+    int32_t *class_order = nullptr;   // bin-37 item indices grouped by launch class
+    int32_t class_caps[NUM_LAUNCH_CLASSES] = {0};
+    int capmax = 0, batch = 0;
     // result
     bool numeric_done = false;
     spgemm_csr_out C{};
@@ -169,6 +174,22 @@ struct spgemm_plan {
         pinned = nullptr;
     }
 };
+
+// Largest shared-memory result capacity of the merge kernel for the plan's batch size.
+static void merge_limits(spgemm_plan *p) {
+    // leave room for the kernel's static shared memory
+    const int smem_limit = (p->smem_optin > 0 ? p->smem_optin : 227 * 1024) - 1024;
+    int batch = p->opts.merge_batch > 0 ? p->opts.merge_batch : 2048;
+    batch = std::max(32, std::min(batch, 2048));
+    int capmax = merge_max_cap(batch, smem_limit);
+    if (p->opts.smem_cap_max > 0) capmax = std::min(capmax, std::max(256, p->opts.smem_cap_max));
+    p->batch = batch;
+    p->capmax = capmax;
+    // learned launch classes: 256, 512, ..., 8192, the largest capacity, and "beyond it"
+    for (int g = 0; g < NUM_LAUNCH_CLASSES - 1; ++g) p->class_caps[g] = std::min(256 << g, capmax);
+    p->class_caps[NUM_LAUNCH_CLASSES - 2] = capmax;
+    p->class_caps[NUM_LAUNCH_CLASSES - 1] = INT32_MAX;
+}
 
 extern "C" {
 
@@ -318,6 +339,20 @@ extern "C" spgemm_status spgemm_symbolic(const spgemm_csr_in *A_in, const spgemm
         SPG_TRY(launch_bound(p->A, p->B, p->S, p->scan_partial, p->st));
         p->time_end();
         p->count(SPGEMM_K_BOUND, 3);
+        merge_limits(p);
+        if (o.alloc_policy == SPGEMM_ALLOC_LEARNED) {
+            // features and predicted temporary sizes of every row (used for bin 37)
+            float *X = nullptr;
+            SPG_TRY(p->alloc_n(&X, m * SPGEMM_MLP_FEATURES));
+            SPG_TRY(p->alloc_n(&p->pred_cap, m));
+            p->time_begin(SPGEMM_K_OTHER);
+            SPG_TRY(launch_row_features(p->A, p->B, X, p->st));
+            SPG_TRY(launch_predict_caps(predictor_params(o.predictor), X, m, nullptr,
+                                        (float)(o.predictor_margin > 0 ? o.predictor_margin : 1.0),
+                                        o.initial_cap, p->pred_cap, p->st));
+            p->time_end();
+            p->count(SPGEMM_K_OTHER, 2);
+        }
         // ---- stage 2: binning ----
         nblk = bin_blocks(m);
         SPG_TRY(p->alloc_n(&p->u, m));
@@ -332,12 +367,23 @@ extern "C" spgemm_status spgemm_symbolic(const spgemm_csr_in *A_in, const spgemm
             SPG_TRY(p->alloc_n(&capp, nblk));
             pol.policy = o.alloc_policy;
             pol.initial_cap = o.initial_cap;
-            pol.pred_cap = nullptr;
+            pol.pred_cap = p->pred_cap;
             p->time_begin(SPGEMM_K_BIN);
             SPG_TRY(launch_binning(m, p->A.rp, p->S, p->S + nnzA, pol, p->u, p->bin, p->nnzc, p->bin_rows,
                                    p->ctil_rp, hist, capp, p->d_summary, p->st));
             p->time_end();
             p->count(SPGEMM_K_BIN, nblk > 0 ? 3 : 1);
+        }
+        if (o.alloc_policy == SPGEMM_ALLOC_LEARNED) {
+            // group the bin-37 rows by the shared-memory class their predicted size needs
+            int32_t *ccap = nullptr, *scratch = nullptr;
+            SPG_TRY(p->alloc_n(&ccap, NUM_LAUNCH_CLASSES));
+            SPG_TRY(cudaMemcpyAsync(ccap, p->class_caps, sizeof(p->class_caps), cudaMemcpyHostToDevice, p->st));
+            SPG_TRY(p->alloc_n(&scratch, 96 + m));
+            SPG_TRY(p->alloc_n(&p->class_order, m));
+            SPG_TRY(launch_class_partition_tail(p->bin_rows, m, p->d_summary, p->pred_cap, ccap,
+                                                NUM_LAUNCH_CLASSES, scratch, p->class_order, p->st));
+            p->count(SPGEMM_K_OTHER, 3);
         }
         SPG_TRY(p->d2h(&p->h_summary, p->d_summary, sizeof(BinSummary)));
         p->bin_start[0] = 0;
@@ -413,13 +459,10 @@ spgemm_status run_bin37(spgemm_plan *p) {
     int64_t list_cap = 0;
     int32_t *ovf_count = nullptr;
     int64_t *g_cap = nullptr, *g_off = nullptr, *g_partial = nullptr, *g_total = nullptr;
-    // leave room for the kernel's static shared memory
-    const int smem_limit = (p->smem_optin > 0 ? p->smem_optin : 227 * 1024) - 1024;
-    int batch = p->opts.merge_batch > 0 ? p->opts.merge_batch : 2048;
-    batch = std::max(32, std::min(batch, 2048));
-    int capmax = merge_max_cap(batch, smem_limit);
-    if (p->opts.smem_cap_max > 0) capmax = std::min(capmax, std::max(256, p->opts.smem_cap_max));
+    const int batch = p->batch;
+    const int capmax = p->capmax;
     const bool use_level1 = p->opts.long_rows == SPGEMM_LONG_ROWS_LEVEL1;
+    const bool learned = p->opts.alloc_policy == SPGEMM_ALLOC_LEARNED;
     int cap;
     if (p->opts.alloc_policy == SPGEMM_ALLOC_UPPER_BOUND) cap = capmax;
     else cap = std::min(capmax, std::max(32, (int)p->opts.initial_cap));
@@ -437,6 +480,40 @@ spgemm_status run_bin37(spgemm_plan *p) {
         SPG_TRY(p->alloc_n(&list[1], list_cap));
         SPG_TRY(launch_merge_init(rows37, n37, p->ctil_rp, p->ctil_col, p->ctil_val, p->items, p->st));
         p->count(SPGEMM_K_OTHER);
+        if (learned) {
+            // one launch per predicted class, each with the shared memory its rows need and
+            // homes of the predicted size; rows that outgrow their home are queued for the
+            // exact fallback below
+            SPG_TRY(cudaMemsetAsync(ovf_count, 0, sizeof(int32_t), p->st));
+            int64_t off = 0;
+            for (int g = 0; g < NUM_LAUNCH_CLASSES; ++g) {
+                const int64_t cnt = p->h_summary.class_count[g];
+                if (cnt == 0) continue;
+                const int ccap = std::min(capmax, p->class_caps[g] == INT32_MAX ? capmax : p->class_caps[g]);
+                MergeLaunch L{};
+                L.work = p->class_order + off;
+                L.nwork = cnt;
+                L.cap = ccap;
+                L.batch = std::min(std::min(batch, ccap), merge_batch_limit(ccap));
+                L.ovf_list = list[which];
+                L.ovf_count = ovf_count;
+                L.err = p->d_err;
+                p->time_begin(SPGEMM_K_MERGE);
+                SPG_TRY(launch_merge(a, p->items, L, p->st));
+                p->time_end();
+                p->count(SPGEMM_K_MERGE);
+                p->stats.merge_rounds += 1;
+                off += cnt;
+            }
+            int32_t novf = 0;
+            SPG_TRY(p->d2h(&novf, ovf_count, sizeof(int32_t)));
+            p->stats.rows_fallback = novf;
+            p->stats.rows_relaunched = novf;
+            cap = capmax;
+            work = list[which];
+            nwork = novf;
+            which ^= 1;
+        }
         while (nwork > 0) {
             if (nwork > list_cap) {  // more work items than the overflow lists can hold
                 list_cap = nwork;
@@ -454,7 +531,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
             L.ovf_count = ovf_count;
             L.err = p->d_err;
             if (!level1 && p->opts.alloc_policy != SPGEMM_ALLOC_UPPER_BOUND &&
-                (work != nullptr || work_base > 0 || cap > p->opts.initial_cap)) {
+                (work != nullptr || work_base > 0 || cap > p->opts.initial_cap || learned)) {
                 SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap));
                 SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap));
                 L.pool_cap = cap;
@@ -495,7 +572,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 status = SPGEMM_ERR_INTERNAL;
                 goto fail;
             }
-            if (work == nullptr && work_base == 0) p->stats.rows_relaunched = novf;
+            if (work == nullptr && work_base == 0 && !learned) p->stats.rows_relaunched = novf;
             if (novf == 0) break;
             if (cap < capmax) {
                 cap = std::min(capmax, cap * 2);

@@ -99,11 +99,11 @@ SPG_DEV int bin_of(int64_t u) {
 }
 
 // Size of row i in C~.  Hybrid (Algorithm 3): u_i for bins 0..36, a fixed
-// initial size (256) for bin 37.  Upper bound: u_i.  Learned: the predicted
-// size, never above u_i.
+// initial size (256) for bin 37.  Upper bound: u_i.  Learned: u_i for bins
+// 0..36, the predicted size (never above u_i) for bin 37.
 SPG_DEV int64_t cap_of(int64_t u, int b, int64_t i, const CapPolicy &P) {
     if (P.policy == POLICY_UPPER_BOUND) return u;
-    if (P.policy == POLICY_LEARNED && P.pred_cap != nullptr && b >= 2) {
+    if (P.policy == POLICY_LEARNED && P.pred_cap != nullptr && b == BIN_MERGE) {
         int64_t c = P.pred_cap[i];
         return c < u ? (c < 1 ? 1 : c) : u;
     }
