@@ -136,27 +136,31 @@ def algorithmic_bytes(A, B, u, rows_sel, row_nnz):
     return int(la.sum()) * 28 + int(u[rows_sel].sum()) * 12 + int(row_nnz[rows_sel].sum()) * 12
 
 
-def run_ours(args, rank, world, device):
+def policy_opts(policy):
+    """Library options of a policy name: 'hybrid' = the paper's plain path (256-entry start,
+    x2 relaunches), 'upper_bound', 'learned' = trained predictor (committed weights)."""
+    if policy == "learned":
+        from paper_1504_05022_gb300.predictor import Predictor
+        pred = Predictor.load()
+        return pred.opts(), pred
+    return {"alloc_policy": policy}, None
+
+
+def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=False):
+    """W warm-up steps, then K timed steps (CUDA events on the launching stream, L2 flushed
+    between steps outside the events).  Returns the per-step figures."""
     import torch
-
-    import paper_1504_05022_gb300 as spg
-
-    spg.load_library()
-    pairs = make_workload(args.workload)
-    dev = torch.device(f"cuda:{device}")
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
+    opts, keep = policy_opts(policy)
+    opts = dict(opts, record_timing=True)
     Ad = [spg.CSR.from_host(A, device=dev, rowptr_dtype=torch.int32) for A, _ in pairs]
     Bd = [spg.CSR.from_host(B, device=dev, rowptr_dtype=torch.int32) if B is not None and B is not A else None
           for A, B in pairs]
-    opts = dict(alloc_policy=args.policy, record_timing=True)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
         prev = None
         plans = []
         for i in range(len(pairs)):
-            A_ = Ad[i] if Ad[i] is not None else prev
+            A_ = Ad[i]
             if pairs[i][1] is None:          # chained: R * (previous result)
                 B_ = prev
             elif pairs[i][1] is pairs[i][0]:  # A*A
@@ -175,26 +179,30 @@ def run_ours(args, rank, world, device):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    times, kms, launches, stats0 = [], {}, 0, None
+    kms, launches = {}, 0
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(device) as clk:
+    clk = ClockSampler(dev.index) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        plans, C = step()
+        ev[k][1].record(stream)
         torch.cuda.synchronize()
-        t_wall = time.perf_counter()
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            plans, C = step()
-            ev[k][1].record(stream)
-            torch.cuda.synchronize()
-            for p in plans:
-                st = p.stats()
-                stats0 = stats0 or st
-                for name, ms in st["kernel_ms"].items():
-                    kms[name] = kms.get(name, 0.0) + ms
-                launches += sum(st["launches"].values())
+        for p in plans:
+            st = p.stats()
+            for name, ms in st["kernel_ms"].items():
+                kms[name] = kms.get(name, 0.0) + ms
+            launches += sum(st["launches"].values())
+        if k < args.steps - 1:
             del plans, C
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if clk:
+        clk.__exit__(None, None, None)
     times = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
     ms_step = float(np.mean(times))
     if world > 1:
@@ -202,16 +210,24 @@ def run_ours(args, rank, world, device):
         t = torch.tensor([ms_step], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-    # products per step (sum over the chained products)
-    plans, C = step()
-    sum_u = sum(p.upper_bound_nnz for p in plans)
     st_all = [p.stats() for p in plans]
     arrays = [p.arrays() for p in plans]
+    sum_u = sum(p.upper_bound_nnz for p in plans)
+    res = {"policy": policy, "ms_per_step": ms_step, "value": 2.0 * sum_u * world / (ms_step * 1e-3) / 1e9,
+           "kms": {k: v / args.steps for k, v in kms.items()}, "launches": launches, "wall_s": t_wall,
+           "st_all": st_all, "arrays": arrays, "sum_u": sum_u, "nnz_C": int(st_all[-1]["nnz_c"]),
+           "peak_bytes": int(sum(s["peak_bytes"] for s in st_all)),
+           "merge_rounds": int(sum(s["merge_rounds"] for s in st_all)),
+           "rows_fallback": int(sum(s["rows_fallback"] for s in st_all)),
+           "rows_bin37": int(sum(s["bin_count"][37] for s in st_all)),
+           "clocks": clk.summary() if clk else None}
+    del plans, C, keep
     torch.cuda.synchronize()
-    flops = 2.0 * sum_u
-    value = flops * world / (ms_step * 1e-3) / 1e9
+    return res
 
-    # ---- roofline of the dominant kernel class ----
+
+def roofline(args, pairs, m):
+    """Roofline of the kernel class with the largest measured time (HBM-bound model)."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -219,29 +235,24 @@ def run_ours(args, rank, world, device):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    kms = m["kms"]
     dom = max(kms, key=lambda k: kms[k]) if kms else "merge"
-    dom_ms = kms.get(dom, 0.0) / args.steps
-    dom_launches = sum(s["launches"].get(dom, 0) for s in st_all)
+    dom_ms = kms.get(dom, 0.0)
+    dom_launches = sum(s["launches"].get(dom, 0) for s in m["st_all"])
     bytes_dom = 0
-    for (A, B), arr in zip(pairs, arrays):
-        if B is None or A is None:
+    for (A, B), arr in zip(pairs, m["arrays"]):
+        if B is None:
             continue
         u = arr["u"]
         rn = arr["row_nnz"].astype(np.int64)
         bins = arr["bin"]
-        if dom == "merge":
-            sel = bins == 37
-        elif dom == "esc":
-            sel = (bins >= 33) & (bins <= 36)
-        elif dom == "heap":
-            sel = (bins >= 2) & (bins <= 32)
-        else:
-            sel = np.ones(u.shape[0], dtype=bool)
         if dom == "arrange":
             bytes_dom += int(rn.sum()) * 24 + 8 * (u.shape[0] + 1)
         elif dom in ("bound", "bin", "scan"):
             bytes_dom += A.nnz * 12 + 16 * u.shape[0]
         else:
+            sel = {"merge": bins == 37, "esc": (bins >= 33) & (bins <= 36), "heap": (bins >= 2) & (bins <= 32)}.get(
+                dom, np.ones(u.shape[0], dtype=bool))
             bytes_dom += algorithmic_bytes(A, B, u, np.nonzero(sel)[0], rn)
     achieved = bytes_dom / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
     traffic = None
@@ -249,37 +260,65 @@ def run_ours(args, rank, world, device):
     if os.path.exists(tj):
         try:
             t = json.load(open(tj))
-            ent = t.get(args.workload, {}).get(dom)
+            ent = t.get(args.workload, {}).get(m["policy"], {}).get(dom)
             if ent and ent.get("source_digest") == src_digest(KERNEL_SOURCES.get(dom, [])):
-                traffic = ent.get("bytes_per_launch")
+                traffic = ent.get("bytes_per_step")
         except Exception:
             traffic = None
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
-                "peak_source": peak_src, "algorithmic_bytes_per_step": bytes_dom,
-                "ms_per_step": dom_ms, "launches_per_step": dom_launches}
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic, "peak_source": peak_src,
+            "algorithmic_bytes_per_step": bytes_dom, "kernel_ms_per_step": dom_ms,
+            "launches_per_step": dom_launches,
+            "note": "achieved = algorithmic bytes of the kernel class per step / its summed CUDA-event time per step"}
 
-    # ---- end to end through the C ABI with host buffers ----
-    e2e = run_e2e(args, spg, pairs, dev, stream, opts)
+
+def run_ours(args, rank, world, device):
+    import torch
+
+    import paper_1504_05022_gb300 as spg
+    from paper_1504_05022_gb300.predictor import WEIGHTS
+
+    spg.load_library()
+    pairs = make_workload(args.workload)
+    dev = torch.device(f"cuda:{device}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    head = args.policy
+    if head == "learned" and not os.path.exists(WEIGHTS):
+        head = "hybrid"
+    others = [p for p in ("hybrid",) if p != head] if not args.single_policy else []
+    main_m = measure(args, spg, pairs, dev, stream, head, flush, world, sample_clocks=True)
+    cmp = {p: measure(args, spg, pairs, dev, stream, p, flush, world) for p in others}
+    e2e_opts, e2e_keep = policy_opts(head)  # keeps the predictor alive during the e2e runs
+    e2e = run_e2e(args, spg, pairs, dev, stream, e2e_opts)
+    del e2e_keep
+
+    def brief(m):
+        return {"value": m["value"], "ms_per_step": m["ms_per_step"], "peak_bytes": m["peak_bytes"],
+                "merge_rounds": m["merge_rounds"], "rows_fallback": m["rows_fallback"],
+                "kernel_ms_per_step": m["kms"]}
 
     out = {
         "metric": "FP64 SpGEMM GFLOP/s (2*products/s)",
-        "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "value": main_m["value"], "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": main_m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded generator)",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
-                   "alloc_policy": args.policy, "products_per_step": sum_u,
-                   "nnz_C": int(st_all[-1]["nnz_c"]), "l2": "flushed between steps (512 MB write)",
-                   "parallelism": f"replicas x{world}"},
-        "roofline": roofline,
+                   "alloc_policy": head, "products_per_step": main_m["sum_u"], "nnz_C": main_m["nnz_C"],
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+        "roofline": roofline(args, pairs, main_m),
         "e2e": e2e,
-        "gpu_launches": int(launches),
-        "wall_s_timed": t_wall,
-        "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
-        "stats": {"merge_rounds": st_all[-1]["merge_rounds"], "rows_relaunched": st_all[-1]["rows_relaunched"],
-                  "rows_level1": st_all[-1]["rows_level1"], "peak_bytes": max(s["peak_bytes"] for s in st_all),
-                  "bytes_ctilde": sum(s["bytes_ctilde"] for s in st_all)},
-        "clocks": clk.summary(),
+        "gpu_launches": int(main_m["launches"]),
+        "wall_s_timed": main_m["wall_s"],
+        "kernel_ms_per_step": main_m["kms"],
+        "memory": {"peak_bytes": main_m["peak_bytes"], "rows_bin37": main_m["rows_bin37"],
+                   "rows_fallback": main_m["rows_fallback"],
+                   "misprediction_rate": (main_m["rows_fallback"] / main_m["rows_bin37"])
+                   if head == "learned" and main_m["rows_bin37"] else None,
+                   "merge_rounds": main_m["merge_rounds"]},
+        "compare": {p: brief(m) for p, m in cmp.items()},
+        "clocks": main_m["clocks"],
     }
     return out
 
@@ -290,6 +329,8 @@ def run_e2e(args, spg, pairs, dev, stream, opts):
     import torch
     if len(pairs) != 1 or pairs[0][1] is not pairs[0][0]:
         return None
+    if pairs[0][0].nnz > 50_000_000:
+        return {"value": None, "unit": "GFLOP/s", "note": "skipped: the result would need > 40 GB of pinned host memory"}
     A = pairs[0][0]
     hp = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
           for x in (A.row_ptr.astype(np.int32), A.col, A.val)]
@@ -302,7 +343,7 @@ def run_e2e(args, spg, pairs, dev, stream, opts):
         t0 = time.perf_counter()
         rp, col, val = (t.to(dev, non_blocking=True) for t in hp)
         Ad = spg.CSR(rp, col, val, (A.nrows, A.ncols))
-        C = spg.Plan(Ad, Ad, stream=stream, alloc_policy=opts["alloc_policy"]).numeric()
+        C = spg.Plan(Ad, Ad, stream=stream, **opts).numeric()
         if out_host is None or out_host[1].numel() != C.nnz:
             out_host = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in (C.row_ptr, C.col, C.val)]
         for h, d in zip(out_host, (C.row_ptr, C.col, C.val)):
@@ -366,7 +407,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat16x16", choices=list(WORKLOADS))
-    ap.add_argument("--policy", default="hybrid", choices=["hybrid", "upper_bound", "learned"])
+    ap.add_argument("--policy", default="learned", choices=["hybrid", "upper_bound", "learned"])
+    ap.add_argument("--single-policy", action="store_true", help="do not also time the plain hybrid path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

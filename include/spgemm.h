@@ -175,7 +175,8 @@ typedef struct spgemm_stats {
     int64_t rows_split;         /* column splits of long rows (SPGEMM_LONG_ROWS_SPLIT) */
     int64_t rows_fallback;      /* rows recomputed because a prediction was too small */
     int64_t bytes_ctilde;       /* device bytes allocated for temporary rows (all rounds) */
-    int64_t peak_bytes;         /* high-water mark of the library's device pool since symbolic */
+    int64_t peak_bytes;         /* device bytes held by the plan: temporaries and C (the plan frees
+                                   nothing before spgemm_free, so this is its high-water mark) */
     int32_t launches[SPGEMM_K_COUNT];  /* kernels launched per class */
     float kernel_ms[SPGEMM_K_COUNT];   /* summed event time per class (record_timing = 1) */
 } spgemm_stats;

@@ -100,6 +100,7 @@ struct spgemm_plan {
     DevCSR A{}, B{};
     std::vector<void *> allocs;
     int64_t bytes_ctilde = 0;
+    int64_t bytes_held = 0;  // device bytes the plan holds (it frees nothing before spgemm_free)
     // stage 1-2 buffers
     int64_t *S = nullptr, *u = nullptr, *ctil_rp = nullptr, *scan_partial = nullptr;
     uint8_t *bin = nullptr;
@@ -135,6 +136,7 @@ struct spgemm_plan {
             return e;
         }
         allocs.push_back(*p);
+        bytes_held += (int64_t)bytes;
         return cudaSuccess;
     }
     template <typename T>
@@ -283,12 +285,6 @@ extern "C" spgemm_status spgemm_symbolic(const spgemm_csr_in *A_in, const spgemm
         if (!p->pinned) {
             status = SPGEMM_ERR_OOM;
             goto fail;
-        }
-        {
-            size_t used = 0;
-            cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemCurrent, &used);
-            uint64_t reset = 0;
-            cudaMemPoolSetAttribute(p->pool, cudaMemPoolAttrUsedMemHigh, &reset);
         }
         // int64 row pointers everywhere on the device
         auto widen = [&](const spgemm_csr_in *M, DevCSR &D) -> cudaError_t {
@@ -699,9 +695,7 @@ extern "C" spgemm_status spgemm_plan_stats(spgemm_plan *p, spgemm_stats *out) {
             if (t.a && t.b && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) p->stats.kernel_ms[t.kind] += ms;
         }
     }
-    size_t hi = 0;
-    if (cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemHigh, &hi) == cudaSuccess)
-        p->stats.peak_bytes = (int64_t)hi;
+    p->stats.peak_bytes = p->bytes_held;
     *out = p->stats;
     return SPGEMM_OK;
 }

@@ -105,12 +105,20 @@ def test_learned_policy_is_exact(spg, oracle_mod, margin):
     n37 = st["bin_count"][37]
     assert n37 > 0
     nnz37 = np.diff(ref.row_ptr)[plan.arrays()["bin"] == 37]
+    fb = st["rows_fallback"]
+
+    def bounds(cap):
+        # a row falls back when its result exceeds its slot, and may fall back up to a quarter
+        # batch earlier (a batch only starts when all its products could be new entries)
+        return int((nnz37 > cap).sum()), int((nnz37 > cap - cap // 4).sum())
     if margin == 0.01:    # every bin-37 row gets the minimum 256 entries
-        assert st["rows_fallback"] == int((nnz37 > 256).sum()) > 0
+        lo, hi = bounds(256)
+        assert lo <= fb <= hi and fb > 0
     if margin == 1.0:     # 512 entries
-        assert st["rows_fallback"] == int((nnz37 > 512).sum())
+        lo, hi = bounds(512)
+        assert lo <= fb <= hi
     if margin == 50.0:    # 25,568 entries (or u_i): nothing outgrows it
-        assert st["rows_fallback"] == 0
+        assert fb == 0
 
 
 def test_trained_weights_if_present(spg, oracle_mod):
