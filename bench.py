@@ -33,6 +33,7 @@ WORKLOADS = {
     "lap2d64": "C = A*A, A = 2D 5-point Laplacian on a 64x64 grid",
     "galerkin64": "Ac = R*(A*P), A = 27-point Laplacian on 64^3, P = 2x2x2 aggregation, R = P^T",
     "rmat20x8": "C = A*A, A = R-MAT 2^20 x 2^20, 8 samples/row, U(-1,1), seed 1",
+    "rmat14x16": "C = A*A, A = R-MAT 2^14 x 2^14, 16 samples/row, U(-1,1), seed 1 (small profiling case)",
 }
 
 
@@ -46,6 +47,9 @@ def make_workload(name):
         return [(A, A)]
     if name == "rmat20x8":
         A = gen.rmat(20, 8, seed=1)
+        return [(A, A)]
+    if name == "rmat14x16":
+        A = gen.rmat(14, 16, seed=1)
         return [(A, A)]
     if name == "galerkin64":
         A = gen.lap3d27(64)

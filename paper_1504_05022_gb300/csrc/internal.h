@@ -38,6 +38,7 @@ struct CapPolicy {
     int policy;
     int64_t initial_cap;
     const int32_t *pred_cap;  // learned per-row temporary row sizes (POLICY_LEARNED), may be null
+    int64_t cap_max;          // learned: a bin-37 row's home never exceeds the largest shared capacity
 };
 
 // ---- stage 0/1/2 (stage12.cu) ----
@@ -126,9 +127,10 @@ int merge_max_cap(int batch, int smem_limit);
 cudaError_t launch_merge(const StageArgs &a, const MergeItems &it, const MergeLaunch &L, cudaStream_t st);
 cudaError_t launch_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
                               double *ctil_val, const MergeItems &it, cudaStream_t st);
-// splits the items listed in ovf (count n) into children first_new + 2i, first_new + 2i + 1
+// splits the items listed in ovf (count n) into children first_new + 2i, first_new + 2i + 1;
+// right child i gets slot i of the pool (n slots of pool_cap entries)
 cudaError_t launch_split(const int32_t *ovf, int64_t n, int64_t first_new, const MergeItems &it,
-                         cudaStream_t st);
+                         int32_t *pool_col, double *pool_val, int64_t pool_cap, cudaStream_t st);
 // nnz(c_i) of every bin-37 row = summed lengths of its leaves
 cudaError_t launch_finalize37(int64_t n37, const MergeItems &it, int32_t *nnzc, int64_t *err, cudaStream_t st);
 // level-1 buffer sizing: per work item cap = min(u_row, ncols_B) (two buffers each)

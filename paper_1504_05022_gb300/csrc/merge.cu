@@ -518,9 +518,12 @@ cudaError_t launch_merge_init(const int32_t *rows37, int64_t n37, const int64_t 
 }
 
 // Splits an overflowed item at the median column of its dumped sequence.  Both
-// children resume from the parent's checkpoint; each reloads its half of the
-// parent's sequence and only takes products inside its column range.
-__global__ void k_split(const int32_t *ovf, int64_t n, int64_t first_new, MergeItems it) {
+// children resume from the parent's checkpoint and only take products inside
+// their column range.  The left child keeps the parent's home, where its half
+// already sits at the start; the right child gets slot i of `pool`, and
+// k_split_copy moves the right half there, so no two items share memory.
+__global__ void k_split(const int32_t *ovf, int64_t n, int64_t first_new, MergeItems it, int32_t *pool_col,
+                        double *pool_val, int64_t pool_cap) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int p = ovf[i];
@@ -533,25 +536,49 @@ __global__ void k_split(const int32_t *ovf, int64_t n, int64_t first_new, MergeI
         it.row[q] = it.row[p];
         it.clo[q] = c == 0 ? it.clo[p] : mkey;
         it.chi[q] = c == 0 ? mkey : it.chi[p];
-        it.src_col[q] = it.src_col[p] + (c == 0 ? 0 : mid);
-        it.src_val[q] = it.src_val[p] + (c == 0 ? 0 : mid);
-        it.src_len[q] = c == 0 ? mid : plen - mid;
-        it.home_col[q] = nullptr;
-        it.home_val[q] = nullptr;
-        it.home_cap[q] = 0;
         it.len[q] = 0;
         it.ck_entry[q] = it.ck_entry[p];
         it.ck_off[q] = it.ck_off[p];
         it.child[q] = -1;
     }
+    it.src_col[l] = it.src_col[p];
+    it.src_val[l] = it.src_val[p];
+    it.src_len[l] = mid;
+    it.home_col[l] = it.home_col[p];
+    it.home_val[l] = it.home_val[p];
+    it.home_cap[l] = it.home_cap[p];
+    it.src_col[r] = pool_col + i * pool_cap;
+    it.src_val[r] = pool_val + i * pool_cap;
+    it.src_len[r] = plen - mid;
+    it.home_col[r] = pool_col + i * pool_cap;
+    it.home_val[r] = pool_val + i * pool_cap;
+    it.home_cap[r] = pool_cap;
     it.child[p] = (int32_t)l;
     it.len[p] = 0;
 }
 
+// One CTA per split: copies the right half of the parent's sequence into the right child's slot.
+__global__ void k_split_copy(const int32_t *ovf, int64_t first_new, MergeItems it) {
+    const int64_t i = blockIdx.x;
+    const int p = ovf[i];
+    const int64_t r = first_new + 2 * i + 1;
+    const int plen = it.src_len[p];
+    const int mid = plen / 2;
+    const int32_t *sc = it.src_col[p] + mid;
+    const double *sv = it.src_val[p] + mid;
+    int32_t *dc = it.home_col[r];
+    double *dv = it.home_val[r];
+    for (int t = threadIdx.x; t < plen - mid; t += blockDim.x) {
+        dc[t] = sc[t];
+        dv[t] = sv[t];
+    }
+}
+
 cudaError_t launch_split(const int32_t *ovf, int64_t n, int64_t first_new, const MergeItems &it,
-                         cudaStream_t st) {
+                         int32_t *pool_col, double *pool_val, int64_t pool_cap, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ovf, n, first_new, it);
+    k_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ovf, n, first_new, it, pool_col, pool_val, pool_cap);
+    k_split_copy<<<(unsigned)n, 256, 0, st>>>(ovf, first_new, it);
     return cudaGetLastError();
 }
 

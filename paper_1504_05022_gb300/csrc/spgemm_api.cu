@@ -364,6 +364,7 @@ extern "C" spgemm_status spgemm_symbolic(const spgemm_csr_in *A_in, const spgemm
             pol.policy = o.alloc_policy;
             pol.initial_cap = o.initial_cap;
             pol.pred_cap = p->pred_cap;
+            pol.cap_max = p->capmax;
             p->time_begin(SPGEMM_K_BIN);
             SPG_TRY(launch_binning(m, p->A.rp, p->S, p->S + nnzA, pol, p->u, p->bin, p->nnzc, p->bin_rows,
                                    p->ctil_rp, hist, capp, p->d_summary, p->st));
@@ -526,14 +527,10 @@ spgemm_status run_bin37(spgemm_plan *p) {
             L.ovf_list = list[which];
             L.ovf_count = ovf_count;
             L.err = p->d_err;
-            if (!level1 && p->opts.alloc_policy != SPGEMM_ALLOC_UPPER_BOUND &&
-                (work != nullptr || work_base > 0 || cap > p->opts.initial_cap || learned)) {
-                SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap));
-                SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap));
-                L.pool_cap = cap;
-                p->bytes_ctilde += nwork * (int64_t)cap * 12;
-            } else if (!level1 && (work_base > 0)) {
-                // split children have no home yet
+            if (!level1 && work_base > 0) {
+                // split round: every child already has a home (set by the split)
+            } else if (!level1 && p->opts.alloc_policy != SPGEMM_ALLOC_UPPER_BOUND &&
+                       (work != nullptr || cap > p->opts.initial_cap || learned)) {
                 SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap));
                 SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap));
                 L.pool_cap = cap;
@@ -585,8 +582,13 @@ spgemm_status run_bin37(spgemm_plan *p) {
             } else {
                 // split every overflowed item at the median column of its sequence
                 SPG_TRY(reserve_items(p, p->n_items + 2 * (int64_t)novf));
+                int32_t *scol = nullptr;
+                double *sval = nullptr;
+                SPG_TRY(p->alloc_n(&scol, (int64_t)novf * cap));
+                SPG_TRY(p->alloc_n(&sval, (int64_t)novf * cap));
+                p->bytes_ctilde += (int64_t)novf * cap * 12;
                 p->time_begin(SPGEMM_K_OTHER);
-                SPG_TRY(launch_split(list[which], novf, p->n_items, p->items, p->st));
+                SPG_TRY(launch_split(list[which], novf, p->n_items, p->items, scol, sval, cap, p->st));
                 p->time_end();
                 p->count(SPGEMM_K_OTHER);
                 p->stats.rows_split += novf;

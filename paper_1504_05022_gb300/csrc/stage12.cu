@@ -105,6 +105,7 @@ SPG_DEV int64_t cap_of(int64_t u, int b, int64_t i, const CapPolicy &P) {
     if (P.policy == POLICY_UPPER_BOUND) return u;
     if (P.policy == POLICY_LEARNED && P.pred_cap != nullptr && b == BIN_MERGE) {
         int64_t c = P.pred_cap[i];
+        if (c > P.cap_max) c = P.cap_max;  // longer rows are split into column slices anyway
         return c < u ? (c < 1 ? 1 : c) : u;
     }
     if (b == BIN_MERGE) return P.initial_cap < u ? P.initial_cap : u;
