@@ -30,7 +30,7 @@ import numpy as np
 
 __all__ = [
     "HostCSR", "from_coo", "transpose", "lap2d", "lap3d27", "agg_P", "rmat",
-    "banded", "blockdiag", "erdos_renyi", "random_sparse", "family_matrix",
+    "banded", "blockdiag", "erdos_renyi", "random_sparse", "family_matrix", "batch_pairs",
 ]
 
 
@@ -250,5 +250,33 @@ def family_matrix(family: str, n: int, param: int, seed: int) -> HostCSR:
         return erdos_renyi(n, param, seed)
     if family == "rmat":
         scale = max(1, int(np.ceil(np.log2(max(n, 2)))))
-        return rmat(scale, param, seed)
+        M = rmat(scale, param, seed)
+        if M.nrows == n:
+            return M
+        # leading n x n block of the 2^scale R-MAT matrix
+        rows = np.repeat(np.arange(M.nrows, dtype=np.int64), np.diff(M.row_ptr))
+        keep = (rows < n) & (M.col < n)
+        S = from_coo(n, n, rows[keep], M.col[keep].astype(np.int64), M.val[keep])
+        return S
     raise ValueError(family)
+
+
+BATCH_FAMILIES = ("banded", "blockdiag", "er", "rmat")
+
+
+def batch_pairs(n_pairs: int = 512, m_lo: int = 256, m_hi: int = 65536, avg_lo: int = 4, avg_hi: int = 32,
+                seed0: int = 0):
+    """Independent square pairs (A_i, B_i): for pair i (seeded with seed0 + i) the size is
+    log-uniform in [m_lo, m_hi], the family is drawn from banded / block-diagonal /
+    Erdos-Renyi / R-MAT, the nonzeros per row from [avg_lo, avg_hi]; A_i and B_i are two
+    seeded matrices of that family and size.  Values U(-1, 1)."""
+    pairs = []
+    for i in range(n_pairs):
+        rng = np.random.default_rng(seed0 + i)
+        m = int(round(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi)))))
+        fam = BATCH_FAMILIES[int(rng.integers(len(BATCH_FAMILIES)))]
+        avg = int(rng.integers(avg_lo, avg_hi + 1))
+        A = family_matrix(fam, m, avg, seed=2 * (seed0 + i))
+        B = family_matrix(fam, m, avg, seed=2 * (seed0 + i) + 1)
+        pairs.append((A, B))
+    return pairs

@@ -208,6 +208,64 @@ typedef struct spgemm_plan_arrays {
 spgemm_status spgemm_plan_arrays_get(spgemm_plan *plan, spgemm_plan_arrays *out);
 
 /*
+ * Batched products (not in the paper): npairs independent C_i = A_i * B_i (host
+ * arrays of npairs descriptors of device matrices) computed as one product of
+ * block-diagonal matrices, diag(A_1..A_n) * diag(B_1..B_n) = diag(A_1 B_1 ..
+ * A_n B_n), so every stage -- including each per-bin kernel of stage 3 -- runs
+ * once for the rows of all pairs.  Requires sum m_i, sum k_i, sum n_i <= 2^31-1.
+ * spgemm_batched_numeric fills C_out[0..npairs) with views owned by the plan:
+ * each C_i has its own int64 row pointers (starting at 0) and columns; values
+ * share the plan's concatenated result.  spgemm_free releases everything.  The
+ * inputs are copied into the plan at symbolic time (their values are read again
+ * by spgemm_numeric_replay).
+ */
+spgemm_status spgemm_batched_symbolic(int64_t npairs, const spgemm_csr_in *A, const spgemm_csr_in *B,
+                                      const spgemm_opts *opts, spgemm_stream_t stream,
+                                      spgemm_plan **plan_out, int64_t *upper_bound_nnz_out);
+spgemm_status spgemm_batched_numeric(spgemm_plan *plan, spgemm_csr_out *C_out);
+
+/*
+ * Values-only replay (not in the paper): after spgemm_numeric (or
+ * spgemm_batched_numeric), recomputes the values of C for new values of A and B
+ * with the SAME structure (row pointers and columns unchanged), into the same C.
+ * The known columns of each long row are preloaded and every product is fused
+ * into them by binary search (sub-step 1 of the merge method, Section 4.1); bins
+ * 2..36 rerun their heap / ESC kernels straight into C.  The first call on a plan
+ * builds its slice table (allocates and synchronises once); later calls neither
+ * allocate nor synchronise, so they can be captured in a CUDA graph.  A product
+ * whose column is missing from C (the structure changed) makes spgemm_plan_check
+ * return SPGEMM_ERR_INTERNAL.  Plans that used the level-1 sequence
+ * (SPGEMM_LONG_ROWS_LEVEL1) are refused with SPGEMM_ERR_INVALID_ARG.
+ */
+spgemm_status spgemm_numeric_replay(spgemm_plan *plan);
+
+/* Reads the plan's device error word (synchronises its stream). */
+spgemm_status spgemm_plan_check(spgemm_plan *plan);
+
+/*
+ * CUDA graph of values-only replays: captures one spgemm_numeric_replay of each of
+ * plans[0..n) in order (all plans must share one non-default stream and have
+ * finished spgemm_numeric); spgemm_graph_launch enqueues the graph on that stream.
+ * Creating the graph runs one replay of each plan first (outside the capture).
+ * The graph stays valid while the plans live.
+ */
+typedef struct spgemm_graph spgemm_graph;
+spgemm_status spgemm_graph_create(spgemm_plan *const *plans, int64_t n, spgemm_graph **out);
+spgemm_status spgemm_graph_launch(spgemm_graph *graph);
+spgemm_status spgemm_graph_free(spgemm_graph *graph);
+
+/*
+ * Galerkin triple product Ac = R * (A * P) as two products (the association the
+ * paper measures as faster for its method, Section 5.2).  *plan_ap owns A*P,
+ * *plan_rap owns Ac (described by *Ac); free both.  Both plans use `stream`, so
+ * spgemm_graph_create on {*plan_ap, *plan_rap} captures the whole chain for new
+ * values of R, A and P with unchanged structure.
+ */
+spgemm_status spgemm_galerkin(const spgemm_csr_in *R, const spgemm_csr_in *A, const spgemm_csr_in *P,
+                              const spgemm_opts *opts, spgemm_stream_t stream, spgemm_plan **plan_ap,
+                              spgemm_plan **plan_rap, spgemm_csr_out *Ac);
+
+/*
  * Allocation-free row-pointer scan (no counterpart in the paper).
  *
  * Computes row_ptr[0..m] from row sizes: row_ptr[i] = row_nnz[0] + ... +

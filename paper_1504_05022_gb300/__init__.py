@@ -4,6 +4,7 @@ The compute path is the CUDA library libspgemm.so (C ABI in include/spgemm.h);
 this package only marshals arguments.  Importing it does not touch the GPU; the
 library is loaded on first use and the call fails loudly if it is missing."""
 from ._lib import SpgemmError, load as load_library, lib_path  # noqa: F401
-from .spgemm import CSR, Plan, make_opts, spgemm  # noqa: F401
+from .spgemm import CSR, BatchPlan, Plan, ReplayGraph, galerkin, make_opts, spgemm, spgemm_batched  # noqa: F401
 
-__all__ = ["CSR", "Plan", "spgemm", "make_opts", "SpgemmError", "load_library", "lib_path"]
+__all__ = ["CSR", "Plan", "BatchPlan", "ReplayGraph", "spgemm", "spgemm_batched", "galerkin", "make_opts",
+           "SpgemmError", "load_library", "lib_path"]

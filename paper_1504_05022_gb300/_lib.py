@@ -62,6 +62,16 @@ SIGNATURES = {
     "spgemm_plan_arrays_get": ([c_ptr, ctypes.POINTER(PlanArrays)], c_i32),
     "spgemm_rowptr_scan_noalloc": ([c_ptr, c_i64, c_ptr, c_ptr], c_i32),
     "spgemm_rowptr_scan_noalloc_max_rows": ([], c_i64),
+    "spgemm_batched_symbolic": ([c_i64, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(Opts), c_ptr,
+                                 ctypes.POINTER(c_ptr), ctypes.POINTER(c_i64)], c_i32),
+    "spgemm_batched_numeric": ([c_ptr, ctypes.POINTER(CsrOut)], c_i32),
+    "spgemm_numeric_replay": ([c_ptr], c_i32),
+    "spgemm_plan_check": ([c_ptr], c_i32),
+    "spgemm_graph_create": ([ctypes.POINTER(c_ptr), c_i64, ctypes.POINTER(c_ptr)], c_i32),
+    "spgemm_graph_launch": ([c_ptr], c_i32),
+    "spgemm_graph_free": ([c_ptr], c_i32),
+    "spgemm_galerkin": ([ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(Opts),
+                         c_ptr, ctypes.POINTER(c_ptr), ctypes.POINTER(c_ptr), ctypes.POINTER(CsrOut)], c_i32),
     "spgemm_predictor_create": ([c_ptr, c_i64, ctypes.POINTER(c_ptr)], c_i32),
     "spgemm_predictor_free": ([c_ptr], c_i32),
     "spgemm_row_features": ([ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_ptr, c_ptr], c_i32),

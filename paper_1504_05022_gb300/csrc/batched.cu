@@ -1,0 +1,132 @@
+// Batched products: many independent C_i = A_i * B_i computed as one product of
+// block-diagonal matrices, diag(A_1..A_n) * diag(B_1..B_n) = diag(A_1 B_1 .. A_n B_n).
+// The concatenation gives A_i's columns an offset of sum_{j<i} k_j and B_i's
+// columns an offset of sum_{j<i} n_j, so every stage of the framework runs once
+// over the rows of all pairs (one launch per bin for the whole batch).  The
+// split step gives each C_i its own row pointers and columns; its values are a
+// view into the concatenated C.
+#include "internal.h"
+#include "common.cuh"
+
+namespace spg {
+
+SPG_DEV int find_pair(const int64_t *off, int64_t npairs, int64_t x) {
+    // largest i with off[i] <= x
+    int64_t lo = 0, hi = npairs - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return (int)lo;
+}
+
+SPG_DEV int64_t rp_at(const void *rp, int bits, int64_t i) {
+    return bits == 64 ? static_cast<const int64_t *>(rp)[i] : (int64_t) static_cast<const int32_t *>(rp)[i];
+}
+
+// Row pointers of the concatenated A (rows of all pairs) and B.
+__global__ void k_concat_rp(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *koff, int64_t M,
+                            int64_t K, int64_t annz, int64_t bnnz, int64_t *a_rp, int64_t *b_rp) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < M) {
+        const int i = find_pair(moff, npairs, r);
+        a_rp[r] = d[i].annz_off + rp_at(d[i].a_rp, d[i].a_bits, r - d[i].moff);
+    } else if (r == M) {
+        a_rp[M] = annz;
+    }
+    if (r < K) {
+        const int i = find_pair(koff, npairs, r);
+        b_rp[r] = d[i].bnnz_off + rp_at(d[i].b_rp, d[i].b_bits, r - d[i].koff);
+    } else if (r == K) {
+        b_rp[K] = bnnz;
+    }
+}
+
+// Entries of the concatenated A and B (columns shifted into the pair's block).
+__global__ void k_concat_entries(const PairDesc *d, int64_t npairs, const int64_t *annz_off, const int64_t *bnnz_off,
+                                 int64_t annz, int64_t bnnz, int32_t *a_col, double *a_val, int32_t *b_col,
+                                 double *b_val, int values_only) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < annz) {
+        const int i = find_pair(annz_off, npairs, t);
+        const int64_t l = t - d[i].annz_off;
+        if (!values_only) a_col[t] = d[i].a_col[l] + (int32_t)d[i].koff;
+        a_val[t] = d[i].a_val[l];
+    }
+    if (t < bnnz) {
+        const int i = find_pair(bnnz_off, npairs, t);
+        const int64_t l = t - d[i].bnnz_off;
+        if (!values_only) b_col[t] = d[i].b_col[l] + (int32_t)d[i].noff;
+        b_val[t] = d[i].b_val[l];
+    }
+}
+
+cudaError_t launch_concat(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *koff,
+                          const int64_t *annz_off, const int64_t *bnnz_off, int64_t M, int64_t K, int64_t annz,
+                          int64_t bnnz, int64_t *a_rp, int32_t *a_col, double *a_val, int64_t *b_rp, int32_t *b_col,
+                          double *b_val, bool values_only, cudaStream_t st) {
+    if (npairs <= 0) return cudaSuccess;
+    if (!values_only) {
+        const int64_t rmax = (M > K ? M : K) + 1;
+        k_concat_rp<<<(unsigned)((rmax + 255) / 256), 256, 0, st>>>(d, npairs, moff, koff, M, K, annz, bnnz, a_rp,
+                                                                   b_rp);
+    }
+    const int64_t emax = annz > bnnz ? annz : bnnz;
+    if (emax > 0)
+        k_concat_entries<<<(unsigned)((emax + 255) / 256), 256, 0, st>>>(d, npairs, annz_off, bnnz_off, annz, bnnz,
+                                                                        a_col, a_val, b_col, b_val,
+                                                                        values_only ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// C_i's row pointers (rebased to 0; pair i occupies rp_out[moff_i + i .. moff_i + i + m_i])
+// and columns (shifted back out of the pair's block).
+__global__ void k_split_out(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *c_rp,
+                            const int32_t *c_col, int64_t M, int64_t nnz, int64_t *rp_out, int32_t *col_out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < M + npairs) {
+        // entry t of the rebased row-pointer array: pair i holds m_i + 1 entries starting at moff_i + i
+        int64_t lo = 0, hi = npairs - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (d[mid].moff + mid <= t) lo = mid; else hi = mid - 1;
+        }
+        const int i = (int)lo;
+        const int64_t r = t - (d[i].moff + i);
+        rp_out[t] = c_rp[d[i].moff + r] - c_rp[d[i].moff];
+    }
+    if (t < nnz) {
+        // the pair of entry t: largest i with c_rp[moff_i] <= t among pairs with rows
+        int64_t lo = 0, hi = npairs - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (c_rp[d[mid].moff] <= t) lo = mid; else hi = mid - 1;
+        }
+        col_out[t] = c_col[t] - (int32_t)d[lo].noff;
+    }
+}
+
+cudaError_t launch_split_out(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *c_rp,
+                             const int32_t *c_col, int64_t M, int64_t nnz, int64_t *rp_out, int32_t *col_out,
+                             cudaStream_t st) {
+    (void)moff;
+    const int64_t n = (M + npairs > nnz) ? M + npairs : nnz;
+    if (n <= 0) return cudaSuccess;
+    k_split_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, npairs, moff, c_rp, c_col, M, nnz, rp_out, col_out);
+    return cudaGetLastError();
+}
+
+// out[i] = c_rp[moff_i] (first entry of C_i in the concatenation), out[np] = c_rp[M].
+__global__ void k_gather_first(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < npairs) out[i] = c_rp[d[i].moff];
+    else if (i == npairs) out[npairs] = c_rp[M];
+}
+
+cudaError_t launch_gather_first(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *out,
+                                cudaStream_t st) {
+    k_gather_first<<<(unsigned)((npairs + 256) / 256), 256, 0, st>>>(d, npairs, c_rp, M, out);
+    return cudaGetLastError();
+}
+
+}  // namespace spg

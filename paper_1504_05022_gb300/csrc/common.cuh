@@ -36,8 +36,10 @@ SPG_DEV T warp_reduce_sum(T v) {
 
 // Block-wide exclusive scan.  `scratch` needs NT/32 + 1 elements of T.  Every
 // thread of the block must call it.  Returns the exclusive prefix; `total`
-// receives the block sum.  Ends with a barrier so scratch can be reused.
-template <int NT, typename T>
+// receives the block sum.  With TRAILING_SYNC it ends with a barrier so scratch
+// can be reused at once; without it the caller must pass a barrier before the
+// next scan that uses the same scratch.
+template <int NT, typename T, bool TRAILING_SYNC = true>
 SPG_DEV T block_exclusive_scan(T v, T *scratch, T &total) {
     constexpr int NW = NT / 32;
     const int lane = lane_id(), wid = warp_id();
@@ -53,7 +55,7 @@ SPG_DEV T block_exclusive_scan(T v, T *scratch, T &total) {
     __syncthreads();
     T res = scratch[wid] + inc - v;
     total = scratch[NW];
-    __syncthreads();
+    if (TRAILING_SYNC) __syncthreads();
     return res;
 }
 
@@ -124,6 +126,28 @@ SPG_DEV int merge_path(const int32_t *a, int na, const int32_t *b, int nb, int d
         if (a[mid] <= b[diag - 1 - mid]) lo = mid + 1; else hi = mid;
     }
     return lo;
+}
+
+// Lockstep lower_bound of up to IPT keys in the sorted array a[0..n): pos[k]
+// receives the number of entries < key[k].  The IPT searches are independent,
+// so their shared-memory loads overlap.
+template <int IPT>
+SPG_DEV void lower_bound_multi(const int32_t *a, int n, const int32_t (&key)[IPT], int cnt, int (&pos)[IPT]) {
+    int hi[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        pos[k] = 0;
+        hi[k] = (k < cnt) ? n : 0;
+    }
+    for (int step = 32 - __clz(n); step > 0; --step) {
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            if (pos[k] < hi[k]) {
+                const int mid = (pos[k] + hi[k]) >> 1;
+                if (a[mid] < key[k]) pos[k] = mid + 1; else hi[k] = mid;
+            }
+        }
+    }
 }
 
 // In-place merge of two disjoint sorted sequences: x (keys xk, values xv,

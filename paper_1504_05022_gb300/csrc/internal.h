@@ -138,6 +138,41 @@ cudaError_t launch_level1_sizes(const MergeItems &it, const int32_t *work, int64
                                 const int64_t *u, int64_t ncols, int64_t *g_cap, int64_t *g_off,
                                 int64_t *partial, int64_t *total, cudaStream_t st);
 
+// ---- values-only replay (replay.cu) ----
+struct ReplayLeaves {
+    int32_t *row, *clo, *chi;
+    int64_t *c_off;   // first entry of the leaf in C
+    int32_t *len;
+    int cap;          // shared-memory capacity of a launch (set by launch_replay)
+};
+constexpr int NUM_REPLAY_CLASSES = 3;
+cudaError_t launch_replay(const StageArgs &a, ReplayLeaves lv, const int32_t *order, int64_t n, int cap,
+                          int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st);
+cudaError_t launch_replay_leaves(int64_t n37, const MergeItems &it, const int64_t *c_rp, const int32_t *class_cap,
+                                 int ncls, int32_t *count, int32_t *start, int32_t *cursor, const ReplayLeaves &lv,
+                                 int32_t *order, int64_t *err, bool scatter, cudaStream_t st);
+
+// ---- batched products (batched.cu): block-diagonal concatenation ----
+struct PairDesc {
+    const void *a_rp, *b_rp;
+    const int32_t *a_col, *b_col;
+    const double *a_val, *b_val;
+    int32_t a_bits, b_bits;
+    int64_t m, k, n;             // A_i is m x k, B_i is k x n
+    int64_t moff, koff, noff;    // row/column offsets in the concatenation
+    int64_t annz_off, bnnz_off;  // entry offsets
+    int64_t annz, bnnz;
+};
+cudaError_t launch_concat(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *koff,
+                          const int64_t *annz_off, const int64_t *bnnz_off, int64_t M, int64_t K, int64_t annz,
+                          int64_t bnnz, int64_t *a_rp, int32_t *a_col, double *a_val, int64_t *b_rp, int32_t *b_col,
+                          double *b_val, bool values_only, cudaStream_t st);
+cudaError_t launch_gather_first(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *out,
+                                cudaStream_t st);
+cudaError_t launch_split_out(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *c_rp,
+                             const int32_t *c_col, int64_t M, int64_t nnz, int64_t *rp_out, int32_t *col_out,
+                             cudaStream_t st);
+
 // ---- stage 4 (arrange.cu) ----
 cudaError_t launch_row_scan(int64_t m, const int32_t *nnzc, int64_t *c_rp, int64_t *partial,
                             cudaStream_t st);

@@ -34,7 +34,7 @@
 namespace spg {
 
 constexpr int MERGE_MAX_IPT = 4;   // products per thread per batch: batch <= NT * 4
-constexpr int MERGE_TN_MAX = 1024; // pending-set capacity
+constexpr int MERGE_TN_MAX = 2048; // pending-set capacity
 
 struct MergeSmem {
     double *Rv, *Nv, *Sav, *Sbv, *wa;
@@ -84,49 +84,31 @@ int merge_max_cap(int batch, int smem_limit) {
     return cap;
 }
 
-// Lockstep lower_bound of up to IPT keys in the sorted array a[0..n): pos[k]
-// receives the number of entries < key[k].  The IPT searches are independent,
-// so their shared-memory loads overlap.
-template <int IPT>
-SPG_DEV void lower_bound_multi(const int32_t *a, int n, const int32_t (&key)[IPT], int cnt, int (&pos)[IPT]) {
-    int hi[IPT];
-#pragma unroll
-    for (int k = 0; k < IPT; ++k) {
-        pos[k] = 0;
-        hi[k] = (k < cnt) ? n : 0;
-    }
-    for (int step = 32 - __clz(n); step > 0; --step) {
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            if (pos[k] < hi[k]) {
-                const int mid = (pos[k] + hi[k]) >> 1;
-                if (a[mid] < key[k]) pos[k] = mid + 1; else hi[k] = mid;
-            }
-        }
-    }
-}
-
-// One level of the pairwise merge of `nruns` sorted runs: run r occupies
-// [runoff[r], runoff[r+1]) of sk/sv; runs 2p and 2p+1 are merged into the same
-// range of dk/dv.  All threads call; ends with a barrier.
+// One level of the pairwise merge of sorted runs.  The runs of the current level
+// are groups of `stride` original runs: run r spans [off(r*stride), off((r+1)*stride))
+// with off(i) = runoff[min(i, nr0)], so the offsets never need rewriting between
+// levels.  Runs 2p and 2p+1 are merged into the same range of dk/dv.  All threads
+// call; ends with a barrier.
 template <int NT>
-SPG_DEV void merge_level(const int32_t *sk, const double *sv, const int32_t *runoff, int nruns, int n,
+SPG_DEV void merge_level(const int32_t *sk, const double *sv, const int32_t *runoff, int nr0, int stride, int n,
                          int32_t *dk, double *dv) {
     const int ipt = (n + NT - 1) / NT;
     int d = threadIdx.x * ipt;
     const int dend = min(n, d + ipt);
     if (d < dend) {
+        const int nruns = (nr0 + stride - 1) / stride;
         const int npairs = (nruns + 1) >> 1;
+        const int pstride = 2 * stride;
         int lo = 0, hi = npairs - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (runoff[2 * mid] <= d) lo = mid; else hi = mid - 1;
+            if (runoff[min(mid * pstride, nr0)] <= d) lo = mid; else hi = mid - 1;
         }
         int p = lo;
         while (d < dend) {
-            const int as = runoff[2 * p];
-            const int am = runoff[min(2 * p + 1, nruns)];
-            const int ae = runoff[min(2 * p + 2, nruns)];
+            const int as = runoff[min(p * pstride, nr0)];
+            const int am = runoff[min(p * pstride + stride, nr0)];
+            const int ae = runoff[min(p * pstride + pstride, nr0)];
             const int i = merge_path(sk + as, am - as, sk + am, ae - am, d - as);
             int ia = as + i, ib = am + (d - as - i);
             const int stop = min(dend, ae);
@@ -154,7 +136,7 @@ SPG_DEV int compress_runs(const int32_t *k, const double *v, int n, int32_t *ok,
     for (int q = q0; q < q1; ++q)
         if (q == 0 || k[q] != k[q - 1]) ++cnt;
     int tot;
-    int o = block_exclusive_scan<NT>(cnt, scan32, tot);
+    int o = block_exclusive_scan<NT, int, false>(cnt, scan32, tot);
     for (int q = q0; q < q1; ++q) {
         if (q == 0 || k[q] != k[q - 1]) {
             const int32_t key = k[q];
@@ -286,7 +268,7 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
             len = be > bs ? be - bs : 0;
         }
         int64_t total;
-        const int64_t ex = block_exclusive_scan<NT>(len, scan64, total);
+        const int64_t ex = block_exclusive_scan<NT, int64_t, false>(len, scan64, total);
         if (threadIdx.x < nW) s.wscan[threadIdx.x] = ex;
         if (threadIdx.x == 0) s.wscan[nW] = total;
         __syncthreads();
@@ -331,18 +313,28 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
             int32_t key[MERGE_MAX_IPT];
             double val[MERGE_MAX_IPT];
             if (cnt > 0) {
+                // all addresses first, then all loads: one L2 round trip per batch, not IPT
+                int te[MERGE_MAX_IPT], to[MERGE_MAX_IPT];  // window entry and offset in its B range
                 int64_t pos = p0 + q0;
                 int t = tf + find_segment_i64(s.wscan + tf, nruns, pos);
 #pragma unroll
                 for (int k = 0; k < MERGE_MAX_IPT; ++k) {
                     if (k < cnt) {
                         while (t + 1 < nW && s.wscan[t + 1] <= pos) ++t;
-                        const int64_t bidx = s.wbs[t] + (pos - s.wscan[t]);
-                        key[k] = a.B.col[bidx];
-                        val[k] = s.wa[t] * a.B.val[bidx];
+                        te[k] = t;
+                        to[k] = (int)(pos - s.wscan[t]);
                         ++pos;
                     }
                 }
+#pragma unroll
+                for (int k = 0; k < MERGE_MAX_IPT; ++k)
+                    if (k < cnt) key[k] = __ldg(a.B.col + s.wbs[te[k]] + to[k]);
+#pragma unroll
+                for (int k = 0; k < MERGE_MAX_IPT; ++k)
+                    if (k < cnt) val[k] = __ldg(a.B.val + s.wbs[te[k]] + to[k]);
+#pragma unroll
+                for (int k = 0; k < MERGE_MAX_IPT; ++k)
+                    if (k < cnt) val[k] *= s.wa[te[k]];
             }
             // (1) fuse products whose column is already in R or N (lockstep binary searches)
             unsigned miss = 0;
@@ -376,7 +368,7 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
             }
             // (2) compact the misses into Sb, keeping one run per B row
             int nnew;
-            int o = block_exclusive_scan<NT>(__popc(miss), scan32, nnew);
+            int o = block_exclusive_scan<NT, int, false>(__popc(miss), scan32, nnew);
 #pragma unroll
             for (int k = 0; k < MERGE_MAX_IPT; ++k) {
                 if (k < cnt) {
@@ -399,16 +391,8 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
                 // (3) pairwise merge-path merges of the runs, then fuse equal columns
                 int32_t *ck = s.Sbk, *okk = s.Sak;
                 double *cv = s.Sbv, *ovv = s.Sav;
-                int nr = nruns;
-                while (nr > 1) {
-                    merge_level<NT>(ck, cv, s.runoff, nr, nnew, okk, ovv);
-                    const int np = (nr + 1) >> 1;
-                    int v = 0;
-                    if (threadIdx.x <= np) v = (threadIdx.x == np) ? nnew : s.runoff[2 * threadIdx.x];
-                    __syncthreads();
-                    if (threadIdx.x <= np) s.runoff[threadIdx.x] = v;
-                    __syncthreads();
-                    nr = np;
+                for (int stride = 1; stride < nruns; stride *= 2) {
+                    merge_level<NT>(ck, cv, s.runoff, nruns, stride, nnew, okk, ovv);
                     int32_t *tk = ck; ck = okk; okk = tk;
                     double *tv = cv; cv = ovv; ovv = tv;
                 }

@@ -50,12 +50,12 @@ __global__ void k_row_features(DevCSR A, DevCSR B, float *__restrict__ X) {
         const int32_t k = A.col[p];
         const int64_t b0 = B.rp[k], b1 = B.rp[k + 1];
         const int64_t len = b1 - b0;
-        const double g = log2(1.0 + (double)len);
+        const float g = log2f(1.f + (float)len);
         sum_len += (double)len;
-        sg += g;
-        sg2 += g * g;
-        gmin = fminf(gmin, (float)g);
-        gmax = fmaxf(gmax, (float)g);
+        sg += (double)g;
+        sg2 += (double)g * (double)g;
+        gmin = fminf(gmin, g);
+        gmax = fmaxf(gmax, g);
         if (len > 0) {
             cmin = min(cmin, B.col[b0]);
             cmax = max(cmax, B.col[b1 - 1]);
@@ -73,8 +73,8 @@ __global__ void k_row_features(DevCSR A, DevCSR B, float *__restrict__ X) {
     if (lane == 0) {
         const double n = (double)(a1 - a0);
         float *x = X + row * MLP_IN;
-        x[0] = (float)log2(1.0 + n);
-        x[1] = (float)log2(1.0 + sum_len);
+        x[0] = log2f(1.f + (float)n);
+        x[1] = log2f(1.f + (float)sum_len);
         if (n > 0) {
             const double mean = sg / n;
             const double var = sg2 / n - mean * mean;
@@ -82,11 +82,11 @@ __global__ void k_row_features(DevCSR A, DevCSR B, float *__restrict__ X) {
             x[3] = gmax;
             x[4] = (float)mean;
             x[5] = (float)sqrt(var > 0.0 ? var : 0.0);
-            x[6] = cmax >= 0 ? (float)log2(1.0 + (double)(cmax - cmin + 1)) : 0.f;
+            x[6] = cmax >= 0 ? log2f(1.f + (float)(cmax - cmin + 1)) : 0.f;
         } else {
             x[2] = x[3] = x[4] = x[5] = x[6] = 0.f;
         }
-        x[7] = (float)log2(1.0 + (double)B.ncols);
+        x[7] = log2f(1.f + (float)B.ncols);
     }
 }
 

@@ -119,6 +119,23 @@ struct spgemm_plan {
     int32_t *class_order = nullptr;   // bin-37 item indices grouped by launch class
     int32_t class_caps[NUM_LAUNCH_CLASSES] = {0};
     int capmax = 0, batch = 0;
+    // batched plans: the pairs and the concatenation offsets
+    int64_t npairs = 0;
+    PairDesc *d_pairs = nullptr;
+    std::vector<PairDesc> h_pairs;
+    int64_t *d_moff = nullptr, *d_koff = nullptr, *d_annz_off = nullptr, *d_bnnz_off = nullptr;
+    int64_t *cat_a_rp = nullptr, *cat_b_rp = nullptr;
+    int32_t *cat_a_col = nullptr, *cat_b_col = nullptr;
+    double *cat_a_val = nullptr, *cat_b_val = nullptr;
+    int64_t *split_rp = nullptr;
+    int32_t *split_col = nullptr;
+    std::vector<spgemm_csr_out> batch_out;
+    // values-only replay
+    bool replay_ready = false;
+    ReplayLeaves leaves{};
+    int32_t *leaf_order = nullptr;
+    int64_t leaf_count[NUM_REPLAY_CLASSES] = {0};
+    int leaf_cap[NUM_REPLAY_CLASSES] = {0};
     // result
     bool numeric_done = false;
     spgemm_csr_out C{};
@@ -255,28 +272,18 @@ StageArgs stage_args(spgemm_plan *p) {
 
 }  // namespace
 
-extern "C" spgemm_status spgemm_symbolic(const spgemm_csr_in *A_in, const spgemm_csr_in *B_in,
-                                         const spgemm_opts *opts, spgemm_stream_t stream,
-                                         spgemm_plan **plan_out, int64_t *upper_bound_nnz_out) {
-    if (!plan_out) return SPGEMM_ERR_INVALID_ARG;
-    *plan_out = nullptr;
-    spgemm_status status = check_in(A_in);
-    if (status != SPGEMM_OK) return status;
-    status = check_in(B_in);
-    if (status != SPGEMM_OK) return status;
-    if (A_in->ncols != B_in->nrows) return SPGEMM_ERR_SHAPE;
+// Creates a plan bound to the current device, the library's memory pool and `stream`.
+static spgemm_status plan_begin(const spgemm_opts *opts, spgemm_stream_t stream, spgemm_plan **out) {
+    *out = nullptr;
     spgemm_opts o;
     if (opts) o = *opts; else spgemm_opts_init(&o);
     if (o.alloc_policy < 0 || o.alloc_policy > 2 || o.initial_cap < 1) return SPGEMM_ERR_INVALID_ARG;
     if (o.alloc_policy == SPGEMM_ALLOC_LEARNED && o.predictor == nullptr) return SPGEMM_ERR_INVALID_ARG;
-
     spgemm_plan *p = new (std::nothrow) spgemm_plan();
     if (!p) return SPGEMM_ERR_OOM;
     p->opts = o;
     p->st = reinterpret_cast<cudaStream_t>(stream);
-    const int64_t m = A_in->nrows, nnzA = A_in->nnz;
-    int64_t nblk;
-    CapPolicy pol{};
+    spgemm_status status = SPGEMM_OK;
     {
         SPG_TRY(cudaGetDevice(&p->device));
         SPG_TRY(get_pool(p->device, &p->pool));
@@ -286,27 +293,29 @@ extern "C" spgemm_status spgemm_symbolic(const spgemm_csr_in *A_in, const spgemm
             status = SPGEMM_ERR_OOM;
             goto fail;
         }
-        // int64 row pointers everywhere on the device
-        auto widen = [&](const spgemm_csr_in *M, DevCSR &D) -> cudaError_t {
-            D.nrows = M->nrows;
-            D.ncols = M->ncols;
-            D.nnz = M->nnz;
-            D.col = M->col_idx;
-            D.val = M->val;
-            if (M->rowptr_bits == 64) {
-                D.rp = static_cast<const int64_t *>(M->row_ptr);
-                return cudaSuccess;
-            }
-            int64_t *rp = nullptr;
-            cudaError_t e = p->alloc_n(&rp, M->nrows + 1);
-            if (e != cudaSuccess) return e;
-            e = launch_widen_rowptr(static_cast<const int32_t *>(M->row_ptr), rp, M->nrows + 1, p->st);
-            p->count(SPGEMM_K_OTHER);
-            D.rp = rp;
-            return e;
-        };
-        SPG_TRY(widen(A_in, p->A));
-        SPG_TRY(widen(B_in, p->B));
+    }
+    *out = p;
+    return SPGEMM_OK;
+fail:
+    p->release();
+    delete p;
+    return status;
+}
+
+static void plan_abort(spgemm_plan *p) {
+    cudaStreamSynchronize(p->st);
+    p->release();
+    delete p;
+}
+
+// Stages 1 and 2 on the plan's A and B (int64 row pointers on the device).
+static spgemm_status plan_symbolic_core(spgemm_plan *p) {
+    spgemm_status status = SPGEMM_OK;
+    const spgemm_opts &o = p->opts;
+    const int64_t m = p->A.nrows, nnzA = p->A.nnz;
+    int64_t nblk;
+    CapPolicy pol{};
+    {
         SPG_TRY(p->alloc_n(&p->d_summary, 1));
         SPG_TRY(p->alloc_n(&p->d_err, 1));
         SPG_TRY(cudaMemsetAsync(p->d_summary, 0, sizeof(BinSummary), p->st));
@@ -393,13 +402,55 @@ extern "C" spgemm_status spgemm_symbolic(const spgemm_csr_in *A_in, const spgemm
         SPG_TRY(p->alloc_n(&p->ctil_val, p->h_summary.sum_cap));
         p->bytes_ctilde += p->h_summary.sum_cap * 12;
     }
+    return SPGEMM_OK;
+fail:
+    return status;
+}
+
+// Widens an int32 row-pointer array into a plan-owned int64 copy when needed.
+static cudaError_t plan_widen(spgemm_plan *p, const spgemm_csr_in *M, DevCSR &D) {
+    D.nrows = M->nrows;
+    D.ncols = M->ncols;
+    D.nnz = M->nnz;
+    D.col = M->col_idx;
+    D.val = M->val;
+    if (M->rowptr_bits == 64) {
+        D.rp = static_cast<const int64_t *>(M->row_ptr);
+        return cudaSuccess;
+    }
+    int64_t *rp = nullptr;
+    cudaError_t e = p->alloc_n(&rp, M->nrows + 1);
+    if (e != cudaSuccess) return e;
+    e = launch_widen_rowptr(static_cast<const int32_t *>(M->row_ptr), rp, M->nrows + 1, p->st);
+    p->count(SPGEMM_K_OTHER);
+    D.rp = rp;
+    return e;
+}
+
+extern "C" spgemm_status spgemm_symbolic(const spgemm_csr_in *A_in, const spgemm_csr_in *B_in,
+                                         const spgemm_opts *opts, spgemm_stream_t stream,
+                                         spgemm_plan **plan_out, int64_t *upper_bound_nnz_out) {
+    if (!plan_out) return SPGEMM_ERR_INVALID_ARG;
+    *plan_out = nullptr;
+    spgemm_status status = check_in(A_in);
+    if (status != SPGEMM_OK) return status;
+    status = check_in(B_in);
+    if (status != SPGEMM_OK) return status;
+    if (A_in->ncols != B_in->nrows) return SPGEMM_ERR_SHAPE;
+    spgemm_plan *p = nullptr;
+    status = plan_begin(opts, stream, &p);
+    if (status != SPGEMM_OK) return status;
+    {
+        SPG_TRY(plan_widen(p, A_in, p->A));
+        SPG_TRY(plan_widen(p, B_in, p->B));
+        status = plan_symbolic_core(p);
+        if (status != SPGEMM_OK) goto fail;
+    }
     if (upper_bound_nnz_out) *upper_bound_nnz_out = p->h_summary.sum_u;
     *plan_out = p;
     return SPGEMM_OK;
 fail:
-    cudaStreamSynchronize(p->st);
-    p->release();
-    delete p;
+    plan_abort(p);
     return status;
 }
 
@@ -711,5 +762,327 @@ extern "C" spgemm_status spgemm_plan_arrays_get(spgemm_plan *p, spgemm_plan_arra
     out->bin_start = p->bin_start;
     out->ctilde_row_ptr = p->ctil_rp;
     out->row_nnz = p->nnzc;
+    return SPGEMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched products: block-diagonal concatenation, one pipeline for all pairs.
+// ---------------------------------------------------------------------------
+
+extern "C" spgemm_status spgemm_batched_symbolic(int64_t npairs, const spgemm_csr_in *A, const spgemm_csr_in *B,
+                                                 const spgemm_opts *opts, spgemm_stream_t stream,
+                                                 spgemm_plan **plan_out, int64_t *upper_bound_nnz_out) {
+    if (!plan_out || npairs < 1 || !A || !B) return SPGEMM_ERR_INVALID_ARG;
+    *plan_out = nullptr;
+    std::vector<PairDesc> hd((size_t)npairs);
+    std::vector<int64_t> moff(npairs), koff(npairs), aoff(npairs), boff(npairs);
+    int64_t M = 0, K = 0, N = 0, annz = 0, bnnz = 0;
+    for (int64_t i = 0; i < npairs; ++i) {
+        spgemm_status st = check_in(&A[i]);
+        if (st != SPGEMM_OK) return st;
+        st = check_in(&B[i]);
+        if (st != SPGEMM_OK) return st;
+        if (A[i].ncols != B[i].nrows) return SPGEMM_ERR_SHAPE;
+        PairDesc &d = hd[i];
+        d.a_rp = A[i].row_ptr;
+        d.b_rp = B[i].row_ptr;
+        d.a_col = A[i].col_idx;
+        d.b_col = B[i].col_idx;
+        d.a_val = A[i].val;
+        d.b_val = B[i].val;
+        d.a_bits = A[i].rowptr_bits;
+        d.b_bits = B[i].rowptr_bits;
+        d.m = A[i].nrows;
+        d.k = A[i].ncols;
+        d.n = B[i].ncols;
+        d.moff = moff[i] = M;
+        d.koff = koff[i] = K;
+        d.noff = N;
+        d.annz_off = aoff[i] = annz;
+        d.bnnz_off = boff[i] = bnnz;
+        d.annz = A[i].nnz;
+        d.bnnz = B[i].nnz;
+        M += d.m;
+        K += d.k;
+        N += d.n;
+        annz += d.annz;
+        bnnz += d.bnnz;
+    }
+    if (M > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return SPGEMM_ERR_SHAPE;
+    spgemm_plan *p = nullptr;
+    spgemm_status status = plan_begin(opts, stream, &p);
+    if (status != SPGEMM_OK) return status;
+    {
+        p->npairs = npairs;
+        p->h_pairs = hd;
+        SPG_TRY(p->alloc_n(&p->d_pairs, npairs));
+        SPG_TRY(p->alloc_n(&p->d_moff, npairs));
+        SPG_TRY(p->alloc_n(&p->d_koff, npairs));
+        SPG_TRY(p->alloc_n(&p->d_annz_off, npairs));
+        SPG_TRY(p->alloc_n(&p->d_bnnz_off, npairs));
+        // pageable sources: the copies are staged before the calls return
+        SPG_TRY(cudaMemcpyAsync(p->d_pairs, hd.data(), sizeof(PairDesc) * npairs, cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(cudaMemcpyAsync(p->d_moff, moff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(cudaMemcpyAsync(p->d_koff, koff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(cudaMemcpyAsync(p->d_annz_off, aoff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(cudaMemcpyAsync(p->d_bnnz_off, boff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(p->alloc_n(&p->cat_a_rp, M + 1));
+        SPG_TRY(p->alloc_n(&p->cat_b_rp, K + 1));
+        SPG_TRY(p->alloc_n(&p->cat_a_col, annz));
+        SPG_TRY(p->alloc_n(&p->cat_a_val, annz));
+        SPG_TRY(p->alloc_n(&p->cat_b_col, bnnz));
+        SPG_TRY(p->alloc_n(&p->cat_b_val, bnnz));
+        p->time_begin(SPGEMM_K_OTHER);
+        SPG_TRY(launch_concat(p->d_pairs, npairs, p->d_moff, p->d_koff, p->d_annz_off, p->d_bnnz_off, M, K, annz, bnnz,
+                              p->cat_a_rp, p->cat_a_col, p->cat_a_val, p->cat_b_rp, p->cat_b_col, p->cat_b_val, false,
+                              p->st));
+        p->time_end();
+        p->count(SPGEMM_K_OTHER, 2);
+        p->A = DevCSR{M, K, annz, p->cat_a_rp, p->cat_a_col, p->cat_a_val};
+        p->B = DevCSR{K, N, bnnz, p->cat_b_rp, p->cat_b_col, p->cat_b_val};
+        status = plan_symbolic_core(p);
+        if (status != SPGEMM_OK) goto fail;
+    }
+    if (upper_bound_nnz_out) *upper_bound_nnz_out = p->h_summary.sum_u;
+    *plan_out = p;
+    return SPGEMM_OK;
+fail:
+    plan_abort(p);
+    return status;
+}
+
+extern "C" spgemm_status spgemm_batched_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
+    if (!p || !C_out || p->npairs < 1) return SPGEMM_ERR_INVALID_ARG;
+    if (!p->batch_out.empty()) {
+        for (int64_t i = 0; i < p->npairs; ++i) C_out[i] = p->batch_out[i];
+        return SPGEMM_OK;
+    }
+    spgemm_csr_out whole;
+    spgemm_status status = spgemm_numeric(p, &whole);
+    if (status != SPGEMM_OK) return status;
+    {
+        const int64_t M = p->A.nrows, nnz = whole.nnz, np = p->npairs;
+        SPG_TRY(p->alloc_n(&p->split_rp, M + np));
+        SPG_TRY(p->alloc_n(&p->split_col, nnz));
+        p->time_begin(SPGEMM_K_OTHER);
+        SPG_TRY(launch_split_out(p->d_pairs, np, p->d_moff, whole.row_ptr, whole.col_idx, M, nnz, p->split_rp,
+                                 p->split_col, p->st));
+        p->time_end();
+        p->count(SPGEMM_K_OTHER);
+        // C_i's first entry in the concatenation: read every pair's first row pointer once
+        std::vector<int64_t> first(np + 1);
+        int64_t *d_first = nullptr;
+        SPG_TRY(p->alloc_n(&d_first, np + 1));
+        SPG_TRY(launch_gather_first(p->d_pairs, np, whole.row_ptr, M, d_first, p->st));
+        SPG_TRY(cudaStreamSynchronize(p->st));
+        SPG_TRY(cudaMemcpy(first.data(), d_first, sizeof(int64_t) * (np + 1), cudaMemcpyDeviceToHost));
+        p->batch_out.resize(np);
+        for (int64_t i = 0; i < np; ++i) {
+            const PairDesc &d = p->h_pairs[i];
+            spgemm_csr_out &c = p->batch_out[i];
+            c.nrows = d.m;
+            c.ncols = d.n;
+            c.nnz = first[i + 1] - first[i];
+            c.row_ptr = p->split_rp + d.moff + i;
+            c.col_idx = p->split_col + first[i];
+            c.val = whole.val + first[i];
+            C_out[i] = c;
+        }
+    }
+    return SPGEMM_OK;
+fail:
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// Values-only replay (capturable): same structure, new values of A and B.
+// ---------------------------------------------------------------------------
+
+static spgemm_status prepare_replay(spgemm_plan *p) {
+    spgemm_status status = SPGEMM_OK;
+    const int64_t n37 = p->h_summary.bin_count[BIN_MERGE];
+    // rows finished with a level-1 sequence can be longer than any shared-memory slice
+    if (p->stats.rows_level1 > 0) return SPGEMM_ERR_INVALID_ARG;
+    {
+        const int64_t nleaves = p->n_items - p->stats.rows_split;
+        int32_t *scratch = nullptr, *ccap = nullptr;
+        const int caps[NUM_REPLAY_CLASSES] = {1024, 4096, std::max(4096, p->capmax)};
+        for (int g = 0; g < NUM_REPLAY_CLASSES; ++g) p->leaf_cap[g] = caps[g];
+        SPG_TRY(p->alloc_n(&ccap, NUM_REPLAY_CLASSES));
+        SPG_TRY(cudaMemcpyAsync(ccap, caps, sizeof(caps), cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(p->alloc_n(&scratch, 96));
+        SPG_TRY(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * 96, p->st));
+        ReplayLeaves &lv = p->leaves;
+        SPG_TRY(p->alloc_n(&lv.row, nleaves));
+        SPG_TRY(p->alloc_n(&lv.clo, nleaves));
+        SPG_TRY(p->alloc_n(&lv.chi, nleaves));
+        SPG_TRY(p->alloc_n(&lv.c_off, nleaves));
+        SPG_TRY(p->alloc_n(&lv.len, nleaves));
+        SPG_TRY(p->alloc_n(&p->leaf_order, nleaves));
+        int32_t *count = scratch, *start = scratch + 32, *cursor = scratch + 64;
+        SPG_TRY(launch_replay_leaves(n37, p->items, p->C.row_ptr, ccap, NUM_REPLAY_CLASSES, count, start, cursor, lv,
+                                     p->leaf_order, p->d_err, false, p->st));
+        int32_t hc[NUM_REPLAY_CLASSES] = {0};
+        SPG_TRY(p->d2h(hc, count, sizeof(hc)));
+        int32_t hs[NUM_REPLAY_CLASSES];
+        int32_t acc = 0;
+        for (int g = 0; g < NUM_REPLAY_CLASSES; ++g) {
+            hs[g] = acc;
+            p->leaf_count[g] = hc[g];
+            acc += hc[g];
+        }
+        if (acc != nleaves) return SPGEMM_ERR_INTERNAL;
+        SPG_TRY(cudaMemcpyAsync(start, hs, sizeof(hs), cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(launch_replay_leaves(n37, p->items, p->C.row_ptr, ccap, NUM_REPLAY_CLASSES, count, start, cursor, lv,
+                                     p->leaf_order, p->d_err, true, p->st));
+        SPG_TRY(cudaStreamSynchronize(p->st));
+        p->replay_ready = true;
+    }
+    return SPGEMM_OK;
+fail:
+    return status;
+}
+
+extern "C" spgemm_status spgemm_numeric_replay(spgemm_plan *p) {
+    if (!p || !p->numeric_done) return SPGEMM_ERR_INVALID_ARG;
+    spgemm_status status = SPGEMM_OK;
+    if (!p->replay_ready) {
+        status = prepare_replay(p);
+        if (status != SPGEMM_OK) return status;
+    }
+    {
+        if (p->npairs > 0) {
+            // refresh the concatenated values from the pairs' inputs
+            SPG_TRY(launch_concat(p->d_pairs, p->npairs, p->d_moff, p->d_koff, p->d_annz_off, p->d_bnnz_off,
+                                  p->A.nrows, p->B.nrows, p->A.nnz, p->B.nnz, p->cat_a_rp, p->cat_a_col,
+                                  p->cat_a_val, p->cat_b_rp, p->cat_b_col, p->cat_b_val, true, p->st));
+        }
+        // bins 2..36: the heap and bitonic-ESC kernels write straight into C
+        StageArgs a = stage_args(p);
+        a.ctil_rp = p->C.row_ptr;
+        a.ctil_col = p->C.col_idx;
+        a.ctil_val = p->C.val;
+        const int heap_nt = p->opts.heap_block > 0 ? p->opts.heap_block : 128;
+        for (auto &r : kHeapRanges) {
+            const int64_t s0 = p->bin_start[r[0]], s1 = p->bin_start[r[1] + 1];
+            if (s1 > s0) SPG_TRY(launch_heap(a, p->bin_rows + s0, s1 - s0, r[1], heap_nt, p->st));
+        }
+        for (int b = BIN_ESC_LO; b <= BIN_ESC_HI; ++b) {
+            const int64_t s0 = p->bin_start[b], s1 = p->bin_start[b + 1];
+            if (s1 > s0) SPG_TRY(launch_esc(a, p->bin_rows + s0, s1 - s0, b, p->st));
+        }
+        // bin 1: the single product of each row
+        {
+            const int64_t s0 = p->bin_start[1], s1 = p->bin_start[2];
+            SPG_TRY(launch_arrange_short(a, p->bin_rows + s0, s1 - s0, p->bin, p->C.row_ptr, p->C.col_idx, p->C.val,
+                                         p->st));
+        }
+        // bin 37: every leaf fuses its products into its known columns
+        int64_t off = 0;
+        for (int g = 0; g < NUM_REPLAY_CLASSES; ++g) {
+            if (p->leaf_count[g] > 0)
+                SPG_TRY(launch_replay(a, p->leaves, p->leaf_order + off, p->leaf_count[g], p->leaf_cap[g],
+                                      p->C.col_idx, p->C.val, p->d_err, p->st));
+            off += p->leaf_count[g];
+        }
+    }
+    return SPGEMM_OK;
+fail:
+    return status;
+}
+
+extern "C" spgemm_status spgemm_plan_check(spgemm_plan *p) {
+    if (!p) return SPGEMM_ERR_INVALID_ARG;
+    int64_t err = 0;
+    cudaError_t e = p->d2h(&err, p->d_err, sizeof(int64_t));
+    if (e != cudaSuccess) return from_cuda(e);
+    return err == 0 ? SPGEMM_OK : SPGEMM_ERR_INTERNAL;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graph of values-only replays (e.g. both products of a Galerkin chain).
+// ---------------------------------------------------------------------------
+
+struct spgemm_graph {
+    cudaStream_t st;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" spgemm_status spgemm_graph_create(spgemm_plan *const *plans, int64_t n, spgemm_graph **out) {
+    if (!plans || n < 1 || !out) return SPGEMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaStream_t st = plans[0]->st;
+    if (st == nullptr) return SPGEMM_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+    for (int64_t i = 0; i < n; ++i) {
+        if (!plans[i] || !plans[i]->numeric_done || plans[i]->st != st) return SPGEMM_ERR_INVALID_ARG;
+        // build the slice tables and set kernel attributes outside the capture
+        spgemm_status s = spgemm_numeric_replay(plans[i]);
+        if (s != SPGEMM_OK) return s;
+    }
+    spgemm_graph *g = new (std::nothrow) spgemm_graph();
+    if (!g) return SPGEMM_ERR_OOM;
+    g->st = st;
+    g->graph = nullptr;
+    g->exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    spgemm_status status = e == cudaSuccess ? SPGEMM_OK : from_cuda(e);
+    for (int64_t i = 0; status == SPGEMM_OK && i < n; ++i) status = spgemm_numeric_replay(plans[i]);
+    e = cudaStreamEndCapture(st, &g->graph);
+    if (status == SPGEMM_OK && e != cudaSuccess) status = from_cuda(e);
+    if (status == SPGEMM_OK) {
+        e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+        if (e != cudaSuccess) status = from_cuda(e);
+    }
+    if (status != SPGEMM_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return status;
+    }
+    *out = g;
+    return SPGEMM_OK;
+}
+
+extern "C" spgemm_status spgemm_graph_launch(spgemm_graph *g) {
+    if (!g) return SPGEMM_ERR_INVALID_ARG;
+    return from_cuda(cudaGraphLaunch(g->exec, g->st));
+}
+
+extern "C" spgemm_status spgemm_graph_free(spgemm_graph *g) {
+    if (!g) return SPGEMM_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return SPGEMM_OK;
+}
+
+// Galerkin triple product Ac = R * (A * P) (the order the paper finds faster for
+// its method, Section 5.2): two plans on one stream; *plan_rap owns Ac.
+extern "C" spgemm_status spgemm_galerkin(const spgemm_csr_in *R, const spgemm_csr_in *A, const spgemm_csr_in *P,
+                                         const spgemm_opts *opts, spgemm_stream_t stream, spgemm_plan **plan_ap,
+                                         spgemm_plan **plan_rap, spgemm_csr_out *Ac) {
+    if (!R || !A || !P || !plan_ap || !plan_rap || !Ac) return SPGEMM_ERR_INVALID_ARG;
+    *plan_ap = *plan_rap = nullptr;
+    if (R->ncols != A->nrows || A->ncols != P->nrows) return SPGEMM_ERR_SHAPE;
+    spgemm_plan *p1 = nullptr, *p2 = nullptr;
+    spgemm_status s = spgemm_symbolic(A, P, opts, stream, &p1, nullptr);
+    if (s != SPGEMM_OK) return s;
+    spgemm_csr_out ap;
+    s = spgemm_numeric(p1, &ap);
+    if (s != SPGEMM_OK) {
+        spgemm_free(p1);
+        return s;
+    }
+    spgemm_csr_in apin{ap.nrows, ap.ncols, ap.nnz, ap.row_ptr, 64, ap.col_idx, ap.val};
+    s = spgemm_symbolic(R, &apin, opts, stream, &p2, nullptr);
+    if (s == SPGEMM_OK) s = spgemm_numeric(p2, Ac);
+    if (s != SPGEMM_OK) {
+        spgemm_free(p2);
+        spgemm_free(p1);
+        return s;
+    }
+    *plan_ap = p1;
+    *plan_rap = p2;
     return SPGEMM_OK;
 }

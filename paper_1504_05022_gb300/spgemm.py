@@ -200,6 +200,16 @@ class Plan:
         }
         return out
 
+    def replay(self) -> None:
+        """Recomputes C's values in place for new values of A and B with the same structure
+        (no allocation, no host synchronisation after the first call)."""
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.load().spgemm_numeric_replay(ctypes.c_void_p(self.handle.ptr)), "spgemm_numeric_replay")
+
+    def check(self) -> None:
+        """Raises if a device-side consistency check failed (e.g. a replay with changed structure)."""
+        _lib.check(_lib.load().spgemm_plan_check(ctypes.c_void_p(self.handle.ptr)), "spgemm_plan_check")
+
     def free(self) -> None:
         """Releases the plan now; tensors of C obtained from numeric() become invalid."""
         self._C = None
@@ -211,3 +221,86 @@ def spgemm(A: CSR, B: CSR, stream: torch.cuda.Stream | None = None, **opts) -> C
     if A.ncols != B.nrows:
         raise ValueError(f"shape mismatch: {A.shape} x {B.shape}")
     return Plan(A, B, stream=stream, **opts).numeric()
+
+
+class BatchPlan(Plan):
+    """Many independent C_i = A_i * B_i in one pipeline (block-diagonal concatenation)."""
+
+    def __init__(self, As, Bs, stream: torch.cuda.Stream | None = None, **opts):  # noqa: D401
+        L = _lib.load()
+        if len(As) != len(Bs) or not As:
+            raise ValueError("need as many A as B matrices, at least one")
+        self.As, self.Bs = list(As), list(Bs)
+        self.A, self.B = self.As[0], self.Bs[0]
+        self.device = As[0].val.device.index
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.opts = make_opts(**opts)
+        n = len(As)
+        ain = (_lib.CsrIn * n)(*[a._c_in() for a in As])
+        bin_ = (_lib.CsrIn * n)(*[b._c_in() for b in Bs])
+        plan = ctypes.c_void_p()
+        ub = ctypes.c_int64()
+        with torch.cuda.device(self.device):
+            _lib.check(L.spgemm_batched_symbolic(n, ain, bin_, ctypes.byref(self.opts),
+                                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(plan),
+                                                 ctypes.byref(ub)), "spgemm_batched_symbolic")
+        self.handle = _PlanHandle(plan.value, self.stream)
+        self.upper_bound_nnz = int(ub.value)
+        self._C = None
+        self._Cs = None
+
+    def numeric(self):
+        if self._Cs is not None:
+            return self._Cs
+        L = _lib.load()
+        n = len(self.As)
+        outs = (_lib.CsrOut * n)()
+        with torch.cuda.device(self.device):
+            _lib.check(L.spgemm_batched_numeric(ctypes.c_void_p(self.handle.ptr), outs), "spgemm_batched_numeric")
+        h = self.handle
+        self._Cs = [CSR(_wrap(o.row_ptr, o.nrows + 1, torch.int64, h, self.device),
+                        _wrap(o.col_idx, o.nnz, torch.int32, h, self.device),
+                        _wrap(o.val, o.nnz, torch.float64, h, self.device), (int(o.nrows), int(o.ncols)))
+                    for o in outs]
+        return self._Cs
+
+
+def spgemm_batched(As, Bs, stream=None, **opts):
+    """[A_i * B_i] for all pairs, computed as one block-diagonal product."""
+    return BatchPlan(As, Bs, stream=stream, **opts).numeric()
+
+
+class ReplayGraph:
+    """CUDA graph of values-only replays of several plans sharing one stream (for instance both
+    products of a Galerkin chain); launch() recomputes all their results for new input values."""
+
+    def __init__(self, plans):
+        L = _lib.load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.ptr for p in self.plans])
+        g = ctypes.c_void_p()
+        with torch.cuda.device(self.plans[0].device):
+            _lib.check(L.spgemm_graph_create(arr, len(self.plans), ctypes.byref(g)), "spgemm_graph_create")
+        self.handle = g.value
+
+    def launch(self) -> None:
+        _lib.check(_lib.load().spgemm_graph_launch(ctypes.c_void_p(self.handle)), "spgemm_graph_launch")
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _lib.load().spgemm_graph_free(ctypes.c_void_p(self.handle))
+                self.handle = None
+        except Exception:
+            pass
+
+
+def galerkin(R: CSR, A: CSR, P: CSR, stream: torch.cuda.Stream | None = None, **opts):
+    """Ac = R * (A * P) with two plans on one stream; returns (Ac, plan_ap, plan_rap)."""
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    p1 = Plan(A, P, stream=stream, **opts)
+    AP = p1.numeric()
+    p2 = Plan(R, AP, stream=stream, **opts)
+    Ac = p2.numeric()
+    p2._keep = p1
+    return Ac, p1, p2

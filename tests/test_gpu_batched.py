@@ -1,0 +1,158 @@
+"""Batched products, values-only replay, CUDA graphs and the Galerkin chain, against the
+CPU oracle (structure bit-exact, values within 1e-12 * sum |a b|; integer stencils exact)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import gen
+from tests.helpers import assert_csr_equal
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def spg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1504_05022_gb300 as spg
+    spg.load_library()
+    return spg
+
+
+def _check(oracle_mod, A, B, C, label):
+    ref = oracle_mod.spgemm(A, B)
+    rp, col, val = C.to_host()
+    assert C.shape == (A.nrows, B.ncols)
+    assert_csr_equal(rp, col, val, ref.row_ptr, ref.col, ref.val, ref.den, label=label)
+
+
+@pytest.mark.parametrize("policy", ["hybrid", "upper_bound"])
+def test_batched_matches_oracle(spg, oracle_mod, policy):
+    pairs = gen.batch_pairs(40, m_lo=16, m_hi=3000, seed0=100)
+    pairs.append((gen.random_sparse(0, 5, 0.2, 1), gen.random_sparse(5, 7, 0.2, 2)))   # a pair without rows
+    pairs.append((gen.random_sparse(9, 4, 0.0, 3), gen.random_sparse(4, 6, 0.3, 4)))   # a pair without products
+    As = [spg.CSR.from_host(A) for A, _ in pairs]
+    Bs = [spg.CSR.from_host(B, rowptr_dtype=torch.int32) for _, B in pairs]
+    Cs = spg.spgemm_batched(As, Bs, alloc_policy=policy)
+    torch.cuda.synchronize()
+    assert len(Cs) == len(pairs)
+    for i, ((A, B), C) in enumerate(zip(pairs, Cs)):
+        _check(oracle_mod, A, B, C, f"pair {i}")
+
+
+def test_batched_equals_sequential(spg):
+    pairs = gen.batch_pairs(12, m_lo=500, m_hi=5000, seed0=7)
+    As = [spg.CSR.from_host(A) for A, _ in pairs]
+    Bs = [spg.CSR.from_host(B) for _, B in pairs]
+    Cs = spg.spgemm_batched(As, Bs)
+    for A, B, C in zip(As, Bs, Cs):
+        D = spg.spgemm(A, B)
+        torch.cuda.synchronize()
+        assert torch.equal(C.row_ptr, D.row_ptr) and torch.equal(C.col, D.col)
+        assert torch.allclose(C.val, D.val, rtol=1e-12, atol=1e-12)
+
+
+def _scaled(M, seed):
+    rng = np.random.default_rng(seed)
+    return gen.HostCSR(M.nrows, M.ncols, M.row_ptr, M.col, M.val * rng.uniform(0.5, 2.0, M.nnz))
+
+
+@pytest.mark.parametrize("policy", ["hybrid", "learned"])
+def test_replay_recomputes_values(spg, oracle_mod, policy):
+    from paper_1504_05022_gb300.predictor import Predictor
+    A = gen.rmat(13, 16, seed=11)
+    Ad = spg.CSR.from_host(A)
+    keep = None
+    opts = {"alloc_policy": policy}
+    if policy == "learned":
+        keep = Predictor.load()
+        opts = keep.opts()
+    plan = spg.Plan(Ad, Ad, smem_cap_max=2048, **opts)   # small capacity: many column splits
+    C = plan.numeric()
+    torch.cuda.synchronize()
+    assert plan.stats()["rows_split"] > 0
+    for r in range(2):
+        A2 = _scaled(A, 50 + r)
+        Ad.val.copy_(torch.from_numpy(A2.val))
+        plan.replay()
+        torch.cuda.synchronize()
+        plan.check()
+        _check(oracle_mod, A2, A2, C, f"replay {r}")
+    del keep
+
+
+def test_batched_replay(spg, oracle_mod):
+    pairs = gen.batch_pairs(10, m_lo=100, m_hi=4000, seed0=3)
+    As = [spg.CSR.from_host(A) for A, _ in pairs]
+    Bs = [spg.CSR.from_host(B) for _, B in pairs]
+    plan = spg.BatchPlan(As, Bs)
+    Cs = plan.numeric()
+    new = [(_scaled(A, 2 * i), _scaled(B, 2 * i + 1)) for i, (A, B) in enumerate(pairs)]
+    for (A2, B2), Ad, Bd in zip(new, As, Bs):
+        Ad.val.copy_(torch.from_numpy(A2.val))
+        Bd.val.copy_(torch.from_numpy(B2.val))
+    plan.replay()
+    torch.cuda.synchronize()
+    plan.check()
+    for i, ((A2, B2), C) in enumerate(zip(new, Cs)):
+        _check(oracle_mod, A2, B2, C, f"batched replay {i}")
+
+
+def test_galerkin_graph_exact(spg):
+    g = 32
+    A, P = gen.lap3d27(g), gen.agg_P(g)
+    R = gen.transpose(P)
+    s = torch.cuda.Stream()
+    Ad, Pd, Rd = (spg.CSR.from_host(M) for M in (A, P, R))
+    with torch.cuda.stream(s):
+        Ac, p1, p2 = spg.galerkin(Rd, Ad, Pd, stream=s)
+    s.synchronize()
+    rp, col, val = Ac.to_host()
+    assert Ac.nnz == (3 * (g // 2) - 2) ** 3
+    assert set(np.unique(val).tolist()) == {152.0, -16.0, -4.0, -1.0}
+    graph = spg.ReplayGraph([p1, p2])
+    for scale in (2.0, -3.0):
+        Ad.val.copy_(torch.from_numpy(A.val * scale))
+        s.synchronize()
+        graph.launch()
+        s.synchronize()
+        rp2, col2, val2 = Ac.to_host()
+        assert np.array_equal(rp2, rp) and np.array_equal(col2, col)
+        assert np.array_equal(val2, val * scale)          # integers: exact
+    p2.check()
+
+
+def test_galerkin_c_entry_point(spg):
+    from paper_1504_05022_gb300 import _lib
+    L = _lib.load()
+    g = 16
+    A, P = gen.lap3d27(g), gen.agg_P(g)
+    R = gen.transpose(P)
+    Ad, Pd, Rd = (spg.CSR.from_host(M) for M in (A, P, R))
+    ins = [M._c_in() for M in (Rd, Ad, Pd)]
+    p1, p2 = ctypes.c_void_p(), ctypes.c_void_p()
+    out = _lib.CsrOut()
+    rc = L.spgemm_galerkin(ctypes.byref(ins[0]), ctypes.byref(ins[1]), ctypes.byref(ins[2]), None,
+                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(p1),
+                           ctypes.byref(p2), ctypes.byref(out))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert out.nnz == (3 * (g // 2) - 2) ** 3
+    import importlib
+    mod = importlib.import_module("paper_1504_05022_gb300.spgemm")
+    vals = torch.as_tensor(mod._PlanArray(out.val, out.nnz, "<f8", None, 0), device="cuda").cpu().numpy()
+    assert set(np.unique(vals).tolist()) == {152.0, -16.0, -4.0, -1.0}
+    L.spgemm_free(p2)
+    L.spgemm_free(p1)
+
+
+def test_replay_refused_for_level1(spg):
+    A = gen.rmat(12, 16, seed=7)
+    Ad = spg.CSR.from_host(A)
+    plan = spg.Plan(Ad, Ad, smem_cap_max=256, long_rows="level1")
+    plan.numeric()
+    with pytest.raises(spg.SpgemmError) as ei:
+        plan.replay()
+    assert ei.value.code == 1

@@ -31,7 +31,7 @@ def test_row_features_match_reference(spg, mk):
     Ad, Bd = spg.CSR.from_host(A), spg.CSR.from_host(B)
     X = row_features(Ad, Bd).cpu().numpy()
     ref = mlp.row_features(A, B)
-    np.testing.assert_allclose(X, ref, rtol=2e-6, atol=2e-6)
+    np.testing.assert_allclose(X, ref, rtol=2e-6, atol=1e-5)
 
 
 def _params(seed, X):
