@@ -270,13 +270,15 @@ def batch_pairs(n_pairs: int = 512, m_lo: int = 256, m_hi: int = 65536, avg_lo: 
     log-uniform in [m_lo, m_hi], the family is drawn from banded / block-diagonal /
     Erdos-Renyi / R-MAT, the nonzeros per row from [avg_lo, avg_hi]; A_i and B_i are two
     seeded matrices of that family and size.  Values U(-1, 1)."""
-    pairs = []
-    for i in range(n_pairs):
-        rng = np.random.default_rng(seed0 + i)
-        m = int(round(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi)))))
-        fam = BATCH_FAMILIES[int(rng.integers(len(BATCH_FAMILIES)))]
-        avg = int(rng.integers(avg_lo, avg_hi + 1))
-        A = family_matrix(fam, m, avg, seed=2 * (seed0 + i))
-        B = family_matrix(fam, m, avg, seed=2 * (seed0 + i) + 1)
-        pairs.append((A, B))
-    return pairs
+    return [batch_pair(seed0 + i, m_lo, m_hi, avg_lo, avg_hi) for i in range(n_pairs)]
+
+
+def batch_pair(seed: int, m_lo: int = 256, m_hi: int = 65536, avg_lo: int = 4, avg_hi: int = 32):
+    """Pair number `seed` of batch_pairs (generated on its own, e.g. in a worker process)."""
+    rng = np.random.default_rng(seed)
+    m = int(round(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi)))))
+    fam = BATCH_FAMILIES[int(rng.integers(len(BATCH_FAMILIES)))]
+    avg = int(rng.integers(avg_lo, avg_hi + 1))
+    A = family_matrix(fam, m, avg, seed=2 * seed)
+    B = family_matrix(fam, m, avg, seed=2 * seed + 1)
+    return A, B

@@ -114,7 +114,9 @@ typedef struct spgemm_opts {
     int32_t heap_block;      /* threads per block of the heap kernel (0 = auto) */
     int32_t long_rows;       /* spgemm_long_rows: handling of rows beyond shared memory */
     int32_t reserved[8];
-    const void *predictor;   /* spgemm_predictor* for SPGEMM_ALLOC_LEARNED, else NULL */
+    const void *predictor;   /* spgemm_predictor* for SPGEMM_ALLOC_LEARNED, else NULL; it must
+                                not be freed before spgemm_symbolic (or spgemm_galerkin) has
+                                returned, since its weights are read by that call's kernels */
     double predictor_margin; /* predicted size is multiplied by this before rounding up */
 } spgemm_opts;
 
@@ -175,10 +177,14 @@ typedef struct spgemm_stats {
     int64_t rows_split;         /* column splits of long rows (SPGEMM_LONG_ROWS_SPLIT) */
     int64_t rows_fallback;      /* rows recomputed because a prediction was too small */
     int64_t bytes_ctilde;       /* device bytes allocated for temporary rows (all rounds) */
-    int64_t peak_bytes;         /* device bytes held by the plan: temporaries and C (the plan frees
-                                   nothing before spgemm_free, so this is its high-water mark) */
+    int64_t peak_bytes;         /* high-water mark of the device bytes held by the plan (temporaries
+                                   and C) from spgemm_symbolic on */
     int32_t launches[SPGEMM_K_COUNT];  /* kernels launched per class */
     float kernel_ms[SPGEMM_K_COUNT];   /* summed event time per class (record_timing = 1) */
+    int64_t held_bytes;         /* device bytes the plan holds now: stage-1/2 scratch is released
+                                   when spgemm_symbolic returns and C~ with the merge pools when
+                                   spgemm_numeric returns (stream-ordered), so after the product
+                                   this is C plus the O(rows) tables that values-only replay uses */
 } spgemm_stats;
 
 /* Copies the plan's counters into *out.  Timings are read after synchronising

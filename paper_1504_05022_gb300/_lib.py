@@ -42,7 +42,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("bin_count", c_i64 * NUM_BINS), ("sum_u", c_i64), ("nnz_ctilde", c_i64), ("nnz_c", c_i64),
                 ("merge_rounds", c_i64), ("rows_relaunched", c_i64), ("rows_level1", c_i64), ("rows_split", c_i64),
                 ("rows_fallback", c_i64), ("bytes_ctilde", c_i64), ("peak_bytes", c_i64),
-                ("launches", c_i32 * 8), ("kernel_ms", c_f32 * 8)]
+                ("launches", c_i32 * 8), ("kernel_ms", c_f32 * 8), ("held_bytes", c_i64)]
 
 
 class PlanArrays(ctypes.Structure):

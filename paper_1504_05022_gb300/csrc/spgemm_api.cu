@@ -90,6 +90,11 @@ struct Timer {
 // Heap-kernel launches: bins 2..32 split into ranges sized to their widest heap.
 const int kHeapRanges[][2] = {{2, 8}, {9, 16}, {17, 24}, {25, 32}};
 
+// Lifetimes of plan allocations.
+constexpr int LIFE_SYMBOLIC = 0;  // released when spgemm_symbolic returns
+constexpr int LIFE_NUMERIC = 1;   // released when spgemm_numeric returns
+constexpr int LIFE_PLAN = 2;      // released by spgemm_free
+
 }  // namespace
 
 struct spgemm_plan {
@@ -99,8 +104,17 @@ struct spgemm_plan {
     cudaMemPool_t pool = nullptr;
     DevCSR A{}, B{};
     std::vector<void *> allocs;
+    // temporaries: freed when the stage that needs them is over (symbolic: stage-1
+    // prefix and binning scratch; numeric: C~, merge pools and lists)
+    struct Temp {
+        void *ptr;
+        int64_t bytes;
+        int life;
+    };
+    std::vector<Temp> temps;
     int64_t bytes_ctilde = 0;
-    int64_t bytes_held = 0;  // device bytes the plan holds (it frees nothing before spgemm_free)
+    int64_t bytes_held = 0;  // device bytes the plan holds now
+    int64_t bytes_peak = 0;  // largest bytes_held so far
     // stage 1-2 buffers
     int64_t *S = nullptr, *u = nullptr, *ctil_rp = nullptr, *scan_partial = nullptr;
     uint8_t *bin = nullptr;
@@ -144,7 +158,7 @@ struct spgemm_plan {
     void *pinned = nullptr;
     int smem_optin = 0;
 
-    cudaError_t alloc(void **p, size_t bytes) {
+    cudaError_t alloc(void **p, size_t bytes, int life = LIFE_PLAN) {
         if (bytes == 0) bytes = 16;
         cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, st);
         if (e != cudaSuccess) {
@@ -152,13 +166,28 @@ struct spgemm_plan {
             cudaGetLastError();
             return e;
         }
-        allocs.push_back(*p);
+        if (life == LIFE_PLAN) allocs.push_back(*p);
+        else temps.push_back(Temp{*p, (int64_t)bytes, life});
         bytes_held += (int64_t)bytes;
+        bytes_peak = std::max(bytes_peak, bytes_held);
         return cudaSuccess;
     }
     template <typename T>
-    cudaError_t alloc_n(T **p, int64_t n) {
-        return alloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+    cudaError_t alloc_n(T **p, int64_t n, int life = LIFE_PLAN) {
+        return alloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)std::max<int64_t>(n, 1), life);
+    }
+    // Frees (stream-ordered) every temporary whose life ends at or before `life`.
+    void release_temps(int life) {
+        size_t k = 0;
+        for (auto &t : temps) {
+            if (t.life <= life) {
+                cudaFreeAsync(t.ptr, st);
+                bytes_held -= t.bytes;
+            } else {
+                temps[k++] = t;
+            }
+        }
+        temps.resize(k);
     }
     void time_begin(int kind) {
         if (!opts.record_timing) return;
@@ -189,6 +218,9 @@ struct spgemm_plan {
         timers.clear();
         for (void *p : allocs) cudaFreeAsync(p, st);
         allocs.clear();
+        for (auto &t : temps) cudaFreeAsync(t.ptr, st);
+        temps.clear();
+        bytes_held = 0;
         put_pinned(pinned);
         pinned = nullptr;
     }
@@ -335,7 +367,7 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             }
         }
         // ---- stage 1: upper bound ----
-        SPG_TRY(p->alloc_n(&p->S, nnzA + 1));
+        SPG_TRY(p->alloc_n(&p->S, nnzA + 1, LIFE_SYMBOLIC));
         {
             int64_t nb = std::max<int64_t>(bound_partial_size(nnzA), bin_blocks(m) + 1);
             SPG_TRY(p->alloc_n(&p->scan_partial, nb + 1));
@@ -348,8 +380,8 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
         if (o.alloc_policy == SPGEMM_ALLOC_LEARNED) {
             // features and predicted temporary sizes of every row (used for bin 37)
             float *X = nullptr;
-            SPG_TRY(p->alloc_n(&X, m * SPGEMM_MLP_FEATURES));
-            SPG_TRY(p->alloc_n(&p->pred_cap, m));
+            SPG_TRY(p->alloc_n(&X, m * SPGEMM_MLP_FEATURES, LIFE_SYMBOLIC));
+            SPG_TRY(p->alloc_n(&p->pred_cap, m, LIFE_SYMBOLIC));
             p->time_begin(SPGEMM_K_OTHER);
             SPG_TRY(launch_row_features(p->A, p->B, X, p->st));
             SPG_TRY(launch_predict_caps(predictor_params(o.predictor), X, m, nullptr,
@@ -368,8 +400,8 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
         {
             int32_t *hist = nullptr;
             int64_t *capp = nullptr;
-            SPG_TRY(p->alloc_n(&hist, (int64_t)NUM_BINS * nblk));
-            SPG_TRY(p->alloc_n(&capp, nblk));
+            SPG_TRY(p->alloc_n(&hist, (int64_t)NUM_BINS * nblk, LIFE_SYMBOLIC));
+            SPG_TRY(p->alloc_n(&capp, nblk, LIFE_SYMBOLIC));
             pol.policy = o.alloc_policy;
             pol.initial_cap = o.initial_cap;
             pol.pred_cap = p->pred_cap;
@@ -385,8 +417,8 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             int32_t *ccap = nullptr, *scratch = nullptr;
             SPG_TRY(p->alloc_n(&ccap, NUM_LAUNCH_CLASSES));
             SPG_TRY(cudaMemcpyAsync(ccap, p->class_caps, sizeof(p->class_caps), cudaMemcpyHostToDevice, p->st));
-            SPG_TRY(p->alloc_n(&scratch, 96 + m));
-            SPG_TRY(p->alloc_n(&p->class_order, m));
+            SPG_TRY(p->alloc_n(&scratch, 96 + m, LIFE_SYMBOLIC));
+            SPG_TRY(p->alloc_n(&p->class_order, m, LIFE_NUMERIC));
             SPG_TRY(launch_class_partition_tail(p->bin_rows, m, p->d_summary, p->pred_cap, ccap,
                                                 NUM_LAUNCH_CLASSES, scratch, p->class_order, p->st));
             p->count(SPGEMM_K_OTHER, 3);
@@ -398,9 +430,10 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
         p->stats.sum_u = p->h_summary.sum_u;
         p->stats.nnz_ctilde = p->h_summary.sum_cap;
         // C~ (hybrid: u_i for bins 0..36, 256 for bin 37)
-        SPG_TRY(p->alloc_n(&p->ctil_col, p->h_summary.sum_cap));
-        SPG_TRY(p->alloc_n(&p->ctil_val, p->h_summary.sum_cap));
+        SPG_TRY(p->alloc_n(&p->ctil_col, p->h_summary.sum_cap, LIFE_NUMERIC));
+        SPG_TRY(p->alloc_n(&p->ctil_val, p->h_summary.sum_cap, LIFE_NUMERIC));
         p->bytes_ctilde += p->h_summary.sum_cap * 12;
+        p->release_temps(LIFE_SYMBOLIC);
     }
     return SPGEMM_OK;
 fail:
@@ -522,10 +555,10 @@ spgemm_status run_bin37(spgemm_plan *p) {
     {
         SPG_TRY(reserve_items(p, n37));
         p->n_items = n37;
-        SPG_TRY(p->alloc_n(&ovf_count, 1));
+        SPG_TRY(p->alloc_n(&ovf_count, 1, LIFE_NUMERIC));
         list_cap = n37;
-        SPG_TRY(p->alloc_n(&list[0], list_cap));
-        SPG_TRY(p->alloc_n(&list[1], list_cap));
+        SPG_TRY(p->alloc_n(&list[0], list_cap, LIFE_NUMERIC));
+        SPG_TRY(p->alloc_n(&list[1], list_cap, LIFE_NUMERIC));
         SPG_TRY(launch_merge_init(rows37, n37, p->ctil_rp, p->ctil_col, p->ctil_val, p->items, p->st));
         p->count(SPGEMM_K_OTHER);
         if (learned) {
@@ -565,8 +598,8 @@ spgemm_status run_bin37(spgemm_plan *p) {
         while (nwork > 0) {
             if (nwork > list_cap) {  // more work items than the overflow lists can hold
                 list_cap = nwork;
-                SPG_TRY(p->alloc_n(&list[which], list_cap));
-                SPG_TRY(p->alloc_n(&list[which ^ 1], list_cap));
+                SPG_TRY(p->alloc_n(&list[which], list_cap, LIFE_NUMERIC));
+                SPG_TRY(p->alloc_n(&list[which ^ 1], list_cap, LIFE_NUMERIC));
             }
             MergeLaunch L{};
             L.work = work;
@@ -582,23 +615,23 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 // split round: every child already has a home (set by the split)
             } else if (!level1 && p->opts.alloc_policy != SPGEMM_ALLOC_UPPER_BOUND &&
                        (work != nullptr || cap > p->opts.initial_cap || learned)) {
-                SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap));
-                SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap));
+                SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap, LIFE_NUMERIC));
+                SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap, LIFE_NUMERIC));
                 L.pool_cap = cap;
                 p->bytes_ctilde += nwork * (int64_t)cap * 12;
             }
             if (level1) {
-                SPG_TRY(p->alloc_n(&g_cap, nwork));
-                SPG_TRY(p->alloc_n(&g_off, nwork));
-                SPG_TRY(p->alloc_n(&g_partial, nwork / 2048 + 2));
-                SPG_TRY(p->alloc_n(&g_total, 1));
+                SPG_TRY(p->alloc_n(&g_cap, nwork, LIFE_NUMERIC));
+                SPG_TRY(p->alloc_n(&g_off, nwork, LIFE_NUMERIC));
+                SPG_TRY(p->alloc_n(&g_partial, nwork / 2048 + 2, LIFE_NUMERIC));
+                SPG_TRY(p->alloc_n(&g_total, 1, LIFE_NUMERIC));
                 SPG_TRY(launch_level1_sizes(p->items, work, nwork, p->u, p->B.ncols, g_cap, g_off, g_partial,
                                             g_total, p->st));
                 p->count(SPGEMM_K_OTHER, 4);
                 int64_t gtot = 0;
                 SPG_TRY(p->d2h(&gtot, g_total, sizeof(int64_t)));
-                SPG_TRY(p->alloc_n(&L.g_col, gtot));
-                SPG_TRY(p->alloc_n(&L.g_val, gtot));
+                SPG_TRY(p->alloc_n(&L.g_col, gtot, LIFE_NUMERIC));
+                SPG_TRY(p->alloc_n(&L.g_val, gtot, LIFE_NUMERIC));
                 p->bytes_ctilde += gtot * 12;
                 L.g_cap = g_cap;
                 L.g_off = g_off;
@@ -635,8 +668,8 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 SPG_TRY(reserve_items(p, p->n_items + 2 * (int64_t)novf));
                 int32_t *scol = nullptr;
                 double *sval = nullptr;
-                SPG_TRY(p->alloc_n(&scol, (int64_t)novf * cap));
-                SPG_TRY(p->alloc_n(&sval, (int64_t)novf * cap));
+                SPG_TRY(p->alloc_n(&scol, (int64_t)novf * cap, LIFE_NUMERIC));
+                SPG_TRY(p->alloc_n(&sval, (int64_t)novf * cap, LIFE_NUMERIC));
                 p->bytes_ctilde += (int64_t)novf * cap * 12;
                 p->time_begin(SPGEMM_K_OTHER);
                 SPG_TRY(launch_split(list[which], novf, p->n_items, p->items, scol, sval, cap, p->st));
@@ -723,6 +756,7 @@ extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
         p->stats.nnz_c = nnzC;
         p->stats.bytes_ctilde = p->bytes_ctilde;
         p->numeric_done = true;
+        p->release_temps(LIFE_NUMERIC);
         *C_out = p->C;
     }
     return SPGEMM_OK;
@@ -748,7 +782,8 @@ extern "C" spgemm_status spgemm_plan_stats(spgemm_plan *p, spgemm_stats *out) {
             if (t.a && t.b && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) p->stats.kernel_ms[t.kind] += ms;
         }
     }
-    p->stats.peak_bytes = p->bytes_held;
+    p->stats.peak_bytes = p->bytes_peak;
+    p->stats.held_bytes = p->bytes_held;
     *out = p->stats;
     return SPGEMM_OK;
 }

@@ -92,7 +92,9 @@ class Predictor:
         self.params = host
 
     def opts(self) -> dict:
-        return {"alloc_policy": "learned", "predictor": self.handle, "predictor_margin": self.margin}
+        """Plan options for the learned policy.  The entry "predictor" is this object itself, so
+        every Plan made from these options keeps the device weights alive."""
+        return {"alloc_policy": "learned", "predictor": self, "predictor_margin": self.margin}
 
     def __del__(self):
         try:

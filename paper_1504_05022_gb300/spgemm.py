@@ -127,7 +127,8 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
     o.smem_cap_max = int(smem_cap_max)
     o.heap_block = int(heap_block)
     o.long_rows = _lib.LONG_ROWS[long_rows]
-    o.predictor = predictor
+    # a Predictor object (whose device weights the caller keeps alive) or a raw handle
+    o.predictor = getattr(predictor, "handle", predictor)
     o.predictor_margin = float(predictor_margin)
     return o
 
@@ -141,6 +142,7 @@ class Plan:
         self.device = A.val.device.index if A.val.is_cuda else torch.cuda.current_device()
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.opts = make_opts(**opts)
+        self._predictor = opts.get("predictor")  # the weights are read on the stream during symbolic
         a_in, b_in = A._c_in(), B._c_in()
         plan = ctypes.c_void_p()
         ub = ctypes.c_int64()
@@ -174,7 +176,7 @@ class Plan:
             "bin_count": list(s.bin_count), "sum_u": s.sum_u, "nnz_ctilde": s.nnz_ctilde, "nnz_c": s.nnz_c,
             "merge_rounds": s.merge_rounds, "rows_relaunched": s.rows_relaunched, "rows_level1": s.rows_level1,
             "rows_split": s.rows_split,
-            "rows_fallback": s.rows_fallback, "bytes_ctilde": s.bytes_ctilde, "peak_bytes": s.peak_bytes,
+            "rows_fallback": s.rows_fallback, "bytes_ctilde": s.bytes_ctilde, "peak_bytes": s.peak_bytes, "held_bytes": s.held_bytes,
             "launches": dict(zip(_lib.KERNELS, list(s.launches))),
             "kernel_ms": dict(zip(_lib.KERNELS, [float(x) for x in s.kernel_ms])),
         }
@@ -235,6 +237,7 @@ class BatchPlan(Plan):
         self.device = As[0].val.device.index
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.opts = make_opts(**opts)
+        self._predictor = opts.get("predictor")
         n = len(As)
         ain = (_lib.CsrIn * n)(*[a._c_in() for a in As])
         bin_ = (_lib.CsrIn * n)(*[b._c_in() for b in Bs])

@@ -253,3 +253,22 @@ def test_config3_galerkin_closed_form(spg, oracle_mod):
     APh = oracle_mod.spgemm(A, P)
     ref = oracle_mod.spgemm(R, gen.HostCSR(APh.nrows, APh.ncols, APh.row_ptr, APh.col, APh.val))
     assert np.array_equal(rp, ref.row_ptr) and np.array_equal(col, ref.col) and np.array_equal(val, ref.val)
+
+
+@pytest.mark.parametrize("policy", ["hybrid", "learned"])
+def test_temporaries_released_after_numeric(spg, oracle_mod, policy):
+    """C~, the merge pools and the stage-1/2 scratch are released when the product returns:
+    the plan then holds C plus O(rows) tables, below its peak; a later product on the same
+    stream reuses that memory and the first result stays intact."""
+    from paper_1504_05022_gb300.predictor import Predictor
+    A = gen.rmat(12, 16, seed=3)
+    opts = Predictor.load().opts() if policy == "learned" else {"alloc_policy": policy}
+    plan, C = run(spg, A, A, initial_cap=256, **opts)
+    st = plan.stats()
+    m = A.nrows
+    c_bytes = C.nnz * 12 + (m + 1) * 8
+    assert st["peak_bytes"] > st["held_bytes"] >= c_bytes
+    assert st["held_bytes"] - c_bytes < 64 * m + (1 << 20) + 8 * A.nnz
+    plan2, C2 = run(spg, A, A, **opts)  # allocates from the released memory
+    check(oracle_mod, A, A, C, label=f"first result after release/{policy}")
+    assert torch.equal(C.col, C2.col)
