@@ -34,6 +34,8 @@ WORKLOADS = {
     "galerkin64": "Ac = R*(A*P), A = 27-point Laplacian on 64^3, P = 2x2x2 aggregation, R = P^T",
     "rmat20x8": "C = A*A, A = R-MAT 2^20 x 2^20, 8 samples/row, U(-1,1), seed 1",
     "rmat14x16": "C = A*A, A = R-MAT 2^14 x 2^14, 16 samples/row, U(-1,1), seed 1 (small profiling case)",
+    "batch512": "512 independent C_i = A_i*B_i, rows log-uniform in [256, 65536], family per pair from "
+                "{banded, block-diagonal, Erdos-Renyi, R-MAT}, 4-32 nnz/row, U(-1,1), seed = pair index",
 }
 
 
@@ -51,12 +53,37 @@ def make_workload(name):
     if name == "rmat14x16":
         A = gen.rmat(14, 16, seed=1)
         return [(A, A)]
+    if name == "batch512":
+        return batch_pairs_parallel(512)
     if name == "galerkin64":
         A = gen.lap3d27(64)
         P = gen.agg_P(64)
         R = gen.transpose(P)
         return [(A, P), (R, None)]  # second product multiplies R by the first result
     raise ValueError(name)
+
+
+def _batch_pair(i):
+    import gen
+    return gen.batch_pair(i)
+
+
+def batch_pairs_parallel(n):
+    """gen.batch_pairs(n), generated by a spawned process pool (pair i depends only on seed i)."""
+    import multiprocessing as mp
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_batch_pair, range(n), chunksize=1)
+
+
+class _Cat:
+    """Row pointers of the block-diagonal concatenation of the batch's A (for the byte model)."""
+
+    def __init__(self, mats):
+        lens = np.concatenate([np.diff(M.row_ptr) for M in mats])
+        self.row_ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        self.nrows = int(lens.size)
+        self.nnz = int(self.row_ptr[-1])
 
 
 def src_digest(files):
@@ -230,6 +257,203 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
     return res
 
 
+def time_steps(args, stream, flush, step, world=1):
+    """W untimed warm-up calls of step(), then K calls each bracketed by CUDA events on
+    `stream`, L2 flushed (512 MB write) before each, outside the events.  step() returns an
+    object kept alive until the next call.  Returns the per-step milliseconds (max over ranks)."""
+    import torch
+    keep = None
+    for _ in range(args.warmup):
+        keep = step()
+        del keep
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    times = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        ev[k][0].record(stream)
+        keep = step()
+        ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        times.append(ev[k][0].elapsed_time(ev[k][1]))
+        if k < args.steps - 1:
+            del keep
+            keep = None
+    ms = float(np.mean(times))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=torch.device("cuda", torch.cuda.current_device()))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, keep
+
+
+def galerkin_graph(args, spg, dev, stream, flush, opts, world):
+    """Galerkin chain Ac = R*(A*P) in both timings: the values-only replay of the two plans
+    captured in one CUDA graph (the structure of A*P and Ac is reused), and the other
+    association (R*A)*P as two plain calls."""
+    import gen
+    import torch
+    A = gen.lap3d27(64)
+    P = gen.agg_P(64)
+    R = gen.transpose(P)
+    Ad, Pd, Rd = (spg.CSR.from_host(M, device=dev, rowptr_dtype=torch.int32) for M in (A, P, R))
+    stream = torch.cuda.Stream(dev)  # a graph is captured from a created stream, not the legacy one
+    torch.cuda.synchronize()
+    Ac, p1, p2 = spg.galerkin(Rd, Ad, Pd, stream=stream, **opts)
+    products = p1.upper_bound_nnz + p2.upper_bound_nnz
+    g = spg.ReplayGraph([p1, p2])
+
+    def replay():
+        g.launch()
+
+    ms_graph, _ = time_steps(args, stream, flush, replay, world)
+    p2.check()
+
+    def ra_p():
+        q1 = spg.Plan(Rd, Ad, stream=stream, **opts)
+        RA = q1.numeric()
+        q2 = spg.Plan(RA, Pd, stream=stream, **opts)
+        q2.numeric()
+        return q1, q2, RA
+
+    ms_rap, keep = time_steps(args, stream, flush, ra_p, world)
+    prod_rap = keep[0].upper_bound_nnz + keep[1].upper_bound_nnz
+    nnz_ac = int(Ac.nnz)
+    del keep, g, Ac, p1, p2
+    torch.cuda.synchronize()
+    return {"graph_replay": {"value": 2.0 * products * world / (ms_graph * 1e-3) / 1e9, "unit": "GFLOP/s",
+                             "ms_per_step": ms_graph, "products": int(products), "launches_per_step": None,
+                             "note": "values-only replay of R*(A*P) (structure of A*P and Ac reused) in one CUDA graph"},
+            "rA_then_P": {"value": 2.0 * prod_rap * world / (ms_rap * 1e-3) / 1e9, "unit": "GFLOP/s",
+                          "ms_per_step": ms_rap, "products": int(prod_rap)},
+            "nnz_Ac": nnz_ac}
+
+
+def run_batch(args, world, device):
+    """512 independent products: one batched pipeline (block-diagonal concatenation) under the
+    learned and the plain policy, 512 sequential plain calls, and the batched plan's
+    values-only replay captured in a CUDA graph."""
+    pairs = make_workload("batch512")  # generated by spawned workers before CUDA is touched
+    import torch
+
+    import paper_1504_05022_gb300 as spg
+    spg.load_library()
+    dev = torch.device(f"cuda:{device}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    As = [spg.CSR.from_host(A, device=dev, rowptr_dtype=torch.int32) for A, _ in pairs]
+    Bs = [spg.CSR.from_host(B, device=dev, rowptr_dtype=torch.int32) for _, B in pairs]
+    products = int(sum(_products_ab(A, B) for A, B in pairs))
+    res = {}
+
+    def batched(policy, clocks=False):
+        opts, keep = policy_opts(policy)
+        opts = dict(opts, record_timing=True)
+
+        def step():
+            bp = spg.BatchPlan(As, Bs, stream=stream, **opts)
+            bp.numeric()
+            return bp
+        clk = ClockSampler(dev.index) if clocks else None
+        if clk:
+            clk.__enter__()
+        ms, bp = time_steps(args, stream, flush, step, world)
+        if clk:
+            clk.__exit__(None, None, None)
+        st = bp.stats()
+        out = {"value": 2.0 * products * world / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+               "peak_bytes": int(st["peak_bytes"]), "held_bytes_after": int(st["held_bytes"]),
+               "launches_per_step": int(sum(st["launches"].values())), "kms": st["kernel_ms"],
+               "rows_bin37": int(st["bin_count"][37]), "rows_fallback": int(st["rows_fallback"]),
+               "merge_rounds": int(st["merge_rounds"]), "clocks": clk.summary() if clk else None}
+        return out, bp, keep
+
+    def sequential(policy):
+        opts, keep = policy_opts(policy)
+        stats = {}
+
+        def step():
+            plans = []
+            for A, B in zip(As, Bs):
+                p = spg.Plan(A, B, stream=stream, **opts)
+                p.numeric()
+                plans.append(p)
+            return plans
+        ms, plans = time_steps(args, stream, flush, step, world)
+        held, peak, launches = 0, 0, 0
+        for p in plans:  # results stay resident, so call i peaks on top of results 0..i-1
+            st = p.stats()
+            peak = max(peak, held + st["peak_bytes"])
+            held += st["held_bytes"]
+            launches += sum(st["launches"].values())
+        stats.update({"value": 2.0 * products * world / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                      "peak_bytes": int(peak), "launches_per_step": int(launches)})
+        del plans, keep
+        return stats
+
+    head = args.policy
+    main, bp, keep = batched(head, clocks=True)
+    arrays = bp.arrays()
+    del bp
+    torch.cuda.synchronize()
+    for p in ("hybrid",):
+        if p != head:
+            r, b2, k2 = batched(p)
+            del b2, k2
+            res["batched_" + p] = r
+    torch.cuda.synchronize()
+    res["sequential_hybrid"] = sequential("hybrid")
+    torch.cuda.synchronize()
+    # values-only replay of the whole batch in one CUDA graph
+    opts, keep_g = policy_opts(head)
+    gstream = torch.cuda.Stream(dev)  # a graph is captured from a created stream, not the legacy one
+    torch.cuda.synchronize()
+    gp = spg.BatchPlan(As, Bs, stream=gstream, **opts)
+    gp.numeric()
+    g = spg.ReplayGraph([gp])
+    ms_g, _ = time_steps(args, gstream, flush, g.launch, world)
+    gp.check()
+    res["graph_replay"] = {"value": 2.0 * products * world / (ms_g * 1e-3) / 1e9, "ms_per_step": ms_g,
+                           "note": "values-only replay (structure reused) of the batched plan, one CUDA graph"}
+    del g, gp, keep_g
+    torch.cuda.synchronize()
+    m = {"policy": head, "kms": main["kms"], "st_all": [{"launches": {}}], "arrays": [arrays]}
+    cat = _Cat([A for A, _ in pairs])
+    rl = roofline(args, [(cat, cat)], m)
+    rl["launches_per_step"] = None
+    main_clocks = main.pop("clocks")
+    out = {
+        "metric": "FP64 SpGEMM GFLOP/s (2*products/s)",
+        "value": main["value"], "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded generator)",
+        "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "alloc_policy": head,
+                   "mode": "batched (block-diagonal concatenation, one pipeline)", "pairs": len(pairs),
+                   "products_per_step": products, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": rl,
+        "e2e": {"value": None, "unit": "GFLOP/s",
+                "note": "not measured for this workload: the 512 results need more pinned host memory than a bench run should take"},
+        "gpu_launches": int(main["launches_per_step"] * args.steps),
+        "kernel_ms_per_step": main["kms"],
+        "memory": {"peak_bytes": main["peak_bytes"], "held_bytes_after": main["held_bytes_after"],
+                   "rows_bin37": main["rows_bin37"], "rows_fallback": main["rows_fallback"],
+                   "misprediction_rate": (main["rows_fallback"] / main["rows_bin37"])
+                   if head == "learned" and main["rows_bin37"] else None},
+        "compare": res,
+        "clocks": main_clocks,
+    }
+    return out, pairs
+
+
+def _products_ab(A, B):
+    blen = np.diff(B.row_ptr)
+    return int(blen[A.col].sum())
+
+
 def roofline(args, pairs, m):
     """Roofline of the kernel class with the largest measured time (HBM-bound model)."""
     peaks = {}
@@ -296,6 +520,7 @@ def run_ours(args, rank, world, device):
     cmp = {p: measure(args, spg, pairs, dev, stream, p, flush, world) for p in others}
     e2e_opts, e2e_keep = policy_opts(head)  # keeps the predictor alive during the e2e runs
     e2e = run_e2e(args, spg, pairs, dev, stream, e2e_opts)
+    chain = galerkin_graph(args, spg, dev, stream, flush, e2e_opts, world) if args.workload == "galerkin64" else None
     del e2e_keep
 
     def brief(m):
@@ -324,6 +549,8 @@ def run_ours(args, rank, world, device):
         "compare": {p: brief(m) for p, m in cmp.items()},
         "clocks": main_m["clocks"],
     }
+    if chain is not None:
+        out["compare"].update(chain)
     return out
 
 
@@ -369,11 +596,13 @@ def _products(A):
     return blen[A.col].sum()
 
 
-def run_cpu_baseline(args, budget_s=20.0):
+def run_cpu_baseline(args, budget_s=20.0, pairs=None):
     """The oracle, as it stands, on the host cores: repeated full passes over the workload
     (or a row sample when a pass is too long), median time, GFLOP/s on the products computed."""
     import oracle
-    pairs = make_workload(args.workload)
+    pairs = make_workload(args.workload) if pairs is None else pairs
+    if args.workload == "batch512":
+        return _cpu_baseline_batch(pairs, budget_s)
     A, B = pairs[0]
     B = A if B is None else B
     nthreads = oracle.num_threads()
@@ -402,6 +631,32 @@ def run_cpu_baseline(args, budget_s=20.0):
     return {"value": 2.0 * prods / t / 1e9, "unit": "GFLOP/s", "cores": nthreads, "kind": "oracle",
             "sample": f"{sample}; {prods} products; median of {len(times)} passes",
             "ms_per_pass": t * 1e3}
+
+
+def _cpu_baseline_batch(pairs, budget_s):
+    """Oracle on a seeded random sample of whole pairs of the batch (bounded product count)."""
+    import oracle
+    nthreads = oracle.num_threads()
+    cap_products = int(20e6 * nthreads * budget_s / 3)
+    order = np.random.default_rng(0).permutation(len(pairs))
+    sel, prods = [], 0
+    for i in order:
+        u = _products_ab(*pairs[i])
+        if prods + u > cap_products and sel:
+            continue
+        sel.append(int(i))
+        prods += u
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < 5 and (time.perf_counter() - t_start) < budget_s:
+        t0 = time.perf_counter()
+        for i in sel:
+            oracle.spgemm_rows(pairs[i][0], pairs[i][1], None, nthreads=nthreads)
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    return {"value": 2.0 * prods / t / 1e9, "unit": "GFLOP/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"{len(sel)} of {len(pairs)} pairs (seeded random order, products capped); {prods} products; "
+                      f"median of {len(times)} passes", "ms_per_pass": t * 1e3}
 
 
 def main():
@@ -438,10 +693,14 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    out = run_ours(args, rank, world, local)
+    pairs = None
+    if args.workload == "batch512":
+        out, pairs = run_batch(args, world, local)
+    else:
+        out = run_ours(args, rank, world, local)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            out["cpu_baseline"] = run_cpu_baseline(args)
+            out["cpu_baseline"] = run_cpu_baseline(args, pairs=pairs)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

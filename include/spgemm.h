@@ -218,12 +218,14 @@ spgemm_status spgemm_plan_arrays_get(spgemm_plan *plan, spgemm_plan_arrays *out)
  * arrays of npairs descriptors of device matrices) computed as one product of
  * block-diagonal matrices, diag(A_1..A_n) * diag(B_1..B_n) = diag(A_1 B_1 ..
  * A_n B_n), so every stage -- including each per-bin kernel of stage 3 -- runs
- * once for the rows of all pairs.  Requires sum m_i, sum k_i, sum n_i <= 2^31-1.
- * spgemm_batched_numeric fills C_out[0..npairs) with views owned by the plan:
- * each C_i has its own int64 row pointers (starting at 0) and columns; values
- * share the plan's concatenated result.  spgemm_free releases everything.  The
- * inputs are copied into the plan at symbolic time (their values are read again
- * by spgemm_numeric_replay).
+ * once for the rows of all pairs.  B_i keeps its own column numbers (a row of
+ * C_i only combines rows of B_i), so the concatenated C holds every C_i with its
+ * own columns.  Requires sum m_i, sum k_i <= 2^31-1.  spgemm_batched_numeric
+ * fills C_out[0..npairs) with views owned by the plan: each C_i has its own
+ * int64 row pointers (starting at 0); its columns and values are slices of the
+ * plan's concatenated result.  spgemm_free releases everything.  The inputs are
+ * copied into the plan at symbolic time (their values are read again by
+ * spgemm_numeric_replay).
  */
 spgemm_status spgemm_batched_symbolic(int64_t npairs, const spgemm_csr_in *A, const spgemm_csr_in *B,
                                       const spgemm_opts *opts, spgemm_stream_t stream,

@@ -1,10 +1,12 @@
 // Batched products: many independent C_i = A_i * B_i computed as one product of
 // block-diagonal matrices, diag(A_1..A_n) * diag(B_1..B_n) = diag(A_1 B_1 .. A_n B_n).
-// The concatenation gives A_i's columns an offset of sum_{j<i} k_j and B_i's
-// columns an offset of sum_{j<i} n_j, so every stage of the framework runs once
-// over the rows of all pairs (one launch per bin for the whole batch).  The
-// split step gives each C_i its own row pointers and columns; its values are a
-// view into the concatenated C.
+// The concatenation gives A_i's columns an offset of sum_{j<i} k_j, so they
+// select B_i's rows; B_i's columns keep their own numbering (0 .. n_i - 1): a
+// row of C_i only ever combines rows of B_i, so no row mixes columns of two
+// pairs, and the concatenated C holds every C_i with its own column numbers.
+// Every stage of the framework runs once over the rows of all pairs (one launch
+// per bin for the whole batch).  The split step only rebases each C_i's row
+// pointers; its columns and values are views into the concatenated C.
 #include "internal.h"
 #include "common.cuh"
 
@@ -42,7 +44,7 @@ __global__ void k_concat_rp(const PairDesc *d, int64_t npairs, const int64_t *mo
     }
 }
 
-// Entries of the concatenated A and B (columns shifted into the pair's block).
+// Entries of the concatenated A (columns shifted into the pair's block) and B.
 __global__ void k_concat_entries(const PairDesc *d, int64_t npairs, const int64_t *annz_off, const int64_t *bnnz_off,
                                  int64_t annz, int64_t bnnz, int32_t *a_col, double *a_val, int32_t *b_col,
                                  double *b_val, int values_only) {
@@ -56,7 +58,7 @@ __global__ void k_concat_entries(const PairDesc *d, int64_t npairs, const int64_
     if (t < bnnz) {
         const int i = find_pair(bnnz_off, npairs, t);
         const int64_t l = t - d[i].bnnz_off;
-        if (!values_only) b_col[t] = d[i].b_col[l] + (int32_t)d[i].noff;
+        if (!values_only) b_col[t] = d[i].b_col[l];
         b_val[t] = d[i].b_val[l];
     }
 }
@@ -79,10 +81,8 @@ cudaError_t launch_concat(const PairDesc *d, int64_t npairs, const int64_t *moff
     return cudaGetLastError();
 }
 
-// C_i's row pointers (rebased to 0; pair i occupies rp_out[moff_i + i .. moff_i + i + m_i])
-// and columns (shifted back out of the pair's block).
-__global__ void k_split_out(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *c_rp,
-                            const int32_t *c_col, int64_t M, int64_t nnz, int64_t *rp_out, int32_t *col_out) {
+// C_i's row pointers, rebased to 0; pair i occupies rp_out[moff_i + i .. moff_i + i + m_i].
+__global__ void k_split_out(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *rp_out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < M + npairs) {
         // entry t of the rebased row-pointer array: pair i holds m_i + 1 entries starting at moff_i + i
@@ -95,24 +95,13 @@ __global__ void k_split_out(const PairDesc *d, int64_t npairs, const int64_t *mo
         const int64_t r = t - (d[i].moff + i);
         rp_out[t] = c_rp[d[i].moff + r] - c_rp[d[i].moff];
     }
-    if (t < nnz) {
-        // the pair of entry t: largest i with c_rp[moff_i] <= t among pairs with rows
-        int64_t lo = 0, hi = npairs - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (c_rp[d[mid].moff] <= t) lo = mid; else hi = mid - 1;
-        }
-        col_out[t] = c_col[t] - (int32_t)d[lo].noff;
-    }
 }
 
-cudaError_t launch_split_out(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *c_rp,
-                             const int32_t *c_col, int64_t M, int64_t nnz, int64_t *rp_out, int32_t *col_out,
+cudaError_t launch_split_out(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *rp_out,
                              cudaStream_t st) {
-    (void)moff;
-    const int64_t n = (M + npairs > nnz) ? M + npairs : nnz;
+    const int64_t n = M + npairs;
     if (n <= 0) return cudaSuccess;
-    k_split_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, npairs, moff, c_rp, c_col, M, nnz, rp_out, col_out);
+    k_split_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, npairs, c_rp, M, rp_out);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@ constexpr int NUM_BINS = 38;
 constexpr int BIN_HEAP_LO = 2, BIN_HEAP_HI = 32;  // bin group 3 (Section 4.1)
 constexpr int BIN_ESC_LO = 33, BIN_ESC_HI = 36;   // bin group 4
 constexpr int BIN_MERGE = 37;                     // bin group 5
+constexpr int64_t BIN_MERGE_MIN_U = 512;          // bin 37 holds the rows with u_i > 512 (Algorithm 3)
 
 enum AllocPolicy { POLICY_HYBRID = 0, POLICY_UPPER_BOUND = 1, POLICY_LEARNED = 2 };
 
@@ -56,9 +57,13 @@ cudaError_t launch_binning(int64_t m, const int64_t *arp, const int64_t *S,
                            BinSummary *summary, cudaStream_t st);
 
 // ---- learned preallocation (predictor.cu) ----
-cudaError_t launch_row_features(const DevCSR &A, const DevCSR &B, float *X, cudaStream_t st);
+// Row features (warp per row).  With the stage-1 prefix S, rows with u_i <= u_min are skipped.
+cudaError_t launch_row_features(const DevCSR &A, const DevCSR &B, float *X, cudaStream_t st,
+                                const int64_t *S = nullptr, int64_t u_min = 0);
+// Predicted temporary size per row (0 for rows skipped through arp/S/u_min).
 cudaError_t launch_predict_caps(const float *params, const float *X, int64_t m, const int64_t *u, float margin,
-                                int32_t min_cap, int32_t *pred_cap, cudaStream_t st);
+                                int32_t min_cap, int32_t *pred_cap, cudaStream_t st, const int64_t *arp = nullptr,
+                                const int64_t *S = nullptr, int64_t u_min = 0);
 // Groups the bin-37 items (tail of bin_rows, size read from summary) by launch
 // class; scratch: 96 + m int32; order: item indices grouped by class; counts go
 // to summary->class_count.
@@ -159,7 +164,7 @@ struct PairDesc {
     const double *a_val, *b_val;
     int32_t a_bits, b_bits;
     int64_t m, k, n;             // A_i is m x k, B_i is k x n
-    int64_t moff, koff, noff;    // row/column offsets in the concatenation
+    int64_t moff, koff;          // row offset of A_i and B_i in the concatenation
     int64_t annz_off, bnnz_off;  // entry offsets
     int64_t annz, bnnz;
 };
@@ -169,8 +174,7 @@ cudaError_t launch_concat(const PairDesc *d, int64_t npairs, const int64_t *moff
                           double *b_val, bool values_only, cudaStream_t st);
 cudaError_t launch_gather_first(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *out,
                                 cudaStream_t st);
-cudaError_t launch_split_out(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *c_rp,
-                             const int32_t *c_col, int64_t M, int64_t nnz, int64_t *rp_out, int32_t *col_out,
+cudaError_t launch_split_out(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *rp_out,
                              cudaStream_t st);
 
 // ---- stage 4 (arrange.cu) ----

@@ -142,7 +142,6 @@ struct spgemm_plan {
     int32_t *cat_a_col = nullptr, *cat_b_col = nullptr;
     double *cat_a_val = nullptr, *cat_b_val = nullptr;
     int64_t *split_rp = nullptr;
-    int32_t *split_col = nullptr;
     std::vector<spgemm_csr_out> batch_out;
     // values-only replay
     bool replay_ready = false;
@@ -383,10 +382,10 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             SPG_TRY(p->alloc_n(&X, m * SPGEMM_MLP_FEATURES, LIFE_SYMBOLIC));
             SPG_TRY(p->alloc_n(&p->pred_cap, m, LIFE_SYMBOLIC));
             p->time_begin(SPGEMM_K_OTHER);
-            SPG_TRY(launch_row_features(p->A, p->B, X, p->st));
+            SPG_TRY(launch_row_features(p->A, p->B, X, p->st, p->S, BIN_MERGE_MIN_U));
             SPG_TRY(launch_predict_caps(predictor_params(o.predictor), X, m, nullptr,
                                         (float)(o.predictor_margin > 0 ? o.predictor_margin : 1.0),
-                                        o.initial_cap, p->pred_cap, p->st));
+                                        o.initial_cap, p->pred_cap, p->st, p->A.rp, p->S, BIN_MERGE_MIN_U));
             p->time_end();
             p->count(SPGEMM_K_OTHER, 2);
         }
@@ -526,58 +525,199 @@ cudaError_t reserve_items(spgemm_plan *p, int64_t need) {
     return cudaSuccess;
 }
 
-// Bin group 5: the merge kernel over all bin-37 rows, then the progressive
-// rounds: items that overflowed are relaunched with twice the capacity (and a
-// twice as large home); at the largest shared-memory capacity an overflowing
-// item is split by column (default) or finished with a level-1 sequence.
+// Progressive rounds (Section 4.1): runs `nwork` work items (work_in, or the
+// items work_base.. when work_in is null) at capacity `cap`; items that
+// overflow are relaunched with twice the capacity in a fresh pool slot, and at
+// the largest shared-memory capacity an overflowing item is split by column
+// (default) or finished with a level-1 sequence.  With split_first the items have
+// already overflowed at the largest capacity and go straight to that step.
+spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t work_base, int64_t nwork, int cap,
+                              bool split_first, int32_t *ovf_count) {
+    spgemm_status status = SPGEMM_OK;
+    if (nwork <= 0) return SPGEMM_OK;
+    StageArgs a = stage_args(p);
+    const int batch = p->batch;
+    const int capmax = p->capmax;
+    const bool use_level1 = p->opts.long_rows == SPGEMM_LONG_ROWS_LEVEL1;
+    const bool learned = p->opts.alloc_policy == SPGEMM_ALLOC_LEARNED;
+    int32_t *list[2] = {nullptr, nullptr};
+    int64_t list_cap = nwork;
+    int64_t *g_cap = nullptr, *g_off = nullptr, *g_partial = nullptr, *g_total = nullptr;
+    const int32_t *work = work_in;
+    int which = 0;
+    bool level1 = false;
+    bool pending_split = split_first;
+    if (pending_split && use_level1) {
+        level1 = true;
+        pending_split = false;
+    }
+    {
+        SPG_TRY(p->alloc_n(&list[0], list_cap, LIFE_NUMERIC));
+        SPG_TRY(p->alloc_n(&list[1], list_cap, LIFE_NUMERIC));
+        while (nwork > 0) {
+            int64_t novf = 0;
+            const int32_t *ovf_items = nullptr;
+            if (pending_split) {
+                novf = nwork;
+                ovf_items = work;
+                pending_split = false;
+            } else {
+                if (nwork > list_cap) {  // more work items than the overflow lists can hold
+                    list_cap = nwork;
+                    SPG_TRY(p->alloc_n(&list[which], list_cap, LIFE_NUMERIC));
+                    SPG_TRY(p->alloc_n(&list[which ^ 1], list_cap, LIFE_NUMERIC));
+                }
+                MergeLaunch L{};
+                L.work = work;
+                L.work_base = work_base;
+                L.nwork = nwork;
+                L.cap = cap;
+                L.batch = std::min(std::min(batch, cap), merge_batch_limit(cap));
+                L.level1 = level1 ? 1 : 0;
+                L.ovf_list = list[which];
+                L.ovf_count = ovf_count;
+                L.err = p->d_err;
+                if (!level1 && work == nullptr && work_base > 0) {
+                    // split round: every child already has a home (set by the split)
+                } else if (!level1 && p->opts.alloc_policy != SPGEMM_ALLOC_UPPER_BOUND &&
+                           (work != nullptr || cap > p->opts.initial_cap || learned)) {
+                    SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap, LIFE_NUMERIC));
+                    SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap, LIFE_NUMERIC));
+                    L.pool_cap = cap;
+                    p->bytes_ctilde += nwork * (int64_t)cap * 12;
+                }
+                if (level1) {
+                    SPG_TRY(p->alloc_n(&g_cap, nwork, LIFE_NUMERIC));
+                    SPG_TRY(p->alloc_n(&g_off, nwork, LIFE_NUMERIC));
+                    SPG_TRY(p->alloc_n(&g_partial, nwork / 2048 + 2, LIFE_NUMERIC));
+                    SPG_TRY(p->alloc_n(&g_total, 1, LIFE_NUMERIC));
+                    SPG_TRY(launch_level1_sizes(p->items, work, nwork, p->u, p->B.ncols, g_cap, g_off, g_partial,
+                                                g_total, p->st));
+                    p->count(SPGEMM_K_OTHER, 4);
+                    int64_t gtot = 0;
+                    SPG_TRY(p->d2h(&gtot, g_total, sizeof(int64_t)));
+                    SPG_TRY(p->alloc_n(&L.g_col, gtot, LIFE_NUMERIC));
+                    SPG_TRY(p->alloc_n(&L.g_val, gtot, LIFE_NUMERIC));
+                    p->bytes_ctilde += gtot * 12;
+                    L.g_cap = g_cap;
+                    L.g_off = g_off;
+                    p->stats.rows_level1 += nwork;
+                }
+                SPG_TRY(cudaMemsetAsync(ovf_count, 0, sizeof(int32_t), p->st));
+                p->time_begin(SPGEMM_K_MERGE);
+                SPG_TRY(launch_merge(a, p->items, L, p->st));
+                p->time_end();
+                p->count(SPGEMM_K_MERGE);
+                p->stats.merge_rounds += 1;
+                int32_t n = 0;
+                SPG_TRY(p->d2h(&n, ovf_count, sizeof(int32_t)));
+                novf = n;
+                if (novf > 0 && level1) {
+                    status = SPGEMM_ERR_INTERNAL;
+                    goto fail;
+                }
+                if (work == nullptr && work_base == 0 && !learned) p->stats.rows_relaunched = novf;
+                if (novf == 0) break;
+                ovf_items = list[which];
+                if (cap < capmax) {
+                    cap = std::min(capmax, cap * 2);
+                    work = list[which];
+                    work_base = 0;
+                    nwork = novf;
+                    which ^= 1;
+                    continue;
+                }
+                if (use_level1) {
+                    level1 = true;
+                    work = list[which];
+                    work_base = 0;
+                    nwork = novf;
+                    which ^= 1;
+                    continue;
+                }
+            }
+            // split every overflowed item at the median column of its sequence
+            SPG_TRY(reserve_items(p, p->n_items + 2 * novf));
+            int32_t *scol = nullptr;
+            double *sval = nullptr;
+            SPG_TRY(p->alloc_n(&scol, novf * (int64_t)capmax, LIFE_NUMERIC));
+            SPG_TRY(p->alloc_n(&sval, novf * (int64_t)capmax, LIFE_NUMERIC));
+            p->bytes_ctilde += novf * (int64_t)capmax * 12;
+            p->time_begin(SPGEMM_K_OTHER);
+            SPG_TRY(launch_split(ovf_items, novf, p->n_items, p->items, scol, sval, capmax, p->st));
+            p->time_end();
+            p->count(SPGEMM_K_OTHER, 2);
+            p->stats.rows_split += novf;
+            cap = capmax;
+            work = nullptr;
+            work_base = p->n_items;
+            nwork = 2 * novf;
+            p->n_items += nwork;
+        }
+    }
+    return SPGEMM_OK;
+fail:
+    return status;
+}
+
+// Bin group 5: the merge kernel over all bin-37 rows.  Plain policies start
+// every row at the initial capacity and go through the progressive rounds.  The
+// learned policy launches each predicted size class with homes of the predicted
+// size; a row that outgrows its prediction continues at twice its class's
+// capacity (and so on up to the largest one), and rows predicted beyond the
+// largest capacity that reach it are split at once.
 spgemm_status run_bin37(spgemm_plan *p) {
     spgemm_status status = SPGEMM_OK;
     const int64_t n37 = p->h_summary.bin_count[BIN_MERGE];
     if (n37 == 0) return SPGEMM_OK;
     const int32_t *rows37 = p->bin_rows + p->bin_start[BIN_MERGE];
     StageArgs a = stage_args(p);
-    int32_t *list[2] = {nullptr, nullptr};
-    int64_t list_cap = 0;
     int32_t *ovf_count = nullptr;
-    int64_t *g_cap = nullptr, *g_off = nullptr, *g_partial = nullptr, *g_total = nullptr;
-    const int batch = p->batch;
     const int capmax = p->capmax;
-    const bool use_level1 = p->opts.long_rows == SPGEMM_LONG_ROWS_LEVEL1;
     const bool learned = p->opts.alloc_policy == SPGEMM_ALLOC_LEARNED;
-    int cap;
-    if (p->opts.alloc_policy == SPGEMM_ALLOC_UPPER_BOUND) cap = capmax;
-    else cap = std::min(capmax, std::max(32, (int)p->opts.initial_cap));
-    const int32_t *work = nullptr;
-    int64_t work_base = 0;
-    int64_t nwork = n37;
-    int which = 0;
-    bool level1 = false;
     {
         SPG_TRY(reserve_items(p, n37));
         p->n_items = n37;
         SPG_TRY(p->alloc_n(&ovf_count, 1, LIFE_NUMERIC));
-        list_cap = n37;
-        SPG_TRY(p->alloc_n(&list[0], list_cap, LIFE_NUMERIC));
-        SPG_TRY(p->alloc_n(&list[1], list_cap, LIFE_NUMERIC));
         SPG_TRY(launch_merge_init(rows37, n37, p->ctil_rp, p->ctil_col, p->ctil_val, p->items, p->st));
         p->count(SPGEMM_K_OTHER);
-        if (learned) {
-            // one launch per predicted class, each with the shared memory its rows need and
-            // homes of the predicted size; rows that outgrow their home are queued for the
-            // exact fallback below
-            SPG_TRY(cudaMemsetAsync(ovf_count, 0, sizeof(int32_t), p->st));
+        if (!learned) {
+            int cap;
+            if (p->opts.alloc_policy == SPGEMM_ALLOC_UPPER_BOUND) cap = capmax;
+            else cap = std::min(capmax, std::max(32, (int)p->opts.initial_cap));
+            status = run_progressive(p, nullptr, 0, n37, cap, false, ovf_count);
+            if (status != SPGEMM_OK) goto fail;
+        } else {
+            // capacity levels of the fallback: 512, 1024, ... below the largest, then the largest
+            std::vector<int> lv;
+            for (int c = 512; c < capmax; c *= 2) lv.push_back(c);
+            lv.push_back(capmax);
+            const int nlv = (int)lv.size();
+            const int SPLIT = nlv;  // target index of rows that overflow at the largest capacity
+            auto level_of = [&](int c) {
+                for (int k = 0; k < nlv; ++k)
+                    if (lv[k] >= c) return k;
+                return nlv - 1;
+            };
+            std::vector<int32_t *> lists(nlv + 1, nullptr);
+            int32_t *counts = nullptr;
+            for (int k = 0; k <= nlv; ++k) SPG_TRY(p->alloc_n(&lists[k], n37, LIFE_NUMERIC));
+            SPG_TRY(p->alloc_n(&counts, nlv + 1, LIFE_NUMERIC));
+            SPG_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (nlv + 1), p->st));
             int64_t off = 0;
             for (int g = 0; g < NUM_LAUNCH_CLASSES; ++g) {
                 const int64_t cnt = p->h_summary.class_count[g];
                 if (cnt == 0) continue;
-                const int ccap = std::min(capmax, p->class_caps[g] == INT32_MAX ? capmax : p->class_caps[g]);
+                const bool beyond = p->class_caps[g] == INT32_MAX;
+                const int ccap = std::min(capmax, beyond ? capmax : p->class_caps[g]);
+                const int tgt = beyond ? SPLIT : level_of(std::min(2 * ccap, capmax));
                 MergeLaunch L{};
                 L.work = p->class_order + off;
                 L.nwork = cnt;
                 L.cap = ccap;
-                L.batch = std::min(std::min(batch, ccap), merge_batch_limit(ccap));
-                L.ovf_list = list[which];
-                L.ovf_count = ovf_count;
+                L.batch = std::min(std::min(p->batch, ccap), merge_batch_limit(ccap));
+                L.ovf_list = lists[tgt];
+                L.ovf_count = counts + tgt;
                 L.err = p->d_err;
                 p->time_begin(SPGEMM_K_MERGE);
                 SPG_TRY(launch_merge(a, p->items, L, p->st));
@@ -586,101 +726,42 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 p->stats.merge_rounds += 1;
                 off += cnt;
             }
-            int32_t novf = 0;
-            SPG_TRY(p->d2h(&novf, ovf_count, sizeof(int32_t)));
-            p->stats.rows_fallback = novf;
-            p->stats.rows_relaunched = novf;
-            cap = capmax;
-            work = list[which];
-            nwork = novf;
-            which ^= 1;
-        }
-        while (nwork > 0) {
-            if (nwork > list_cap) {  // more work items than the overflow lists can hold
-                list_cap = nwork;
-                SPG_TRY(p->alloc_n(&list[which], list_cap, LIFE_NUMERIC));
-                SPG_TRY(p->alloc_n(&list[which ^ 1], list_cap, LIFE_NUMERIC));
-            }
-            MergeLaunch L{};
-            L.work = work;
-            L.work_base = work_base;
-            L.nwork = nwork;
-            L.cap = cap;
-            L.batch = std::min(std::min(batch, cap), merge_batch_limit(cap));
-            L.level1 = level1 ? 1 : 0;
-            L.ovf_list = list[which];
-            L.ovf_count = ovf_count;
-            L.err = p->d_err;
-            if (!level1 && work_base > 0) {
-                // split round: every child already has a home (set by the split)
-            } else if (!level1 && p->opts.alloc_policy != SPGEMM_ALLOC_UPPER_BOUND &&
-                       (work != nullptr || cap > p->opts.initial_cap || learned)) {
-                SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap, LIFE_NUMERIC));
-                SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap, LIFE_NUMERIC));
-                L.pool_cap = cap;
-                p->bytes_ctilde += nwork * (int64_t)cap * 12;
-            }
-            if (level1) {
-                SPG_TRY(p->alloc_n(&g_cap, nwork, LIFE_NUMERIC));
-                SPG_TRY(p->alloc_n(&g_off, nwork, LIFE_NUMERIC));
-                SPG_TRY(p->alloc_n(&g_partial, nwork / 2048 + 2, LIFE_NUMERIC));
-                SPG_TRY(p->alloc_n(&g_total, 1, LIFE_NUMERIC));
-                SPG_TRY(launch_level1_sizes(p->items, work, nwork, p->u, p->B.ncols, g_cap, g_off, g_partial,
-                                            g_total, p->st));
-                p->count(SPGEMM_K_OTHER, 4);
-                int64_t gtot = 0;
-                SPG_TRY(p->d2h(&gtot, g_total, sizeof(int64_t)));
-                SPG_TRY(p->alloc_n(&L.g_col, gtot, LIFE_NUMERIC));
-                SPG_TRY(p->alloc_n(&L.g_val, gtot, LIFE_NUMERIC));
-                p->bytes_ctilde += gtot * 12;
-                L.g_cap = g_cap;
-                L.g_off = g_off;
-                p->stats.rows_level1 += nwork;
-            }
-            SPG_TRY(cudaMemsetAsync(ovf_count, 0, sizeof(int32_t), p->st));
-            p->time_begin(SPGEMM_K_MERGE);
-            SPG_TRY(launch_merge(a, p->items, L, p->st));
-            p->time_end();
-            p->count(SPGEMM_K_MERGE);
-            p->stats.merge_rounds += 1;
-            int32_t novf = 0;
-            SPG_TRY(p->d2h(&novf, ovf_count, sizeof(int32_t)));
-            if (novf > 0 && level1) {
-                status = SPGEMM_ERR_INTERNAL;
-                goto fail;
-            }
-            if (work == nullptr && work_base == 0 && !learned) p->stats.rows_relaunched = novf;
-            if (novf == 0) break;
-            if (cap < capmax) {
-                cap = std::min(capmax, cap * 2);
-                work = list[which];
-                work_base = 0;
-                nwork = novf;
-                which ^= 1;
-            } else if (use_level1) {
-                level1 = true;
-                work = list[which];
-                work_base = 0;
-                nwork = novf;
-                which ^= 1;
-            } else {
-                // split every overflowed item at the median column of its sequence
-                SPG_TRY(reserve_items(p, p->n_items + 2 * (int64_t)novf));
-                int32_t *scol = nullptr;
-                double *sval = nullptr;
-                SPG_TRY(p->alloc_n(&scol, (int64_t)novf * cap, LIFE_NUMERIC));
-                SPG_TRY(p->alloc_n(&sval, (int64_t)novf * cap, LIFE_NUMERIC));
-                p->bytes_ctilde += (int64_t)novf * cap * 12;
-                p->time_begin(SPGEMM_K_OTHER);
-                SPG_TRY(launch_split(list[which], novf, p->n_items, p->items, scol, sval, cap, p->st));
+            std::vector<int32_t> hc(nlv + 1, 0);
+            SPG_TRY(p->d2h(hc.data(), counts, sizeof(int32_t) * (nlv + 1)));
+            int64_t fell = 0;
+            for (int k = 0; k < nlv; ++k) fell += hc[k];
+            p->stats.rows_fallback = fell;  // rows whose result outgrew the predicted size
+            p->stats.rows_relaunched = fell;
+            // levels below the largest capacity, in ascending order: each launch's
+            // overflow lands on a higher level
+            for (int k = 0; k + 1 < nlv; ++k) {
+                int32_t nk = 0;
+                SPG_TRY(p->d2h(&nk, counts + k, sizeof(int32_t)));
+                if (nk == 0) continue;
+                const int tgt = level_of(std::min(2 * lv[k], capmax));
+                MergeLaunch L{};
+                L.work = lists[k];
+                L.nwork = nk;
+                L.cap = lv[k];
+                L.batch = std::min(std::min(p->batch, lv[k]), merge_batch_limit(lv[k]));
+                L.ovf_list = lists[tgt];
+                L.ovf_count = counts + tgt;
+                L.err = p->d_err;
+                SPG_TRY(p->alloc_n(&L.pool_col, (int64_t)nk * lv[k], LIFE_NUMERIC));
+                SPG_TRY(p->alloc_n(&L.pool_val, (int64_t)nk * lv[k], LIFE_NUMERIC));
+                L.pool_cap = lv[k];
+                p->bytes_ctilde += (int64_t)nk * lv[k] * 12;
+                p->time_begin(SPGEMM_K_MERGE);
+                SPG_TRY(launch_merge(a, p->items, L, p->st));
                 p->time_end();
-                p->count(SPGEMM_K_OTHER);
-                p->stats.rows_split += novf;
-                work = nullptr;
-                work_base = p->n_items;
-                nwork = 2 * (int64_t)novf;
-                p->n_items += nwork;
+                p->count(SPGEMM_K_MERGE);
+                p->stats.merge_rounds += 1;
             }
+            SPG_TRY(p->d2h(hc.data(), counts, sizeof(int32_t) * (nlv + 1)));
+            status = run_progressive(p, lists[nlv - 1], 0, hc[nlv - 1], capmax, false, ovf_count);
+            if (status != SPGEMM_OK) goto fail;
+            status = run_progressive(p, lists[SPLIT], 0, hc[SPLIT], capmax, true, ovf_count);
+            if (status != SPGEMM_OK) goto fail;
         }
         SPG_TRY(launch_finalize37(n37, p->items, p->nnzc, p->d_err, p->st));
         p->count(SPGEMM_K_OTHER);
@@ -832,14 +913,13 @@ extern "C" spgemm_status spgemm_batched_symbolic(int64_t npairs, const spgemm_cs
         d.n = B[i].ncols;
         d.moff = moff[i] = M;
         d.koff = koff[i] = K;
-        d.noff = N;
         d.annz_off = aoff[i] = annz;
         d.bnnz_off = boff[i] = bnnz;
         d.annz = A[i].nnz;
         d.bnnz = B[i].nnz;
         M += d.m;
         K += d.k;
-        N += d.n;
+        N = std::max(N, d.n);  // B_i keeps its own column numbers
         annz += d.annz;
         bnnz += d.bnnz;
     }
@@ -896,12 +976,10 @@ extern "C" spgemm_status spgemm_batched_numeric(spgemm_plan *p, spgemm_csr_out *
     spgemm_status status = spgemm_numeric(p, &whole);
     if (status != SPGEMM_OK) return status;
     {
-        const int64_t M = p->A.nrows, nnz = whole.nnz, np = p->npairs;
+        const int64_t M = p->A.nrows, np = p->npairs;
         SPG_TRY(p->alloc_n(&p->split_rp, M + np));
-        SPG_TRY(p->alloc_n(&p->split_col, nnz));
         p->time_begin(SPGEMM_K_OTHER);
-        SPG_TRY(launch_split_out(p->d_pairs, np, p->d_moff, whole.row_ptr, whole.col_idx, M, nnz, p->split_rp,
-                                 p->split_col, p->st));
+        SPG_TRY(launch_split_out(p->d_pairs, np, whole.row_ptr, M, p->split_rp, p->st));
         p->time_end();
         p->count(SPGEMM_K_OTHER);
         // C_i's first entry in the concatenation: read every pair's first row pointer once
@@ -919,7 +997,7 @@ extern "C" spgemm_status spgemm_batched_numeric(spgemm_plan *p, spgemm_csr_out *
             c.ncols = d.n;
             c.nnz = first[i + 1] - first[i];
             c.row_ptr = p->split_rp + d.moff + i;
-            c.col_idx = p->split_col + first[i];
+            c.col_idx = whole.col_idx + first[i];
             c.val = whole.val + first[i];
             C_out[i] = c;
         }

@@ -137,3 +137,36 @@ def test_trained_weights_if_present(spg, oracle_mod):
     assert_csr_equal(rp, col, val, ref.row_ptr, ref.col, ref.val, ref.den, label="trained")
     st = plan.stats()
     assert st["rows_fallback"] <= 0.25 * st["bin_count"][37]
+
+
+@pytest.mark.parametrize("margin,long_rows", [(0.01, "split"), (1.0, "split"), (50.0, "split"), (50.0, "level1"),
+                                              (1.0, "level1")])
+def test_learned_fallback_levels_and_long_rows(spg, oracle_mod, margin, long_rows):
+    """Largest capacity lowered to 1024 entries: rows that outgrow a small prediction climb the
+    capacity levels (512, 1024) and then take the long-row path; rows predicted beyond the
+    largest capacity (margin 50) go to the long-row path as soon as they reach it."""
+    from paper_1504_05022_gb300.predictor import Predictor, row_features
+    A = gen.rmat(12, 16, seed=21)
+    Ad = spg.CSR.from_host(A)
+    X = row_features(Ad, Ad).cpu().numpy()
+    th = mlp.init_params(5, mu=X.mean(0), sigma=X.std(0) + 0.1)
+    w3 = 32 * 8 + 32 + 32 * 32 + 32
+    th[w3:w3 + 17 * 32] = 0.0
+    th[mlp.N_PARAMS - 1] = 9.0        # 511 entries before the margin
+    pred = Predictor(th, margin=margin)
+    plan = spg.Plan(Ad, Ad, smem_cap_max=1024, long_rows=long_rows, **pred.opts())
+    C = plan.numeric()
+    torch.cuda.synchronize()
+    ref = oracle_mod.spgemm(A, A)
+    rp, col, val = C.to_host()
+    assert_csr_equal(rp, col, val, ref.row_ptr, ref.col, ref.val, ref.den, label=f"learned {margin}/{long_rows}")
+    st = plan.stats()
+    nnz37 = np.diff(ref.row_ptr)[plan.arrays()["bin"] == 37]
+    assert (nnz37 > 1024).sum() > 0
+    if long_rows == "split":
+        assert st["rows_split"] > 0 and st["rows_level1"] == 0
+    else:
+        assert st["rows_level1"] > 0 and st["rows_split"] == 0
+    if margin == 50.0:
+        assert st["rows_fallback"] == 0
+    plan.check()
