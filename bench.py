@@ -349,9 +349,9 @@ def run_batch(args, world, device):
     products = int(sum(_products_ab(A, B) for A, B in pairs))
     res = {}
 
-    def batched(policy, clocks=False):
+    def batched(policy, clocks=False, wave_mproducts=0):
         opts, keep = policy_opts(policy)
-        opts = dict(opts, record_timing=True)
+        opts = dict(opts, record_timing=True, wave_mproducts=wave_mproducts)
 
         def step():
             bp = spg.BatchPlan(As, Bs, stream=stream, **opts)
@@ -368,7 +368,8 @@ def run_batch(args, world, device):
                "peak_bytes": int(st["peak_bytes"]), "held_bytes_after": int(st["held_bytes"]),
                "launches_per_step": int(sum(st["launches"].values())), "kms": st["kernel_ms"],
                "rows_bin37": int(st["bin_count"][37]), "rows_fallback": int(st["rows_fallback"]),
-               "merge_rounds": int(st["merge_rounds"]), "clocks": clk.summary() if clk else None}
+               "merge_rounds": int(st["merge_rounds"]), "waves": bp.n_waves,
+               "clocks": clk.summary() if clk else None}
         return out, bp, keep
 
     def sequential(policy):
@@ -397,6 +398,7 @@ def run_batch(args, world, device):
     head = args.policy
     main, bp, keep = batched(head, clocks=True)
     arrays = bp.arrays()
+    order = bp.pair_order()
     del bp
     torch.cuda.synchronize()
     for p in ("hybrid",):
@@ -404,6 +406,10 @@ def run_batch(args, world, device):
             r, b2, k2 = batched(p)
             del b2, k2
             res["batched_" + p] = r
+    torch.cuda.synchronize()
+    r, b2, k2 = batched(head, wave_mproducts=-1)  # all pairs in one wave: fewer launches, more memory
+    del b2, k2
+    res[f"batched_{head}_one_wave"] = r
     torch.cuda.synchronize()
     res["sequential_hybrid"] = sequential("hybrid")
     torch.cuda.synchronize()
@@ -421,7 +427,7 @@ def run_batch(args, world, device):
     del g, gp, keep_g
     torch.cuda.synchronize()
     m = {"policy": head, "kms": main["kms"], "st_all": [{"launches": {}}], "arrays": [arrays]}
-    cat = _Cat([A for A, _ in pairs])
+    cat = _Cat([pairs[i][0] for i in order])  # rows in the order of the plan's arrays
     rl = roofline(args, [(cat, cat)], m)
     rl["launches_per_step"] = None
     main_clocks = main.pop("clocks")
@@ -431,7 +437,8 @@ def run_batch(args, world, device):
         "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded generator)",
         "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "alloc_policy": head,
-                   "mode": "batched (block-diagonal concatenation, one pipeline)", "pairs": len(pairs),
+                   "mode": "batched (block-diagonal concatenation, waves of <= 1024M products)",
+                   "waves": main["waves"], "pairs": len(pairs),
                    "products_per_step": products, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": rl,

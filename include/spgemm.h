@@ -113,7 +113,11 @@ typedef struct spgemm_opts {
     int32_t smem_cap_max;    /* largest result capacity held in shared memory (0 = auto) */
     int32_t heap_block;      /* threads per block of the heap kernel (0 = auto) */
     int32_t long_rows;       /* spgemm_long_rows: handling of rows beyond shared memory */
-    int32_t reserved[8];
+    int32_t wave_mproducts;  /* batched products: largest number of products (in millions) that
+                                one wave of pairs may hold; pairs are grouped in order into waves
+                                computed one after another, each releasing its temporaries
+                                before the next (0 = 1024, negative = one wave) */
+    int32_t reserved[7];
     const void *predictor;   /* spgemm_predictor* for SPGEMM_ALLOC_LEARNED, else NULL; it must
                                 not be freed before spgemm_symbolic (or spgemm_galerkin) has
                                 returned, since its weights are read by that call's kernels */
@@ -231,6 +235,33 @@ spgemm_status spgemm_batched_symbolic(int64_t npairs, const spgemm_csr_in *A, co
                                       const spgemm_opts *opts, spgemm_stream_t stream,
                                       spgemm_plan **plan_out, int64_t *upper_bound_nnz_out);
 spgemm_status spgemm_batched_numeric(spgemm_plan *plan, spgemm_csr_out *C_out);
+
+/*
+ * Waves of a batched plan.  spgemm_batched_symbolic counts every pair's products
+ * (Algorithm 2 summed over its rows) and a lower bound of nnz(C_i) (the sum over
+ * rows of the longest B row they merge), orders the pairs by descending product
+ * count and groups consecutive pairs of that order into waves.  A wave holds at
+ * most opts->wave_mproducts million products (a larger pair is a wave of its
+ * own), and beyond 32 million products it also stops growing once its products
+ * (which bound its temporary entries) exceed the lower bounds of the pairs still
+ * to come.  With more than one wave, spgemm_batched_numeric computes the waves
+ * one after another, each as a batched product of its own whose temporaries are
+ * released before the next wave starts: the largest pairs run while few results
+ * are resident and no wave's temporaries outgrow the results that follow it, so
+ * the peak stays near the size of all results.  C_out[i] is still the product of
+ * pair i.  In this mode the inputs are read by
+ * spgemm_batched_numeric and must stay valid until its work has completed, and
+ * spgemm_plan_arrays_get is refused (read each wave's arrays instead).
+ * spgemm_batched_waves gives the number of waves (1 without wave mode);
+ * spgemm_batched_wave gives wave i's plan (borrowed, owned by the batched plan;
+ * available after spgemm_batched_numeric; wave 0 of a single-wave plan is the
+ * plan itself) and the position of its first pair in the wave order;
+ * spgemm_batched_wave_pairs fills order[0..npairs) with the pair at each
+ * position of that order (the identity without wave mode).
+ */
+spgemm_status spgemm_batched_waves(spgemm_plan *plan, int64_t *n_waves);
+spgemm_status spgemm_batched_wave(spgemm_plan *plan, int64_t i, spgemm_plan **wave, int64_t *first_pair);
+spgemm_status spgemm_batched_wave_pairs(spgemm_plan *plan, int64_t *order);
 
 /*
  * Values-only replay (not in the paper): after spgemm_numeric (or

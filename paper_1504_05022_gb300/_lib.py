@@ -34,7 +34,8 @@ class CsrOut(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("alloc_policy", c_i32), ("initial_cap", c_i32), ("check_inputs", c_i32),
                 ("record_timing", c_i32), ("merge_batch", c_i32), ("smem_cap_max", c_i32),
-                ("heap_block", c_i32), ("long_rows", c_i32), ("reserved", c_i32 * 8), ("predictor", c_ptr),
+                ("heap_block", c_i32), ("long_rows", c_i32), ("wave_mproducts", c_i32), ("reserved", c_i32 * 7),
+                ("predictor", c_ptr),
                 ("predictor_margin", c_f64)]
 
 
@@ -62,6 +63,9 @@ SIGNATURES = {
     "spgemm_plan_arrays_get": ([c_ptr, ctypes.POINTER(PlanArrays)], c_i32),
     "spgemm_rowptr_scan_noalloc": ([c_ptr, c_i64, c_ptr, c_ptr], c_i32),
     "spgemm_rowptr_scan_noalloc_max_rows": ([], c_i64),
+    "spgemm_batched_waves": ([c_ptr, ctypes.POINTER(c_i64)], c_i32),
+    "spgemm_batched_wave": ([c_ptr, c_i64, ctypes.POINTER(c_ptr), ctypes.POINTER(c_i64)], c_i32),
+    "spgemm_batched_wave_pairs": ([c_ptr, ctypes.POINTER(c_i64)], c_i32),
     "spgemm_batched_symbolic": ([c_i64, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(Opts), c_ptr,
                                  ctypes.POINTER(c_ptr), ctypes.POINTER(c_i64)], c_i32),
     "spgemm_batched_numeric": ([c_ptr, ctypes.POINTER(CsrOut)], c_i32),

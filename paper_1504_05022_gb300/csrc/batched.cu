@@ -105,6 +105,66 @@ cudaError_t launch_split_out(const PairDesc *d, int64_t npairs, const int64_t *c
     return cudaGetLastError();
 }
 
+// Per pair i: prod[i] = sum over the entries a_ik of A_i of nnz(b_k*), the
+// products of the pair (Algorithm 2 summed over its rows), and clow[i] = sum
+// over the rows of A_i of max_k nnz(b_k*), a lower bound of nnz(C_i) (a row of
+// C contains every column of each B row it merges).  Grid (PAIR_BLOCKS, npairs),
+// a warp per row; columns outside [0, k_i) are skipped (they are rejected later
+// when inputs are checked).  prod and clow must be zeroed.
+constexpr int PAIR_BLOCKS = 64;
+
+__global__ void k_pair_products(const PairDesc *d, unsigned long long *prod, unsigned long long *clow) {
+    __shared__ int64_t sh[2][256 / 32];
+    const PairDesc q = d[blockIdx.y];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t s = 0, lo = 0;
+    for (int64_t r = (int64_t)blockIdx.x * 8 + wid; r < q.m; r += (int64_t)PAIR_BLOCKS * 8) {
+        const int64_t a0 = rp_at(q.a_rp, q.a_bits, r), a1 = rp_at(q.a_rp, q.a_bits, r + 1);
+        int64_t rs = 0, rm = 0;
+        for (int64_t e = a0 + lane; e < a1; e += 32) {
+            const int32_t k = q.a_col[e];
+            if (k >= 0 && k < q.k) {
+                const int64_t len = rp_at(q.b_rp, q.b_bits, k + 1) - rp_at(q.b_rp, q.b_bits, k);
+                rs += len;
+                rm = len > rm ? len : rm;
+            }
+        }
+        s += rs;
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t x = __shfl_xor_sync(SPG_FULL, rm, o);
+            rm = x > rm ? x : rm;
+        }
+        lo += rm;  // the same on every lane
+    }
+    s = warp_reduce_sum(s);
+    if (lane == 0) {
+        sh[0][wid] = s;
+        sh[1][wid] = lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t ts = 0, tl = 0;
+        for (int w = 0; w < 8; ++w) {
+            ts += sh[0][w];
+            tl += sh[1][w];
+        }
+        if (ts) atomicAdd(prod + blockIdx.y, (unsigned long long)ts);
+        if (tl) atomicAdd(clow + blockIdx.y, (unsigned long long)tl);
+    }
+}
+
+cudaError_t launch_pair_products(const PairDesc *d, int64_t npairs, int64_t *prod, int64_t *clow,
+                                 cudaStream_t st) {
+    if (npairs <= 0) return cudaSuccess;
+    if (npairs > 65535) return cudaErrorInvalidValue;  // grid.y limit; the caller then uses one wave
+    cudaError_t e = cudaMemsetAsync(prod, 0, sizeof(int64_t) * npairs, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(clow, 0, sizeof(int64_t) * npairs, st);
+    if (e != cudaSuccess) return e;
+    k_pair_products<<<dim3(PAIR_BLOCKS, (unsigned)npairs), 256, 0, st>>>(
+        d, reinterpret_cast<unsigned long long *>(prod), reinterpret_cast<unsigned long long *>(clow));
+    return cudaGetLastError();
+}
+
 // out[i] = c_rp[moff_i] (first entry of C_i in the concatenation), out[np] = c_rp[M].
 __global__ void k_gather_first(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

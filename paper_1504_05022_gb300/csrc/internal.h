@@ -174,6 +174,8 @@ cudaError_t launch_concat(const PairDesc *d, int64_t npairs, const int64_t *moff
                           double *b_val, bool values_only, cudaStream_t st);
 cudaError_t launch_gather_first(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *out,
                                 cudaStream_t st);
+cudaError_t launch_pair_products(const PairDesc *d, int64_t npairs, int64_t *prod, int64_t *clow,
+                                 cudaStream_t st);
 cudaError_t launch_split_out(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *rp_out,
                              cudaStream_t st);
 

@@ -143,6 +143,13 @@ struct spgemm_plan {
     double *cat_a_val = nullptr, *cat_b_val = nullptr;
     int64_t *split_rp = nullptr;
     std::vector<spgemm_csr_out> batch_out;
+    // batched plans in waves: groups of pairs computed one after another, each a
+    // batched sub-plan of its own made by spgemm_batched_numeric
+    bool wave_mode = false;
+    std::vector<spgemm_csr_in> wave_A, wave_B;
+    std::vector<int64_t> wave_order;  // pairs by descending product count: wave_A[q] = A[wave_order[q]]
+    std::vector<int64_t> wave_start;  // first position (in wave_order) of each wave, then npairs
+    std::vector<spgemm_plan *> waves;
     // values-only replay
     bool replay_ready = false;
     ReplayLeaves leaves{};
@@ -210,6 +217,13 @@ struct spgemm_plan {
         return cudaSuccess;
     }
     void release() {
+        for (spgemm_plan *w : waves) {
+            if (w) {
+                w->release();
+                delete w;
+            }
+        }
+        waves.clear();
         for (auto &t : timers) {
             if (t.a) cudaEventDestroy(t.a);
             if (t.b) cudaEventDestroy(t.b);
@@ -777,7 +791,7 @@ fail:
 }  // namespace
 
 extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
-    if (!p || !C_out) return SPGEMM_ERR_INVALID_ARG;
+    if (!p || !C_out || p->wave_mode) return SPGEMM_ERR_INVALID_ARG;
     if (p->numeric_done) {
         *C_out = p->C;
         return SPGEMM_OK;
@@ -866,11 +880,56 @@ extern "C" spgemm_status spgemm_plan_stats(spgemm_plan *p, spgemm_stats *out) {
     p->stats.peak_bytes = p->bytes_peak;
     p->stats.held_bytes = p->bytes_held;
     *out = p->stats;
+    for (spgemm_plan *w : p->waves) {  // wave mode: sums over the waves
+        spgemm_stats ws;
+        spgemm_status st = spgemm_plan_stats(w, &ws);
+        if (st != SPGEMM_OK) return st;
+        for (int b = 0; b < NUM_BINS; ++b) out->bin_count[b] += ws.bin_count[b];
+        out->nnz_ctilde += ws.nnz_ctilde;
+        out->nnz_c += ws.nnz_c;
+        out->merge_rounds += ws.merge_rounds;
+        out->rows_relaunched += ws.rows_relaunched;
+        out->rows_level1 += ws.rows_level1;
+        out->rows_split += ws.rows_split;
+        out->rows_fallback += ws.rows_fallback;
+        out->bytes_ctilde += ws.bytes_ctilde;
+        out->held_bytes += ws.held_bytes;
+        for (int k = 0; k < SPGEMM_K_COUNT; ++k) {
+            out->launches[k] += ws.launches[k];
+            out->kernel_ms[k] += ws.kernel_ms[k];
+        }
+    }
+    return SPGEMM_OK;
+}
+
+extern "C" spgemm_status spgemm_batched_waves(spgemm_plan *p, int64_t *n) {
+    if (!p || !n) return SPGEMM_ERR_INVALID_ARG;
+    *n = p->wave_mode ? (int64_t)p->wave_start.size() - 1 : 1;
+    return SPGEMM_OK;
+}
+
+extern "C" spgemm_status spgemm_batched_wave(spgemm_plan *p, int64_t i, spgemm_plan **sub, int64_t *first_pair) {
+    if (!p || !sub || i < 0) return SPGEMM_ERR_INVALID_ARG;
+    if (!p->wave_mode) {
+        if (i != 0) return SPGEMM_ERR_INVALID_ARG;
+        *sub = p;
+        if (first_pair) *first_pair = 0;
+        return SPGEMM_OK;
+    }
+    if (i >= (int64_t)p->waves.size()) return SPGEMM_ERR_INVALID_ARG;
+    *sub = p->waves[i];
+    if (first_pair) *first_pair = p->wave_start[i];
+    return SPGEMM_OK;
+}
+
+extern "C" spgemm_status spgemm_batched_wave_pairs(spgemm_plan *p, int64_t *order) {
+    if (!p || !order) return SPGEMM_ERR_INVALID_ARG;
+    for (int64_t q = 0; q < p->npairs; ++q) order[q] = p->wave_mode ? p->wave_order[q] : q;
     return SPGEMM_OK;
 }
 
 extern "C" spgemm_status spgemm_plan_arrays_get(spgemm_plan *p, spgemm_plan_arrays *out) {
-    if (!p || !out) return SPGEMM_ERR_INVALID_ARG;
+    if (!p || !out || p->wave_mode) return SPGEMM_ERR_INVALID_ARG;
     out->nrows = p->A.nrows;
     out->u = p->u;
     out->bin = p->bin;
@@ -941,6 +1000,60 @@ extern "C" spgemm_status spgemm_batched_symbolic(int64_t npairs, const spgemm_cs
         SPG_TRY(cudaMemcpyAsync(p->d_koff, koff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
         SPG_TRY(cudaMemcpyAsync(p->d_annz_off, aoff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
         SPG_TRY(cudaMemcpyAsync(p->d_bnnz_off, boff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
+        const int64_t budget = p->opts.wave_mproducts < 0 ? INT64_MAX
+                               : (int64_t)(p->opts.wave_mproducts > 0 ? p->opts.wave_mproducts : 1024) * 1000000;
+        if (npairs > 1 && npairs <= 65535 && budget < INT64_MAX) {
+            // products and a lower bound of nnz(C_i) of every pair, then waves
+            int64_t *d_prod = nullptr, *d_clow = nullptr;
+            SPG_TRY(p->alloc_n(&d_prod, npairs, LIFE_SYMBOLIC));
+            SPG_TRY(p->alloc_n(&d_clow, npairs, LIFE_SYMBOLIC));
+            SPG_TRY(launch_pair_products(p->d_pairs, npairs, d_prod, d_clow, p->st));
+            p->count(SPGEMM_K_OTHER);
+            std::vector<int64_t> prod(npairs), clow(npairs);
+            SPG_TRY(cudaStreamSynchronize(p->st));
+            SPG_TRY(cudaMemcpy(prod.data(), d_prod, sizeof(int64_t) * npairs, cudaMemcpyDeviceToHost));
+            SPG_TRY(cudaMemcpy(clow.data(), d_clow, sizeof(int64_t) * npairs, cudaMemcpyDeviceToHost));
+            // largest pairs first: they run while few results are resident.  A wave grows
+            // while its products (which bound its temporary entries) fit the budget and do
+            // not exceed the entries of the results still to come (sum of the lower bounds
+            // of the later pairs), so the peak stays near the size of all results; waves
+            // of up to WAVE_MIN products are always allowed, which bounds their number.
+            constexpr int64_t WAVE_MIN = 32 * 1000000LL;
+            std::vector<int64_t> order(npairs);
+            for (int64_t i = 0; i < npairs; ++i) order[i] = i;
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int64_t x, int64_t y) { return prod[x] > prod[y]; });
+            std::vector<int64_t> after(npairs + 1, 0);  // after[q] = sum of clow over positions >= q
+            for (int64_t q = npairs - 1; q >= 0; --q) after[q] = after[q + 1] + clow[order[q]];
+            std::vector<int64_t> starts{0};
+            int64_t acc = 0, total = 0;
+            for (int64_t q = 0; q < npairs; ++q) {
+                const int64_t pq = prod[order[q]];
+                const int64_t grown = acc + pq;
+                if (acc > 0 && (grown > budget || (grown > WAVE_MIN && grown > after[q + 1]))) {
+                    starts.push_back(q);
+                    acc = 0;
+                }
+                acc += pq;
+                total += pq;
+            }
+            starts.push_back(npairs);
+            if (starts.size() > 2) {
+                p->wave_mode = true;
+                p->wave_order = order;
+                for (int64_t q = 0; q < npairs; ++q) {
+                    p->wave_A.push_back(A[order[q]]);
+                    p->wave_B.push_back(B[order[q]]);
+                }
+                p->wave_start = starts;
+                p->h_summary.sum_u = total;
+                p->stats.sum_u = total;
+                p->release_temps(LIFE_SYMBOLIC);
+                if (upper_bound_nnz_out) *upper_bound_nnz_out = total;
+                *plan_out = p;
+                return SPGEMM_OK;
+            }
+        }
         SPG_TRY(p->alloc_n(&p->cat_a_rp, M + 1));
         SPG_TRY(p->alloc_n(&p->cat_b_rp, K + 1));
         SPG_TRY(p->alloc_n(&p->cat_a_col, annz));
@@ -966,12 +1079,47 @@ fail:
     return status;
 }
 
+// Wave mode: every wave is a batched product of its own, made, computed and
+// stripped of its temporaries before the next one starts.
+static spgemm_status batched_numeric_waves(spgemm_plan *p, spgemm_csr_out *C_out) {
+    spgemm_opts o = p->opts;
+    o.wave_mproducts = -1;
+    int64_t held_before = 0;
+    for (spgemm_plan *w : p->waves) held_before += w->bytes_held;
+    const int nw = (int)p->wave_start.size() - 1;
+    std::vector<spgemm_csr_out> outs(p->npairs);
+    for (int w = 0; w < nw; ++w) {
+        const int64_t s0 = p->wave_start[w], n = p->wave_start[w + 1] - s0;
+        spgemm_status st = SPGEMM_OK;
+        if (w >= (int)p->waves.size()) {
+            spgemm_plan *sub = nullptr;
+            st = spgemm_batched_symbolic(n, p->wave_A.data() + s0, p->wave_B.data() + s0, &o,
+                                         reinterpret_cast<spgemm_stream_t>(p->st), &sub, nullptr);
+            if (st != SPGEMM_OK) return st;
+            p->waves.push_back(sub);
+            st = spgemm_batched_numeric(sub, outs.data() + s0);
+            if (st != SPGEMM_OK) return st;
+            p->bytes_peak = std::max(p->bytes_peak, held_before + sub->bytes_peak);
+            held_before += sub->bytes_held;
+        } else {
+            st = spgemm_batched_numeric(p->waves[w], outs.data() + s0);  // finished earlier
+            if (st != SPGEMM_OK) return st;
+        }
+    }
+    p->batch_out.resize(p->npairs);
+    for (int64_t q = 0; q < p->npairs; ++q) p->batch_out[p->wave_order[q]] = outs[q];
+    for (int64_t i = 0; i < p->npairs; ++i) C_out[i] = p->batch_out[i];
+    p->numeric_done = true;
+    return SPGEMM_OK;
+}
+
 extern "C" spgemm_status spgemm_batched_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
     if (!p || !C_out || p->npairs < 1) return SPGEMM_ERR_INVALID_ARG;
     if (!p->batch_out.empty()) {
         for (int64_t i = 0; i < p->npairs; ++i) C_out[i] = p->batch_out[i];
         return SPGEMM_OK;
     }
+    if (p->wave_mode) return batched_numeric_waves(p, C_out);
     spgemm_csr_out whole;
     spgemm_status status = spgemm_numeric(p, &whole);
     if (status != SPGEMM_OK) return status;
@@ -1058,6 +1206,13 @@ fail:
 
 extern "C" spgemm_status spgemm_numeric_replay(spgemm_plan *p) {
     if (!p || !p->numeric_done) return SPGEMM_ERR_INVALID_ARG;
+    if (p->wave_mode) {
+        for (spgemm_plan *w : p->waves) {
+            spgemm_status st = spgemm_numeric_replay(w);
+            if (st != SPGEMM_OK) return st;
+        }
+        return SPGEMM_OK;
+    }
     spgemm_status status = SPGEMM_OK;
     if (!p->replay_ready) {
         status = prepare_replay(p);
@@ -1106,6 +1261,11 @@ fail:
 
 extern "C" spgemm_status spgemm_plan_check(spgemm_plan *p) {
     if (!p) return SPGEMM_ERR_INVALID_ARG;
+    for (spgemm_plan *w : p->waves) {
+        spgemm_status st = spgemm_plan_check(w);
+        if (st != SPGEMM_OK) return st;
+    }
+    if (p->wave_mode) return SPGEMM_OK;
     int64_t err = 0;
     cudaError_t e = p->d2h(&err, p->d_err, sizeof(int64_t));
     if (e != cudaSuccess) return from_cuda(e);

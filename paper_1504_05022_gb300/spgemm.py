@@ -115,7 +115,7 @@ def _wrap_u8(ptr: int, n: int, owner: _PlanHandle, device: int) -> torch.Tensor:
 def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs: bool = False,
               record_timing: bool = False, merge_batch: int = 0, smem_cap_max: int = 0,
               heap_block: int = 0, long_rows: str = "split", predictor=None,
-              predictor_margin: float = 1.0) -> _lib.Opts:
+              predictor_margin: float = 1.0, wave_mproducts: int = 0) -> _lib.Opts:
     L = _lib.load()
     o = _lib.Opts()
     _lib.check(L.spgemm_opts_init(ctypes.byref(o)), "spgemm_opts_init")
@@ -127,6 +127,7 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
     o.smem_cap_max = int(smem_cap_max)
     o.heap_block = int(heap_block)
     o.long_rows = _lib.LONG_ROWS[long_rows]
+    o.wave_mproducts = int(wave_mproducts)
     # a Predictor object (whose device weights the caller keeps alive) or a raw handle
     o.predictor = getattr(predictor, "handle", predictor)
     o.predictor_margin = float(predictor_margin)
@@ -184,10 +185,12 @@ class Plan:
     def arrays(self) -> dict:
         """Copies of the plan's intermediate arrays to host numpy (for inspection and tests):
         u, bin, bin_rows, bin_start, ctilde_row_ptr, row_nnz."""
+        return self._arrays_of(self.handle.ptr)
+
+    def _arrays_of(self, ptr: int) -> dict:
         L = _lib.load()
         a = _lib.PlanArrays()
-        _lib.check(L.spgemm_plan_arrays_get(ctypes.c_void_p(self.handle.ptr), ctypes.byref(a)),
-                   "spgemm_plan_arrays_get")
+        _lib.check(L.spgemm_plan_arrays_get(ctypes.c_void_p(ptr), ctypes.byref(a)), "spgemm_plan_arrays_get")
         self.stream.synchronize()
         m = int(a.nrows)
         h = self.handle
@@ -266,6 +269,39 @@ class BatchPlan(Plan):
                         _wrap(o.val, o.nnz, torch.float64, h, self.device), (int(o.nrows), int(o.ncols)))
                     for o in outs]
         return self._Cs
+
+
+    @property
+    def n_waves(self) -> int:
+        n = ctypes.c_int64()
+        _lib.check(_lib.load().spgemm_batched_waves(ctypes.c_void_p(self.handle.ptr), ctypes.byref(n)),
+                   "spgemm_batched_waves")
+        return int(n.value)
+
+    def pair_order(self) -> np.ndarray:
+        """Pairs in the order the waves compute them (largest product count first)."""
+        order = np.zeros(len(self.As), dtype=np.int64)
+        _lib.check(_lib.load().spgemm_batched_wave_pairs(ctypes.c_void_p(self.handle.ptr),
+                                                         order.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+                   "spgemm_batched_wave_pairs")
+        return order
+
+    def arrays(self) -> dict:
+        """As Plan.arrays, for the rows of all pairs concatenated in pair_order(); with several
+        waves only u, bin and row_nnz (the per-wave bin_rows, bin_start and ctilde_row_ptr are
+        not merged)."""
+        nw = self.n_waves
+        if nw == 1:
+            return super().arrays()
+        L = _lib.load()
+        parts = []
+        for i in range(nw):
+            sub = ctypes.c_void_p()
+            first = ctypes.c_int64()
+            _lib.check(L.spgemm_batched_wave(ctypes.c_void_p(self.handle.ptr), i, ctypes.byref(sub),
+                                             ctypes.byref(first)), "spgemm_batched_wave")
+            parts.append(self._arrays_of(sub.value))
+        return {k: np.concatenate([p[k] for p in parts]) for k in ("u", "bin", "row_nnz")}
 
 
 def spgemm_batched(As, Bs, stream=None, **opts):

@@ -156,3 +156,60 @@ def test_replay_refused_for_level1(spg):
     with pytest.raises(spg.SpgemmError) as ei:
         plan.replay()
     assert ei.value.code == 1
+
+
+def _greedy_waves(prods, budget):
+    starts, acc = [0], 0
+    for i, p in enumerate(sorted(prods, reverse=True)):
+        if acc > 0 and acc + p > budget:
+            starts.append(i)
+            acc = 0
+        acc += p
+    return len(starts)
+
+
+@pytest.mark.parametrize("policy", ["hybrid", "learned"])
+def test_batched_waves(spg, oracle_mod, policy):
+    """Pairs grouped into waves of at most 1M products: same results as the oracle, the
+    waves the greedy grouping gives, a peak no higher than one wave over all pairs, and
+    values-only replay of every wave captured in one CUDA graph."""
+    from paper_1504_05022_gb300.predictor import Predictor
+    pairs = gen.batch_pairs(24, m_lo=200, m_hi=6000, seed0=300)
+    prods = [int(np.diff(B.row_ptr)[A.col].sum()) for A, B in pairs]
+    keep = Predictor.load() if policy == "learned" else None
+    opts = keep.opts() if keep else {"alloc_policy": policy}
+    s = torch.cuda.Stream()
+    As = [spg.CSR.from_host(A) for A, _ in pairs]
+    Bs = [spg.CSR.from_host(B, rowptr_dtype=torch.int32) for _, B in pairs]
+    torch.cuda.synchronize()
+    plan = spg.BatchPlan(As, Bs, stream=s, wave_mproducts=1, **opts)
+    assert plan.upper_bound_nnz == sum(prods)
+    assert plan.n_waves == _greedy_waves(prods, 1_000_000) > 1
+    Cs = plan.numeric()
+    s.synchronize()
+    for i, ((A, B), C) in enumerate(zip(pairs, Cs)):
+        _check(oracle_mod, A, B, C, f"wave pair {i}")
+    st = plan.stats()
+    assert st["sum_u"] == sum(prods) and st["nnz_c"] == sum(C.nnz for C in Cs)
+    one = spg.BatchPlan(As, Bs, stream=s, wave_mproducts=-1, **opts)
+    assert one.n_waves == 1
+    one.numeric()
+    s.synchronize()
+    assert st["peak_bytes"] <= one.stats()["peak_bytes"]
+    ar = plan.arrays()
+    order = plan.pair_order()
+    assert sorted(order) == list(range(len(pairs)))
+    assert all(prods[order[q]] >= prods[order[q + 1]] for q in range(len(pairs) - 1))
+    assert ar["u"].shape[0] == sum(pairs[i][0].nrows for i in order) and ar["u"].sum() == sum(prods)
+    new = [(_scaled(A, 7 * i), _scaled(B, 7 * i + 1)) for i, (A, B) in enumerate(pairs)]
+    for (A2, B2), Ad, Bd in zip(new, As, Bs):
+        Ad.val.copy_(torch.from_numpy(A2.val))
+        Bd.val.copy_(torch.from_numpy(B2.val))
+    torch.cuda.synchronize()
+    g = spg.ReplayGraph([plan])
+    g.launch()
+    s.synchronize()
+    plan.check()
+    for i, ((A2, B2), C) in enumerate(zip(new, Cs)):
+        _check(oracle_mod, A2, B2, C, f"wave replay {i}")
+    del g, keep
