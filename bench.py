@@ -167,27 +167,44 @@ def algorithmic_bytes(A, B, u, rows_sel, row_nnz):
     return int(la.sum()) * 28 + int(u[rows_sel].sum()) * 12 + int(row_nnz[rows_sel].sum()) * 12
 
 
-def policy_opts(policy):
+def policy_opts(policy, tuned_workload=None):
     """Library options of a policy name: 'hybrid' = the paper's plain path (256-entry start,
-    x2 relaunches), 'upper_bound', 'learned' = trained predictor (committed weights)."""
+    x2 relaunches), 'upper_bound', 'learned' = trained predictor (committed weights).  With
+    tuned_workload, the autotuner's parameters for that workload and policy are applied
+    (when paper_1504_05022_gb300/tuned.json has them)."""
+    pred = None
     if policy == "learned":
         from paper_1504_05022_gb300.predictor import Predictor
         pred = Predictor.load()
-        return pred.opts(), pred
-    return {"alloc_policy": policy}, None
+        opts = pred.opts()
+    else:
+        opts = {"alloc_policy": policy}
+    if tuned_workload:
+        from paper_1504_05022_gb300 import autotune
+        params = autotune.load(tuned_workload, policy)
+        if params:
+            opts = autotune.apply(opts, params)
+    return opts, pred
 
 
-def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=False):
+def tuned_params(args, policy):
+    if not args.tuned:
+        return None
+    from paper_1504_05022_gb300 import autotune
+    return autotune.load(args.workload, policy)
+
+
+def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=False, tuned=False):
     """W warm-up steps, then K timed steps (CUDA events on the launching stream, L2 flushed
     between steps outside the events).  Returns the per-step figures."""
     import torch
-    opts, keep = policy_opts(policy)
-    opts = dict(opts, record_timing=True)
+    opts, keep = policy_opts(policy, args.workload if tuned and args.tuned else None)
+    timing_opts = dict(opts, record_timing=True)  # per-kernel split, taken in one extra untimed step
     Ad = [spg.CSR.from_host(A, device=dev, rowptr_dtype=torch.int32) for A, _ in pairs]
     Bd = [spg.CSR.from_host(B, device=dev, rowptr_dtype=torch.int32) if B is not None and B is not A else None
           for A, B in pairs]
 
-    def step():
+    def step(o=opts):
         prev = None
         plans = []
         for i in range(len(pairs)):
@@ -198,7 +215,7 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
                 B_ = A_
             else:
                 B_ = Bd[i]
-            plan = spg.Plan(A_, B_, stream=stream, **opts)
+            plan = spg.Plan(A_, B_, stream=stream, **o)
             prev = plan.numeric()
             plans.append(plan)
         return plans, prev
@@ -224,10 +241,7 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
         ev[k][1].record(stream)
         torch.cuda.synchronize()
         for p in plans:
-            st = p.stats()
-            for name, ms in st["kernel_ms"].items():
-                kms[name] = kms.get(name, 0.0) + ms
-            launches += sum(st["launches"].values())
+            launches += sum(p.stats()["launches"].values())
         if k < args.steps - 1:
             del plans, C
     torch.cuda.synchronize()
@@ -235,17 +249,20 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
     if clk:
         clk.__exit__(None, None, None)
     times = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
-    ms_step = float(np.mean(times))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    flush.fill_(-1.0)
+    torch.cuda.synchronize()
+    tplans, tC = step(timing_opts)  # the same step once more, with CUDA events around every kernel
+    torch.cuda.synchronize()
+    for p in tplans:
+        for name, ms in p.stats()["kernel_ms"].items():
+            kms[name] = kms.get(name, 0.0) + ms
+    del tplans, tC
     st_all = [p.stats() for p in plans]
     arrays = [p.arrays() for p in plans]
     sum_u = sum(p.upper_bound_nnz for p in plans)
-    res = {"policy": policy, "ms_per_step": ms_step, "value": 2.0 * sum_u * world / (ms_step * 1e-3) / 1e9,
-           "kms": {k: v / args.steps for k, v in kms.items()}, "launches": launches, "wall_s": t_wall,
+    value, ms_step = job_gflops(sum_u, float(np.mean(times)), world, dev)
+    res = {"policy": policy, "ms_per_step": ms_step, "value": value,
+           "kms": kms, "launches": launches, "wall_s": t_wall,
            "st_all": st_all, "arrays": arrays, "sum_u": sum_u, "nnz_C": int(st_all[-1]["nnz_c"]),
            "peak_bytes": int(sum(s["peak_bytes"] for s in st_all)),
            "merge_rounds": int(sum(s["merge_rounds"] for s in st_all)),
@@ -257,10 +274,25 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
     return res
 
 
-def time_steps(args, stream, flush, step, world=1):
+def job_gflops(products, ms, world, device):
+    """Whole-job GFLOP/s over `world` ranks (2 * products of all ranks / the slowest rank's
+    step time) and that time.  Every rank must call it; device is where the collective's
+    tensors live (a CUDA device for NCCL, the CPU for gloo)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        u = torch.tensor([float(products)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, products = float(t.item()), float(u.item())
+    return 2.0 * products / (ms * 1e-3) / 1e9, ms
+
+
+def time_steps(args, stream, flush, step):
     """W untimed warm-up calls of step(), then K calls each bracketed by CUDA events on
     `stream`, L2 flushed (512 MB write) before each, outside the events.  step() returns an
-    object kept alive until the next call.  Returns the per-step milliseconds (max over ranks)."""
+    object kept alive until the next call.  Returns this rank's mean milliseconds per step."""
     import torch
     keep = None
     for _ in range(args.warmup):
@@ -280,13 +312,7 @@ def time_steps(args, stream, flush, step, world=1):
         if k < args.steps - 1:
             del keep
             keep = None
-    ms = float(np.mean(times))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=torch.device("cuda", torch.cuda.current_device()))
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms, keep
+    return float(np.mean(times)), keep
 
 
 def galerkin_graph(args, spg, dev, stream, flush, opts, world):
@@ -308,7 +334,8 @@ def galerkin_graph(args, spg, dev, stream, flush, opts, world):
     def replay():
         g.launch()
 
-    ms_graph, _ = time_steps(args, stream, flush, replay, world)
+    ms_graph, _ = time_steps(args, stream, flush, replay)
+    v_graph, ms_graph = job_gflops(products, ms_graph, world, dev)
     p2.check()
 
     def ra_p():
@@ -318,15 +345,16 @@ def galerkin_graph(args, spg, dev, stream, flush, opts, world):
         q2.numeric()
         return q1, q2, RA
 
-    ms_rap, keep = time_steps(args, stream, flush, ra_p, world)
+    ms_rap, keep = time_steps(args, stream, flush, ra_p)
     prod_rap = keep[0].upper_bound_nnz + keep[1].upper_bound_nnz
+    v_rap, ms_rap = job_gflops(prod_rap, ms_rap, world, dev)
     nnz_ac = int(Ac.nnz)
     del keep, g, Ac, p1, p2
     torch.cuda.synchronize()
-    return {"graph_replay": {"value": 2.0 * products * world / (ms_graph * 1e-3) / 1e9, "unit": "GFLOP/s",
+    return {"graph_replay": {"value": v_graph, "unit": "GFLOP/s",
                              "ms_per_step": ms_graph, "products": int(products), "launches_per_step": None,
                              "note": "values-only replay of R*(A*P) (structure of A*P and Ac reused) in one CUDA graph"},
-            "rA_then_P": {"value": 2.0 * prod_rap * world / (ms_rap * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "rA_then_P": {"value": v_rap, "unit": "GFLOP/s",
                           "ms_per_step": ms_rap, "products": int(prod_rap)},
             "nnz_Ac": nnz_ac}
 
@@ -349,24 +377,31 @@ def run_batch(args, world, device):
     products = int(sum(_products_ab(A, B) for A, B in pairs))
     res = {}
 
-    def batched(policy, clocks=False, wave_mproducts=0):
-        opts, keep = policy_opts(policy)
-        opts = dict(opts, record_timing=True, wave_mproducts=wave_mproducts)
+    def batched(policy, clocks=False, wave_mproducts=0, tuned=False):
+        opts, keep = policy_opts(policy, "batch512" if tuned and args.tuned else None)
+        opts = dict(opts, wave_mproducts=wave_mproducts)
 
-        def step():
-            bp = spg.BatchPlan(As, Bs, stream=stream, **opts)
+        def step(o=opts):
+            bp = spg.BatchPlan(As, Bs, stream=stream, **o)
             bp.numeric()
             return bp
         clk = ClockSampler(dev.index) if clocks else None
         if clk:
             clk.__enter__()
-        ms, bp = time_steps(args, stream, flush, step, world)
+        ms, bp = time_steps(args, stream, flush, step)
+        value, ms = job_gflops(products, ms, world, dev)
         if clk:
             clk.__exit__(None, None, None)
         st = bp.stats()
-        out = {"value": 2.0 * products * world / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+        flush.fill_(-1.0)
+        torch.cuda.synchronize()
+        tp = step(dict(opts, record_timing=True))  # once more with CUDA events around every kernel
+        torch.cuda.synchronize()
+        kms = tp.stats()["kernel_ms"]
+        del tp
+        out = {"value": value, "ms_per_step": ms,
                "peak_bytes": int(st["peak_bytes"]), "held_bytes_after": int(st["held_bytes"]),
-               "launches_per_step": int(sum(st["launches"].values())), "kms": st["kernel_ms"],
+               "launches_per_step": int(sum(st["launches"].values())), "kms": kms,
                "rows_bin37": int(st["bin_count"][37]), "rows_fallback": int(st["rows_fallback"]),
                "merge_rounds": int(st["merge_rounds"]), "waves": bp.n_waves,
                "clocks": clk.summary() if clk else None}
@@ -383,20 +418,21 @@ def run_batch(args, world, device):
                 p.numeric()
                 plans.append(p)
             return plans
-        ms, plans = time_steps(args, stream, flush, step, world)
+        ms, plans = time_steps(args, stream, flush, step)
+        value, ms = job_gflops(products, ms, world, dev)
         held, peak, launches = 0, 0, 0
         for p in plans:  # results stay resident, so call i peaks on top of results 0..i-1
             st = p.stats()
             peak = max(peak, held + st["peak_bytes"])
             held += st["held_bytes"]
             launches += sum(st["launches"].values())
-        stats.update({"value": 2.0 * products * world / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+        stats.update({"value": value, "ms_per_step": ms,
                       "peak_bytes": int(peak), "launches_per_step": int(launches)})
         del plans, keep
         return stats
 
     head = args.policy
-    main, bp, keep = batched(head, clocks=True)
+    main, bp, keep = batched(head, clocks=True, tuned=True)
     arrays = bp.arrays()
     order = bp.pair_order()
     del bp
@@ -407,22 +443,23 @@ def run_batch(args, world, device):
             del b2, k2
             res["batched_" + p] = r
     torch.cuda.synchronize()
-    r, b2, k2 = batched(head, wave_mproducts=-1)  # all pairs in one wave: fewer launches, more memory
+    r, b2, k2 = batched(head, wave_mproducts=-1, tuned=True)  # one wave: fewer launches, more memory
     del b2, k2
     res[f"batched_{head}_one_wave"] = r
     torch.cuda.synchronize()
     res["sequential_hybrid"] = sequential("hybrid")
     torch.cuda.synchronize()
     # values-only replay of the whole batch in one CUDA graph
-    opts, keep_g = policy_opts(head)
+    opts, keep_g = policy_opts(head, "batch512" if args.tuned else None)
     gstream = torch.cuda.Stream(dev)  # a graph is captured from a created stream, not the legacy one
     torch.cuda.synchronize()
     gp = spg.BatchPlan(As, Bs, stream=gstream, **opts)
     gp.numeric()
     g = spg.ReplayGraph([gp])
-    ms_g, _ = time_steps(args, gstream, flush, g.launch, world)
+    ms_g, _ = time_steps(args, gstream, flush, g.launch)
+    v_g, ms_g = job_gflops(products, ms_g, world, dev)
     gp.check()
-    res["graph_replay"] = {"value": 2.0 * products * world / (ms_g * 1e-3) / 1e9, "ms_per_step": ms_g,
+    res["graph_replay"] = {"value": v_g, "ms_per_step": ms_g,
                            "note": "values-only replay (structure reused) of the batched plan, one CUDA graph"}
     del g, gp, keep_g
     torch.cuda.synchronize()
@@ -437,6 +474,7 @@ def run_batch(args, world, device):
         "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded generator)",
         "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "alloc_policy": head,
+                   "tuned": tuned_params(args, head),
                    "mode": "batched (block-diagonal concatenation, waves of <= 1024M products)",
                    "waves": main["waves"], "pairs": len(pairs),
                    "products_per_step": products, "l2": "flushed between steps (512 MB write)",
@@ -523,10 +561,10 @@ def run_ours(args, rank, world, device):
     if head == "learned" and not os.path.exists(WEIGHTS):
         head = "hybrid"
     others = [p for p in ("hybrid",) if p != head] if not args.single_policy else []
-    main_m = measure(args, spg, pairs, dev, stream, head, flush, world, sample_clocks=True)
+    main_m = measure(args, spg, pairs, dev, stream, head, flush, world, sample_clocks=True, tuned=True)
     cmp = {p: measure(args, spg, pairs, dev, stream, p, flush, world) for p in others}
-    e2e_opts, e2e_keep = policy_opts(head)  # keeps the predictor alive during the e2e runs
-    e2e = run_e2e(args, spg, pairs, dev, stream, e2e_opts)
+    e2e_opts, e2e_keep = policy_opts(head, args.workload if args.tuned else None)  # keeps the predictor alive
+    e2e = run_e2e(args, spg, pairs, dev, stream, e2e_opts, world)
     chain = galerkin_graph(args, spg, dev, stream, flush, e2e_opts, world) if args.workload == "galerkin64" else None
     del e2e_keep
 
@@ -541,7 +579,8 @@ def run_ours(args, rank, world, device):
         "ms_per_step": main_m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded generator)",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
-                   "alloc_policy": head, "products_per_step": main_m["sum_u"], "nnz_C": main_m["nnz_C"],
+                   "alloc_policy": head, "tuned": tuned_params(args, head),
+                   "products_per_step": main_m["sum_u"], "nnz_C": main_m["nnz_C"],
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roofline(args, pairs, main_m),
         "e2e": e2e,
@@ -561,7 +600,7 @@ def run_ours(args, rank, world, device):
     return out
 
 
-def run_e2e(args, spg, pairs, dev, stream, opts):
+def run_e2e(args, spg, pairs, dev, stream, opts, world=1):
     """Same metric through the public API with host buffers: pinned host -> device copies of
     the inputs, the product, and a device -> host read of the whole result, all timed."""
     import torch
@@ -593,9 +632,9 @@ def run_e2e(args, spg, pairs, dev, stream, opts):
         if k > 0:
             times.append(dt)
     u_sum = int(_products(A))
-    t = float(np.median(times))
-    return {"value": 2.0 * u_sum / t / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": t * 1e3}
+    value, ms = job_gflops(u_sum, float(np.median(times)) * 1e3, world, dev)
+    return {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms}
 
 
 def _products(A):
@@ -676,6 +715,8 @@ def main():
     ap.add_argument("--policy", default="learned", choices=["hybrid", "upper_bound", "learned"])
     ap.add_argument("--single-policy", action="store_true", help="do not also time the plain hybrid path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tuned", dest="tuned", action="store_false",
+                    help="do not apply the autotuner's parameters to the reported policy")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -117,7 +117,12 @@ typedef struct spgemm_opts {
                                 one wave of pairs may hold; pairs are grouped in order into waves
                                 computed one after another, each releasing its temporaries
                                 before the next (0 = 1024, negative = one wave) */
-    int32_t reserved[7];
+    int32_t heap_max_u;      /* rows with u_i <= heap_max_u use the heap kernel; the longer rows
+                                of bins 2..32 use the bitonic ESC kernel with 32 slots
+                                (0 = 32, the paper's split; 2..32 allowed) */
+    int32_t merge_wide_above; /* bin-37 launches with a result capacity above this use 512-thread
+                                 CTAs, smaller ones 256 (128 up to 512 entries); 0 = 2048 */
+    int32_t reserved[5];
     const void *predictor;   /* spgemm_predictor* for SPGEMM_ALLOC_LEARNED, else NULL; it must
                                 not be freed before spgemm_symbolic (or spgemm_galerkin) has
                                 returned, since its weights are read by that call's kernels */

@@ -1,0 +1,208 @@
+"""Autotuner for the library's launch parameters on a given workload.
+
+The paper notes that the bin boundaries and the kernel chosen for each bin depend
+on the architecture (Section 4.1).  This tuner searches, by coordinate descent on
+measured device time, over the parameters the library exposes for that choice:
+
+* heap_max_u   - the longest rows (u_i) given to the heap kernel; the rest of
+                 bins 2..32 go to the bitonic ESC kernel with 32 slots;
+* heap_block   - threads per block of the heap kernel;
+* merge_batch  - products absorbed per batch by the bin-37 merge kernel;
+* smem_cap_max - the largest result held in shared memory by the merge kernel
+                 (smaller values leave room for more CTAs per SM, and split
+                 long rows earlier);
+* merge_wide_above - result capacities above this run 512-thread merge CTAs,
+                 smaller ones 256-thread CTAs (two can share an SM);
+* initial_cap  - the first bin-37 row size of the plain (hybrid) policy;
+* predictor_margin - the safety factor of the learned policy.
+
+A configuration is kept only if it is faster and its peak device memory stays
+within 5% of the default configuration's, so tuning never buys time with memory.
+Results are exact for every configuration (the tests check that), so the tuner
+only ever trades time.  Each trial times the whole product (symbolic + numeric)
+with CUDA events after a warm-up, median of `reps`.
+
+    python -m paper_1504_05022_gb300.autotune --workload rmat16x16 [--policy learned]
+
+writes the best parameters to paper_1504_05022_gb300/tuned.json, which
+bench.py applies to the policy it reports.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import sys
+import time
+
+import numpy as np
+
+_ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if _ROOT not in sys.path:
+    sys.path.insert(0, _ROOT)
+
+TUNED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+SPACE = {
+    "heap_max_u": [32, 24, 16, 8],
+    "heap_block": [128, 64, 256],
+    "merge_batch": [2048, 1024, 512],
+    "smem_cap_max": [0, 8192, 6144, 4096],
+    "merge_wide_above": [2048, 4096, 6144, 1 << 20],
+    "initial_cap": [256, 512, 1024],
+    "predictor_margin": [None, 1.15, 1.5, 2.0],  # None = the margin stored with the weights
+}
+POLICY_PARAMS = {
+    "hybrid": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "initial_cap"],
+    "learned": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "predictor_margin"],
+    "upper_bound": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above"],
+}
+MEMORY_SLACK = 1.05
+
+
+def workload(name: str):
+    """(A, B) host pairs of a named workload (the products bench.py times)."""
+    import gen
+    if name.startswith("rmat"):
+        scale, avg = (int(x) for x in name[4:].split("x"))
+        A = gen.rmat(scale, avg, seed=1)
+        return [(A, A)]
+    if name == "lap2d64":
+        A = gen.lap2d(64)
+        return [(A, A)]
+    if name == "batch512":
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+            return pool.map(gen.batch_pair, range(512), chunksize=1)
+    raise ValueError(f"unknown workload {name}")
+
+
+def base_opts(policy: str, predictor=None) -> dict:
+    if policy == "learned":
+        return predictor.opts()
+    return {"alloc_policy": policy}
+
+
+def apply(opts: dict, params: dict, predictor=None) -> dict:
+    out = dict(opts)
+    for k, v in params.items():
+        if k == "predictor_margin":
+            if v is not None:
+                out["predictor_margin"] = float(v)
+        elif v is not None:
+            out[k] = v
+    return out
+
+
+class Runner:
+    """Times one configuration of the whole product on device-resident inputs."""
+
+    def __init__(self, pairs, device="cuda"):
+        import torch
+
+        from .spgemm import CSR
+        self.torch = torch
+        self.batched = len(pairs) > 1
+        self.A = [CSR.from_host(A, device=device, rowptr_dtype=torch.int32) for A, _ in pairs]
+        self.B = [a if B is A else CSR.from_host(B, device=device, rowptr_dtype=torch.int32)
+                  for a, (A, B) in zip(self.A, pairs)]
+        self.stream = torch.cuda.current_stream()
+
+    def once(self, opts):
+        from .spgemm import BatchPlan, Plan
+        if self.batched:
+            p = BatchPlan(self.A, self.B, stream=self.stream, **opts)
+        else:
+            p = Plan(self.A[0], self.B[0], stream=self.stream, **opts)
+        p.numeric()
+        return p
+
+    def time(self, opts, reps: int = 3):
+        torch = self.torch
+        p = self.once(opts)  # warm-up (also loads kernels)
+        peak = p.stats()["peak_bytes"]
+        del p
+        times = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            p = self.once(opts)
+            e1.record(self.stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            del p
+        return statistics.median(times), peak
+
+
+def tune(runner: Runner, policy: str, predictor=None, rounds: int = 2, reps: int = 3, log=print) -> dict:
+    """Coordinate descent over POLICY_PARAMS[policy]; returns the result record."""
+    names = POLICY_PARAMS[policy]
+    best = {k: SPACE[k][0] for k in names}
+    opts0 = base_opts(policy, predictor)
+    default_ms, default_peak = runner.time(apply(opts0, best), reps)
+    best_ms = default_ms
+    trials = [{"params": dict(best), "ms": default_ms, "peak_bytes": default_peak}]
+    log(f"default {best}: {default_ms:.3f} ms, peak {default_peak / 1e9:.2f} GB")
+    for r in range(rounds):
+        changed = False
+        for k in names:
+            for v in SPACE[k]:
+                if v == best[k]:
+                    continue
+                cand = dict(best, **{k: v})
+                ms, peak = runner.time(apply(opts0, cand), reps)
+                trials.append({"params": cand, "ms": ms, "peak_bytes": peak})
+                ok = peak <= default_peak * MEMORY_SLACK
+                log(f"  round {r} {k}={v}: {ms:.3f} ms, peak {peak / 1e9:.2f} GB{'' if ok else ' (memory)'}")
+                if ok and ms < best_ms * 0.99:
+                    best, best_ms, changed = cand, ms, True
+        if not changed:
+            break
+    log(f"best {best}: {best_ms:.3f} ms (default {default_ms:.3f} ms)")
+    return {"params": best, "ms": best_ms, "default_ms": default_ms, "default_peak_bytes": default_peak,
+            "trials": len(trials), "reps": reps}
+
+
+def load(workload_name: str, policy: str) -> dict | None:
+    """Tuned parameters for (workload, policy), or None."""
+    if not os.path.exists(TUNED):
+        return None
+    try:
+        rec = json.load(open(TUNED)).get(workload_name, {}).get(policy)
+    except (OSError, ValueError):
+        return None
+    return None if rec is None else rec.get("params")
+
+
+def main():
+    import torch
+
+    from .predictor import Predictor
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", required=True)
+    ap.add_argument("--policy", default="learned", choices=list(POLICY_PARAMS))
+    ap.add_argument("--rounds", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--out", default=TUNED)
+    args = ap.parse_args()
+    if not torch.cuda.is_available():
+        raise SystemExit("autotune needs a CUDA device")
+    t0 = time.time()
+    pairs = workload(args.workload)
+    runner = Runner(pairs)
+    pred = Predictor.load() if args.policy == "learned" else None
+    rec = tune(runner, args.policy, pred, rounds=args.rounds, reps=args.reps)
+    rec["products"] = int(sum(np.diff(B.row_ptr)[A.col].sum() for A, B in pairs))
+    rec["device"] = torch.cuda.get_device_name()
+    rec["tuning_seconds"] = round(time.time() - t0, 1)
+    doc = json.load(open(args.out)) if os.path.exists(args.out) else {}
+    doc.setdefault(args.workload, {})[args.policy] = rec
+    with open(args.out, "w") as f:
+        json.dump(doc, f, indent=1, sort_keys=True)
+    print(json.dumps(rec))
+
+
+if __name__ == "__main__":
+    main()

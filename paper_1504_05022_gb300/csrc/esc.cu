@@ -1,5 +1,6 @@
 // Stage 3, bin group 4 (u_i = 33..512): the bitonic ESC method of Section 4.1
-// (expand, sort, compress).
+// (expand, sort, compress).  With N = 32 it also serves rows of the heap bins
+// (u_i <= 32) when the heap kernel is limited to shorter rows (heap_max_u).
 //
 // One warp per row.  The warp expands the row's u_i products into a per-warp
 // shared-memory array padded to N = 32*E entries (64, 128, 256 or 512, the bin's
@@ -178,6 +179,7 @@ cudaError_t launch_esc(const StageArgs &a, const int32_t *rows, int64_t nrows, i
     if (nrows <= 0) return cudaSuccess;
     unsigned grid = (unsigned)((nrows + ESC_WARPS - 1) / ESC_WARPS);
     switch (bin) {
+        case 32: k_esc<1><<<grid, ESC_WARPS * 32, 0, st>>>(a, rows, nrows); break;  // u <= 32 (heap bins)
         case 33: k_esc<2><<<grid, ESC_WARPS * 32, 0, st>>>(a, rows, nrows); break;
         case 34: k_esc<4><<<grid, ESC_WARPS * 32, 0, st>>>(a, rows, nrows); break;
         case 35: k_esc<8><<<grid, ESC_WARPS * 32, 0, st>>>(a, rows, nrows); break;

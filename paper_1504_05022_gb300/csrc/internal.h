@@ -124,11 +124,12 @@ struct MergeLaunch {
     int32_t *ovf_list;       // items that overflowed
     int32_t *ovf_count;
     int64_t *err;            // device error word
+    int wide_above;          // capacities above this use 512-thread CTAs (0 = 2048)
 };
 
-int merge_smem_bytes(int cap, int batch);
-int merge_batch_limit(int cap);
-int merge_max_cap(int batch, int smem_limit);
+int merge_smem_bytes(int cap, int batch, int wide_above);
+int merge_batch_limit(int cap, int wide_above);
+int merge_max_cap(int batch, int smem_limit, int wide_above);
 cudaError_t launch_merge(const StageArgs &a, const MergeItems &it, const MergeLaunch &L, cudaStream_t st);
 cudaError_t launch_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
                               double *ctil_val, const MergeItems &it, cudaStream_t st);

@@ -71,16 +71,22 @@ __host__ __device__ inline size_t merge_layout(int cap, int kb, int W, unsigned 
     return off;
 }
 
-// Threads per CTA for a launch with result capacity `cap`.
-inline int merge_threads(int cap) { return cap <= 512 ? 128 : (cap <= 2048 ? 256 : 512); }
-
-int merge_smem_bytes(int cap, int batch) {
-    return (int)merge_layout(cap, batch, merge_threads(cap), nullptr, nullptr);
+// Threads per CTA for a launch with result capacity `cap`: 128 up to 512 entries,
+// 256 up to `wide_above` entries (0 = 2048), 512 beyond.
+inline int merge_threads(int cap, int wide_above) {
+    if (wide_above <= 0) wide_above = 2048;
+    return cap <= 512 ? 128 : (cap <= wide_above ? 256 : 512);
 }
 
-int merge_max_cap(int batch, int smem_limit) {
+int merge_smem_bytes(int cap, int batch, int wide_above) {
+    return (int)merge_layout(cap, batch, merge_threads(cap, wide_above), nullptr, nullptr);
+}
+
+int merge_max_cap(int batch, int smem_limit, int wide_above) {
     int cap = 256;
-    while (merge_smem_bytes(cap + 256, std::min(batch, 4 * merge_threads(cap + 256))) <= smem_limit) cap += 256;
+    while (merge_smem_bytes(cap + 256, std::min(batch, 4 * merge_threads(cap + 256, wide_above)), wide_above) <=
+           smem_limit)
+        cap += 256;
     return cap;
 }
 
@@ -643,15 +649,15 @@ static cudaError_t launch_merge_nt(const StageArgs &a, const MergeItems &s, cons
 
 cudaError_t launch_merge(const StageArgs &a, const MergeItems &s, const MergeLaunch &L, cudaStream_t st) {
     if (L.nwork <= 0) return cudaSuccess;
-    const int nt = merge_threads(L.cap);
+    const int nt = merge_threads(L.cap, L.wide_above);
     // batch >= 32 keeps every loop of the kernel progressing (the level-1 stream takes batch/2 per step)
     if (L.batch > nt * MERGE_MAX_IPT || L.batch < 32 || L.batch > L.cap) return cudaErrorInvalidValue;
-    const int smem = merge_smem_bytes(L.cap, L.batch);
+    const int smem = merge_smem_bytes(L.cap, L.batch, L.wide_above);
     if (nt == 128) return launch_merge_nt<128, 4>(a, s, L, smem, st);
     if (nt == 256) return launch_merge_nt<256, 2>(a, s, L, smem, st);
     return launch_merge_nt<512, 1>(a, s, L, smem, st);
 }
 
-int merge_batch_limit(int cap) { return MERGE_MAX_IPT * merge_threads(cap); }
+int merge_batch_limit(int cap, int wide_above) { return MERGE_MAX_IPT * merge_threads(cap, wide_above); }
 
 }  // namespace spg

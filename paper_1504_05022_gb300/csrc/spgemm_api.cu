@@ -132,7 +132,7 @@ struct spgemm_plan {
     int32_t *pred_cap = nullptr;      // predicted temporary size per row
     int32_t *class_order = nullptr;   // bin-37 item indices grouped by launch class
     int32_t class_caps[NUM_LAUNCH_CLASSES] = {0};
-    int capmax = 0, batch = 0;
+    int capmax = 0, batch = 0, wide_above = 2048;
     // batched plans: the pairs and the concatenation offsets
     int64_t npairs = 0;
     PairDesc *d_pairs = nullptr;
@@ -245,7 +245,8 @@ static void merge_limits(spgemm_plan *p) {
     const int smem_limit = (p->smem_optin > 0 ? p->smem_optin : 227 * 1024) - 1024;
     int batch = p->opts.merge_batch > 0 ? p->opts.merge_batch : 2048;
     batch = std::max(32, std::min(batch, 2048));
-    int capmax = merge_max_cap(batch, smem_limit);
+    p->wide_above = p->opts.merge_wide_above > 0 ? p->opts.merge_wide_above : 2048;
+    int capmax = merge_max_cap(batch, smem_limit, p->wide_above);
     if (p->opts.smem_cap_max > 0) capmax = std::min(capmax, std::max(256, p->opts.smem_cap_max));
     p->batch = batch;
     p->capmax = capmax;
@@ -313,6 +314,45 @@ StageArgs stage_args(spgemm_plan *p) {
     a.ctil_val = p->ctil_val;
     a.nnzc = p->nnzc;
     return a;
+}
+
+// Stage 3, bins 2..36 (bin groups 3 and 4): the heap kernel for bins 2..heap_max_u
+// (one launch per range, sized to the range's widest heap), the bitonic ESC kernel
+// with 32 slots for the rest of bins up to 32, and ESC for bins 33..36.
+cudaError_t launch_short_bins(spgemm_plan *p, const StageArgs &a, bool account) {
+    cudaError_t e = cudaSuccess;
+    const int hmax = (p->opts.heap_max_u >= 2 && p->opts.heap_max_u <= 32) ? p->opts.heap_max_u : 32;
+    const int heap_nt = p->opts.heap_block > 0 ? p->opts.heap_block : 128;
+    auto run = [&](int kind, auto &&launch) {
+        if (account) p->time_begin(kind);
+        e = launch();
+        if (account) {
+            p->time_end();
+            p->count(kind);
+        }
+        return e;
+    };
+    for (auto &r : kHeapRanges) {
+        const int lo = r[0], hi = std::min(r[1], hmax);
+        if (lo > hi) continue;
+        const int64_t s0 = p->bin_start[lo], s1 = p->bin_start[hi + 1];
+        if (s1 > s0 && run(SPGEMM_K_HEAP, [&] { return launch_heap(a, p->bin_rows + s0, s1 - s0, hi, heap_nt, p->st); }) !=
+                           cudaSuccess)
+            return e;
+    }
+    if (hmax < 32) {
+        const int64_t s0 = p->bin_start[hmax + 1], s1 = p->bin_start[33];
+        if (s1 > s0 && run(SPGEMM_K_ESC, [&] { return launch_esc(a, p->bin_rows + s0, s1 - s0, 32, p->st); }) !=
+                           cudaSuccess)
+            return e;
+    }
+    for (int b = BIN_ESC_LO; b <= BIN_ESC_HI; ++b) {
+        const int64_t s0 = p->bin_start[b], s1 = p->bin_start[b + 1];
+        if (s1 > s0 && run(SPGEMM_K_ESC, [&] { return launch_esc(a, p->bin_rows + s0, s1 - s0, b, p->st); }) !=
+                           cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -582,11 +622,12 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
                     SPG_TRY(p->alloc_n(&list[which ^ 1], list_cap, LIFE_NUMERIC));
                 }
                 MergeLaunch L{};
+                L.wide_above = p->wide_above;
                 L.work = work;
                 L.work_base = work_base;
                 L.nwork = nwork;
                 L.cap = cap;
-                L.batch = std::min(std::min(batch, cap), merge_batch_limit(cap));
+                L.batch = std::min(std::min(batch, cap), merge_batch_limit(cap, p->wide_above));
                 L.level1 = level1 ? 1 : 0;
                 L.ovf_list = list[which];
                 L.ovf_count = ovf_count;
@@ -726,10 +767,11 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 const int ccap = std::min(capmax, beyond ? capmax : p->class_caps[g]);
                 const int tgt = beyond ? SPLIT : level_of(std::min(2 * ccap, capmax));
                 MergeLaunch L{};
+                L.wide_above = p->wide_above;
                 L.work = p->class_order + off;
                 L.nwork = cnt;
                 L.cap = ccap;
-                L.batch = std::min(std::min(p->batch, ccap), merge_batch_limit(ccap));
+                L.batch = std::min(std::min(p->batch, ccap), merge_batch_limit(ccap, p->wide_above));
                 L.ovf_list = lists[tgt];
                 L.ovf_count = counts + tgt;
                 L.err = p->d_err;
@@ -754,10 +796,11 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 if (nk == 0) continue;
                 const int tgt = level_of(std::min(2 * lv[k], capmax));
                 MergeLaunch L{};
+                L.wide_above = p->wide_above;
                 L.work = lists[k];
                 L.nwork = nk;
                 L.cap = lv[k];
-                L.batch = std::min(std::min(p->batch, lv[k]), merge_batch_limit(lv[k]));
+                L.batch = std::min(std::min(p->batch, lv[k]), merge_batch_limit(lv[k], p->wide_above));
                 L.ovf_list = lists[tgt];
                 L.ovf_count = counts + tgt;
                 L.err = p->d_err;
@@ -801,26 +844,7 @@ extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
     StageArgs a = stage_args(p);
     {
         // ---- stage 3: bin groups 3 (heap) and 4 (bitonic ESC) ----
-        const int heap_nt = p->opts.heap_block > 0 ? p->opts.heap_block : 128;
-        for (auto &r : kHeapRanges) {
-            const int64_t s0 = p->bin_start[r[0]], s1 = p->bin_start[r[1] + 1];
-            if (s1 > s0) {
-                const int slots = r[1];
-                p->time_begin(SPGEMM_K_HEAP);
-                SPG_TRY(launch_heap(a, p->bin_rows + s0, s1 - s0, slots, heap_nt, p->st));
-                p->time_end();
-                p->count(SPGEMM_K_HEAP);
-            }
-        }
-        for (int b = BIN_ESC_LO; b <= BIN_ESC_HI; ++b) {
-            const int64_t s0 = p->bin_start[b], s1 = p->bin_start[b + 1];
-            if (s1 > s0) {
-                p->time_begin(SPGEMM_K_ESC);
-                SPG_TRY(launch_esc(a, p->bin_rows + s0, s1 - s0, b, p->st));
-                p->time_end();
-                p->count(SPGEMM_K_ESC);
-            }
-        }
+        SPG_TRY(launch_short_bins(p, a, true));
         // ---- stage 3: bin group 5 (merge, progressive) ----
         status = run_bin37(p);
         if (status != SPGEMM_OK) goto fail;
@@ -1230,15 +1254,7 @@ extern "C" spgemm_status spgemm_numeric_replay(spgemm_plan *p) {
         a.ctil_rp = p->C.row_ptr;
         a.ctil_col = p->C.col_idx;
         a.ctil_val = p->C.val;
-        const int heap_nt = p->opts.heap_block > 0 ? p->opts.heap_block : 128;
-        for (auto &r : kHeapRanges) {
-            const int64_t s0 = p->bin_start[r[0]], s1 = p->bin_start[r[1] + 1];
-            if (s1 > s0) SPG_TRY(launch_heap(a, p->bin_rows + s0, s1 - s0, r[1], heap_nt, p->st));
-        }
-        for (int b = BIN_ESC_LO; b <= BIN_ESC_HI; ++b) {
-            const int64_t s0 = p->bin_start[b], s1 = p->bin_start[b + 1];
-            if (s1 > s0) SPG_TRY(launch_esc(a, p->bin_rows + s0, s1 - s0, b, p->st));
-        }
+        SPG_TRY(launch_short_bins(p, a, false));
         // bin 1: the single product of each row
         {
             const int64_t s0 = p->bin_start[1], s1 = p->bin_start[2];

@@ -115,7 +115,8 @@ def _wrap_u8(ptr: int, n: int, owner: _PlanHandle, device: int) -> torch.Tensor:
 def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs: bool = False,
               record_timing: bool = False, merge_batch: int = 0, smem_cap_max: int = 0,
               heap_block: int = 0, long_rows: str = "split", predictor=None,
-              predictor_margin: float = 1.0, wave_mproducts: int = 0) -> _lib.Opts:
+              predictor_margin: float = 1.0, wave_mproducts: int = 0, heap_max_u: int = 0,
+              merge_wide_above: int = 0) -> _lib.Opts:
     L = _lib.load()
     o = _lib.Opts()
     _lib.check(L.spgemm_opts_init(ctypes.byref(o)), "spgemm_opts_init")
@@ -128,6 +129,8 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
     o.heap_block = int(heap_block)
     o.long_rows = _lib.LONG_ROWS[long_rows]
     o.wave_mproducts = int(wave_mproducts)
+    o.heap_max_u = int(heap_max_u)
+    o.merge_wide_above = int(merge_wide_above)
     # a Predictor object (whose device weights the caller keeps alive) or a raw handle
     o.predictor = getattr(predictor, "handle", predictor)
     o.predictor_margin = float(predictor_margin)

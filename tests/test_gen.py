@@ -40,3 +40,15 @@ def test_families_valid():
         M = gen.family_matrix(fam, 1000, param, seed=3)
         M.validate()
         assert M.nrows >= 1000
+
+
+def test_autotune_apply_and_load(tmp_path, monkeypatch):
+    from paper_1504_05022_gb300 import autotune
+    opts = autotune.apply({"alloc_policy": "learned", "predictor_margin": 1.3},
+                          {"heap_max_u": 16, "predictor_margin": None, "merge_batch": 1024})
+    assert opts == {"alloc_policy": "learned", "predictor_margin": 1.3, "heap_max_u": 16, "merge_batch": 1024}
+    f = tmp_path / "tuned.json"
+    f.write_text('{"w": {"hybrid": {"params": {"heap_block": 64}}}}')
+    monkeypatch.setattr(autotune, "TUNED", str(f))
+    assert autotune.load("w", "hybrid") == {"heap_block": 64}
+    assert autotune.load("w", "learned") is None and autotune.load("x", "hybrid") is None

@@ -272,3 +272,45 @@ def test_temporaries_released_after_numeric(spg, oracle_mod, policy):
     plan2, C2 = run(spg, A, A, **opts)  # allocates from the released memory
     check(oracle_mod, A, A, C, label=f"first result after release/{policy}")
     assert torch.equal(C.col, C2.col)
+
+
+@pytest.mark.parametrize("heap_max_u", [2, 8, 17, 32])
+def test_heap_esc_boundary(spg, oracle_mod, heap_max_u):
+    """Rows of bins heap_max_u+1..32 go to the bitonic ESC kernel with 32 slots instead of the
+    heap kernel: same structure and values within tolerance, and replay agrees."""
+    A = gen.erdos_renyi(3000, 5, seed=4)   # u_i spread over bins 2..64
+    plan, C = run(spg, A, A, heap_max_u=heap_max_u)
+    ref = check(oracle_mod, A, A, C, label=f"heap_max_u={heap_max_u}")
+    bins = plan.arrays()["bin"]
+    assert ((bins >= 2) & (bins <= 32)).sum() > 1000
+    st = plan.stats()
+    if heap_max_u < 32:
+        assert st["launches"]["esc"] >= 1
+    plan.replay()
+    torch.cuda.synchronize()
+    check(oracle_mod, A, A, C, label=f"replay heap_max_u={heap_max_u}")
+    del ref
+
+
+def test_autotune_smoke(spg):
+    """The tuner runs on a small product, keeps the memory bound and returns values of its space."""
+    from paper_1504_05022_gb300 import autotune
+    A = gen.rmat(11, 8, seed=5)
+    runner = autotune.Runner([(A, A)])
+    rec = autotune.tune(runner, "hybrid", rounds=1, reps=1, log=lambda *_: None)
+    for k, v in rec["params"].items():
+        assert v in autotune.SPACE[k]
+    assert rec["ms"] <= rec["default_ms"]
+
+
+@pytest.mark.parametrize("wide_above,smem_cap_max,policy", [(4096, 0, "hybrid"), (1 << 20, 0, "hybrid"),
+                                                           (6144, 6144, "hybrid"), (1 << 20, 0, "learned")])
+def test_merge_cta_width(spg, oracle_mod, wide_above, smem_cap_max, policy):
+    """256-thread merge CTAs for larger result capacities (merge_wide_above) give the same C."""
+    from paper_1504_05022_gb300.predictor import Predictor
+    A = gen.rmat(13, 16, seed=31)
+    keep = Predictor.load() if policy == "learned" else None
+    opts = keep.opts() if keep else {"alloc_policy": policy}
+    plan, C = run(spg, A, A, merge_wide_above=wide_above, smem_cap_max=smem_cap_max, **opts)
+    check(oracle_mod, A, A, C, label=f"wide_above={wide_above}/{smem_cap_max}/{policy}")
+    assert plan.stats()["bin_count"][37] > 0
