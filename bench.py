@@ -463,9 +463,11 @@ def run_batch(args, world, device):
                            "note": "values-only replay (structure reused) of the batched plan, one CUDA graph"}
     del g, gp, keep_g
     torch.cuda.synchronize()
-    m = {"policy": head, "kms": main["kms"], "st_all": [{"launches": {}}], "arrays": [arrays]}
-    cat = _Cat([pairs[i][0] for i in order])  # rows in the order of the plan's arrays
-    rl = roofline(args, [(cat, cat)], m)
+    m = {"policy": head, "kms": main["kms"], "st_all": [{"launches": {}}], "arrays": [arrays],
+         "ms_per_step": main["ms_per_step"]}
+    cat_a = _Cat([pairs[i][0] for i in order])  # rows in the order of the plan's arrays
+    cat_b = _Cat([pairs[i][1] for i in order])
+    rl = roofline(args, [(cat_a, cat_b)], m)
     rl["launches_per_step"] = None
     main_clocks = main.pop("clocks")
     out = {
@@ -538,7 +540,17 @@ def roofline(args, pairs, m):
                 traffic = ent.get("bytes_per_step")
         except Exception:
             traffic = None
+    # compulsory bytes: A, B and C read or written once each, over the whole step time
+    comp = 0
+    for (A, B), arr in zip(pairs, m["arrays"]):
+        if B is None:
+            continue
+        comp += A.nnz * 12 + (A.nrows + 1) * 4 + int(arr["row_nnz"].astype(np.int64).sum()) * 12 + (A.nrows + 1) * 8
+        if B is not A:
+            comp += B.nnz * 12 + (B.nrows + 1) * 4
+    comp_gbs = comp / (m["ms_per_step"] * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "compulsory_bytes_per_step": comp, "compulsory_gbs": comp_gbs, "compulsory_frac": comp_gbs / hbm_peak,
             "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic, "peak_source": peak_src,
             "algorithmic_bytes_per_step": bytes_dom, "kernel_ms_per_step": dom_ms,
             "launches_per_step": dom_launches,

@@ -13,6 +13,7 @@ Functions (each follows a passage of Liu & Vinter's paper):
                          dense sparse accumulator (Section 2.2); structural zeros kept
                          (Section 3.1); returns also den_ij = sum_k |a_ik b_kj|.
 * :func:`spgemm_rows`    the same for a subset of rows (sampled parity at full size).
+* :func:`row_counts`     nnz per row only (row pointers checked at full size).
 * :func:`upper_bound`    u_i of Algorithm 2.
 * :func:`binning`        bins and temporary-row sizes of Algorithm 3.
 """
@@ -86,6 +87,23 @@ def _csr_arrays(M):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def row_counts(A, B, rows: np.ndarray | None = None, nthreads: int = 0, variant: int = 0) -> np.ndarray:
+    """nnz of the selected rows of C = A*B (all rows for rows=None): the size pass of
+    spgemm_rows alone (Gustavson's structure, Alg. 1), for checking row pointers at full size."""
+    lib = _load(variant)
+    if A.ncols != B.nrows:
+        raise ValueError("shape mismatch")
+    arp, acol, _ = _csr_arrays(A)
+    brp, bcol, _ = _csr_arrays(B)
+    rows_arr = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nsel = A.nrows if rows_arr is None else rows_arr.shape[0]
+    counts = np.zeros(max(nsel, 1), dtype=np.int64)
+    if lib.oracle_rows_count(B.ncols, _p(arp), _p(acol), _p(brp), _p(bcol),
+                             _p(rows_arr) if rows_arr is not None else None, nsel, _p(counts), nthreads) != 0:
+        raise MemoryError("oracle accumulator allocation failed")
+    return counts[:nsel]
 
 
 def spgemm_rows(A, B, rows: np.ndarray | None, nthreads: int = 0, variant: int = 0):

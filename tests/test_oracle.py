@@ -292,3 +292,12 @@ def test_planted_mistakes_fail_a_pin(oracle_mod, variant):
     A = gen.lap2d(16)
     caught.append(_as_dict(oracle_mod.spgemm(A, A, variant=variant)) != _lap2d_expected(16))
     assert all(caught)
+
+
+def test_row_counts_match_full_product():
+    import oracle
+    A = gen.rmat(10, 8, seed=4)
+    ref = oracle.spgemm(A, A)
+    assert np.array_equal(oracle.row_counts(A, A), np.diff(ref.row_ptr))
+    rows = np.array([5, 0, 1023, 7])
+    assert np.array_equal(oracle.row_counts(A, A, rows), np.diff(ref.row_ptr)[rows])
