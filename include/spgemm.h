@@ -103,6 +103,20 @@ typedef enum spgemm_long_rows {
     SPGEMM_LONG_ROWS_LEVEL1 = 1
 } spgemm_long_rows;
 
+/* Form of the bin-37 merge kernel (Section 4.1, merge method). */
+typedef enum spgemm_merge_kernel {
+    /* Bitmap form when B has at most 131072 columns and long rows are split, else the
+       merge-path form (default). */
+    SPGEMM_MERGE_AUTO = 0,
+    /* Merge-path form: every batch's new columns are sorted by pairwise merge-path
+       merges and merged into a pending set, then into the result, in place. */
+    SPGEMM_MERGE_PATH = 1,
+    /* Bitmap form: a bitmap with a rank directory over the item's column range gives
+       each product's position in the result in O(1); new columns are buffered and
+       merged into the result by rank when the buffer fills (same eligibility as AUTO). */
+    SPGEMM_MERGE_BITMAP = 2
+} spgemm_merge_kernel;
+
 /* Options; initialise with spgemm_opts_init and change fields as needed. */
 typedef struct spgemm_opts {
     int32_t alloc_policy;    /* spgemm_alloc_policy */
@@ -122,7 +136,10 @@ typedef struct spgemm_opts {
                                 (0 = 32, the paper's split; 2..32 allowed) */
     int32_t merge_wide_above; /* bin-37 launches with a result capacity above this use 512-thread
                                  CTAs, smaller ones 256 (128 up to 512 entries); 0 = 2048 */
-    int32_t reserved[5];
+    int32_t merge_kernel;    /* spgemm_merge_kernel: form of the bin-37 kernel */
+    int32_t merge_miss;      /* bitmap form: products whose column is new are buffered up to this
+                                many entries before they are merged into the result (0 = 4096) */
+    int32_t reserved[3];
     const void *predictor;   /* spgemm_predictor* for SPGEMM_ALLOC_LEARNED, else NULL; it must
                                 not be freed before spgemm_symbolic (or spgemm_galerkin) has
                                 returned, since its weights are read by that call's kernels */

@@ -35,7 +35,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("alloc_policy", c_i32), ("initial_cap", c_i32), ("check_inputs", c_i32),
                 ("record_timing", c_i32), ("merge_batch", c_i32), ("smem_cap_max", c_i32),
                 ("heap_block", c_i32), ("long_rows", c_i32), ("wave_mproducts", c_i32), ("heap_max_u", c_i32),
-                ("merge_wide_above", c_i32), ("reserved", c_i32 * 5),
+                ("merge_wide_above", c_i32), ("merge_kernel", c_i32), ("merge_miss", c_i32),
+                ("reserved", c_i32 * 3),
                 ("predictor", c_ptr),
                 ("predictor_margin", c_f64)]
 

@@ -125,9 +125,16 @@ struct MergeLaunch {
     int32_t *ovf_count;
     int64_t *err;            // device error word
     int wide_above;          // capacities above this use 512-thread CTAs (0 = 2048)
+    int bm_words;            // > 0: bitmap kernel, bitmap words covering B's columns
+    int bm_miss;             // bitmap kernel: miss-buffer entries
 };
 
 int merge_smem_bytes(int cap, int batch, int wide_above);
+// Bitmap form of the bin-37 kernel (merge_bm.cu), for B with at most BM_MAX_COLS columns.
+constexpr int64_t BM_MAX_COLS = 131072;
+int merge_bm_smem_bytes(int cap, int nwords, int miss, int wide_above);
+int merge_bm_max_cap(int nwords, int miss, int smem_limit, int wide_above);
+cudaError_t launch_merge_bm(const StageArgs &a, const MergeItems &s, const MergeLaunch &L, cudaStream_t st);
 int merge_batch_limit(int cap, int wide_above);
 int merge_max_cap(int batch, int smem_limit, int wide_above);
 cudaError_t launch_merge(const StageArgs &a, const MergeItems &it, const MergeLaunch &L, cudaStream_t st);

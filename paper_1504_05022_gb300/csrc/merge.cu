@@ -649,6 +649,7 @@ static cudaError_t launch_merge_nt(const StageArgs &a, const MergeItems &s, cons
 
 cudaError_t launch_merge(const StageArgs &a, const MergeItems &s, const MergeLaunch &L, cudaStream_t st) {
     if (L.nwork <= 0) return cudaSuccess;
+    if (L.bm_words > 0 && !L.level1) return launch_merge_bm(a, s, L, st);
     const int nt = merge_threads(L.cap, L.wide_above);
     // batch >= 32 keeps every loop of the kernel progressing (the level-1 stream takes batch/2 per step)
     if (L.batch > nt * MERGE_MAX_IPT || L.batch < 32 || L.batch > L.cap) return cudaErrorInvalidValue;

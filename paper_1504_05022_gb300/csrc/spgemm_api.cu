@@ -132,7 +132,7 @@ struct spgemm_plan {
     int32_t *pred_cap = nullptr;      // predicted temporary size per row
     int32_t *class_order = nullptr;   // bin-37 item indices grouped by launch class
     int32_t class_caps[NUM_LAUNCH_CLASSES] = {0};
-    int capmax = 0, batch = 0, wide_above = 2048;
+    int capmax = 0, batch = 0, wide_above = 2048, bm_words = 0, bm_miss = 0;
     // batched plans: the pairs and the concatenation offsets
     int64_t npairs = 0;
     PairDesc *d_pairs = nullptr;
@@ -247,6 +247,16 @@ static void merge_limits(spgemm_plan *p) {
     batch = std::max(32, std::min(batch, 2048));
     p->wide_above = p->opts.merge_wide_above > 0 ? p->opts.merge_wide_above : 2048;
     int capmax = merge_max_cap(batch, smem_limit, p->wide_above);
+    // the bitmap kernel when B's columns fit its bitmap and long rows are split
+    p->bm_words = 0;
+    p->bm_miss = 0;
+    if (p->opts.merge_kernel != SPGEMM_MERGE_PATH && p->opts.long_rows == SPGEMM_LONG_ROWS_SPLIT && p->B.ncols > 0 &&
+        p->B.ncols <= BM_MAX_COLS) {
+        p->bm_words = (int)((p->B.ncols + 31) / 32);
+        const int miss = p->opts.merge_miss > 0 ? p->opts.merge_miss : 4096;
+        p->bm_miss = std::max(batch, std::min(miss, 16384));
+        capmax = merge_bm_max_cap(p->bm_words, p->bm_miss, smem_limit, p->wide_above);
+    }
     if (p->opts.smem_cap_max > 0) capmax = std::min(capmax, std::max(256, p->opts.smem_cap_max));
     p->batch = batch;
     p->capmax = capmax;
@@ -623,6 +633,8 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
                 }
                 MergeLaunch L{};
                 L.wide_above = p->wide_above;
+                L.bm_words = p->bm_words;
+                L.bm_miss = p->bm_miss;
                 L.work = work;
                 L.work_base = work_base;
                 L.nwork = nwork;
@@ -768,6 +780,8 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 const int tgt = beyond ? SPLIT : level_of(std::min(2 * ccap, capmax));
                 MergeLaunch L{};
                 L.wide_above = p->wide_above;
+                L.bm_words = p->bm_words;
+                L.bm_miss = p->bm_miss;
                 L.work = p->class_order + off;
                 L.nwork = cnt;
                 L.cap = ccap;
@@ -797,6 +811,8 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 const int tgt = level_of(std::min(2 * lv[k], capmax));
                 MergeLaunch L{};
                 L.wide_above = p->wide_above;
+                L.bm_words = p->bm_words;
+                L.bm_miss = p->bm_miss;
                 L.work = lists[k];
                 L.nwork = nk;
                 L.cap = lv[k];

@@ -116,7 +116,7 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
               record_timing: bool = False, merge_batch: int = 0, smem_cap_max: int = 0,
               heap_block: int = 0, long_rows: str = "split", predictor=None,
               predictor_margin: float = 1.0, wave_mproducts: int = 0, heap_max_u: int = 0,
-              merge_wide_above: int = 0) -> _lib.Opts:
+              merge_wide_above: int = 0, merge_kernel: str = "auto", merge_miss: int = 0) -> _lib.Opts:
     L = _lib.load()
     o = _lib.Opts()
     _lib.check(L.spgemm_opts_init(ctypes.byref(o)), "spgemm_opts_init")
@@ -131,6 +131,8 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
     o.wave_mproducts = int(wave_mproducts)
     o.heap_max_u = int(heap_max_u)
     o.merge_wide_above = int(merge_wide_above)
+    o.merge_kernel = {"auto": 0, "merge_path": 1, "bitmap": 2}[merge_kernel]
+    o.merge_miss = int(merge_miss)
     # a Predictor object (whose device weights the caller keeps alive) or a raw handle
     o.predictor = getattr(predictor, "handle", predictor)
     o.predictor_margin = float(predictor_margin)

@@ -314,3 +314,34 @@ def test_merge_cta_width(spg, oracle_mod, wide_above, smem_cap_max, policy):
     plan, C = run(spg, A, A, merge_wide_above=wide_above, smem_cap_max=smem_cap_max, **opts)
     check(oracle_mod, A, A, C, label=f"wide_above={wide_above}/{smem_cap_max}/{policy}")
     assert plan.stats()["bin_count"][37] > 0
+
+
+@pytest.mark.parametrize("kernel", ["merge_path", "bitmap"])
+@pytest.mark.parametrize("policy,initial_cap,smem_cap_max,batch,miss", [
+    ("hybrid", 256, 0, 0, 0), ("hybrid", 64, 1024, 256, 256), ("learned", 256, 0, 0, 0),
+    ("upper_bound", 256, 2048, 512, 512)])
+def test_merge_kernel_forms(spg, oracle_mod, kernel, policy, initial_cap, smem_cap_max, batch, miss):
+    """Both forms of the bin-37 kernel (merge-path and bitmap/rank) give the oracle's C,
+    with progressive rounds, column splits and small miss buffers forced."""
+    from paper_1504_05022_gb300.predictor import Predictor
+    A = gen.rmat(13, 16, seed=41)
+    keep = Predictor.load() if policy == "learned" else None
+    opts = keep.opts() if keep else {"alloc_policy": policy}
+    plan, C = run(spg, A, A, merge_kernel=kernel, initial_cap=initial_cap, smem_cap_max=smem_cap_max,
+                  merge_batch=batch, merge_miss=miss, **opts)
+    check(oracle_mod, A, A, C, label=f"{kernel}/{policy}/{initial_cap}/{smem_cap_max}/{miss}")
+    st = plan.stats()
+    assert st["bin_count"][37] > 0
+    if smem_cap_max:
+        assert st["rows_split"] > 0
+    plan.check()
+
+
+def test_bitmap_kernel_rectangular_and_split_children(spg, oracle_mod):
+    """Bitmap form on a rectangular B (bitmap sized by B's columns) and on column slices
+    whose origin is not 0."""
+    A = gen.rmat(12, 24, seed=43)
+    B = gen.erdos_renyi(4096, 12, seed=44, ncols=70000)
+    plan, C = run(spg, A, B, merge_kernel="bitmap", smem_cap_max=1024, merge_batch=512, merge_miss=512)
+    check(oracle_mod, A, B, C, label="bitmap rectangular")
+    assert plan.stats()["rows_split"] > 0
