@@ -13,6 +13,8 @@ measured device time, over the parameters the library exposes for that choice:
                  long rows earlier);
 * merge_wide_above - result capacities above this run 512-thread merge CTAs,
                  smaller ones 256-thread CTAs (two can share an SM);
+* merge_miss   - entries of the bitmap merge kernel's miss buffer (how often new
+                 columns are merged into the result);
 * initial_cap  - the first bin-37 row size of the plain (hybrid) policy;
 * predictor_margin - the safety factor of the learned policy.
 
@@ -50,12 +52,15 @@ SPACE = {
     "merge_batch": [2048, 1024, 512],
     "smem_cap_max": [0, 8192, 6144, 4096],
     "merge_wide_above": [2048, 4096, 6144, 1 << 20],
+    "merge_miss": [4096, 2048, 8192],
     "initial_cap": [256, 512, 1024],
     "predictor_margin": [None, 1.15, 1.5, 2.0],  # None = the margin stored with the weights
 }
 POLICY_PARAMS = {
-    "hybrid": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "initial_cap"],
-    "learned": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "predictor_margin"],
+    "hybrid": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "merge_miss",
+               "initial_cap"],
+    "learned": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "merge_miss",
+                "predictor_margin"],
     "upper_bound": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above"],
 }
 MEMORY_SLACK = 1.05

@@ -76,7 +76,7 @@ SPG_DEV int bm_rank(const BmSmem &s, int nwords, int32_t *scan32) {
     int sum = 0;
     for (int w = w0; w < w1; ++w) sum += __popc(s.Bm[w]);
     int tot;
-    int ex = block_exclusive_scan<NT, int, true>(sum, scan32, tot);
+    int ex = block_exclusive_scan<NT, int, false>(sum, scan32, tot);
     for (int w = w0; w < w1; ++w) {
         s.Rd[w] = ex;
         ex += __popc(s.Bm[w]);
@@ -100,8 +100,9 @@ SPG_DEV int bm_merge_misses(const BmSmem &s, int rlen, int nm, int32_t lo, int n
     if (threadIdx.x == 0) *nmiss_shared = 0;
     const int fnew = bm_rank<NT>(s, nwords, scan32);
     // old entries move right (to their rank in the union), a chunk at a time from
-    // the right end: a chunk's targets lie at or beyond its own old positions, so
-    // they never overwrite an entry that a chunk to its left still has to read
+    // the right end.  A chunk's targets lie at or beyond its own old positions, so
+    // they never overwrite an entry that a chunk to its left still has to read;
+    // only the chunk's own reads must finish before its writes (one barrier).
     constexpr int CH = NT * 4;
     for (int hi = rlen; hi > 0; hi -= CH) {
         const int base = hi > CH ? hi - CH : 0;
@@ -127,8 +128,8 @@ SPG_DEV int bm_merge_misses(const BmSmem &s, int rlen, int nm, int32_t lo, int n
                 s.Rv[np[q]] = vv[q];
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
     // new columns: key and a zero value (duplicate misses write the same), then the sums
     for (int m = threadIdx.x; m < nm; m += NT) {
         const int32_t c = s.Mk[m];
