@@ -70,16 +70,31 @@ SPG_DEV int bm_pos(const BmSmem &s, int32_t c, int32_t lo) {
 // bits.  All threads call; ends with a barrier.
 template <int NT>
 SPG_DEV int bm_rank(const BmSmem &s, int nwords, int32_t *scan32) {
-    const int per = (nwords + NT - 1) / NT;
+    // each thread takes a run of `per` consecutive words, a multiple of 4 so that
+    // they are read and written as 16-byte vectors (no bank conflicts between lanes)
+    const int per = ((nwords + NT - 1) / NT + 3) & ~3;
     const int w0 = threadIdx.x * per;
-    const int w1 = min(nwords, w0 + per);
+    int c[4] = {0, 0, 0, 0};
     int sum = 0;
-    for (int w = w0; w < w1; ++w) sum += __popc(s.Bm[w]);
+    if (per == 4 && w0 + 4 <= nwords) {
+        const uint4 b = *reinterpret_cast<const uint4 *>(s.Bm + w0);
+        c[0] = __popc(b.x);
+        c[1] = __popc(b.y);
+        c[2] = __popc(b.z);
+        c[3] = __popc(b.w);
+        sum = c[0] + c[1] + c[2] + c[3];
+    } else {
+        for (int w = w0; w < min(nwords, w0 + per); ++w) sum += __popc(s.Bm[w]);
+    }
     int tot;
     int ex = block_exclusive_scan<NT, int, false>(sum, scan32, tot);
-    for (int w = w0; w < w1; ++w) {
-        s.Rd[w] = ex;
-        ex += __popc(s.Bm[w]);
+    if (per == 4 && w0 + 4 <= nwords) {
+        *reinterpret_cast<int4 *>(s.Rd + w0) = make_int4(ex, ex + c[0], ex + c[0] + c[1], ex + c[0] + c[1] + c[2]);
+    } else {
+        for (int w = w0; w < min(nwords, w0 + per); ++w) {
+            s.Rd[w] = ex;
+            ex += __popc(s.Bm[w]);
+        }
     }
     __syncthreads();
     return tot;
@@ -106,18 +121,18 @@ SPG_DEV int bm_merge_misses(const BmSmem &s, int rlen, int nm, int32_t lo, int n
     constexpr int CH = NT * 4;
     for (int hi = rlen; hi > 0; hi -= CH) {
         const int base = hi > CH ? hi - CH : 0;
-        const int p = base + threadIdx.x * 4;
         int32_t kk[4];
         double vv[4];
         int np[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 4; ++q) {  // entry base + q*NT + thread: consecutive lanes, consecutive words
+            const int p = base + q * NT + threadIdx.x;
             np[q] = -1;
-            if (p + q < hi) {
-                kk[q] = s.Rk[p + q];
-                vv[q] = s.Rv[p + q];
+            if (p < hi) {
+                kk[q] = s.Rk[p];
+                vv[q] = s.Rv[p];
                 const int t = bm_pos(s, kk[q], lo);
-                if (t != p + q) np[q] = t;
+                if (t != p) np[q] = t;
             }
         }
         __syncthreads();
