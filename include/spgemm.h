@@ -105,7 +105,7 @@ typedef enum spgemm_long_rows {
 
 /* Form of the bin-37 merge kernel (Section 4.1, merge method). */
 typedef enum spgemm_merge_kernel {
-    /* Bitmap form when B has at most 131072 columns and long rows are split, else the
+    /* Bitmap form when long rows are split and B has at most 131072 columns, else the
        merge-path form (default). */
     SPGEMM_MERGE_AUTO = 0,
     /* Merge-path form: every batch's new columns are sorted by pairwise merge-path
@@ -113,7 +113,9 @@ typedef enum spgemm_merge_kernel {
     SPGEMM_MERGE_PATH = 1,
     /* Bitmap form: a bitmap with a rank directory over the item's column range gives
        each product's position in the result in O(1); new columns are buffered and
-       merged into the result by rank when the buffer fills (same eligibility as AUTO). */
+       merged into the result by rank when the buffer fills.  For B with more than
+       131072 columns (up to 64 times that, not with the upper-bound policy) every
+       bin-37 row is first cut into 2^d column slices of at most 131072 columns. */
     SPGEMM_MERGE_BITMAP = 2
 } spgemm_merge_kernel;
 

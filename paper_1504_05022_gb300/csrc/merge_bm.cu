@@ -199,7 +199,7 @@ k_merge_bm(StageArgs a, MergeItems it, MergeLaunch L) {
             cap = (int)dst_cap;
         }
     }
-    if (rlen > cap) {  // cannot happen: an item is relaunched with at least its length
+    if (nwords > L.bm_words || rlen > cap) {  // cannot happen: slices fit the bitmap; relaunches fit R
         if (threadIdx.x == 0) atomicExch((unsigned long long *)L.err, 1ull);
         return;
     }
@@ -413,7 +413,7 @@ cudaError_t launch_merge_bm(const StageArgs &a, const MergeItems &s, const Merge
     const int nt = bm_threads(L.cap, L.wide_above);
     // every batch fits the miss buffer and the free capacity; batch >= 32 keeps the loops progressing
     if (L.level1 || L.bm_words <= 0 || L.batch > nt * BM_IPT || L.batch < 32 || L.batch > L.cap ||
-        L.bm_miss < L.batch || (int64_t)L.bm_words * 32 < a.B.ncols)
+        L.bm_miss < L.batch || (!L.bm_sliced && (int64_t)L.bm_words * 32 < a.B.ncols))
         return cudaErrorInvalidValue;
     const int smem = merge_bm_smem_bytes(L.cap, L.bm_words, L.bm_miss, L.wide_above);
     if (nt == 128) return launch_bm_nt<128, 4>(a, s, L, smem, st);

@@ -345,3 +345,22 @@ def test_bitmap_kernel_rectangular_and_split_children(spg, oracle_mod):
     plan, C = run(spg, A, B, merge_kernel="bitmap", smem_cap_max=1024, merge_batch=512, merge_miss=512)
     check(oracle_mod, A, B, C, label="bitmap rectangular")
     assert plan.stats()["rows_split"] > 0
+
+
+@pytest.mark.parametrize("policy,smem_cap_max", [("hybrid", 0), ("learned", 0), ("hybrid", 1024)])
+def test_bitmap_kernel_wide_b_column_slices(spg, oracle_mod, policy, smem_cap_max):
+    """B with more columns than the bitmap holds: every bin-37 row is cut into column slices
+    (here 4 of 75,008 columns), which may split further; C equals the oracle's."""
+    from paper_1504_05022_gb300.predictor import Predictor
+    A = gen.rmat(12, 16, seed=51)
+    B = gen.erdos_renyi(4096, 24, seed=52, ncols=300000)
+    keep = Predictor.load() if policy == "learned" else None
+    opts = keep.opts() if keep else {"alloc_policy": policy}
+    plan, C = run(spg, A, B, smem_cap_max=smem_cap_max, merge_kernel="bitmap", **opts)
+    check(oracle_mod, A, B, C, label=f"wide B/{policy}/{smem_cap_max}")
+    st = plan.stats()
+    assert st["bin_count"][37] > 0 and st["rows_split"] >= 3 * st["bin_count"][37]
+    plan.replay()
+    torch.cuda.synchronize()
+    plan.check()
+    check(oracle_mod, A, B, C, label=f"wide B replay/{policy}")
