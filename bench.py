@@ -180,12 +180,17 @@ def policy_opts(policy, tuned_workload=None):
         opts = pred.opts()
     else:
         opts = {"alloc_policy": policy}
+    if MERGE_KERNEL != "auto":
+        opts["merge_kernel"] = MERGE_KERNEL
     if tuned_workload:
         from paper_1504_05022_gb300 import autotune
         params = autotune.load(tuned_workload, policy)
         if params:
             opts = autotune.apply(opts, params)
     return opts, pred
+
+
+MERGE_KERNEL = "auto"  # form of the bin-37 kernel (--merge-kernel)
 
 
 def tuned_params(args, policy):
@@ -592,7 +597,7 @@ def run_ours(args, rank, world, device):
         "ms_per_step": main_m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded generator)",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
-                   "alloc_policy": head, "tuned": tuned_params(args, head),
+                   "alloc_policy": head, "tuned": tuned_params(args, head), "merge_kernel": args.merge_kernel,
                    "products_per_step": main_m["sum_u"], "nnz_C": main_m["nnz_C"],
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roofline(args, pairs, main_m),
@@ -730,7 +735,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tuned", dest="tuned", action="store_false",
                     help="do not apply the autotuner's parameters to the reported policy")
+    ap.add_argument("--merge-kernel", default="auto", choices=["auto", "merge_path", "bitmap"],
+                    help="form of the bin-37 kernel for every policy")
     args = ap.parse_args()
+    global MERGE_KERNEL
+    MERGE_KERNEL = args.merge_kernel
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
