@@ -60,44 +60,13 @@ __host__ __device__ inline size_t bm_layout(int cap, int nwords, int miss, int W
 }
 
 // Position of column c (already in the bitmap) in R.
-SPG_DEV int bm_pos(const BmSmem &s, int32_t c, int32_t lo) {
-    const int x = c - lo;
-    const uint32_t wd = s.Bm[x >> 5];
-    return s.Rd[x >> 5] + __popc(wd & ((1u << (x & 31)) - 1u));
-}
+SPG_DEV int bm_pos(const BmSmem &s, int32_t c, int32_t lo) { return bitmap_pos(s.Bm, s.Rd, c - lo); }
 
 // Rebuilds the rank directory of words [0, nwords); returns the number of set
 // bits.  All threads call; ends with a barrier.
 template <int NT>
 SPG_DEV int bm_rank(const BmSmem &s, int nwords, int32_t *scan32) {
-    // each thread takes a run of `per` consecutive words, a multiple of 4 so that
-    // they are read and written as 16-byte vectors (no bank conflicts between lanes)
-    const int per = ((nwords + NT - 1) / NT + 3) & ~3;
-    const int w0 = threadIdx.x * per;
-    int c[4] = {0, 0, 0, 0};
-    int sum = 0;
-    if (per == 4 && w0 + 4 <= nwords) {
-        const uint4 b = *reinterpret_cast<const uint4 *>(s.Bm + w0);
-        c[0] = __popc(b.x);
-        c[1] = __popc(b.y);
-        c[2] = __popc(b.z);
-        c[3] = __popc(b.w);
-        sum = c[0] + c[1] + c[2] + c[3];
-    } else {
-        for (int w = w0; w < min(nwords, w0 + per); ++w) sum += __popc(s.Bm[w]);
-    }
-    int tot;
-    int ex = block_exclusive_scan<NT, int, false>(sum, scan32, tot);
-    if (per == 4 && w0 + 4 <= nwords) {
-        *reinterpret_cast<int4 *>(s.Rd + w0) = make_int4(ex, ex + c[0], ex + c[0] + c[1], ex + c[0] + c[1] + c[2]);
-    } else {
-        for (int w = w0; w < min(nwords, w0 + per); ++w) {
-            s.Rd[w] = ex;
-            ex += __popc(s.Bm[w]);
-        }
-    }
-    __syncthreads();
-    return tot;
+    return bitmap_rank<NT>(s.Bm, s.Rd, nwords, scan32);
 }
 
 // Merges the nm buffered misses into R (length rlen) by rank; returns the new

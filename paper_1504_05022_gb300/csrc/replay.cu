@@ -1,8 +1,9 @@
 // Values-only replay of a finished product: C's structure is known (its row
 // pointers and columns, and for long rows the column slices of the split tree),
 // so recomputing C's values for new values of A and B needs only sub-step (1) of
-// the merge method of Section 4.1 -- every product is fused by binary search into
-// the already known, sorted result sequence.  Rows of bins 2..36 are recomputed by
+// the merge method of Section 4.1 -- every product is fused into the already
+// known, sorted result sequence, by a bitmap rank when B's columns fit the bitmap
+// and by binary search otherwise.  Rows of bins 2..36 are recomputed by
 // the heap and bitonic-ESC kernels writing straight into C.  Nothing here
 // allocates or synchronises with the host, so a replay can be captured in a CUDA
 // graph.
@@ -108,7 +109,121 @@ k_replay(StageArgs a, ReplayLeaves lv, const int32_t *__restrict__ order, int32_
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch((unsigned long long *)err, 3ull);
 }
 
+// Bitmap form: the leaf's known columns are entered in a bitmap over its column
+// range with a rank directory, so a product finds its position in O(1) (two
+// shared loads) instead of a binary search; used when B's columns fit the bitmap.
+template <int NT>
+__global__ void __launch_bounds__(NT, 2048 / NT / 2)
+k_replay_bm(StageArgs a, ReplayLeaves lv, const int32_t *__restrict__ order, int nwords_max,
+            int32_t *__restrict__ c_col, double *__restrict__ c_val, int64_t *err) {
+    extern __shared__ __align__(16) unsigned char rsmem[];
+    __shared__ int64_t scan64[NT / 32 + 1];
+    __shared__ int32_t scan32[NT / 32 + 1];
+    constexpr int W = NT;
+    const int q = order[blockIdx.x];
+    const int row = lv.row[q];
+    const int32_t clo = lv.clo[q], chi = lv.chi[q];
+    const bool filtered = (clo > 0) || (chi < INT32_MAX);
+    const int32_t lo = clo > 0 ? clo : 0;
+    const int64_t hicol = min((int64_t)chi, a.B.ncols);
+    const int nwords = hicol > lo ? (int)((hicol - lo + 31) >> 5) : 1;
+    const int64_t coff = lv.c_off[q];
+    const int len = lv.len[q];
+    if (len > lv.cap || nwords > nwords_max) {  // cannot happen: leaves fit their class and the bitmap
+        if (threadIdx.x == 0) atomicExch((unsigned long long *)err, 4ull);
+        return;
+    }
+    double *Rv = reinterpret_cast<double *>(rsmem);
+    double *wa = Rv + lv.cap;
+    int64_t *wbs = reinterpret_cast<int64_t *>(wa + W);
+    int64_t *wscan = wbs + W;
+    int32_t *Rd = reinterpret_cast<int32_t *>(wscan + W + 1 + 1);  // 16-byte aligned (W is a multiple of 32)
+    uint32_t *Bm = reinterpret_cast<uint32_t *>(Rd + ((nwords_max + 4) & ~3));
+    for (int t = threadIdx.x; t < nwords; t += NT) Bm[t] = 0u;
+    __syncthreads();
+    bool bad = false;
+    for (int t = threadIdx.x; t < len; t += NT) {
+        const int x = c_col[coff + t] - lo;
+        Rv[t] = 0.0;
+        if ((unsigned)x < (unsigned)(nwords << 5)) atomicOr(&Bm[x >> 5], 1u << (x & 31));
+        else bad = true;
+    }
+    __syncthreads();
+    bitmap_rank<NT>(Bm, Rd, nwords, scan32);
+    const int64_t a0 = a.A.rp[row], a1 = a.A.rp[row + 1];
+    for (int64_t e = a0; e < a1; e += W) {
+        const int nW = (int)min((int64_t)W, a1 - e);
+        int64_t blen = 0;
+        if (threadIdx.x < nW) {
+            const int64_t idx = e + threadIdx.x;
+            const int32_t kk = a.A.col[idx];
+            const int64_t rs = a.B.rp[kk];
+            int64_t bs = rs, be = a.B.rp[kk + 1];
+            if (filtered) {
+                const int n = (int)(be - rs);
+                if (clo > 0) bs = rs + lower_bound_i32(a.B.col + rs, n, clo);
+                if (chi < INT32_MAX) be = rs + lower_bound_i32(a.B.col + rs, n, chi);
+            }
+            wbs[threadIdx.x] = bs;
+            wa[threadIdx.x] = a.A.val[idx];
+            blen = be > bs ? be - bs : 0;
+        }
+        int64_t total;
+        const int64_t ex = block_exclusive_scan<NT, int64_t, false>(blen, scan64, total);
+        if (threadIdx.x < nW) wscan[threadIdx.x] = ex;
+        if (threadIdx.x == 0) wscan[nW] = total;
+        __syncthreads();
+        for (int64_t p0 = 0; p0 < total; p0 += (int64_t)NT * REPLAY_IPT) {
+            const int nb = (int)min((int64_t)NT * REPLAY_IPT, total - p0);
+            const int ipt = (nb + NT - 1) / NT;
+            const int q0 = threadIdx.x * ipt;
+            const int cnt = max(0, min(ipt, nb - q0));
+            if (cnt > 0) {
+                int te[REPLAY_IPT], to[REPLAY_IPT];
+                int32_t key[REPLAY_IPT];
+                double val[REPLAY_IPT];
+                int64_t pos = p0 + q0;
+                int t = find_segment_i64(wscan, nW, pos);
+#pragma unroll
+                for (int k = 0; k < REPLAY_IPT; ++k) {
+                    if (k < cnt) {
+                        while (t + 1 < nW && wscan[t + 1] <= pos) ++t;
+                        te[k] = t;
+                        to[k] = (int)(pos - wscan[t]);
+                        ++pos;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < REPLAY_IPT; ++k)
+                    if (k < cnt) key[k] = __ldg(a.B.col + wbs[te[k]] + to[k]);
+#pragma unroll
+                for (int k = 0; k < REPLAY_IPT; ++k)
+                    if (k < cnt) val[k] = wa[te[k]] * __ldg(a.B.val + wbs[te[k]] + to[k]);
+#pragma unroll
+                for (int k = 0; k < REPLAY_IPT; ++k) {
+                    if (k < cnt) {
+                        const int x = key[k] - lo;
+                        if ((unsigned)x < (unsigned)(nwords << 5) && ((Bm[x >> 5] >> (x & 31)) & 1u))
+                            atomicAdd(&Rv[bitmap_pos(Bm, Rd, x)], val[k]);
+                        else
+                            bad = true;  // the structure of A or B changed since the product was planned
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < len; t += NT) c_val[coff + t] = Rv[t];
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch((unsigned long long *)err, 3ull);
+}
+
 int replay_threads(int cap) { return cap <= 1024 ? 128 : (cap <= 4096 ? 256 : 512); }
+
+int replay_bm_smem_bytes(int cap, int nwords_max) {
+    const int W = replay_threads(cap);
+    return (int)(sizeof(double) * (cap + W) + sizeof(int64_t) * (2 * W + 2) +
+                 sizeof(int32_t) * ((nwords_max + 4) & ~3) + sizeof(uint32_t) * nwords_max + 64);
+}
 
 int replay_smem_bytes(int cap) {
     const int W = replay_threads(cap);
@@ -125,10 +240,35 @@ static cudaError_t launch_replay_nt(const StageArgs &a, const ReplayLeaves &lv, 
     return cudaGetLastError();
 }
 
+template <int NT>
+static cudaError_t launch_replay_bm_nt(const StageArgs &a, const ReplayLeaves &lv, const int32_t *order, int64_t n,
+                                      int nwords, int32_t *c_col, double *c_val, int64_t *err, int smem,
+                                      cudaStream_t st) {
+    auto kern = k_replay_bm<NT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)n, NT, smem, st>>>(a, lv, order, nwords, c_col, c_val, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_replay(const StageArgs &a, ReplayLeaves lv, const int32_t *order, int64_t n, int cap,
                           int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     lv.cap = cap;
+    if (a.B.ncols > 0 && a.B.ncols <= BM_MAX_COLS) {
+        const int nwords = (int)((a.B.ncols + 31) / 32);
+        const int smem = replay_bm_smem_bytes(cap, nwords);
+        int optin = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (smem <= optin) {
+            switch (replay_threads(cap)) {
+                case 128: return launch_replay_bm_nt<128>(a, lv, order, n, nwords, c_col, c_val, err, smem, st);
+                case 256: return launch_replay_bm_nt<256>(a, lv, order, n, nwords, c_col, c_val, err, smem, st);
+                default: return launch_replay_bm_nt<512>(a, lv, order, n, nwords, c_col, c_val, err, smem, st);
+            }
+        }
+    }
     const int smem = replay_smem_bytes(cap);
     switch (replay_threads(cap)) {
         case 128: return launch_replay_nt<128>(a, lv, order, n, c_col, c_val, err, smem, st);
