@@ -128,6 +128,17 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def wait_first_sample(self, timeout_s=5.0):
+        """Waits until nvidia-smi has written its first sample (it is then polling steadily)."""
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < timeout_s:
+            self.fh.flush()
+            if os.path.exists(self.path) and os.path.getsize(self.path) > 0:
+                return
+            if self.proc.poll() is not None:
+                return
+            time.sleep(0.02)
+
     def __exit__(self, *a):
         if self.proc is not None:
             self.proc.terminate()
@@ -226,6 +237,12 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
             plans.append(plan)
         return plans, prev
 
+    # the clock sampler starts before the warm-up: its start-up (NVML initialisation in
+    # nvidia-smi) stalls CUDA calls for milliseconds and must not fall on a timed step
+    clk = ClockSampler(dev.index) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+        clk.wait_first_sample()
     for _ in range(args.warmup):
         plans, C = step()
         del plans, C
@@ -235,9 +252,6 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
         dist.barrier()
     kms, launches = {}, 0
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clk = ClockSampler(dev.index) if sample_clocks else None
-    if clk:
-        clk.__enter__()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
     for k in range(args.steps):
@@ -394,6 +408,7 @@ def run_batch(args, world, device):
         clk = ClockSampler(dev.index) if clocks else None
         if clk:
             clk.__enter__()
+            clk.wait_first_sample()
         ms, bp = time_steps(args, stream, flush, step)
         value, ms = job_gflops(products, ms, world, dev)
         if clk:
@@ -578,7 +593,8 @@ def run_ours(args, rank, world, device):
     head = args.policy
     if head == "learned" and not os.path.exists(WEIGHTS):
         head = "hybrid"
-    others = [p for p in ("hybrid",) if p != head] if not args.single_policy else []
+    # the paper's plain form (hybrid) and its upper-bound allocation, for the memory comparison
+    others = [p for p in ("hybrid", "upper_bound") if p != head] if not args.single_policy else []
     main_m = measure(args, spg, pairs, dev, stream, head, flush, world, sample_clocks=True, tuned=True)
     cmp = {p: measure(args, spg, pairs, dev, stream, p, flush, world) for p in others}
     e2e_opts, e2e_keep = policy_opts(head, args.workload if args.tuned else None)  # keeps the predictor alive
@@ -605,7 +621,9 @@ def run_ours(args, rank, world, device):
         "gpu_launches": int(main_m["launches"]),
         "wall_s_timed": main_m["wall_s"],
         "kernel_ms_per_step": main_m["kms"],
-        "memory": {"peak_bytes": main_m["peak_bytes"], "rows_bin37": main_m["rows_bin37"],
+        "memory": {"peak_bytes": main_m["peak_bytes"],
+                   "c_bytes": int(main_m["nnz_C"]) * 12 + 8 * (int(main_m["arrays"][-1]["u"].shape[0]) + 1),
+                   "rows_bin37": main_m["rows_bin37"],
                    "rows_fallback": main_m["rows_fallback"],
                    "misprediction_rate": (main_m["rows_fallback"] / main_m["rows_bin37"])
                    if head == "learned" and main_m["rows_bin37"] else None,
@@ -692,9 +710,19 @@ def run_cpu_baseline(args, budget_s=20.0, pairs=None):
         oracle.spgemm_rows(A, B, rows, nthreads=nthreads)
         times.append(time.perf_counter() - t0)
     t = float(np.median(times))
+    # one core, on a smaller row sample (about 80 M products)
+    rng1 = np.random.default_rng(1)
+    perm1 = rng1.permutation(A.nrows)
+    cs1 = np.cumsum(u[perm1])
+    rows1 = np.sort(perm1[: int(np.searchsorted(cs1, 80_000_000)) + 1])
+    t1 = time.perf_counter()
+    oracle.spgemm_rows(A, B, rows1, nthreads=1)
+    t1 = time.perf_counter() - t1
     return {"value": 2.0 * prods / t / 1e9, "unit": "GFLOP/s", "cores": nthreads, "kind": "oracle",
             "sample": f"{sample}; {prods} products; median of {len(times)} passes",
-            "ms_per_pass": t * 1e3}
+            "ms_per_pass": t * 1e3,
+            "one_core": {"value": 2.0 * int(u[rows1].sum()) / t1 / 1e9, "unit": "GFLOP/s",
+                         "sample": f"{rows1.size} random rows (seed 1), {int(u[rows1].sum())} products, one pass"}}
 
 
 def _cpu_baseline_batch(pairs, budget_s):
