@@ -225,46 +225,28 @@ k_merge_bm(StageArgs a, MergeItems it, MergeLaunch L) {
         int64_t p0 = 0;
         while (p0 < total) {
             const int need = (int)min((int64_t)kb, total - p0);
-            int avail = cap - rlen - nmiss;
-            if (nmiss + need > mcap || avail < need) {
-                if (nmiss > 0) {
-                    rlen = bm_merge_misses<NT>(s, rlen, nmiss, lo, nwords, scan32, &s_nmiss);
-                    nmiss = 0;
-                    avail = cap - rlen;
-                }
-                if (avail < need && (avail < (kb >> 2) || avail <= 0)) {
-                    // checkpoint at product p0 of this window (offset counted in the full B row)
-                    const int t = find_segment_i64(s.wscan, nW, p0);
-                    if (threadIdx.x == 0) {
-                        const int32_t kk = a.A.col[e + t];
-                        it.ck_entry[j] = (e + t) - a0;
-                        it.ck_off[j] = s.wbs[t] + (p0 - s.wscan[t]) - a.B.rp[kk];
-                    }
-                    overflow = true;
-                    break;
-                }
+            if (nmiss + need > mcap) {  // room in the miss buffer first
+                rlen = bm_merge_misses<NT>(s, rlen, nmiss, lo, nwords, scan32, &s_nmiss);
+                nmiss = 0;
             }
-            const int nb = min(need, avail);
+            int avail = cap - rlen - nmiss;
             const int tf = find_segment_i64(s.wscan, nW, p0);
-            const int tl = find_segment_i64(s.wscan, nW, p0 + nb - 1);
+            const int tl = find_segment_i64(s.wscan, nW, p0 + need - 1);
             const int nruns = tl - tf + 1;
-            // (0) each thread expands IPT consecutive products of the batch into registers
-            const int ipt = (nb + NT - 1) / NT;
-            const int q0 = threadIdx.x * ipt;
-            const int cnt = max(0, min(ipt, nb - q0));
+            // (0) each thread expands products threadIdx.x + k*NT of the batch into
+            // registers: consecutive lanes read consecutive B entries (coalesced)
+            int cnt = need > (int)threadIdx.x ? min(BM_IPT, (need - (int)threadIdx.x + NT - 1) / NT) : 0;
             int32_t key[BM_IPT];
             double val[BM_IPT];
-            if (cnt > 0) {
+            {
                 int te[BM_IPT], to[BM_IPT];
-                int64_t pos = p0 + q0;
-                int t = tf + find_segment_i64(s.wscan + tf, nruns, pos);
 #pragma unroll
                 for (int k = 0; k < BM_IPT; ++k) {
                     if (k < cnt) {
-                        while (t + 1 < nW && s.wscan[t + 1] <= pos) ++t;
+                        const int64_t pos = p0 + threadIdx.x + k * NT;
+                        const int t = tf + find_segment_i64(s.wscan + tf, nruns, pos);
                         te[k] = t;
                         to[k] = (int)(pos - s.wscan[t]);
-                        ++pos;
                     }
                 }
 #pragma unroll
@@ -277,10 +259,12 @@ k_merge_bm(StageArgs a, MergeItems it, MergeLaunch L) {
                 for (int k = 0; k < BM_IPT; ++k)
                     if (k < cnt) val[k] *= s.wa[te[k]];
             }
-            // (1) fuse products whose column is in R: position from the rank directory
+            // (1) which products' columns are in R (position from the rank directory)
+            int rpos[BM_IPT];
             unsigned miss = 0;
 #pragma unroll
             for (int k = 0; k < BM_IPT; ++k) {
+                rpos[k] = -1;
                 if (k < cnt) {
                     const int x = key[k] - lo;
                     if ((unsigned)x >= (unsigned)(nwords << 5)) {  // a column outside [0, ncols): bad input
@@ -288,12 +272,57 @@ k_merge_bm(StageArgs a, MergeItems it, MergeLaunch L) {
                         continue;
                     }
                     const uint32_t wd = s.Bm[x >> 5];
-                    if ((wd >> (x & 31)) & 1u)
-                        atomicAdd(&s.Rv[s.Rd[x >> 5] + __popc(wd & ((1u << (x & 31)) - 1u))], val[k]);
-                    else
-                        miss |= 1u << k;
+                    if ((wd >> (x & 31)) & 1u) rpos[k] = s.Rd[x >> 5] + __popc(wd & ((1u << (x & 31)) - 1u));
+                    else miss |= 1u << k;
                 }
             }
+            int nb = need;
+            if (avail < need) {
+                // the batch fits if its actual misses fit the free capacity (its hits take none)
+                int cm = block_reduce_sum<NT, int>(__popc(miss), scan32);
+                if (cm > avail && nmiss > 0) {
+                    rlen = bm_merge_misses<NT>(s, rlen, nmiss, lo, nwords, scan32, &s_nmiss);
+                    nmiss = 0;
+                    avail = cap - rlen;
+                    miss = 0;  // the bitmap changed: look the products up again
+#pragma unroll
+                    for (int k = 0; k < BM_IPT; ++k) {
+                        rpos[k] = -1;
+                        if (k < cnt) {
+                            const int x = key[k] - lo;
+                            if ((unsigned)x >= (unsigned)(nwords << 5)) continue;
+                            const uint32_t wd = s.Bm[x >> 5];
+                            if ((wd >> (x & 31)) & 1u) rpos[k] = s.Rd[x >> 5] + __popc(wd & ((1u << (x & 31)) - 1u));
+                            else miss |= 1u << k;
+                        }
+                    }
+                    cm = block_reduce_sum<NT, int>(__popc(miss), scan32);
+                }
+                if (cm > avail) {
+                    if (avail < (kb >> 2) || avail <= 0) {
+                        // checkpoint at product p0 of this window (offset counted in the full B row)
+                        const int t = find_segment_i64(s.wscan, nW, p0);
+                        if (threadIdx.x == 0) {
+                            const int32_t kk = a.A.col[e + t];
+                            it.ck_entry[j] = (e + t) - a0;
+                            it.ck_off[j] = s.wbs[t] + (p0 - s.wscan[t]) - a.B.rp[kk];
+                        }
+                        overflow = true;
+                        break;
+                    }
+                    // only the first `avail` products: each adds at most one new column
+                    nb = avail;
+                    cnt = nb > (int)threadIdx.x ? min(BM_IPT, (nb - (int)threadIdx.x + NT - 1) / NT) : 0;
+#pragma unroll
+                    for (int k = 0; k < BM_IPT; ++k)
+                        if (k >= cnt) rpos[k] = -1;
+                    miss &= (1u << cnt) - 1u;
+                }
+            }
+            // fuse the hits
+#pragma unroll
+            for (int k = 0; k < BM_IPT; ++k)
+                if (rpos[k] >= 0) atomicAdd(&s.Rv[rpos[k]], val[k]);
             // (2)-(3) append the misses to the buffer: one shared atomic per warp
             {
                 const int nm = __popc(miss);
@@ -381,7 +410,7 @@ cudaError_t launch_merge_bm(const StageArgs &a, const MergeItems &s, const Merge
     if (L.nwork <= 0) return cudaSuccess;
     const int nt = bm_threads(L.cap, L.wide_above);
     // every batch fits the miss buffer and the free capacity; batch >= 32 keeps the loops progressing
-    if (L.level1 || L.bm_words <= 0 || L.batch > nt * BM_IPT || L.batch < 32 || L.batch > L.cap ||
+    if (L.level1 || L.bm_words <= 0 || L.batch > nt * BM_IPT || L.batch < 32 ||
         L.bm_miss < L.batch || (!L.bm_sliced && (int64_t)L.bm_words * 32 < a.B.ncols))
         return cudaErrorInvalidValue;
     const int smem = merge_bm_smem_bytes(L.cap, L.bm_words, L.bm_miss, L.wide_above);

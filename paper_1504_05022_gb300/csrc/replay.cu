@@ -175,22 +175,21 @@ k_replay_bm(StageArgs a, ReplayLeaves lv, const int32_t *__restrict__ order, int
         __syncthreads();
         for (int64_t p0 = 0; p0 < total; p0 += (int64_t)NT * REPLAY_IPT) {
             const int nb = (int)min((int64_t)NT * REPLAY_IPT, total - p0);
-            const int ipt = (nb + NT - 1) / NT;
-            const int q0 = threadIdx.x * ipt;
-            const int cnt = max(0, min(ipt, nb - q0));
+            const int tf = find_segment_i64(wscan, nW, p0);
+            const int tl = find_segment_i64(wscan, nW, p0 + nb - 1);
+            // products threadIdx.x + k*NT: consecutive lanes read consecutive B entries
+            const int cnt = nb > (int)threadIdx.x ? min(REPLAY_IPT, (nb - (int)threadIdx.x + NT - 1) / NT) : 0;
             if (cnt > 0) {
                 int te[REPLAY_IPT], to[REPLAY_IPT];
                 int32_t key[REPLAY_IPT];
                 double val[REPLAY_IPT];
-                int64_t pos = p0 + q0;
-                int t = find_segment_i64(wscan, nW, pos);
 #pragma unroll
                 for (int k = 0; k < REPLAY_IPT; ++k) {
                     if (k < cnt) {
-                        while (t + 1 < nW && wscan[t + 1] <= pos) ++t;
+                        const int64_t pos = p0 + threadIdx.x + k * NT;
+                        const int t = tf + find_segment_i64(wscan + tf, tl - tf + 1, pos);
                         te[k] = t;
                         to[k] = (int)(pos - wscan[t]);
-                        ++pos;
                     }
                 }
 #pragma unroll

@@ -70,6 +70,25 @@ void *get_pinned() {
     return p;
 }
 
+// Auxiliary streams per device (created once, kept for the process): the learned
+// launch classes of bin 37 run on them concurrently, so one class's tail of long
+// CTAs overlaps the next class instead of idling the SMs.
+constexpr int NUM_AUX_STREAMS = 4;
+std::mutex g_aux_mu;
+std::vector<std::vector<cudaStream_t>> g_aux;
+
+cudaStream_t aux_stream(int device, int i) {
+    std::lock_guard<std::mutex> lk(g_aux_mu);
+    if ((int)g_aux.size() <= device) g_aux.resize(device + 1);
+    auto &v = g_aux[device];
+    while ((int)v.size() < NUM_AUX_STREAMS) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        v.push_back(s);
+    }
+    return v[i % NUM_AUX_STREAMS];
+}
+
 void put_pinned(void *p) {
     if (!p) return;
     std::lock_guard<std::mutex> lk(g_pin_mu);
@@ -603,6 +622,15 @@ cudaError_t reserve_items(spgemm_plan *p, int64_t need) {
     return cudaSuccess;
 }
 
+// Products per batch of a bin-37 launch with capacity `cap`: the plan's batch and
+// at most what the CTA's threads hold; the merge-path form (and level-1) also at
+// most the capacity, while the bitmap form admits a larger batch whenever its
+// actual new columns fit.
+int launch_batch(const spgemm_plan *p, int cap, bool level1) {
+    const int b = std::min(p->batch, merge_batch_limit(cap, p->wide_above));
+    return (p->bm_words > 0 && !level1) ? b : std::min(b, cap);
+}
+
 // Progressive rounds (Section 4.1): runs `nwork` work items (work_in, or the
 // items work_base.. when work_in is null) at capacity `cap`; items that
 // overflow are relaunched with twice the capacity in a fresh pool slot, and at
@@ -654,7 +682,7 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
                 L.work_base = work_base;
                 L.nwork = nwork;
                 L.cap = cap;
-                L.batch = std::min(std::min(batch, cap), merge_batch_limit(cap, p->wide_above));
+                L.batch = launch_batch(p, cap, level1);
                 L.level1 = level1 ? 1 : 0;
                 L.ovf_list = list[which];
                 L.ovf_count = ovf_count;
@@ -801,10 +829,34 @@ spgemm_status run_bin37(spgemm_plan *p) {
             for (int k = 0; k <= nlv; ++k) SPG_TRY(p->alloc_n(&lists[k], n37, LIFE_NUMERIC));
             SPG_TRY(p->alloc_n(&counts, nlv + 1, LIFE_NUMERIC));
             SPG_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (nlv + 1), p->st));
-            int64_t off = 0;
-            for (int g = 0; g < NUM_LAUNCH_CLASSES; ++g) {
+            // the classes are independent: without per-kernel timing they run on auxiliary
+            // streams, largest capacity first, and the plan's stream waits for all of them
+            const bool concurrent = !p->opts.record_timing;
+            cudaEvent_t ready = nullptr;
+            std::vector<cudaEvent_t> joins;
+            if (concurrent) {
+                SPG_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+                joins.push_back(ready);
+                SPG_TRY(cudaEventRecord(ready, p->st));
+            }
+            int64_t class_off[NUM_LAUNCH_CLASSES + 1] = {0};
+            for (int g = 0; g < NUM_LAUNCH_CLASSES; ++g) class_off[g + 1] = class_off[g] + p->h_summary.class_count[g];
+            int nlaunched = 0;
+            for (int gi = NUM_LAUNCH_CLASSES - 1; gi >= 0; --gi) {
+                const int g = concurrent ? gi : NUM_LAUNCH_CLASSES - 1 - gi;
                 const int64_t cnt = p->h_summary.class_count[g];
+                const int64_t off = class_off[g];
                 if (cnt == 0) continue;
+                cudaStream_t cs = p->st;
+                if (concurrent) {
+                    cs = aux_stream(p->device, nlaunched);
+                    if (cs == nullptr) {
+                        status = SPGEMM_ERR_CUDA;
+                        goto fail;
+                    }
+                    SPG_TRY(cudaStreamWaitEvent(cs, ready, 0));
+                }
+                ++nlaunched;
                 const bool beyond = p->class_caps[g] == INT32_MAX;
                 const int ccap = std::min(capmax, beyond ? capmax : p->class_caps[g]);
                 const int tgt = beyond ? SPLIT : level_of(std::min(2 * ccap, capmax));
@@ -816,17 +868,24 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 L.work = p->class_order + off;
                 L.nwork = cnt;
                 L.cap = ccap;
-                L.batch = std::min(std::min(p->batch, ccap), merge_batch_limit(ccap, p->wide_above));
+                L.batch = launch_batch(p, ccap, false);
                 L.ovf_list = lists[tgt];
                 L.ovf_count = counts + tgt;
                 L.err = p->d_err;
                 p->time_begin(SPGEMM_K_MERGE);
-                SPG_TRY(launch_merge(a, p->items, L, p->st));
+                SPG_TRY(launch_merge(a, p->items, L, cs));
                 p->time_end();
                 p->count(SPGEMM_K_MERGE);
                 p->stats.merge_rounds += 1;
-                off += cnt;
+                if (concurrent) {
+                    cudaEvent_t done = nullptr;
+                    SPG_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+                    joins.push_back(done);
+                    SPG_TRY(cudaEventRecord(done, cs));
+                    SPG_TRY(cudaStreamWaitEvent(p->st, done, 0));
+                }
             }
+            for (cudaEvent_t ev : joins) cudaEventDestroy(ev);  // released once their work is done
             std::vector<int32_t> hc(nlv + 1, 0);
             SPG_TRY(p->d2h(hc.data(), counts, sizeof(int32_t) * (nlv + 1)));
             int64_t fell = 0;
@@ -848,7 +907,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 L.work = lists[k];
                 L.nwork = nk;
                 L.cap = lv[k];
-                L.batch = std::min(std::min(p->batch, lv[k]), merge_batch_limit(lv[k], p->wide_above));
+                L.batch = launch_batch(p, lv[k], false);
                 L.ovf_list = lists[tgt];
                 L.ovf_count = counts + tgt;
                 L.err = p->d_err;
