@@ -76,6 +76,10 @@ def workload(name: str):
     if name == "lap2d64":
         A = gen.lap2d(64)
         return [(A, A)]
+    if name == "galerkin64":
+        A = gen.lap3d27(64)
+        P = gen.agg_P(64)
+        return [(A, P), (gen.transpose(P), None)]  # R * (A*P): the second product takes the first's result
     if name == "batch512":
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
@@ -108,20 +112,28 @@ class Runner:
 
         from .spgemm import CSR
         self.torch = torch
-        self.batched = len(pairs) > 1
+        self.chain = len(pairs) == 2 and pairs[1][1] is None
+        self.batched = len(pairs) > 1 and not self.chain
         self.A = [CSR.from_host(A, device=device, rowptr_dtype=torch.int32) for A, _ in pairs]
-        self.B = [a if B is A else CSR.from_host(B, device=device, rowptr_dtype=torch.int32)
+        self.B = [a if B is A else (None if B is None else CSR.from_host(B, device=device, rowptr_dtype=torch.int32))
                   for a, (A, B) in zip(self.A, pairs)]
         self.stream = torch.cuda.current_stream()
 
     def once(self, opts):
         from .spgemm import BatchPlan, Plan
+        if self.chain:  # R * (A*P)
+            p1 = Plan(self.A[0], self.B[0], stream=self.stream, **opts)
+            p2 = Plan(self.A[1], p1.numeric(), stream=self.stream, **opts)
+            p2.numeric()
+            p2._keep = p1
+            return _Chain(p1, p2)
         if self.batched:
             p = BatchPlan(self.A, self.B, stream=self.stream, **opts)
         else:
             p = Plan(self.A[0], self.B[0], stream=self.stream, **opts)
         p.numeric()
         return p
+
 
     def time(self, opts, reps: int = 3):
         torch = self.torch
@@ -139,6 +151,17 @@ class Runner:
             times.append(e0.elapsed_time(e1))
             del p
         return statistics.median(times), peak
+
+
+class _Chain:
+    """Two plans of a chained product; stats() reports the larger peak."""
+
+    def __init__(self, p1, p2):
+        self.p1, self.p2 = p1, p2
+
+    def stats(self):
+        s1, s2 = self.p1.stats(), self.p2.stats()
+        return {"peak_bytes": max(s1["peak_bytes"], s1["held_bytes"] + s2["peak_bytes"])}
 
 
 def tune(runner: Runner, policy: str, predictor=None, rounds: int = 2, reps: int = 3, log=print) -> dict:
@@ -199,7 +222,7 @@ def main():
     runner = Runner(pairs)
     pred = Predictor.load() if args.policy == "learned" else None
     rec = tune(runner, args.policy, pred, rounds=args.rounds, reps=args.reps)
-    rec["products"] = int(sum(np.diff(B.row_ptr)[A.col].sum() for A, B in pairs))
+    rec["products"] = int(sum(np.diff(B.row_ptr)[A.col].sum() for A, B in pairs if B is not None))
     rec["device"] = torch.cuda.get_device_name()
     rec["tuning_seconds"] = round(time.time() - t0, 1)
     doc = json.load(open(args.out)) if os.path.exists(args.out) else {}
