@@ -105,17 +105,17 @@ typedef enum spgemm_long_rows {
 
 /* Form of the bin-37 merge kernel (Section 4.1, merge method). */
 typedef enum spgemm_merge_kernel {
-    /* Bitmap form when long rows are split and B has at most 131072 columns, else the
-       merge-path form (default). */
+    /* Bitmap form when long rows are split and B has at most 4,194,304 columns, else
+       the merge-path form (default). */
     SPGEMM_MERGE_AUTO = 0,
     /* Merge-path form: every batch's new columns are sorted by pairwise merge-path
        merges and merged into a pending set, then into the result, in place. */
     SPGEMM_MERGE_PATH = 1,
-    /* Bitmap form: a bitmap with a rank directory over the item's column range gives
-       each product's position in the result in O(1); new columns are buffered and
-       merged into the result by rank when the buffer fills.  For B with more than
-       131072 columns (up to 64 times that, not with the upper-bound policy) every
-       bin-37 row is first cut into 2^d column slices of at most 131072 columns. */
+    /* Bitmap form: an index over the item's column range gives each product's
+       position in the result in O(1) -- a bitmap with a rank directory for B with at
+       most 131,072 columns, else a two-level index (occupied 32-column words, then
+       their bits) up to 4,194,304 columns; new columns are buffered and merged into
+       the result by rank when the buffer fills (same eligibility as AUTO). */
     SPGEMM_MERGE_BITMAP = 2
 } spgemm_merge_kernel;
 

@@ -125,20 +125,19 @@ struct MergeLaunch {
     int32_t *ovf_count;
     int64_t *err;            // device error word
     int wide_above;          // capacities above this use 512-thread CTAs (0 = 2048)
-    int bm_words;            // > 0: bitmap kernel, bitmap words covering an item's column range
-    int bm_sliced;           // 1: items are column slices of at most bm_words * 32 columns
+    int bm_words;            // > 0: bitmap kernel; flat: bitmap words, two-level: level-1 words
+    int bm_two;              // 1: two-level index
     int bm_miss;             // bitmap kernel: miss-buffer entries
 };
 
 int merge_smem_bytes(int cap, int batch, int wide_above);
-// Bitmap form of the bin-37 kernel (merge_bm.cu), for B with at most BM_MAX_COLS columns.
+// Bitmap form of the bin-37 kernel (merge_bm.cu): a flat bitmap index for B with at
+// most BM_MAX_COLS columns, a two-level index up to BM2_MAX_COLS.
 constexpr int64_t BM_MAX_COLS = 131072;
-int merge_bm_smem_bytes(int cap, int nwords, int miss, int wide_above);
-int merge_bm_max_cap(int nwords, int miss, int smem_limit, int wide_above);
+constexpr int64_t BM2_MAX_COLS = (int64_t)1 << 22;
+int merge_bm_smem_bytes(int cap, int nwords, int miss, int wide_above, bool two);
+int merge_bm_max_cap(int nwords, int miss, int smem_limit, int wide_above, bool two);
 cudaError_t launch_merge_bm(const StageArgs &a, const MergeItems &s, const MergeLaunch &L, cudaStream_t st);
-// Column slices of every bin-37 row for B wider than the bitmap (k = 2^d slices of `width` columns).
-cudaError_t launch_presplit(int64_t n37, int d, int32_t width, int64_t first_new, const MergeItems &it,
-                            int32_t *leaves, cudaStream_t st);
 int merge_batch_limit(int cap, int wide_above);
 int merge_max_cap(int batch, int smem_limit, int wide_above);
 cudaError_t launch_merge(const StageArgs &a, const MergeItems &it, const MergeLaunch &L, cudaStream_t st);

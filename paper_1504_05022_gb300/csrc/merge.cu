@@ -547,56 +547,6 @@ __global__ void k_split(const int32_t *ovf, int64_t n, int64_t first_new, MergeI
     it.len[p] = 0;
 }
 
-// Column slices for B wider than the bitmap of the bitmap kernel: bin-37 row item
-// j becomes the root of a complete binary tree whose k = 2^d leaves cover the
-// columns in k consecutive ranges of `width` columns (the last one open-ended).
-// The 2k - 2 new items of row j are first_new + j*(2k-2) + (2^l - 2) + i for
-// node i of level l = 1..d, so the children of a node are consecutive, as the
-// split tree requires; leaves start empty, with no home, at checkpoint 0, and
-// are listed in leaves[j*k + i].
-__global__ void k_presplit(int64_t n37, int d, int32_t width, int64_t first_new, MergeItems it, int32_t *leaves) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n37) return;
-    const int k = 1 << d;
-    const int64_t base = first_new + j * (int64_t)(2 * k - 2);
-    const int row = it.row[j];
-    it.child[j] = (int32_t)base;
-    it.len[j] = 0;
-    for (int l = 1; l <= d; ++l) {
-        const int n = 1 << l;
-        const int per = k / n;  // leaves under a node of this level
-        for (int i = 0; i < n; ++i) {
-            const int64_t q = base + (n - 2) + i;
-            const int64_t c0 = (int64_t)i * per * width;
-            it.row[q] = row;
-            it.clo[q] = (int32_t)c0;
-            it.chi[q] = (i == n - 1) ? INT32_MAX : (int32_t)(c0 + (int64_t)per * width);
-            it.len[q] = 0;
-            it.src_len[q] = 0;
-            it.src_col[q] = nullptr;
-            it.src_val[q] = nullptr;
-            it.home_col[q] = nullptr;
-            it.home_val[q] = nullptr;
-            it.home_cap[q] = 0;
-            it.ck_entry[q] = 0;
-            it.ck_off[q] = 0;
-            if (l < d) {
-                it.child[q] = (int32_t)(base + ((2 << l) - 2) + 2 * i);
-            } else {
-                it.child[q] = -1;
-                leaves[j * k + i] = (int32_t)q;
-            }
-        }
-    }
-}
-
-cudaError_t launch_presplit(int64_t n37, int d, int32_t width, int64_t first_new, const MergeItems &it,
-                            int32_t *leaves, cudaStream_t st) {
-    if (n37 <= 0) return cudaSuccess;
-    k_presplit<<<(unsigned)((n37 + 127) / 128), 128, 0, st>>>(n37, d, width, first_new, it, leaves);
-    return cudaGetLastError();
-}
-
 // One CTA per split: copies the right half of the parent's sequence into the right child's slot.
 __global__ void k_split_copy(const int32_t *ovf, int64_t first_new, MergeItems it) {
     const int64_t i = blockIdx.x;

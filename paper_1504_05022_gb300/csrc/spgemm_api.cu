@@ -151,8 +151,7 @@ struct spgemm_plan {
     int32_t *pred_cap = nullptr;      // predicted temporary size per row
     int32_t *class_order = nullptr;   // bin-37 item indices grouped by launch class
     int32_t class_caps[NUM_LAUNCH_CLASSES] = {0};
-    int capmax = 0, batch = 0, wide_above = 2048, bm_words = 0, bm_miss = 0, bm_slice_d = 0;
-    int32_t bm_width = 0;
+    int capmax = 0, batch = 0, wide_above = 2048, bm_words = 0, bm_miss = 0, bm_two = 0;
     // batched plans: the pairs and the concatenation offsets
     int64_t npairs = 0;
     PairDesc *d_pairs = nullptr;
@@ -270,25 +269,15 @@ static void merge_limits(spgemm_plan *p) {
     // the bitmap kernel when B's columns fit its bitmap and long rows are split
     p->bm_words = 0;
     p->bm_miss = 0;
-    p->bm_slice_d = 0;
-    p->bm_width = 0;
-    // column slices for wider B only on request: on the 2^20-column R-MAT they cost more
-    // (per-slice bitmaps and A-row passes) than the merge-path form saves
-    const bool sliceable = p->opts.merge_kernel == SPGEMM_MERGE_BITMAP &&
-                           p->opts.alloc_policy != SPGEMM_ALLOC_UPPER_BOUND;  // slices need pool homes
+    p->bm_two = 0;
     if (p->opts.merge_kernel != SPGEMM_MERGE_PATH && p->opts.long_rows == SPGEMM_LONG_ROWS_SPLIT && p->B.ncols > 0 &&
-        p->B.ncols <= (sliceable ? BM_MAX_COLS * 64 : BM_MAX_COLS)) {
-        // B wider than the bitmap: every bin-37 row is cut into 2^d column slices of at most
-        // BM_MAX_COLS columns, each slice an item of its own
-        int d = 0;
-        while (((int64_t)BM_MAX_COLS << d) < p->B.ncols) ++d;
-        const int64_t width = (((p->B.ncols + (1 << d) - 1) >> d) + 31) / 32 * 32;
-        p->bm_slice_d = d;
-        p->bm_width = (int32_t)width;
-        p->bm_words = (int)(width / 32);
+        p->B.ncols <= BM2_MAX_COLS) {
+        // flat bitmap up to BM_MAX_COLS columns, the two-level index beyond
+        p->bm_two = p->B.ncols > BM_MAX_COLS ? 1 : 0;
+        p->bm_words = p->bm_two ? (int)((p->B.ncols + 1023) / 1024) : (int)((p->B.ncols + 31) / 32);
         const int miss = p->opts.merge_miss > 0 ? p->opts.merge_miss : 4096;
         p->bm_miss = std::max(batch, std::min(miss, 16384));
-        capmax = merge_bm_max_cap(p->bm_words, p->bm_miss, smem_limit, p->wide_above);
+        capmax = merge_bm_max_cap(p->bm_words, p->bm_miss, smem_limit, p->wide_above, p->bm_two != 0);
     }
     if (p->opts.smem_cap_max > 0) capmax = std::min(capmax, std::max(256, p->opts.smem_cap_max));
     p->batch = batch;
@@ -677,7 +666,7 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
                 L.wide_above = p->wide_above;
                 L.bm_words = p->bm_words;
                 L.bm_miss = p->bm_miss;
-                L.bm_sliced = p->bm_slice_d > 0 ? 1 : 0;
+                L.bm_two = p->bm_two;
                 L.work = work;
                 L.work_base = work_base;
                 L.nwork = nwork;
@@ -791,22 +780,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
         SPG_TRY(p->alloc_n(&ovf_count, 1, LIFE_NUMERIC));
         SPG_TRY(launch_merge_init(rows37, n37, p->ctil_rp, p->ctil_col, p->ctil_val, p->items, p->st));
         p->count(SPGEMM_K_OTHER);
-        if (p->bm_slice_d > 0) {
-            // B wider than the bitmap: column slices of every row, each started at the
-            // initial capacity (the rows' homes are not used)
-            const int d = p->bm_slice_d;
-            const int64_t k = (int64_t)1 << d;
-            int32_t *leaves = nullptr;
-            SPG_TRY(reserve_items(p, n37 + n37 * (2 * k - 2)));
-            SPG_TRY(p->alloc_n(&leaves, n37 * k, LIFE_NUMERIC));
-            SPG_TRY(launch_presplit(n37, d, p->bm_width, n37, p->items, leaves, p->st));
-            p->count(SPGEMM_K_OTHER);
-            p->n_items = n37 + n37 * (2 * k - 2);
-            p->stats.rows_split += n37 * (k - 1);
-            const int cap = std::min(capmax, std::max(256, (int)p->opts.initial_cap));
-            status = run_progressive(p, leaves, 0, n37 * k, cap, false, ovf_count);
-            if (status != SPGEMM_OK) goto fail;
-        } else if (!learned) {
+        if (!learned) {
             int cap;
             if (p->opts.alloc_policy == SPGEMM_ALLOC_UPPER_BOUND) cap = capmax;
             else cap = std::min(capmax, std::max(32, (int)p->opts.initial_cap));
@@ -864,7 +838,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 L.wide_above = p->wide_above;
                 L.bm_words = p->bm_words;
                 L.bm_miss = p->bm_miss;
-                L.bm_sliced = p->bm_slice_d > 0 ? 1 : 0;
+                L.bm_two = p->bm_two;
                 L.work = p->class_order + off;
                 L.nwork = cnt;
                 L.cap = ccap;
@@ -903,7 +877,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 L.wide_above = p->wide_above;
                 L.bm_words = p->bm_words;
                 L.bm_miss = p->bm_miss;
-                L.bm_sliced = p->bm_slice_d > 0 ? 1 : 0;
+                L.bm_two = p->bm_two;
                 L.work = lists[k];
                 L.nwork = nk;
                 L.cap = lv[k];
