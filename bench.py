@@ -284,6 +284,7 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
     res = {"policy": policy, "ms_per_step": ms_step, "value": value,
            "kms": kms, "launches": launches, "wall_s": t_wall,
            "st_all": st_all, "arrays": arrays, "sum_u": sum_u, "nnz_C": int(st_all[-1]["nnz_c"]),
+           "heap_max_u": opts.get("heap_max_u"),
            "peak_bytes": int(sum(s["peak_bytes"] for s in st_all)),
            "merge_rounds": int(sum(s["merge_rounds"] for s in st_all)),
            "rows_fallback": int(sum(s["rows_fallback"] for s in st_all)),
@@ -547,7 +548,8 @@ def roofline(args, pairs, m):
         elif dom in ("bound", "bin", "scan"):
             bytes_dom += A.nnz * 12 + 16 * u.shape[0]
         else:
-            sel = {"merge": bins == 37, "esc": (bins >= 33) & (bins <= 36), "heap": (bins >= 2) & (bins <= 32)}.get(
+            hmax = m.get("heap_max_u") or 32  # bins above it (up to 36) run the bitmap ESC kernel
+            sel = {"merge": bins == 37, "esc": (bins > hmax) & (bins <= 36), "heap": (bins >= 2) & (bins <= hmax)}.get(
                 dom, np.ones(u.shape[0], dtype=bool))
             bytes_dom += algorithmic_bytes(A, B, u, np.nonzero(sel)[0], rn)
     achieved = bytes_dom / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
