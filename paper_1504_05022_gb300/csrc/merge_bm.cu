@@ -16,9 +16,10 @@
 //       moves (right to left, in chunks) to its rank in the union, and every
 //       new column takes its rank; duplicate misses add into the same entry.
 // A batch of products therefore costs one block barrier, and the merge work
-// is paid once per miss buffer instead of once per batch.  Capacity, the
-// checkpoint at overflow and the progressive relaunch are those of k_merge:
-// a batch never exceeds the free capacity, so a merge can always complete.
+// is paid once per miss buffer instead of once per batch.  A batch is admitted
+// when its actual new columns fit the free capacity (its hits take none), so a
+// merge can always complete.  The checkpoint at overflow and the progressive
+// relaunch are those of k_merge.
 // The index has two forms.  Flat (B with at most BM_MAX_COLS columns): one bit
 // per column of the item's range.  Two-level (wider B, up to BM2_MAX_COLS): a
 // level-1 bitmap marks the occupied 32-column words, and a word table in word
