@@ -142,6 +142,41 @@ def lap3d27(g: int) -> HostCSR:
     return _stencil(g, 3, offs, 26.0, -1.0)
 
 
+def lap2d9(g: int) -> HostCSR:
+    """2D 9-point Laplacian, g x g grid, diagonal 8.0, off-diagonal -1.0, no wrap-around."""
+    offs = [(dx, dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    return _stencil(g, 2, offs, 8.0, -1.0)
+
+
+def lap3d7(g: int) -> HostCSR:
+    """3D 7-point Laplacian, g^3 grid, diagonal 6.0, off-diagonal -1.0, no wrap-around."""
+    offs = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    return _stencil(g, 3, offs, 6.0, -1.0)
+
+
+def agg_P2(g: int, dim: int) -> HostCSR:
+    """Piecewise-constant aggregation over 2^dim blocks of a g^dim grid (g even): fine point
+    x + g*y (+ g^2*z) maps to aggregate (x/2) + (g/2)*(y/2) (+ (g/2)^2*(z/2)); one 1.0 per row."""
+    assert g % 2 == 0 and dim in (2, 3)
+    n = g ** dim
+    h = g // 2
+    idx = np.arange(n, dtype=np.int64)
+    agg = np.zeros(n, dtype=np.int64)
+    for d in range(dim):
+        agg += ((idx // g ** d) % g // 2) * h ** d
+    return from_coo(n, h ** dim, idx, agg, np.ones(n))
+
+
+def galerkin_levels(g: int, dim: int, coarsest: int = 4):
+    """Aggregation operators of a piecewise-constant hierarchy on a g^dim grid: P_l for
+    levels l = 0, 1, ... while the grid is larger than `coarsest` (halved each level)."""
+    Ps = []
+    while g > coarsest:
+        Ps.append(agg_P2(g, dim))
+        g //= 2
+    return Ps
+
+
 def agg_P(g: int) -> HostCSR:
     """Piecewise-constant aggregation over 2x2x2 blocks of a g^3 grid (g even).
 

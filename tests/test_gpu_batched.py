@@ -213,3 +213,47 @@ def test_batched_waves(spg, oracle_mod, policy):
     for i, ((A2, B2), C) in enumerate(zip(new, Cs)):
         _check(oracle_mod, A2, B2, C, f"wave replay {i}")
     del g, keep
+
+
+@pytest.mark.parametrize("stencil,g,dim", [("lap2d9", 256, 2), ("lap3d7", 32, 3), ("lap3d27", 32, 3)])
+@pytest.mark.parametrize("policy", ["hybrid", "learned"])
+def test_galerkin_hierarchy_exact(spg, oracle_mod, stencil, g, dim, policy):
+    """A piecewise-constant aggregation hierarchy A_{l+1} = P_l^T (A_l P_l) down to a 4^dim grid,
+    each level's product fed by the previous one on the device: every level equals the oracle's
+    exactly (integer-valued operators), and all levels' plans replayed from one CUDA graph after
+    scaling the finest operator scale every level."""
+    from paper_1504_05022_gb300.predictor import Predictor
+    A = getattr(gen, stencil)(g)
+    Ps = gen.galerkin_levels(g, dim)
+    opts = Predictor.load().opts() if policy == "learned" else {"alloc_policy": policy}
+    s = torch.cuda.Stream()
+    Ad = spg.CSR.from_host(A)
+    cur, plans, levels, keep = Ad, [], [], []
+    with torch.cuda.stream(s):
+        for P in Ps:
+            Pd, Rd = spg.CSR.from_host(P), spg.CSR.from_host(gen.transpose(P))
+            cur, p1, p2 = spg.galerkin(Rd, cur, Pd, stream=s, **opts)
+            plans += [p1, p2]
+            levels.append(cur)
+            keep += [Pd, Rd]
+    s.synchronize()
+    ref, host = A, []
+    for P, Ac in zip(Ps, levels):
+        AP = oracle_mod.spgemm(ref, P)
+        Rc = oracle_mod.spgemm(gen.transpose(P), gen.HostCSR(AP.nrows, AP.ncols, AP.row_ptr, AP.col, AP.val))
+        rp, col, val = Ac.to_host()
+        assert np.array_equal(rp, Rc.row_ptr) and np.array_equal(col, Rc.col) and np.array_equal(val, Rc.val)
+        host.append((rp, col, val))
+        ref = gen.HostCSR(Rc.nrows, Rc.ncols, Rc.row_ptr, Rc.col, Rc.val)
+    assert levels[-1].shape == (4 ** dim, 4 ** dim)
+    graph = spg.ReplayGraph(plans)
+    for scale in (2.0, -3.0):
+        Ad.val.copy_(torch.from_numpy(A.val * scale))
+        s.synchronize()
+        graph.launch()
+        s.synchronize()
+        for Ac, (rp, col, val) in zip(levels, host):
+            rp2, col2, val2 = Ac.to_host()
+            assert np.array_equal(col2, col) and np.array_equal(val2, val * scale)
+    for p in plans:
+        p.check()

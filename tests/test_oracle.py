@@ -301,3 +301,54 @@ def test_row_counts_match_full_product():
     assert np.array_equal(oracle.row_counts(A, A), np.diff(ref.row_ptr))
     rows = np.array([5, 0, 1023, 7])
     assert np.array_equal(oracle.row_counts(A, A, rows), np.diff(ref.row_ptr)[rows])
+
+
+def _galerkin_oracle(A, P):
+    import oracle
+    R = gen.transpose(P)
+    AP = oracle.spgemm(A, P)
+    APm = gen.HostCSR(A.nrows, P.ncols, AP.row_ptr, AP.col, AP.val)
+    return oracle.spgemm(R, APm)
+
+
+def _coarse_entry(Ac, i, j):
+    s, e = Ac.row_ptr[i], Ac.row_ptr[i + 1]
+    hit = np.nonzero(Ac.col[s:e] == j)[0]
+    return None if hit.size == 0 else Ac.val[s + hit[0]]
+
+
+def test_galerkin_2d9_closed_form():
+    """2D 9-point Laplacian with 2x2 aggregation: the coarse operator is a 9-point stencil on the
+    (g/2)^2 grid, nnz (3g/2 - 2)^2; interior diagonal 4*(8 - 3) = 20, edge neighbours -2*2 = -4,
+    corner neighbours -1, interior row sums 0."""
+    g = 16
+    Ac = _galerkin_oracle(gen.lap2d9(g), gen.agg_P2(g, 2))
+    h = g // 2
+    assert Ac.nnz == (3 * h - 2) ** 2
+    i = 3 + h * 4
+    assert _coarse_entry(Ac, i, i) == 20.0
+    assert _coarse_entry(Ac, i, i + 1) == -4.0 and _coarse_entry(Ac, i, i + h) == -4.0
+    assert _coarse_entry(Ac, i, i + h + 1) == -1.0 and _coarse_entry(Ac, i, i - h - 1) == -1.0
+    assert Ac.val[Ac.row_ptr[i]:Ac.row_ptr[i + 1]].sum() == 0.0
+
+
+def test_galerkin_3d7_closed_form():
+    """3D 7-point Laplacian with 2x2x2 aggregation: a 7-point coarse stencil, nnz 7h^3 - 6h^2
+    (h = g/2); diagonal 8*(6 - 3) = 24 everywhere (Dirichlet truncation keeps the fine diagonal),
+    face neighbours -4 (four fine couplings across a block face)."""
+    g = 12
+    Ac = _galerkin_oracle(gen.lap3d7(g), gen.agg_P2(g, 3))
+    h = g // 2
+    assert Ac.nnz == 7 * h ** 3 - 6 * h ** 2
+    diag = np.array([_coarse_entry(Ac, i, i) for i in range(h ** 3)])
+    assert np.all(diag == 24.0)
+    i = 2 + h * (2 + h * 2)
+    for d in (1, h, h * h):
+        assert _coarse_entry(Ac, i, i + d) == -4.0 and _coarse_entry(Ac, i, i - d) == -4.0
+
+
+def test_aggregation_generators_agree():
+    for g in (4, 8):
+        assert np.array_equal(gen.agg_P2(g, 3).col, gen.agg_P(g).col)
+    assert [(P.nrows, P.ncols) for P in gen.galerkin_levels(32, 3)] == \
+        [(32 ** 3, 16 ** 3), (16 ** 3, 8 ** 3), (8 ** 3, 4 ** 3)]
