@@ -141,7 +141,16 @@ typedef struct spgemm_opts {
     int32_t merge_kernel;    /* spgemm_merge_kernel: form of the bin-37 kernel */
     int32_t merge_miss;      /* bitmap form: products whose column is new are buffered up to this
                                 many entries before they are merged into the result (0 = 4096) */
-    int32_t reserved[3];
+    int32_t dense_min_u;     /* bin-37 rows with u_i >= this are computed by the dense-slice
+                                kernels instead of the merge kernel: B's columns are cut into
+                                slices that fit shared memory as fp64 sums, one CTA per (row,
+                                slice), after a pass that counts the columns of every slice.
+                                0 = ncols(B) / 8; negative = never.  Off with
+                                SPGEMM_MERGE_PATH, SPGEMM_LONG_ROWS_LEVEL1 and when B needs more
+                                than 16 slices */
+    int32_t dense_span;      /* widest dense slice in columns (0 = the widest that fits shared
+                                memory, at least 1,024) */
+    int32_t reserved[1];
     const void *predictor;   /* spgemm_predictor* for SPGEMM_ALLOC_LEARNED, else NULL; it must
                                 not be freed before spgemm_symbolic (or spgemm_galerkin) has
                                 returned, since its weights are read by that call's kernels */
@@ -213,6 +222,8 @@ typedef struct spgemm_stats {
                                    when spgemm_symbolic returns and C~ with the merge pools when
                                    spgemm_numeric returns (stream-ordered), so after the product
                                    this is C plus the O(rows) tables that values-only replay uses */
+    int64_t rows_dense;         /* bin-37 rows computed by the dense-slice kernels */
+    int64_t dense_slices;       /* column slices of B used by them (0 when none) */
 } spgemm_stats;
 
 /* Copies the plan's counters into *out.  Timings are read after synchronising

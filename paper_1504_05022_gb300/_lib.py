@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
                 ("record_timing", c_i32), ("merge_batch", c_i32), ("smem_cap_max", c_i32),
                 ("heap_block", c_i32), ("long_rows", c_i32), ("wave_mproducts", c_i32), ("heap_max_u", c_i32),
                 ("merge_wide_above", c_i32), ("merge_kernel", c_i32), ("merge_miss", c_i32),
-                ("reserved", c_i32 * 3),
+                ("dense_min_u", c_i32), ("dense_span", c_i32), ("reserved", c_i32 * 1),
                 ("predictor", c_ptr),
                 ("predictor_margin", c_f64)]
 
@@ -45,7 +45,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("bin_count", c_i64 * NUM_BINS), ("sum_u", c_i64), ("nnz_ctilde", c_i64), ("nnz_c", c_i64),
                 ("merge_rounds", c_i64), ("rows_relaunched", c_i64), ("rows_level1", c_i64), ("rows_split", c_i64),
                 ("rows_fallback", c_i64), ("bytes_ctilde", c_i64), ("peak_bytes", c_i64),
-                ("launches", c_i32 * 8), ("kernel_ms", c_f32 * 8), ("held_bytes", c_i64)]
+                ("launches", c_i32 * 8), ("kernel_ms", c_f32 * 8), ("held_bytes", c_i64), ("rows_dense", c_i64),
+                ("dense_slices", c_i64)]
 
 
 class PlanArrays(ctypes.Structure):

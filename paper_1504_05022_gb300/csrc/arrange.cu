@@ -76,6 +76,7 @@ cudaError_t launch_arrange_short(const StageArgs &a, const int32_t *rows, int64_
 
 // One CTA per bin-37 row: its leaves (column slices) are visited in column order
 // by a depth-first walk of the split tree (left child first) and copied back to back.
+// Rows of the dense-slice kernels are already in C.
 __global__ void __launch_bounds__(ARR_NT)
 k_arrange_long(MergeItems it, const int64_t *__restrict__ c_rp, int32_t *__restrict__ c_col,
                double *__restrict__ c_val) {
@@ -84,6 +85,7 @@ k_arrange_long(MergeItems it, const int64_t *__restrict__ c_rp, int32_t *__restr
     __shared__ int stack[STACK];
     __shared__ int sp, nleaves;
     const int j = blockIdx.x;
+    if (it.child[j] == ITEM_DENSE) return;  // written into C by the dense-slice kernel
     int64_t o = c_rp[it.row[j]];
     if (threadIdx.x == 0) {
         sp = 0;

@@ -1,0 +1,388 @@
+// Stage 3, bin group 5, for the rows whose products cover a large part of B's
+// column range (u_i >= a threshold of the order of ncols(B)): a dense
+// accumulator over column slices instead of the merge of Section 4.1.
+//
+// B's columns are cut into K slices of W columns (W a multiple of 32, K W >=
+// ncols).  A slice of a row is one CTA.  Its shared memory holds W fp64 sums and
+// W flag bytes; every product of the row whose column falls in the slice adds
+// into its column's sum (a shared fp64 atomic) and stores 1 into its column's
+// flag.  There are no misses, no merges and no capacity to outgrow: the cost is
+// the products plus O(W) to clear the slice and to write it out in column order.
+// The part of each B row that falls in slice s is read from a table of per-row
+// slice boundaries, built once per call, and is cut into chunks of consecutive
+// entries that the warps share out.
+//
+// The rows' sizes are counted first (the same expansion with only the flags), so
+// the dense rows need no temporary space at all: their sizes go into the row
+// counts of C with the other rows', and the values are written straight into C
+// once its row pointers exist.  The same launch recomputes the values for a
+// values-only replay.
+#include "internal.h"
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace spg {
+
+// ---- per-B-row slice boundaries ----
+
+__global__ void k_dense_bounds(DevCSR B, int K, int W, int32_t *bnd) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.nrows * (K + 1)) return;
+    const int64_t k = i / (K + 1);
+    const int s = (int)(i - k * (K + 1));
+    const int64_t rs = B.rp[k];
+    const int n = (int)(B.rp[k + 1] - rs);
+    int v;
+    if (s == 0) v = 0;
+    else if (s == K) v = n;
+    else v = lower_bound_i32(B.col + rs, n, (int32_t)((int64_t)s * W));
+    bnd[i] = v;
+}
+
+cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cudaStream_t st) {
+    const int64_t n = B.nrows * (K + 1);
+    if (n <= 0 || K <= 1) return cudaSuccess;
+    k_dense_bounds<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, K, W, bnd);
+    return cudaGetLastError();
+}
+
+// ---- selection of the dense rows among the bin-37 rows ----
+// Bucket g = 63 - floor(log2 u) (the leading zeros of u) for a dense row, so that
+// larger rows come first; DENSE_BUCKETS for the others.  order[0..nd) lists the
+// dense items, order[nd..n37) the rest.
+
+constexpr int DENSE_BUCKETS = 64;
+
+__global__ void k_dense_select_count(const int32_t *bin_rows, int64_t m, const BinSummary *summary, const int64_t *u,
+                                     int64_t dmin, int32_t *cls_of, int32_t *count) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n37 = summary->bin_count[BIN_MERGE];
+    if (j >= n37) return;
+    const int64_t uu = u[bin_rows[m - n37 + j]];
+    const int g = uu >= dmin ? __clzll((long long)uu) : DENSE_BUCKETS;
+    cls_of[j] = g;
+    atomicAdd(&count[g], 1);
+}
+
+__global__ void k_dense_select_starts(const int32_t *count, int32_t *start, int32_t *cursor, BinSummary *summary) {
+    if (threadIdx.x == 0) {
+        int32_t s = 0;
+        for (int g = 0; g <= DENSE_BUCKETS; ++g) {
+            start[g] = s;
+            cursor[g] = 0;
+            if (g == DENSE_BUCKETS) summary->dense_count = s;
+            s += count[g];
+        }
+    }
+}
+
+__global__ void k_dense_select_scatter(const BinSummary *summary, const int32_t *cls_of, const int32_t *start,
+                                       int32_t *cursor, int32_t *order) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= summary->bin_count[BIN_MERGE]) return;
+    const int g = cls_of[j];
+    order[start[g] + atomicAdd(&cursor[g], 1)] = (int32_t)j;
+}
+
+int64_t dense_select_scratch(int64_t m) { return 3 * (DENSE_BUCKETS + 1) + m; }
+
+cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *summary, const int64_t *u,
+                                int64_t dmin, int32_t *scratch, int32_t *order, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    int32_t *count = scratch, *start = count + DENSE_BUCKETS + 1, *cursor = start + DENSE_BUCKETS + 1,
+            *cls_of = cursor + DENSE_BUCKETS + 1;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t) * (DENSE_BUCKETS + 1), st);
+    if (e != cudaSuccess) return e;
+    const unsigned g = (unsigned)((m + 255) / 256);
+    k_dense_select_count<<<g, 256, 0, st>>>(bin_rows, m, summary, u, dmin, cls_of, count);
+    k_dense_select_starts<<<1, 32, 0, st>>>(count, start, cursor, summary);
+    k_dense_select_scatter<<<g, 256, 0, st>>>(summary, cls_of, start, cursor, order);
+    return cudaGetLastError();
+}
+
+// ---- the product expansion shared by the count and fill kernels ----
+// Walks the A entries of `row` in windows of NT.  For each window, the part of
+// every selected B row inside slice s is cut into chunks of DENSE_CH consecutive
+// entries; warp w takes the w-th contiguous range of the window's chunks, and its
+// lanes read a chunk's entries 32 at a time (coalesced, one B row per access, so
+// the 32 columns of an access are distinct), DENSE_UN accesses in flight.
+// f(p, ok, t) gets DENSE_UN entry positions p[] of B, which of them are valid,
+// and the window slot t of their A entry.  Ends with a barrier.
+constexpr int DENSE_CH = 256;
+constexpr int DENSE_UN = 4;
+
+template <int NT, bool VALS, typename F>
+SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int row, int s, int64_t *wbs,
+                          int32_t *wlen, int64_t *cscan, double *wa, int64_t *scan64, F f) {
+    constexpr int NW = NT / 32;
+    const int lane = lane_id(), wid = warp_id();
+    const int64_t a0 = A.rp[row], a1 = A.rp[row + 1];
+    const int K1 = D.K + 1;
+    for (int64_t e = a0; e < a1; e += NT) {
+        const int nW = (int)min((int64_t)NT, a1 - e);
+        int64_t nch = 0;
+        if (threadIdx.x < nW) {
+            const int32_t k = A.col[e + threadIdx.x];
+            const int64_t rs = B.rp[k];
+            int64_t bs, be;
+            if (D.K > 1) {
+                const int32_t *bk = D.bnd + (int64_t)k * K1 + s;
+                bs = rs + bk[0];
+                be = rs + bk[1];
+            } else {
+                bs = rs;
+                be = B.rp[k + 1];
+            }
+            wbs[threadIdx.x] = bs;
+            wlen[threadIdx.x] = (int32_t)(be - bs);  // a B row has at most ncols < 2^31 entries
+            if (VALS) wa[threadIdx.x] = A.val[e + threadIdx.x];
+            nch = (be - bs + DENSE_CH - 1) / DENSE_CH;
+        }
+        int64_t tc;
+        const int64_t ex = block_exclusive_scan<NT, int64_t, false>(nch, scan64, tc);
+        if (threadIdx.x < nW) cscan[threadIdx.x] = ex;
+        __syncthreads();
+        const int64_t c0 = tc * wid / NW, c1 = tc * (wid + 1) / NW;
+        int t = 0;
+        if (c0 < c1) {  // the entry of chunk c0: the last one whose first chunk is <= c0
+            int lo = 0, hi = nW - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cscan[mid] <= c0) lo = mid; else hi = mid - 1;
+            }
+            t = lo;
+        }
+        for (int64_t c = c0; c < c1; ++c) {
+            while (t + 1 < nW && cscan[t + 1] <= c) ++t;  // warp-uniform: skips entries without chunks
+            const int64_t off = (c - cscan[t]) * DENSE_CH;
+            const int64_t p0 = wbs[t] + off;
+            const int n = (int)min((int64_t)DENSE_CH, (int64_t)wlen[t] - off);
+            for (int i = lane; i < n; i += 32 * DENSE_UN) {
+                int64_t p[DENSE_UN];
+                bool ok[DENSE_UN];
+#pragma unroll
+                for (int u = 0; u < DENSE_UN; ++u) {
+                    ok[u] = i + 32 * u < n;
+                    p[u] = p0 + i + 32 * u;
+                }
+                f(p, ok, t);
+            }
+        }
+        __syncthreads();  // the window's tables are reused
+    }
+}
+
+// ---- pass 1: the number of columns of every (row, slice) ----
+// Shared memory: one flag byte per column of the slice (a plain store of 1 per
+// product: every writer stores the same value, so no atomics are needed).
+
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_dense_count(DevCSR A, DevCSR B, MergeItems it, DenseArgs D, int64_t *err) {
+    extern __shared__ __align__(16) uint8_t dc_flag[];
+    __shared__ int64_t wbs[NT], cscan[NT], scan64[NT / 32 + 1];
+    __shared__ int32_t wlen[NT], scan32[NT / 32 + 1];
+    const int64_t b = blockIdx.x;
+    const int64_t d = b / D.K;
+    const int s = (int)(b - d * D.K);
+    const int row = it.row[D.items[d]];
+    const int64_t lo = (int64_t)s * D.W;
+    const int span = (int)min((int64_t)D.W, B.ncols - lo);
+    const int nq = (span + 15) >> 4;  // 16-byte groups of flags
+    uint4 *f4 = reinterpret_cast<uint4 *>(dc_flag);
+    for (int q = threadIdx.x; q < nq; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    bool bad = false;
+    volatile uint8_t *fl = dc_flag;
+    dense_expand<NT, false>(A, B, D, row, s, wbs, wlen, cscan, nullptr, scan64,
+                            [&](const int64_t *p, const bool *ok, int) {
+        int32_t c[DENSE_UN];
+#pragma unroll
+        for (int u = 0; u < DENSE_UN; ++u)
+            if (ok[u]) c[u] = __ldg(B.col + p[u]);
+#pragma unroll
+        for (int u = 0; u < DENSE_UN; ++u) {
+            if (!ok[u]) continue;
+            const int x = (int)(c[u] - lo);
+            if ((unsigned)x >= (unsigned)span) {  // cannot happen: the slice boundaries select the columns
+                bad = true;
+                continue;
+            }
+            fl[x] = 1;
+        }
+    });
+    int n = 0;
+    for (int q = threadIdx.x; q < nq; q += NT) {
+        const uint4 v = f4[q];
+        n += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    }
+    n = block_reduce_sum<NT, int>(n, scan32);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch((unsigned long long *)err, 5ull);
+    if (threadIdx.x == 0) D.cnt[b] = n;
+}
+
+// One thread per dense item: the slices' offsets inside the row and the row's length.
+__global__ void k_dense_rows(MergeItems it, DenseArgs D) {
+    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= D.n) return;
+    int32_t acc = 0;
+    for (int s = 0; s < D.K; ++s) {
+        D.soff[d * D.K + s] = acc;
+        acc += D.cnt[d * D.K + s];
+    }
+    const int j = D.items[d];
+    it.len[j] = acc;
+    it.src_len[j] = 0;
+    it.home_cap[j] = 0;
+    it.home_col[j] = nullptr;
+    it.home_val[j] = nullptr;
+    it.child[j] = ITEM_DENSE;
+}
+
+// ---- pass 2: the values, written into C ----
+// Shared memory: W fp64 sums, W flag bytes, then the flags as a bitmap and its
+// rank directory for the write-out.
+
+__host__ __device__ inline int dense_nw4(int W) { return ((W + 31) / 32 + 4) & ~3; }
+
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+k_dense_fill(DevCSR A, DevCSR B, MergeItems it, DenseArgs D, const int64_t *c_rp, int32_t *c_col, double *c_val,
+             int64_t *err) {
+    extern __shared__ __align__(16) unsigned char df_smem[];
+    __shared__ int64_t wbs[NT], cscan[NT], scan64[NT / 32 + 1];
+    __shared__ double wa[NT];
+    __shared__ int32_t wlen[NT], scan32[NT / 32 + 1];
+    const int64_t b = blockIdx.x;
+    const int expected = D.cnt[b];
+    if (expected == 0) return;
+    const int64_t d = b / D.K;
+    const int s = (int)(b - d * D.K);
+    const int row = it.row[D.items[d]];
+    const int64_t lo = (int64_t)s * D.W;
+    const int span = (int)min((int64_t)D.W, B.ncols - lo);
+    const int nwords = (span + 31) >> 5;
+    const int nw4 = dense_nw4(D.W);
+    double *V = reinterpret_cast<double *>(df_smem);
+    uint8_t *flag = reinterpret_cast<uint8_t *>(V + D.W);
+    uint32_t *Bm = reinterpret_cast<uint32_t *>(flag + D.W);  // D.W is a multiple of 32
+    int32_t *Rd = reinterpret_cast<int32_t *>(Bm + nw4);
+    {
+        double2 *v2 = reinterpret_cast<double2 *>(V);
+        for (int x = threadIdx.x; x < (span + 1) >> 1; x += NT) v2[x] = make_double2(0.0, 0.0);
+        uint4 *f4 = reinterpret_cast<uint4 *>(flag);  // whole 32-column words, as read below
+        for (int q = threadIdx.x; q < 2 * nwords; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
+    bool bad = false;
+    volatile uint8_t *fl = flag;
+    dense_expand<NT, true>(A, B, D, row, s, wbs, wlen, cscan, wa, scan64,
+                           [&](const int64_t *p, const bool *ok, int t) {
+        int32_t c[DENSE_UN];
+        double v[DENSE_UN];
+#pragma unroll
+        for (int u = 0; u < DENSE_UN; ++u)
+            if (ok[u]) c[u] = __ldg(B.col + p[u]);
+#pragma unroll
+        for (int u = 0; u < DENSE_UN; ++u)
+            if (ok[u]) v[u] = __ldg(B.val + p[u]);
+        const double a = wa[t];
+#pragma unroll
+        for (int u = 0; u < DENSE_UN; ++u) {
+            if (!ok[u]) continue;
+            const int x = (int)(c[u] - lo);
+            if ((unsigned)x >= (unsigned)span) {  // cannot happen: the slice boundaries select the columns
+                bad = true;
+                continue;
+            }
+            atomicAdd(&V[x], a * v[u]);
+            fl[x] = 1;
+        }
+    });
+    // flags -> bitmap (32 columns per word), then its rank directory
+    for (int w = threadIdx.x; w < nwords; w += NT) {
+        const uint4 *f4 = reinterpret_cast<const uint4 *>(flag + 32 * w);
+        const uint4 lo4 = f4[0], hi4 = f4[1];
+        const uint32_t q[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            // byte j of q[k] (0 or 1) is column 4k + j
+            const uint32_t y = q[k];
+            m |= ((y & 1u) | ((y >> 7) & 2u) | ((y >> 14) & 4u) | ((y >> 21) & 8u)) << (4 * k);
+        }
+        Bm[w] = m;
+    }
+    __syncthreads();
+    const int tot = bitmap_rank<NT>(Bm, Rd, nwords, scan32);
+    if (__syncthreads_or(bad || tot != expected)) {  // the counting pass saw other columns: cannot happen
+        if (threadIdx.x == 0) atomicExch((unsigned long long *)err, 6ull);
+        return;
+    }
+    // column order: consecutive threads take consecutive columns, so a warp's stores
+    // land in one contiguous run of C
+    const int64_t o = c_rp[row] + D.soff[b];
+    for (int x = threadIdx.x; x < span; x += NT) {
+        const uint32_t wd = Bm[x >> 5];  // the same word for the whole warp
+        if (wd == 0u) continue;
+        if ((wd >> (x & 31)) & 1u) {
+            const int64_t pos = o + Rd[x >> 5] + __popc(wd & ((1u << (x & 31)) - 1u));
+            c_col[pos] = (int32_t)(lo + x);
+            c_val[pos] = V[x];
+        }
+    }
+}
+
+constexpr int DENSE_COUNT_NT = 256;
+constexpr int DENSE_FILL_NT = 512;
+
+int dense_fill_smem_bytes(int W) {
+    return (int)((sizeof(double) + 1) * (size_t)W + 2 * sizeof(int32_t) * (size_t)dense_nw4(W));
+}
+
+// Largest dynamic shared memory of a fill CTA when `per_sm` of them share an SM
+// (228 KB per SM, 1 KB of it reserved per CTA, at most 227 KB per CTA).
+int dense_fill_max_dynamic(int per_sm) {
+    const int per_cta = std::min(227 * 1024, 228 * 1024 / per_sm - 1024);
+    return per_cta - dense_fill_static_smem();
+}
+
+int dense_fill_static_smem() {
+    return (int)(DENSE_FILL_NT * (2 * sizeof(int64_t) + sizeof(double) + sizeof(int32_t)) +
+                 (DENSE_FILL_NT / 32 + 1) * 12 + 64);
+}
+
+cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const MergeItems &it, const DenseArgs &D,
+                               int64_t *err, cudaStream_t st) {
+    if (D.n <= 0) return cudaSuccess;
+    const int64_t nb = D.n * D.K;
+    if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
+    const int smem = D.W;  // flag bytes (a multiple of 32)
+    auto kern = k_dense_count<DENSE_COUNT_NT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nb, DENSE_COUNT_NT, smem, st>>>(A, B, it, D, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_dense_rows<<<(unsigned)((D.n + 127) / 128), 128, 0, st>>>(it, D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const MergeItems &it, const DenseArgs &D,
+                              const int64_t *c_rp, int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st) {
+    if (D.n <= 0) return cudaSuccess;
+    const int64_t nb = D.n * D.K;
+    if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
+    const int smem = dense_fill_smem_bytes(D.W);
+    // two CTAs per SM when two slices fit the SM's shared memory (64 registers a thread)
+    auto kern = smem <= dense_fill_max_dynamic(2) ? k_dense_fill<DENSE_FILL_NT, 2> : k_dense_fill<DENSE_FILL_NT, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nb, DENSE_FILL_NT, smem, st>>>(A, B, it, D, c_rp, c_col, c_val, err);
+    return cudaGetLastError();
+}
+
+}  // namespace spg

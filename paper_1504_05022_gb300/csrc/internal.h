@@ -33,6 +33,7 @@ struct BinSummary {
     int64_t status;    // validation result (0 = ok)
     int64_t pad;
     int64_t class_count[NUM_LAUNCH_CLASSES];  // learned: bin-37 rows per launch class
+    int64_t dense_count;                      // bin-37 rows computed by the dense-slice kernels
 };
 
 struct CapPolicy {
@@ -40,6 +41,7 @@ struct CapPolicy {
     int64_t initial_cap;
     const int32_t *pred_cap;  // learned per-row temporary row sizes (POLICY_LEARNED), may be null
     int64_t cap_max;          // learned: a bin-37 row's home never exceeds the largest shared capacity
+    int64_t dense_min_u;      // bin-37 rows with u_i >= this take no C~ space (dense-slice kernels)
 };
 
 // ---- stage 0/1/2 (stage12.cu) ----
@@ -65,11 +67,12 @@ cudaError_t launch_predict_caps(const float *params, const float *X, int64_t m, 
                                 int32_t min_cap, int32_t *pred_cap, cudaStream_t st, const int64_t *arp = nullptr,
                                 const int64_t *S = nullptr, int64_t u_min = 0);
 // Groups the bin-37 items (tail of bin_rows, size read from summary) by launch
-// class; scratch: 96 + m int32; order: item indices grouped by class; counts go
-// to summary->class_count.
+// class; items of rows with u >= dmin go after the last class; scratch: 96 + m
+// int32; order: item indices grouped by class; counts go to summary->class_count.
 cudaError_t launch_class_partition_tail(const int32_t *bin_rows, int64_t m, BinSummary *summary,
                                         const int32_t *pred_cap, const int32_t *class_cap, int ncls,
-                                        int32_t *scratch, int32_t *order, cudaStream_t st);
+                                        const int64_t *u, int64_t dmin, int32_t *scratch, int32_t *order,
+                                        cudaStream_t st);
 const float *predictor_params(const void *pred);
 
 // ---- stage 3 ----
@@ -153,6 +156,34 @@ cudaError_t launch_finalize37(int64_t n37, const MergeItems &it, int32_t *nnzc, 
 cudaError_t launch_level1_sizes(const MergeItems &it, const int32_t *work, int64_t nwork,
                                 const int64_t *u, int64_t ncols, int64_t *g_cap, int64_t *g_off,
                                 int64_t *partial, int64_t *total, cudaStream_t st);
+
+// ---- dense column slices for the longest bin-37 rows (dense.cu) ----
+constexpr int32_t ITEM_DENSE = -2;  // MergeItems.child of a row computed by the dense-slice kernels
+constexpr int DENSE_MAX_SLICES = 16;
+struct DenseArgs {
+    const int32_t *items;  // dense items (indices into MergeItems), larger rows first
+    int64_t n;             // number of dense items
+    int K;                 // column slices of B
+    int W;                 // slice width (a multiple of 32); slice s holds columns [s W, (s + 1) W)
+    const int32_t *bnd;    // K > 1: per B row, K + 1 offsets of the slices' first entries in the row
+    int32_t *cnt;          // n K columns per (row, slice)
+    int32_t *soff;         // n K offsets of the slices inside their row of C
+};
+cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cudaStream_t st);
+int64_t dense_select_scratch(int64_t m);
+// order[0..nd) = items of the bin-37 rows with u >= dmin (larger first), order[nd..n37) = the rest;
+// nd goes to summary->dense_count
+cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *summary, const int64_t *u,
+                                int64_t dmin, int32_t *scratch, int32_t *order, cudaStream_t st);
+// counts the columns of every (row, slice), then sets the items' lengths and slice offsets
+cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const MergeItems &it, const DenseArgs &D,
+                               int64_t *err, cudaStream_t st);
+// accumulates every (row, slice) and writes it into C at c_rp[row] + soff
+cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const MergeItems &it, const DenseArgs &D,
+                              const int64_t *c_rp, int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st);
+int dense_fill_smem_bytes(int W);
+int dense_fill_static_smem();
+int dense_fill_max_dynamic(int per_sm);
 
 // ---- values-only replay (replay.cu) ----
 struct ReplayLeaves {

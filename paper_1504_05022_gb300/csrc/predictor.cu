@@ -301,22 +301,25 @@ cudaError_t launch_predict_caps(const float *params, const float *X, int64_t m, 
 
 // Launch-class partition of the bin-37 rows by predicted size: class g holds
 // the rows whose predicted size is at most class_cap[g] (the smallest such g).
+// Rows with u_i >= dmin (the dense-slice rows) go to slot ncls, after the classes.
 // Bin 37 is the last segment of bin_rows; its size is read from the stage-2
 // summary on the device, so no host round trip is needed.  The order inside a
 // class is not fixed (atomics); it only affects scheduling, not C.
 __global__ void k_class_count(const int32_t *bin_rows, int64_t m, const BinSummary *summary,
-                              const int32_t *pred_cap, const int32_t *class_cap, int ncls, int32_t *cls_of,
-                              int32_t *count) {
+                              const int32_t *pred_cap, const int32_t *class_cap, int ncls, const int64_t *u,
+                              int64_t dmin, int32_t *cls_of, int32_t *count) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n37 = summary->bin_count[BIN_MERGE];
     if (j >= n37) return;
-    const int32_t c = pred_cap[bin_rows[m - n37 + j]];
+    const int32_t row = bin_rows[m - n37 + j];
+    const int32_t c = pred_cap[row];
     int g = ncls - 1;
     for (int k = 0; k < ncls; ++k)
         if (c <= class_cap[k]) {
             g = k;
             break;
         }
+    if (u[row] >= dmin) g = ncls;
     cls_of[j] = g;
     atomicAdd(&count[g], 1);
 }
@@ -325,10 +328,10 @@ __global__ void k_class_starts(const int32_t *count, int ncls, int32_t *start, i
                                BinSummary *summary) {
     if (threadIdx.x == 0) {
         int32_t s = 0;
-        for (int g = 0; g < ncls; ++g) {
+        for (int g = 0; g <= ncls; ++g) {
             start[g] = s;
             cursor[g] = 0;
-            summary->class_count[g] = count[g];
+            if (g < ncls) summary->class_count[g] = count[g];
             s += count[g];
         }
     }
@@ -344,13 +347,14 @@ __global__ void k_class_scatter(int64_t m, const BinSummary *summary, const int3
 
 cudaError_t launch_class_partition_tail(const int32_t *bin_rows, int64_t m, BinSummary *summary,
                                         const int32_t *pred_cap, const int32_t *class_cap, int ncls,
-                                        int32_t *scratch, int32_t *order, cudaStream_t st) {
-    if (m <= 0 || ncls > 32) return m <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+                                        const int64_t *u, int64_t dmin, int32_t *scratch, int32_t *order,
+                                        cudaStream_t st) {
+    if (m <= 0 || ncls > 31) return m <= 0 ? cudaSuccess : cudaErrorInvalidValue;
     int32_t *count = scratch, *start = scratch + 32, *cursor = scratch + 64, *cls_of = scratch + 96;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t) * 32, st);
     if (e != cudaSuccess) return e;
     const unsigned g = (unsigned)((m + 255) / 256);
-    k_class_count<<<g, 256, 0, st>>>(bin_rows, m, summary, pred_cap, class_cap, ncls, cls_of, count);
+    k_class_count<<<g, 256, 0, st>>>(bin_rows, m, summary, pred_cap, class_cap, ncls, u, dmin, cls_of, count);
     k_class_starts<<<1, 32, 0, st>>>(count, ncls, start, cursor, summary);
     k_class_scatter<<<g, 256, 0, st>>>(m, summary, cls_of, start, cursor, order);
     return cudaGetLastError();

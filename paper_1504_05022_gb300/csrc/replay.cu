@@ -292,6 +292,7 @@ __global__ void k_replay_leaves(int64_t n37, MergeItems it, const int64_t *c_rp,
     while (sp > 0) {
         const int x = stack[--sp];
         const int c = it.child[x];
+        if (c == ITEM_DENSE) continue;  // replayed by the dense-slice kernel
         if (c >= 0) {
             if (sp + 2 > STACK) {
                 atomicExch((unsigned long long *)err, 2ull);

@@ -152,6 +152,16 @@ struct spgemm_plan {
     int32_t *class_order = nullptr;   // bin-37 item indices grouped by launch class
     int32_t class_caps[NUM_LAUNCH_CLASSES] = {0};
     int capmax = 0, batch = 0, wide_above = 2048, bm_words = 0, bm_miss = 0, bm_two = 0;
+    // dense column slices for the longest bin-37 rows (off when dense_K == 0)
+    int dense_K = 0, dense_W = 0;
+    int64_t dense_min_u = INT64_MAX;
+    int64_t dense_n = 0;                  // dense bin-37 rows
+    int32_t *dense_order = nullptr;       // bin-37 items: the dense ones (larger first), then the rest
+    int32_t *dense_bnd = nullptr;         // per B row, K + 1 slice boundaries (K > 1)
+    int32_t *dense_cnt = nullptr, *dense_soff = nullptr;
+    DenseArgs dense_args() const {
+        return DenseArgs{dense_order, dense_n, dense_K, dense_W, dense_bnd, dense_cnt, dense_soff};
+    }
     // batched plans: the pairs and the concatenation offsets
     int64_t npairs = 0;
     PairDesc *d_pairs = nullptr;
@@ -282,6 +292,33 @@ static void merge_limits(spgemm_plan *p) {
     if (p->opts.smem_cap_max > 0) capmax = std::min(capmax, std::max(256, p->opts.smem_cap_max));
     p->batch = batch;
     p->capmax = capmax;
+    // dense column slices: by default the widest slice that fits shared memory (one fill
+    // CTA per SM; fill CTAs are bound by the SM's shared fp64 atomics, so two narrower
+    // ones per SM are no faster); dense_span narrows it, and slices narrow enough for two
+    // CTAs per SM run that way.  B's columns are cut into equal slices of a multiple of 32
+    p->dense_K = 0;
+    p->dense_W = 0;
+    p->dense_min_u = INT64_MAX;
+    if (p->opts.dense_min_u >= 0 && p->opts.merge_kernel != SPGEMM_MERGE_PATH &&
+        p->opts.long_rows == SPGEMM_LONG_ROWS_SPLIT && p->B.ncols > 0) {
+        const int64_t n = p->B.ncols;
+        auto widest = [](int limit) {
+            int w = (int)(limit / 9.25) & ~31;
+            while (w > 32 && dense_fill_smem_bytes(w) > limit) w -= 32;
+            return w;
+        };
+        const int w1 = widest(std::min(smem_limit - dense_fill_static_smem(), dense_fill_max_dynamic(1)));
+        int wmax = w1;
+        if (p->opts.dense_span > 0) wmax = std::min(w1, std::max(1024, p->opts.dense_span & ~31));
+        const int64_t k0 = (n + wmax - 1) / wmax;
+        if (wmax >= 32 && k0 <= DENSE_MAX_SLICES) {
+            const int64_t w = ((n + k0 - 1) / k0 + 31) & ~int64_t(31);
+            p->dense_W = (int)w;
+            p->dense_K = (int)((n + w - 1) / w);
+            p->dense_min_u = p->opts.dense_min_u > 0 ? (int64_t)p->opts.dense_min_u
+                                                     : std::max<int64_t>(BIN_MERGE_MIN_U + 1, n / 8);
+        }
+    }
     // learned launch classes: 256, 512, ..., 8192, the largest capacity, and "beyond it"
     for (int g = 0; g < NUM_LAUNCH_CLASSES - 1; ++g) p->class_caps[g] = std::min(256 << g, capmax);
     p->class_caps[NUM_LAUNCH_CLASSES - 2] = capmax;
@@ -491,6 +528,7 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             pol.initial_cap = o.initial_cap;
             pol.pred_cap = p->pred_cap;
             pol.cap_max = p->capmax;
+            pol.dense_min_u = p->dense_min_u;
             p->time_begin(SPGEMM_K_BIN);
             SPG_TRY(launch_binning(m, p->A.rp, p->S, p->S + nnzA, pol, p->u, p->bin, p->nnzc, p->bin_rows,
                                    p->ctil_rp, hist, capp, p->d_summary, p->st));
@@ -505,7 +543,17 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             SPG_TRY(p->alloc_n(&scratch, 96 + m, LIFE_SYMBOLIC));
             SPG_TRY(p->alloc_n(&p->class_order, m, LIFE_NUMERIC));
             SPG_TRY(launch_class_partition_tail(p->bin_rows, m, p->d_summary, p->pred_cap, ccap,
-                                                NUM_LAUNCH_CLASSES, scratch, p->class_order, p->st));
+                                                NUM_LAUNCH_CLASSES, p->u, p->dense_min_u, scratch,
+                                                p->class_order, p->st));
+            p->count(SPGEMM_K_OTHER, 3);
+        }
+        if (p->dense_K > 0) {
+            // the bin-37 rows for the dense-slice kernels, larger first, then the others
+            int32_t *scratch = nullptr;
+            SPG_TRY(p->alloc_n(&scratch, dense_select_scratch(m), LIFE_SYMBOLIC));
+            SPG_TRY(p->alloc_n(&p->dense_order, m));
+            SPG_TRY(launch_dense_select(p->bin_rows, m, p->d_summary, p->u, p->dense_min_u, scratch, p->dense_order,
+                                        p->st));
             p->count(SPGEMM_K_OTHER, 3);
         }
         SPG_TRY(p->d2h(&p->h_summary, p->d_summary, sizeof(BinSummary)));
@@ -514,6 +562,19 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
         for (int b = 0; b < NUM_BINS; ++b) p->stats.bin_count[b] = p->h_summary.bin_count[b];
         p->stats.sum_u = p->h_summary.sum_u;
         p->stats.nnz_ctilde = p->h_summary.sum_cap;
+        p->dense_n = p->dense_K > 0 ? p->h_summary.dense_count : 0;
+        p->stats.rows_dense = p->dense_n;
+        p->stats.dense_slices = p->dense_n > 0 ? p->dense_K : 0;
+        if (p->dense_n > 0) {
+            // kept for values-only replay: the slice boundaries, counts and offsets
+            if (p->dense_K > 1) {
+                SPG_TRY(p->alloc_n(&p->dense_bnd, p->B.nrows * (p->dense_K + 1)));
+                SPG_TRY(launch_dense_bounds(p->B, p->dense_K, p->dense_W, p->dense_bnd, p->st));
+                p->count(SPGEMM_K_OTHER);
+            }
+            SPG_TRY(p->alloc_n(&p->dense_cnt, p->dense_n * p->dense_K));
+            SPG_TRY(p->alloc_n(&p->dense_soff, p->dense_n * p->dense_K));
+        }
         // C~ (hybrid: u_i for bins 0..36, 256 for bin 37)
         SPG_TRY(p->alloc_n(&p->ctil_col, p->h_summary.sum_cap, LIFE_NUMERIC));
         SPG_TRY(p->alloc_n(&p->ctil_val, p->h_summary.sum_cap, LIFE_NUMERIC));
@@ -625,9 +686,11 @@ int launch_batch(const spgemm_plan *p, int cap, bool level1) {
 // overflow are relaunched with twice the capacity in a fresh pool slot, and at
 // the largest shared-memory capacity an overflowing item is split by column
 // (default) or finished with a level-1 sequence.  With split_first the items have
-// already overflowed at the largest capacity and go straight to that step.
+// already overflowed at the largest capacity and go straight to that step.  With
+// first_in_home the listed items are fresh rows whose homes in C~ hold `cap`
+// entries, as the items work_base.. of a first round do.
 spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t work_base, int64_t nwork, int cap,
-                              bool split_first, int32_t *ovf_count) {
+                              bool split_first, int32_t *ovf_count, bool first_in_home = false) {
     spgemm_status status = SPGEMM_OK;
     if (nwork <= 0) return SPGEMM_OK;
     StageArgs a = stage_args(p);
@@ -676,8 +739,11 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
                 L.ovf_list = list[which];
                 L.ovf_count = ovf_count;
                 L.err = p->d_err;
+                const bool fresh = first_in_home && work == work_in;
                 if (!level1 && work == nullptr && work_base > 0) {
                     // split round: every child already has a home (set by the split)
+                } else if (fresh) {
+                    // first round over fresh rows: their homes in C~ are large enough
                 } else if (!level1 && p->opts.alloc_policy != SPGEMM_ALLOC_UPPER_BOUND &&
                            (work != nullptr || cap > p->opts.initial_cap || learned)) {
                     SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap, LIFE_NUMERIC));
@@ -715,7 +781,7 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
                     status = SPGEMM_ERR_INTERNAL;
                     goto fail;
                 }
-                if (work == nullptr && work_base == 0 && !learned) p->stats.rows_relaunched = novf;
+                if (((work == nullptr && work_base == 0) || fresh) && !learned) p->stats.rows_relaunched = novf;
                 if (novf == 0) break;
                 ovf_items = list[which];
                 if (cap < capmax) {
@@ -780,11 +846,24 @@ spgemm_status run_bin37(spgemm_plan *p) {
         SPG_TRY(p->alloc_n(&ovf_count, 1, LIFE_NUMERIC));
         SPG_TRY(launch_merge_init(rows37, n37, p->ctil_rp, p->ctil_col, p->ctil_val, p->items, p->st));
         p->count(SPGEMM_K_OTHER);
+        if (p->dense_n > 0) {
+            // dense-slice rows: their column counts now, their values once C exists
+            p->time_begin(SPGEMM_K_MERGE);
+            SPG_TRY(launch_dense_count(p->A, p->B, p->items, p->dense_args(), p->d_err, p->st));
+            p->time_end();
+            p->count(SPGEMM_K_MERGE, 2);
+        }
         if (!learned) {
             int cap;
             if (p->opts.alloc_policy == SPGEMM_ALLOC_UPPER_BOUND) cap = capmax;
             else cap = std::min(capmax, std::max(32, (int)p->opts.initial_cap));
-            status = run_progressive(p, nullptr, 0, n37, cap, false, ovf_count);
+            if (p->dense_n == 0) {
+                status = run_progressive(p, nullptr, 0, n37, cap, false, ovf_count);
+            } else if (n37 > p->dense_n) {
+                // the other rows, listed after the dense ones
+                status = run_progressive(p, p->dense_order + p->dense_n, 0, n37 - p->dense_n, cap, false, ovf_count,
+                                         true);
+            }
             if (status != SPGEMM_OK) goto fail;
         } else {
             // capacity levels of the fallback: 512, 1024, ... below the largest, then the largest
@@ -950,6 +1029,14 @@ extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
             if (n37 > 0) p->count(SPGEMM_K_ARRANGE);
         }
         p->time_end();
+        if (p->dense_n > 0) {
+            // the dense-slice rows write their values straight into C
+            p->time_begin(SPGEMM_K_MERGE);
+            SPG_TRY(launch_dense_fill(p->A, p->B, p->items, p->dense_args(), p->C.row_ptr, p->C.col_idx, p->C.val,
+                                      p->d_err, p->st));
+            p->time_end();
+            p->count(SPGEMM_K_MERGE);
+        }
         p->C.nrows = m;
         p->C.ncols = p->B.ncols;
         p->C.nnz = nnzC;
@@ -999,6 +1086,8 @@ extern "C" spgemm_status spgemm_plan_stats(spgemm_plan *p, spgemm_stats *out) {
         out->rows_fallback += ws.rows_fallback;
         out->bytes_ctilde += ws.bytes_ctilde;
         out->held_bytes += ws.held_bytes;
+        out->rows_dense += ws.rows_dense;
+        out->dense_slices = std::max(out->dense_slices, ws.dense_slices);
         for (int k = 0; k < SPGEMM_K_COUNT; ++k) {
             out->launches[k] += ws.launches[k];
             out->kernel_ms[k] += ws.kernel_ms[k];
@@ -1270,7 +1359,7 @@ static spgemm_status prepare_replay(spgemm_plan *p) {
     // rows finished with a level-1 sequence can be longer than any shared-memory slice
     if (p->stats.rows_level1 > 0) return SPGEMM_ERR_INVALID_ARG;
     {
-        const int64_t nleaves = p->n_items - p->stats.rows_split;
+        const int64_t nleaves = p->n_items - p->stats.rows_split - p->dense_n;
         int32_t *scratch = nullptr, *ccap = nullptr;
         const int caps[NUM_REPLAY_CLASSES] = {1024, 4096, std::max(4096, p->capmax)};
         for (int g = 0; g < NUM_REPLAY_CLASSES; ++g) p->leaf_cap[g] = caps[g];
@@ -1350,6 +1439,9 @@ extern "C" spgemm_status spgemm_numeric_replay(spgemm_plan *p) {
                                       p->C.col_idx, p->C.val, p->d_err, p->st));
             off += p->leaf_count[g];
         }
+        if (p->dense_n > 0)
+            SPG_TRY(launch_dense_fill(p->A, p->B, p->items, p->dense_args(), p->C.row_ptr, p->C.col_idx, p->C.val,
+                                      p->d_err, p->st));
     }
     return SPGEMM_OK;
 fail:

@@ -116,7 +116,8 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
               record_timing: bool = False, merge_batch: int = 0, smem_cap_max: int = 0,
               heap_block: int = 0, long_rows: str = "split", predictor=None,
               predictor_margin: float = 1.0, wave_mproducts: int = 0, heap_max_u: int = 0,
-              merge_wide_above: int = 0, merge_kernel: str = "auto", merge_miss: int = 0) -> _lib.Opts:
+              merge_wide_above: int = 0, merge_kernel: str = "auto", merge_miss: int = 0,
+              dense_min_u: int = 0, dense_span: int = 0) -> _lib.Opts:
     L = _lib.load()
     o = _lib.Opts()
     _lib.check(L.spgemm_opts_init(ctypes.byref(o)), "spgemm_opts_init")
@@ -133,6 +134,8 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
     o.merge_wide_above = int(merge_wide_above)
     o.merge_kernel = {"auto": 0, "merge_path": 1, "bitmap": 2}[merge_kernel]
     o.merge_miss = int(merge_miss)
+    o.dense_min_u = int(dense_min_u)
+    o.dense_span = int(dense_span)
     # a Predictor object (whose device weights the caller keeps alive) or a raw handle
     o.predictor = getattr(predictor, "handle", predictor)
     o.predictor_margin = float(predictor_margin)
@@ -183,6 +186,7 @@ class Plan:
             "merge_rounds": s.merge_rounds, "rows_relaunched": s.rows_relaunched, "rows_level1": s.rows_level1,
             "rows_split": s.rows_split,
             "rows_fallback": s.rows_fallback, "bytes_ctilde": s.bytes_ctilde, "peak_bytes": s.peak_bytes, "held_bytes": s.held_bytes,
+            "rows_dense": s.rows_dense, "dense_slices": s.dense_slices,
             "launches": dict(zip(_lib.KERNELS, list(s.launches))),
             "kernel_ms": dict(zip(_lib.KERNELS, [float(x) for x in s.kernel_ms])),
         }

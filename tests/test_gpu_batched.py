@@ -69,7 +69,7 @@ def test_replay_recomputes_values(spg, oracle_mod, policy):
     if policy == "learned":
         keep = Predictor.load()
         opts = keep.opts()
-    plan = spg.Plan(Ad, Ad, smem_cap_max=2048, **opts)   # small capacity: many column splits
+    plan = spg.Plan(Ad, Ad, smem_cap_max=2048, dense_min_u=-1, **opts)   # small capacity: many column splits
     C = plan.numeric()
     torch.cuda.synchronize()
     assert plan.stats()["rows_split"] > 0

@@ -66,7 +66,7 @@ def test_stage1_stage2_bit_exact(spg, oracle_mod, name, mk):
     A, B = mk()
     B = A if B is None else B
     for policy in ("hybrid", "upper_bound"):
-        plan, _ = run(spg, A, B, alloc_policy=policy)
+        plan, _ = run(spg, A, B, alloc_policy=policy, dense_min_u=-1)  # Algorithm 3's sizes
         arr = plan.arrays()
         u = oracle_mod.upper_bound(A, B)
         assert np.array_equal(arr["u"], u), name
@@ -95,7 +95,7 @@ def test_progressive_split_and_level1_paths(spg, oracle_mod, initial_cap, smem_c
     smem_cap_max, through column splitting or the level-1 sequence."""
     A = gen.rmat(12, 16, seed=7)
     plan, C = run(spg, A, A, initial_cap=initial_cap, smem_cap_max=smem_cap_max, merge_batch=batch,
-                  long_rows=long_rows)
+                  long_rows=long_rows, dense_min_u=-1)
     check(oracle_mod, A, A, C, label=f"cap{initial_cap}/{smem_cap_max}/{batch}/{long_rows}")
     st = plan.stats()
     assert st["merge_rounds"] >= 2 and st["rows_relaunched"] > 0
@@ -222,14 +222,20 @@ def test_repeat_is_structurally_identical(spg, oracle_mod):
     assert np.all(np.abs(v1 - v2) <= 2 * REL_TOL * ref.den)
 
 
-def test_config2_rmat16_full(spg, oracle_mod):
-    """R-MAT 2^16 rows, 16 samples/row, A*A: every bin group, progressive rounds, level-1."""
+@pytest.mark.parametrize("dense", [True, False])
+def test_config2_rmat16_full(spg, oracle_mod, dense):
+    """R-MAT 2^16 rows, 16 samples/row, A*A: every bin group; with the dense-slice rows, or
+    with every bin-37 row through the progressive rounds and column splits."""
     A = gen.rmat(16, 16, seed=1)
-    plan, C = run(spg, A, A, rowptr_dtype=torch.int32, record_timing=True)
-    check(oracle_mod, A, A, C, label="cfg2")
+    plan, C = run(spg, A, A, rowptr_dtype=torch.int32, record_timing=True, dense_min_u=0 if dense else -1)
+    check(oracle_mod, A, A, C, label=f"cfg2 dense={dense}")
     st = plan.stats()
-    assert st["merge_rounds"] >= 3 and st["rows_split"] > 0
+    if dense:
+        assert st["rows_dense"] > 0 and st["dense_slices"] >= 3 and st["merge_rounds"] >= 1
+    else:
+        assert st["merge_rounds"] >= 3 and st["rows_split"] > 0 and st["rows_dense"] == 0
     assert all(st["bin_count"][b] > 0 for b in (0, 1, 2, 33, 34, 35, 36, 37))
+    plan.check()
 
 
 def test_config3_galerkin_closed_form(spg, oracle_mod):
@@ -311,7 +317,7 @@ def test_merge_cta_width(spg, oracle_mod, wide_above, smem_cap_max, policy):
     A = gen.rmat(13, 16, seed=31)
     keep = Predictor.load() if policy == "learned" else None
     opts = keep.opts() if keep else {"alloc_policy": policy}
-    plan, C = run(spg, A, A, merge_wide_above=wide_above, smem_cap_max=smem_cap_max, **opts)
+    plan, C = run(spg, A, A, merge_wide_above=wide_above, smem_cap_max=smem_cap_max, dense_min_u=-1, **opts)
     check(oracle_mod, A, A, C, label=f"wide_above={wide_above}/{smem_cap_max}/{policy}")
     assert plan.stats()["bin_count"][37] > 0
 
@@ -328,7 +334,7 @@ def test_merge_kernel_forms(spg, oracle_mod, kernel, policy, initial_cap, smem_c
     keep = Predictor.load() if policy == "learned" else None
     opts = keep.opts() if keep else {"alloc_policy": policy}
     plan, C = run(spg, A, A, merge_kernel=kernel, initial_cap=initial_cap, smem_cap_max=smem_cap_max,
-                  merge_batch=batch, merge_miss=miss, **opts)
+                  merge_batch=batch, merge_miss=miss, dense_min_u=-1, **opts)
     check(oracle_mod, A, A, C, label=f"{kernel}/{policy}/{initial_cap}/{smem_cap_max}/{miss}")
     st = plan.stats()
     assert st["bin_count"][37] > 0
@@ -342,7 +348,8 @@ def test_bitmap_kernel_rectangular_and_split_children(spg, oracle_mod):
     whose origin is not 0."""
     A = gen.rmat(12, 24, seed=43)
     B = gen.erdos_renyi(4096, 12, seed=44, ncols=70000)
-    plan, C = run(spg, A, B, merge_kernel="bitmap", smem_cap_max=1024, merge_batch=512, merge_miss=512)
+    plan, C = run(spg, A, B, merge_kernel="bitmap", smem_cap_max=1024, merge_batch=512, merge_miss=512,
+                  dense_min_u=-1)
     check(oracle_mod, A, B, C, label="bitmap rectangular")
     assert plan.stats()["rows_split"] > 0
 
@@ -356,7 +363,7 @@ def test_bitmap_kernel_wide_b_two_level(spg, oracle_mod, policy, smem_cap_max):
     B = gen.erdos_renyi(4096, 24, seed=52, ncols=300000)
     keep = Predictor.load() if policy == "learned" else None
     opts = keep.opts() if keep else {"alloc_policy": policy}
-    plan, C = run(spg, A, B, smem_cap_max=smem_cap_max, merge_kernel="bitmap", **opts)
+    plan, C = run(spg, A, B, smem_cap_max=smem_cap_max, merge_kernel="bitmap", dense_min_u=-1, **opts)
     check(oracle_mod, A, B, C, label=f"wide B/{policy}/{smem_cap_max}")
     st = plan.stats()
     assert st["bin_count"][37] > 0
@@ -371,6 +378,6 @@ def test_bitmap_kernel_wide_b_two_level(spg, oracle_mod, policy, smem_cap_max):
 def test_bitmap_kernel_two_level_rmat(spg, oracle_mod):
     """Two-level index on an R-MAT product with 2^18 columns (hub rows, splits)."""
     A = gen.rmat(18, 4, seed=53)
-    plan, C = run(spg, A, A, merge_kernel="bitmap")
+    plan, C = run(spg, A, A, merge_kernel="bitmap", dense_min_u=-1)
     check(oracle_mod, A, A, C, label="two-level R-MAT 2^18")
     assert plan.stats()["bin_count"][37] > 0

@@ -95,7 +95,7 @@ def test_learned_policy_is_exact(spg, oracle_mod, margin):
     th[w3:w3 + 17 * 32] = 0.0         # W3 = 0: the regression head outputs b3[16] for every row
     th[mlp.N_PARAMS - 1] = 9.0        # b3[16] = 9: 2^9 - 1 = 511 entries before the margin
     pred = Predictor(th, margin=margin)
-    plan = spg.Plan(Ad, Ad, **pred.opts())
+    plan = spg.Plan(Ad, Ad, dense_min_u=-1, **pred.opts())  # every bin-37 row predicted
     C = plan.numeric()
     torch.cuda.synchronize()
     ref = oracle_mod.spgemm(A, A)
@@ -154,7 +154,7 @@ def test_learned_fallback_levels_and_long_rows(spg, oracle_mod, margin, long_row
     th[w3:w3 + 17 * 32] = 0.0
     th[mlp.N_PARAMS - 1] = 9.0        # 511 entries before the margin
     pred = Predictor(th, margin=margin)
-    plan = spg.Plan(Ad, Ad, smem_cap_max=1024, long_rows=long_rows, **pred.opts())
+    plan = spg.Plan(Ad, Ad, smem_cap_max=1024, long_rows=long_rows, dense_min_u=-1, **pred.opts())
     C = plan.numeric()
     torch.cuda.synchronize()
     ref = oracle_mod.spgemm(A, A)
