@@ -537,6 +537,7 @@ def roofline(args, pairs, m):
     dom_ms = kms.get(dom, 0.0)
     dom_launches = sum(s["launches"].get(dom, 0) for s in m["st_all"])
     bytes_dom = 0
+    flops_dom = 0
     for (A, B), arr in zip(pairs, m["arrays"]):
         if B is None:
             continue
@@ -552,7 +553,20 @@ def roofline(args, pairs, m):
             sel = {"merge": bins == 37, "esc": (bins > hmax) & (bins <= 36), "heap": (bins >= 2) & (bins <= hmax)}.get(
                 dom, np.ones(u.shape[0], dtype=bool))
             bytes_dom += algorithmic_bytes(A, B, u, np.nonzero(sel)[0], rn)
+            flops_dom += 2 * int(u[sel].astype(np.int64).sum())  # a multiply and an add per product
     achieved = bytes_dom / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
+    # FP64 ceiling: 2 FP64 FMA per clock per SM (the 1.25 TFLOP/s nominal rate at 2,070 MHz), 152 SMs,
+    # at the SM clock sampled during the timed steps
+    sm_mhz = (m.get("clocks") or {}).get("sm_mhz") or 2070.0
+    fp64_peak = 2 * 2 * 152 * sm_mhz * 1e6 / 1e9
+    fp64 = None
+    if flops_dom and dom_ms > 0:
+        ach = flops_dom / (dom_ms * 1e-3) / 1e9
+        fp64 = {"achieved": ach, "peak": fp64_peak, "unit": "GFLOP/s", "frac": ach / fp64_peak,
+                "flops_per_step": flops_dom, "arithmetic_intensity": flops_dom / max(1, bytes_dom),
+                "ridge": fp64_peak / hbm_peak,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 2 flop x 152 SMs x sampled SM clock "
+                               "(a DFMA micro-benchmark measured 1.60/clk/SM at an assumed 2,070 MHz)"}
     traffic = None
     tj = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tj):
@@ -576,8 +590,9 @@ def roofline(args, pairs, m):
             "compulsory_bytes_per_step": comp, "compulsory_gbs": comp_gbs, "compulsory_frac": comp_gbs / hbm_peak,
             "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic, "peak_source": peak_src,
             "algorithmic_bytes_per_step": bytes_dom, "kernel_ms_per_step": dom_ms,
-            "launches_per_step": dom_launches,
-            "note": "achieved = algorithmic bytes of the kernel class per step / its summed CUDA-event time per step"}
+            "launches_per_step": dom_launches, "fp64": fp64,
+            "note": "achieved = algorithmic bytes of the kernel class per step / its summed CUDA-event time per step; "
+                    "the class's arithmetic intensity is below the FP64/HBM ridge, so HBM is its roofline bound"}
 
 
 def run_ours(args, rank, world, device):

@@ -102,7 +102,7 @@ cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *
 }
 
 // ---- the product expansion shared by the count and fill kernels ----
-// Walks the A entries of `row` in windows of NT.  For each window, the part of
+// Walks the A entries of `row` in windows of WIN (<= NT).  For each window, the part of
 // every selected B row inside slice s is cut into chunks of DENSE_CH consecutive
 // entries; warp w takes the w-th contiguous range of the window's chunks, and its
 // lanes read a chunk's entries 32 at a time (coalesced, one B row per access, so
@@ -112,15 +112,15 @@ cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *
 constexpr int DENSE_CH = 256;
 constexpr int DENSE_UN = 4;
 
-template <int NT, bool VALS, typename F>
+template <int NT, int WIN, bool VALS, typename F>
 SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int row, int s, int64_t *wbs,
                           int32_t *wlen, int64_t *cscan, double *wa, int64_t *scan64, F f) {
     constexpr int NW = NT / 32;
     const int lane = lane_id(), wid = warp_id();
     const int64_t a0 = A.rp[row], a1 = A.rp[row + 1];
     const int K1 = D.K + 1;
-    for (int64_t e = a0; e < a1; e += NT) {
-        const int nW = (int)min((int64_t)NT, a1 - e);
+    for (int64_t e = a0; e < a1; e += WIN) {
+        const int nW = (int)min((int64_t)WIN, a1 - e);
         int64_t nch = 0;
         if (threadIdx.x < nW) {
             const int32_t k = A.col[e + threadIdx.x];
@@ -195,7 +195,7 @@ k_dense_count(DevCSR A, DevCSR B, MergeItems it, DenseArgs D, int64_t *err) {
     __syncthreads();
     bool bad = false;
     volatile uint8_t *fl = dc_flag;
-    dense_expand<NT, false>(A, B, D, row, s, wbs, wlen, cscan, nullptr, scan64,
+    dense_expand<NT, NT, false>(A, B, D, row, s, wbs, wlen, cscan, nullptr, scan64,
                             [&](const int64_t *p, const bool *ok, int) {
         int32_t c[DENSE_UN];
 #pragma unroll
@@ -243,6 +243,16 @@ __global__ void k_dense_rows(MergeItems it, DenseArgs D) {
 // ---- pass 2: the values, written into C ----
 // Shared memory: W fp64 sums, W flag bytes, then the flags as a bitmap and its
 // rank directory for the write-out.
+//
+// The columns of one B row are distinct, so while the whole CTA works on a single
+// B-row part no two threads add into the same sum and plain adds suffice; parts of
+// at least DENSE_LONG products are done that way, one after another (a barrier
+// between two parts), each product one fused multiply-add.  The shorter parts are
+// shared out to the warps in chunks and added with shared fp64 atomics, before the
+// long ones.  (A compare-and-swap loop around a fused multiply-add, one FP64
+// instruction per product instead of two, measured twice as slow as atomicAdd.)
+constexpr int DENSE_FILL_WIN = 512;  // A entries per window
+constexpr int DENSE_LONG = 512;
 
 __host__ __device__ inline int dense_nw4(int W) { return ((W + 31) / 32 + 4) & ~3; }
 
@@ -250,10 +260,12 @@ template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_dense_fill(DevCSR A, DevCSR B, MergeItems it, DenseArgs D, const int64_t *c_rp, int32_t *c_col, double *c_val,
              int64_t *err) {
+    constexpr int WIN = DENSE_FILL_WIN;
+    constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char df_smem[];
-    __shared__ int64_t wbs[NT], cscan[NT], scan64[NT / 32 + 1];
-    __shared__ double wa[NT];
-    __shared__ int32_t wlen[NT], scan32[NT / 32 + 1];
+    __shared__ int64_t wbs[WIN], cscan[WIN], scan64[NT / 32 + 1];
+    __shared__ double wa[WIN];
+    __shared__ int32_t wlen[WIN], lidx[WIN], scan32[NT / 32 + 1];
     const int64_t b = blockIdx.x;
     const int expected = D.cnt[b];
     if (expected == 0) return;
@@ -277,29 +289,155 @@ k_dense_fill(DevCSR A, DevCSR B, MergeItems it, DenseArgs D, const int64_t *c_rp
     __syncthreads();
     bool bad = false;
     volatile uint8_t *fl = flag;
-    dense_expand<NT, true>(A, B, D, row, s, wbs, wlen, cscan, wa, scan64,
-                           [&](const int64_t *p, const bool *ok, int t) {
-        int32_t c[DENSE_UN];
-        double v[DENSE_UN];
-#pragma unroll
-        for (int u = 0; u < DENSE_UN; ++u)
-            if (ok[u]) c[u] = __ldg(B.col + p[u]);
-#pragma unroll
-        for (int u = 0; u < DENSE_UN; ++u)
-            if (ok[u]) v[u] = __ldg(B.val + p[u]);
-        const double a = wa[t];
-#pragma unroll
-        for (int u = 0; u < DENSE_UN; ++u) {
-            if (!ok[u]) continue;
-            const int x = (int)(c[u] - lo);
-            if ((unsigned)x >= (unsigned)span) {  // cannot happen: the slice boundaries select the columns
-                bad = true;
-                continue;
+    const int lane = lane_id(), wid = warp_id();
+    const int64_t a0 = A.rp[row], a1 = A.rp[row + 1];
+    const int K1 = D.K + 1;
+    for (int64_t e = a0; e < a1; e += WIN) {
+        const int nW = (int)min((int64_t)WIN, a1 - e);
+        // chunks of the short parts (low 40 bits) and the count of long parts (above)
+        int64_t packed = 0;
+        if (threadIdx.x < nW) {
+            const int32_t k = A.col[e + threadIdx.x];
+            const int64_t rs = B.rp[k];
+            int64_t bs, be;
+            if (D.K > 1) {
+                const int32_t *bk = D.bnd + (int64_t)k * K1 + s;
+                bs = rs + bk[0];
+                be = rs + bk[1];
+            } else {
+                bs = rs;
+                be = B.rp[k + 1];
             }
-            atomicAdd(&V[x], a * v[u]);
-            fl[x] = 1;
+            const int64_t len = be - bs;
+            wbs[threadIdx.x] = bs;
+            wlen[threadIdx.x] = (int32_t)len;  // a B row has at most ncols < 2^31 entries
+            wa[threadIdx.x] = A.val[e + threadIdx.x];
+            packed = len >= DENSE_LONG ? (int64_t(1) << 40) : (len + DENSE_CH - 1) / DENSE_CH;
         }
-    });
+        int64_t ptot;
+        const int64_t ex = block_exclusive_scan<NT, int64_t, false>(packed, scan64, ptot);
+        if (threadIdx.x < nW) {
+            cscan[threadIdx.x] = ex & ((int64_t(1) << 40) - 1);
+            if (packed >> 40) lidx[ex >> 40] = threadIdx.x;
+        }
+        const int64_t tc = ptot & ((int64_t(1) << 40) - 1);
+        const int nlong = (int)(ptot >> 40);
+        __syncthreads();
+        // short parts: the warps' contiguous chunk ranges, shared fp64 atomics
+        {
+            const int64_t c0 = tc * wid / NW, c1 = tc * (wid + 1) / NW;
+            int t = 0;
+            if (c0 < c1) {
+                int lo_ = 0, hi = nW - 1;
+                while (lo_ < hi) {
+                    const int mid = (lo_ + hi + 1) >> 1;
+                    if (cscan[mid] <= c0) lo_ = mid; else hi = mid - 1;
+                }
+                t = lo_;
+            }
+            for (int64_t c = c0; c < c1; ++c) {
+                // skips the entries without chunks (long parts have none)
+                while (t + 1 < nW && cscan[t + 1] <= c) ++t;
+                const int64_t off = (c - cscan[t]) * DENSE_CH;
+                const int64_t p0 = wbs[t] + off;
+                const int n = (int)min((int64_t)DENSE_CH, (int64_t)wlen[t] - off);
+                const double a = wa[t];
+                for (int i = lane; i < n; i += 32 * DENSE_UN) {
+                    int32_t cc[DENSE_UN];
+                    double v[DENSE_UN];
+#pragma unroll
+                    for (int u = 0; u < DENSE_UN; ++u)
+                        if (i + 32 * u < n) cc[u] = __ldg(B.col + p0 + i + 32 * u);
+#pragma unroll
+                    for (int u = 0; u < DENSE_UN; ++u)
+                        if (i + 32 * u < n) v[u] = __ldg(B.val + p0 + i + 32 * u);
+#pragma unroll
+                    for (int u = 0; u < DENSE_UN; ++u) {
+                        if (i + 32 * u >= n) continue;
+                        const int x = (int)(cc[u] - lo);
+                        if ((unsigned)x >= (unsigned)span) {  // cannot happen: the slice boundaries select the columns
+                            bad = true;
+                            continue;
+                        }
+                        atomicAdd(&V[x], a * v[u]);
+                        fl[x] = 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // long parts: one at a time, the whole CTA, plain adds.  A round is NT * DENSE_UN
+        // consecutive entries of one part; the loads of the next two rounds are in flight
+        // while a round is added (they touch no shared memory, so they may cross the
+        // barrier between two parts)
+        if (nlong > 0) {
+            constexpr int RND = NT * DENSE_UN;
+            // rounds r0 (being added), r1 and r2 (loading); part index nlong: no round
+            int32_t c0[DENSE_UN], c1[DENSE_UN], c2[DENSE_UN];
+            double v0[DENSE_UN], v1[DENSE_UN], v2[DENSE_UN];
+            int j0 = 0, o0 = 0, j1, o1, j2, o2;
+            auto load = [&](int32_t (&cc)[DENSE_UN], double (&vv)[DENSE_UN], int j, int i0) {
+                if (j >= nlong) return;
+                const int t = lidx[j];
+                const int64_t p0 = wbs[t] + i0;
+                const int n = wlen[t] - i0;
+#pragma unroll
+                for (int u = 0; u < DENSE_UN; ++u)
+                    if ((int)threadIdx.x + NT * u < n) cc[u] = __ldg(B.col + p0 + threadIdx.x + NT * u);
+#pragma unroll
+                for (int u = 0; u < DENSE_UN; ++u)
+                    if ((int)threadIdx.x + NT * u < n) vv[u] = __ldg(B.val + p0 + threadIdx.x + NT * u);
+            };
+            auto after = [&](int j, int i0, int &nj, int &ni) {
+                if (j >= nlong) {
+                    nj = nlong;
+                    ni = 0;
+                } else if (i0 + RND < wlen[lidx[j]]) {
+                    nj = j;
+                    ni = i0 + RND;
+                } else {
+                    nj = j + 1;
+                    ni = 0;
+                }
+            };
+            load(c0, v0, j0, o0);
+            after(j0, o0, j1, o1);
+            load(c1, v1, j1, o1);
+            while (j0 < nlong) {
+                after(j1, o1, j2, o2);
+                load(c2, v2, j2, o2);
+                {
+                    const int t = lidx[j0];
+                    const int n = wlen[t] - o0;
+                    const double a = wa[t];
+#pragma unroll
+                    for (int u = 0; u < DENSE_UN; ++u) {
+                        if ((int)threadIdx.x + NT * u >= n) continue;
+                        const int x = (int)(c0[u] - lo);
+                        if ((unsigned)x >= (unsigned)span) {
+                            bad = true;
+                            continue;
+                        }
+                        V[x] += a * v0[u];
+                        fl[x] = 1;
+                    }
+                }
+                if (j1 != j0) __syncthreads();  // the next part may add into the same columns
+#pragma unroll
+                for (int u = 0; u < DENSE_UN; ++u) {
+                    c0[u] = c1[u];
+                    v0[u] = v1[u];
+                    c1[u] = c2[u];
+                    v1[u] = v2[u];
+                }
+                j0 = j1;
+                o0 = o1;
+                j1 = j2;
+                o1 = o2;
+            }
+        }
+        __syncthreads();  // the window's tables are reused
+    }
     // flags -> bitmap (32 columns per word), then its rank directory
     for (int w = threadIdx.x; w < nwords; w += NT) {
         const uint4 *f4 = reinterpret_cast<const uint4 *>(flag + 32 * w);
@@ -335,7 +473,10 @@ k_dense_fill(DevCSR A, DevCSR B, MergeItems it, DenseArgs D, const int64_t *c_rp
 }
 
 constexpr int DENSE_COUNT_NT = 256;
-constexpr int DENSE_FILL_NT = 512;
+#ifndef DENSE_FILL_THREADS
+#define DENSE_FILL_THREADS 512
+#endif
+constexpr int DENSE_FILL_NT = DENSE_FILL_THREADS;
 
 int dense_fill_smem_bytes(int W) {
     return (int)((sizeof(double) + 1) * (size_t)W + 2 * sizeof(int32_t) * (size_t)dense_nw4(W));
@@ -349,7 +490,7 @@ int dense_fill_max_dynamic(int per_sm) {
 }
 
 int dense_fill_static_smem() {
-    return (int)(DENSE_FILL_NT * (2 * sizeof(int64_t) + sizeof(double) + sizeof(int32_t)) +
+    return (int)(DENSE_FILL_WIN * (2 * sizeof(int64_t) + sizeof(double) + 2 * sizeof(int32_t)) +
                  (DENSE_FILL_NT / 32 + 1) * 12 + 64);
 }
 
