@@ -96,7 +96,7 @@ def src_digest(files):
 
 KERNEL_SOURCES = {
     "merge": ["paper_1504_05022_gb300/csrc/merge.cu", "paper_1504_05022_gb300/csrc/merge_bm.cu",
-              "paper_1504_05022_gb300/csrc/common.cuh"],
+              "paper_1504_05022_gb300/csrc/dense.cu", "paper_1504_05022_gb300/csrc/common.cuh"],
     "arrange": ["paper_1504_05022_gb300/csrc/arrange.cu", "paper_1504_05022_gb300/csrc/scan.cuh"],
     "esc": ["paper_1504_05022_gb300/csrc/esc.cu"],
     "heap": ["paper_1504_05022_gb300/csrc/heap.cu"],
