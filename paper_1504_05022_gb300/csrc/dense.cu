@@ -77,18 +77,22 @@ __global__ void k_dense_select_starts(const int32_t *count, int32_t *start, int3
     }
 }
 
-__global__ void k_dense_select_scatter(const BinSummary *summary, const int32_t *cls_of, const int32_t *start,
-                                       int32_t *cursor, int32_t *order) {
+__global__ void k_dense_select_scatter(const int32_t *bin_rows, int64_t m, const BinSummary *summary,
+                                       const int32_t *cls_of, const int32_t *start, int32_t *cursor, int32_t *order,
+                                       int32_t *rows) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= summary->bin_count[BIN_MERGE]) return;
+    const int64_t n37 = summary->bin_count[BIN_MERGE];
+    if (j >= n37) return;
     const int g = cls_of[j];
-    order[start[g] + atomicAdd(&cursor[g], 1)] = (int32_t)j;
+    const int32_t pos = start[g] + atomicAdd(&cursor[g], 1);
+    order[pos] = (int32_t)j;
+    if (g < DENSE_BUCKETS) rows[pos] = bin_rows[m - n37 + j];
 }
 
 int64_t dense_select_scratch(int64_t m) { return 3 * (DENSE_BUCKETS + 1) + m; }
 
 cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *summary, const int64_t *u,
-                                int64_t dmin, int32_t *scratch, int32_t *order, cudaStream_t st) {
+                                int64_t dmin, int32_t *scratch, int32_t *order, int32_t *rows, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     int32_t *count = scratch, *start = count + DENSE_BUCKETS + 1, *cursor = start + DENSE_BUCKETS + 1,
             *cls_of = cursor + DENSE_BUCKETS + 1;
@@ -97,7 +101,7 @@ cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *
     const unsigned g = (unsigned)((m + 255) / 256);
     k_dense_select_count<<<g, 256, 0, st>>>(bin_rows, m, summary, u, dmin, cls_of, count);
     k_dense_select_starts<<<1, 32, 0, st>>>(count, start, cursor, summary);
-    k_dense_select_scatter<<<g, 256, 0, st>>>(summary, cls_of, start, cursor, order);
+    k_dense_select_scatter<<<g, 256, 0, st>>>(bin_rows, m, summary, cls_of, start, cursor, order, rows);
     return cudaGetLastError();
 }
 
@@ -179,14 +183,14 @@ SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, 
 
 template <int NT>
 __global__ void __launch_bounds__(NT)
-k_dense_count(DevCSR A, DevCSR B, MergeItems it, DenseArgs D, int64_t *err) {
+k_dense_count(DevCSR A, DevCSR B, DenseArgs D, int64_t *err) {
     extern __shared__ __align__(16) uint8_t dc_flag[];
     __shared__ int64_t wbs[NT], cscan[NT], scan64[NT / 32 + 1];
     __shared__ int32_t wlen[NT], scan32[NT / 32 + 1];
     const int64_t b = blockIdx.x;
     const int64_t d = b / D.K;
     const int s = (int)(b - d * D.K);
-    const int row = it.row[D.items[d]];
+    const int row = D.rows[d];
     const int64_t lo = (int64_t)s * D.W;
     const int span = (int)min((int64_t)D.W, B.ncols - lo);
     const int nq = (span + 15) >> 4;  // 16-byte groups of flags
@@ -252,14 +256,16 @@ __global__ void k_dense_rows(MergeItems it, DenseArgs D) {
 // long ones.  (A compare-and-swap loop around a fused multiply-add, one FP64
 // instruction per product instead of two, measured twice as slow as atomicAdd.)
 constexpr int DENSE_FILL_WIN = 512;  // A entries per window
-constexpr int DENSE_LONG = 512;
+#ifndef DENSE_LONG_MIN
+#define DENSE_LONG_MIN 512
+#endif
+constexpr int DENSE_LONG = DENSE_LONG_MIN;
 
 __host__ __device__ inline int dense_nw4(int W) { return ((W + 31) / 32 + 4) & ~3; }
 
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
-k_dense_fill(DevCSR A, DevCSR B, MergeItems it, DenseArgs D, const int64_t *c_rp, int32_t *c_col, double *c_val,
-             int64_t *err) {
+k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_col, double *c_val, int64_t *err) {
     constexpr int WIN = DENSE_FILL_WIN;
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char df_smem[];
@@ -271,7 +277,7 @@ k_dense_fill(DevCSR A, DevCSR B, MergeItems it, DenseArgs D, const int64_t *c_rp
     if (expected == 0) return;
     const int64_t d = b / D.K;
     const int s = (int)(b - d * D.K);
-    const int row = it.row[D.items[d]];
+    const int row = D.rows[d];
     const int64_t lo = (int64_t)s * D.W;
     const int span = (int)min((int64_t)D.W, B.ncols - lo);
     const int nwords = (span + 31) >> 5;
@@ -494,8 +500,7 @@ int dense_fill_static_smem() {
                  (DENSE_FILL_NT / 32 + 1) * 12 + 64);
 }
 
-cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const MergeItems &it, const DenseArgs &D,
-                               int64_t *err, cudaStream_t st) {
+cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t *err, cudaStream_t st) {
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
@@ -503,15 +508,18 @@ cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const MergeItem
     auto kern = k_dense_count<DENSE_COUNT_NT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)nb, DENSE_COUNT_NT, smem, st>>>(A, B, it, D, err);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nb, DENSE_COUNT_NT, smem, st>>>(A, B, D, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_rows(const MergeItems &it, const DenseArgs &D, cudaStream_t st) {
+    if (D.n <= 0) return cudaSuccess;
     k_dense_rows<<<(unsigned)((D.n + 127) / 128), 128, 0, st>>>(it, D);
     return cudaGetLastError();
 }
 
-cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const MergeItems &it, const DenseArgs &D,
-                              const int64_t *c_rp, int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st) {
+cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs &D, const int64_t *c_rp,
+                              int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st) {
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
@@ -522,7 +530,7 @@ cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const MergeItems
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)nb, DENSE_FILL_NT, smem, st>>>(A, B, it, D, c_rp, c_col, c_val, err);
+    kern<<<(unsigned)nb, DENSE_FILL_NT, smem, st>>>(A, B, D, c_rp, c_col, c_val, err);
     return cudaGetLastError();
 }
 

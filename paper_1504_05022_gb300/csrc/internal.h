@@ -162,6 +162,7 @@ constexpr int32_t ITEM_DENSE = -2;  // MergeItems.child of a row computed by the
 constexpr int DENSE_MAX_SLICES = 16;
 struct DenseArgs {
     const int32_t *items;  // dense items (indices into MergeItems), larger rows first
+    const int32_t *rows;   // their rows of A
     int64_t n;             // number of dense items
     int K;                 // column slices of B
     int W;                 // slice width (a multiple of 32); slice s holds columns [s W, (s + 1) W)
@@ -172,15 +173,17 @@ struct DenseArgs {
 cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cudaStream_t st);
 int64_t dense_select_scratch(int64_t m);
 // order[0..nd) = items of the bin-37 rows with u >= dmin (larger first), order[nd..n37) = the rest;
-// nd goes to summary->dense_count
+// rows[0..nd) = the rows of the dense items; nd goes to summary->dense_count
 cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *summary, const int64_t *u,
-                                int64_t dmin, int32_t *scratch, int32_t *order, cudaStream_t st);
-// counts the columns of every (row, slice), then sets the items' lengths and slice offsets
-cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const MergeItems &it, const DenseArgs &D,
-                               int64_t *err, cudaStream_t st);
+                                int64_t dmin, int32_t *scratch, int32_t *order, int32_t *rows, cudaStream_t st);
+// counts the columns of every (row, slice) into D.cnt (reads no work-item table, so it
+// may run beside the merge launches)
+cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t *err, cudaStream_t st);
+// slice offsets inside the rows, and the dense items' lengths in the work-item table
+cudaError_t launch_dense_rows(const MergeItems &it, const DenseArgs &D, cudaStream_t st);
 // accumulates every (row, slice) and writes it into C at c_rp[row] + soff
-cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const MergeItems &it, const DenseArgs &D,
-                              const int64_t *c_rp, int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st);
+cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs &D, const int64_t *c_rp,
+                              int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st);
 int dense_fill_smem_bytes(int W);
 int dense_fill_static_smem();
 int dense_fill_max_dynamic(int per_sm);

@@ -73,7 +73,8 @@ void *get_pinned() {
 // Auxiliary streams per device (created once, kept for the process): the learned
 // launch classes of bin 37 run on them concurrently, so one class's tail of long
 // CTAs overlaps the next class instead of idling the SMs.
-constexpr int NUM_AUX_STREAMS = 4;
+constexpr int NUM_AUX_STREAMS = 5;
+constexpr int DENSE_AUX = NUM_AUX_STREAMS - 1;  // the dense-slice kernels; the others take the launch classes
 std::mutex g_aux_mu;
 std::vector<std::vector<cudaStream_t>> g_aux;
 
@@ -157,10 +158,11 @@ struct spgemm_plan {
     int64_t dense_min_u = INT64_MAX;
     int64_t dense_n = 0;                  // dense bin-37 rows
     int32_t *dense_order = nullptr;       // bin-37 items: the dense ones (larger first), then the rest
+    int32_t *dense_rows = nullptr;        // rows of the dense items
     int32_t *dense_bnd = nullptr;         // per B row, K + 1 slice boundaries (K > 1)
     int32_t *dense_cnt = nullptr, *dense_soff = nullptr;
     DenseArgs dense_args() const {
-        return DenseArgs{dense_order, dense_n, dense_K, dense_W, dense_bnd, dense_cnt, dense_soff};
+        return DenseArgs{dense_order, dense_rows, dense_n, dense_K, dense_W, dense_bnd, dense_cnt, dense_soff};
     }
     // batched plans: the pairs and the concatenation offsets
     int64_t npairs = 0;
@@ -237,6 +239,17 @@ struct spgemm_plan {
         cudaEventRecord(timers.back().b, st);
     }
     void count(int kind, int n = 1) { stats.launches[kind] += n; }
+    // two 8-byte device words with one synchronisation
+    cudaError_t d2h2(int64_t *dst, const int64_t *src0, const int64_t *src1) {
+        int64_t *pin = static_cast<int64_t *>(pinned);
+        cudaError_t e = cudaMemcpyAsync(pin, src0, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pin + 1, src1, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        dst[0] = pin[0];
+        dst[1] = pin[1];
+        return cudaSuccess;
+    }
     cudaError_t d2h(void *dst, const void *src, size_t bytes) {
         cudaError_t e = cudaMemcpyAsync(pinned, src, bytes, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return e;
@@ -552,8 +565,9 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             int32_t *scratch = nullptr;
             SPG_TRY(p->alloc_n(&scratch, dense_select_scratch(m), LIFE_SYMBOLIC));
             SPG_TRY(p->alloc_n(&p->dense_order, m));
+            SPG_TRY(p->alloc_n(&p->dense_rows, m));
             SPG_TRY(launch_dense_select(p->bin_rows, m, p->d_summary, p->u, p->dense_min_u, scratch, p->dense_order,
-                                        p->st));
+                                        p->dense_rows, p->st));
             p->count(SPGEMM_K_OTHER, 3);
         }
         SPG_TRY(p->d2h(&p->h_summary, p->d_summary, sizeof(BinSummary)));
@@ -840,19 +854,34 @@ spgemm_status run_bin37(spgemm_plan *p) {
     int32_t *ovf_count = nullptr;
     const int capmax = p->capmax;
     const bool learned = p->opts.alloc_policy == SPGEMM_ALLOC_LEARNED;
+    cudaEvent_t dense_done = nullptr;
     {
+        if (p->dense_n > 0) {
+            // dense-slice rows: their column counts now (on their own stream, beside the merge
+            // launches, unless every kernel is timed), their values once C exists
+            cudaStream_t ds = p->st;
+            if (!p->opts.record_timing) {
+                ds = aux_stream(p->device, DENSE_AUX);
+                if (ds == nullptr) return SPGEMM_ERR_CUDA;
+                cudaEvent_t go = nullptr;
+                SPG_TRY(cudaEventCreateWithFlags(&go, cudaEventDisableTiming));
+                cudaError_t e = cudaEventRecord(go, p->st);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, go, 0);
+                cudaEventDestroy(go);
+                SPG_TRY(e);
+                SPG_TRY(cudaEventCreateWithFlags(&dense_done, cudaEventDisableTiming));
+            }
+            p->time_begin(SPGEMM_K_MERGE);
+            SPG_TRY(launch_dense_count(p->A, p->B, p->dense_args(), p->d_err, ds));
+            p->time_end();
+            p->count(SPGEMM_K_MERGE);
+            if (dense_done) SPG_TRY(cudaEventRecord(dense_done, ds));
+        }
         SPG_TRY(reserve_items(p, n37));
         p->n_items = n37;
         SPG_TRY(p->alloc_n(&ovf_count, 1, LIFE_NUMERIC));
         SPG_TRY(launch_merge_init(rows37, n37, p->ctil_rp, p->ctil_col, p->ctil_val, p->items, p->st));
         p->count(SPGEMM_K_OTHER);
-        if (p->dense_n > 0) {
-            // dense-slice rows: their column counts now, their values once C exists
-            p->time_begin(SPGEMM_K_MERGE);
-            SPG_TRY(launch_dense_count(p->A, p->B, p->items, p->dense_args(), p->d_err, p->st));
-            p->time_end();
-            p->count(SPGEMM_K_MERGE, 2);
-        }
         if (!learned) {
             int cap;
             if (p->opts.alloc_policy == SPGEMM_ALLOC_UPPER_BOUND) cap = capmax;
@@ -902,7 +931,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 if (cnt == 0) continue;
                 cudaStream_t cs = p->st;
                 if (concurrent) {
-                    cs = aux_stream(p->device, nlaunched);
+                    cs = aux_stream(p->device, nlaunched % DENSE_AUX);
                     if (cs == nullptr) {
                         status = SPGEMM_ERR_CUDA;
                         goto fail;
@@ -947,10 +976,12 @@ spgemm_status run_bin37(spgemm_plan *p) {
             p->stats.rows_relaunched = fell;
             // levels below the largest capacity, in ascending order: each launch's
             // overflow lands on a higher level
+            bool stale = false;  // a level was launched since hc was read
             for (int k = 0; k + 1 < nlv; ++k) {
-                int32_t nk = 0;
-                SPG_TRY(p->d2h(&nk, counts + k, sizeof(int32_t)));
+                int32_t nk = hc[k];
+                if (stale) SPG_TRY(p->d2h(&nk, counts + k, sizeof(int32_t)));
                 if (nk == 0) continue;
+                stale = true;
                 const int tgt = level_of(std::min(2 * lv[k], capmax));
                 MergeLaunch L{};
                 L.wide_above = p->wide_above;
@@ -974,20 +1005,29 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 p->count(SPGEMM_K_MERGE);
                 p->stats.merge_rounds += 1;
             }
-            SPG_TRY(p->d2h(hc.data(), counts, sizeof(int32_t) * (nlv + 1)));
+            if (stale) SPG_TRY(p->d2h(hc.data(), counts, sizeof(int32_t) * (nlv + 1)));
             status = run_progressive(p, lists[nlv - 1], 0, hc[nlv - 1], capmax, false, ovf_count);
             if (status != SPGEMM_OK) goto fail;
             status = run_progressive(p, lists[SPLIT], 0, hc[SPLIT], capmax, true, ovf_count);
             if (status != SPGEMM_OK) goto fail;
         }
+        if (dense_done) {
+            SPG_TRY(cudaStreamWaitEvent(p->st, dense_done, 0));
+            cudaEventDestroy(dense_done);
+            dense_done = nullptr;
+        }
+        SPG_TRY(launch_dense_rows(p->items, p->dense_args(), p->st));
+        if (p->dense_n > 0) p->count(SPGEMM_K_MERGE);
+        // the error word is read with nnz(C), after the row scan
         SPG_TRY(launch_finalize37(n37, p->items, p->nnzc, p->d_err, p->st));
         p->count(SPGEMM_K_OTHER);
-        int64_t err = 0;
-        SPG_TRY(p->d2h(&err, p->d_err, sizeof(int64_t)));
-        if (err != 0) status = SPGEMM_ERR_INTERNAL;
     }
     return status;
 fail:
+    if (dense_done) {
+        cudaStreamWaitEvent(p->st, dense_done, 0);
+        cudaEventDestroy(dense_done);
+    }
     return status;
 }
 
@@ -1015,9 +1055,49 @@ extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
         p->time_end();
         p->count(SPGEMM_K_SCAN, 3);
         int64_t nnzC = 0;
-        SPG_TRY(p->d2h(&nnzC, p->C.row_ptr + m, sizeof(int64_t)));
+        {
+            // nnz(C) and the device error word of stage 3, with one synchronisation
+            int64_t both[2] = {0, 0};
+            SPG_TRY(p->d2h2(both, p->C.row_ptr + m, p->d_err));
+            nnzC = both[0];
+            if (both[1] != 0) {
+                status = SPGEMM_ERR_INTERNAL;
+                goto fail;
+            }
+        }
         SPG_TRY(p->alloc_n(&p->C.col_idx, nnzC));
         SPG_TRY(p->alloc_n(&p->C.val, nnzC));
+        cudaEvent_t fill_done = nullptr;
+        if (p->dense_n > 0) {
+            // the dense-slice rows write their values straight into C, beside the copy of
+            // the other rows (their own stream unless every kernel is timed)
+            cudaStream_t ds = p->st;
+            if (!p->opts.record_timing) {
+                ds = aux_stream(p->device, DENSE_AUX);
+                if (ds == nullptr) {
+                    status = SPGEMM_ERR_CUDA;
+                    goto fail;
+                }
+                cudaEvent_t go = nullptr;
+                SPG_TRY(cudaEventCreateWithFlags(&go, cudaEventDisableTiming));
+                cudaError_t e = cudaEventRecord(go, p->st);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, go, 0);
+                cudaEventDestroy(go);
+                SPG_TRY(e);
+                SPG_TRY(cudaEventCreateWithFlags(&fill_done, cudaEventDisableTiming));
+            }
+            p->time_begin(SPGEMM_K_MERGE);
+            cudaError_t e = launch_dense_fill(p->A, p->B, p->dense_args(), p->C.row_ptr, p->C.col_idx, p->C.val,
+                                              p->d_err, ds);
+            if (e == cudaSuccess && fill_done) e = cudaEventRecord(fill_done, ds);
+            p->time_end();
+            p->count(SPGEMM_K_MERGE);
+            if (e != cudaSuccess) {
+                if (fill_done) cudaEventDestroy(fill_done);
+                status = from_cuda(e);
+                goto fail;
+            }
+        }
         p->time_begin(SPGEMM_K_ARRANGE);
         {
             const int64_t s0 = p->bin_start[1], s1 = p->bin_start[BIN_MERGE];
@@ -1029,13 +1109,9 @@ extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
             if (n37 > 0) p->count(SPGEMM_K_ARRANGE);
         }
         p->time_end();
-        if (p->dense_n > 0) {
-            // the dense-slice rows write their values straight into C
-            p->time_begin(SPGEMM_K_MERGE);
-            SPG_TRY(launch_dense_fill(p->A, p->B, p->items, p->dense_args(), p->C.row_ptr, p->C.col_idx, p->C.val,
-                                      p->d_err, p->st));
-            p->time_end();
-            p->count(SPGEMM_K_MERGE);
+        if (fill_done) {
+            SPG_TRY(cudaStreamWaitEvent(p->st, fill_done, 0));
+            cudaEventDestroy(fill_done);
         }
         p->C.nrows = m;
         p->C.ncols = p->B.ncols;
@@ -1440,8 +1516,8 @@ extern "C" spgemm_status spgemm_numeric_replay(spgemm_plan *p) {
             off += p->leaf_count[g];
         }
         if (p->dense_n > 0)
-            SPG_TRY(launch_dense_fill(p->A, p->B, p->items, p->dense_args(), p->C.row_ptr, p->C.col_idx, p->C.val,
-                                      p->d_err, p->st));
+            SPG_TRY(launch_dense_fill(p->A, p->B, p->dense_args(), p->C.row_ptr, p->C.col_idx, p->C.val, p->d_err,
+                                      p->st));
     }
     return SPGEMM_OK;
 fail:
