@@ -59,13 +59,14 @@ cudaError_t launch_binning(int64_t m, const int64_t *arp, const int64_t *S,
                            BinSummary *summary, cudaStream_t st);
 
 // ---- learned preallocation (predictor.cu) ----
-// Row features (warp per row).  With the stage-1 prefix S, rows with u_i <= u_min are skipped.
+// Row features (warp per row).  With the stage-1 prefix S, rows with u_i <= u_min or
+// u_i >= u_max are skipped.
 cudaError_t launch_row_features(const DevCSR &A, const DevCSR &B, float *X, cudaStream_t st,
-                                const int64_t *S = nullptr, int64_t u_min = 0);
-// Predicted temporary size per row (0 for rows skipped through arp/S/u_min).
+                                const int64_t *S = nullptr, int64_t u_min = 0, int64_t u_max = INT64_MAX);
+// Predicted temporary size per row (0 for rows skipped through arp/S/u_min/u_max).
 cudaError_t launch_predict_caps(const float *params, const float *X, int64_t m, const int64_t *u, float margin,
                                 int32_t min_cap, int32_t *pred_cap, cudaStream_t st, const int64_t *arp = nullptr,
-                                const int64_t *S = nullptr, int64_t u_min = 0);
+                                const int64_t *S = nullptr, int64_t u_min = 0, int64_t u_max = INT64_MAX);
 // Groups the bin-37 items (tail of bin_rows, size read from summary) by launch
 // class; items of rows with u >= dmin go after the last class; scratch: 96 + m
 // int32; order: item indices grouped by class; counts go to summary->class_count.

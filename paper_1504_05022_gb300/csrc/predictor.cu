@@ -38,14 +38,15 @@ constexpr int R_XH = 0, R_H1 = MLP_IN, R_H2 = R_H1 + MLP_HID, R_DZ1 = R_H2 + MLP
 
 // One warp per row: the 8 features (log2(1+.) of nnz(a_i*), u_i, min/max/mean/std
 // of the selected B-row lengths, the column span of the selected B rows, ncols(B)).
-__global__ void k_row_features(DevCSR A, DevCSR B, const int64_t *__restrict__ S, int64_t u_min,
+__global__ void k_row_features(DevCSR A, DevCSR B, const int64_t *__restrict__ S, int64_t u_min, int64_t u_max,
                                float *__restrict__ X) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= A.nrows) return;
     const int64_t a0 = A.rp[row], a1 = A.rp[row + 1];
-    // with the stage-1 prefix S given, only rows with u_i > u_min (bin 37) need features
-    if (S != nullptr && S[a1] - S[a0] <= u_min) return;
+    // with the stage-1 prefix S given, only rows with u_min < u_i < u_max need features (bin 37
+    // without the dense-slice rows)
+    if (S != nullptr && (S[a1] - S[a0] <= u_min || S[a1] - S[a0] >= u_max)) return;
     double sum_len = 0.0, sg = 0.0, sg2 = 0.0;
     float gmin = 3.4e38f, gmax = -3.4e38f;
     int32_t cmin = INT_MAX, cmax = -1;
@@ -94,10 +95,10 @@ __global__ void k_row_features(DevCSR A, DevCSR B, const int64_t *__restrict__ S
 }
 
 cudaError_t launch_row_features(const DevCSR &A, const DevCSR &B, float *X, cudaStream_t st, const int64_t *S,
-                                int64_t u_min) {
+                                int64_t u_min, int64_t u_max) {
     if (A.nrows <= 0) return cudaSuccess;
     const int64_t threads = A.nrows * 32;
-    k_row_features<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, B, S, u_min, X);
+    k_row_features<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, B, S, u_min, u_max, X);
     return cudaGetLastError();
 }
 
@@ -267,16 +268,19 @@ __global__ void k_mlp_adam(float *__restrict__ params, const float *__restrict__
 // from the regression head, times `margin`, rounded up to 32.
 __global__ void k_mlp_predict_caps(const float *__restrict__ params, const float *__restrict__ X, int64_t m,
                                    const int64_t *__restrict__ u, const int64_t *__restrict__ arp,
-                                   const int64_t *__restrict__ S, int64_t u_min, float margin, int32_t min_cap,
-                                   int32_t *__restrict__ pred_cap) {
+                                   const int64_t *__restrict__ S, int64_t u_min, int64_t u_max, float margin,
+                                   int32_t min_cap, int32_t *__restrict__ pred_cap) {
     __shared__ float P[SPGEMM_MLP_NUM_TOTAL];
     for (int t = threadIdx.x; t < SPGEMM_MLP_NUM_TOTAL; t += blockDim.x) P[t] = params[t];
     __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= m) return;
-    if (S != nullptr && S[arp[s + 1]] - S[arp[s]] <= u_min) {  // not in bin 37: no prediction needed
-        pred_cap[s] = 0;
-        return;
+    if (S != nullptr) {  // outside bin 37, or a dense-slice row: no prediction needed
+        const int64_t us = S[arp[s + 1]] - S[arp[s]];
+        if (us <= u_min || us >= u_max) {
+            pred_cap[s] = 0;
+            return;
+        }
     }
     float xh[MLP_IN], h1[MLP_HID], h2[MLP_HID], o[MLP_OUT];
     mlp_forward_one(P, X + s * MLP_IN, xh, h1, h2, o);
@@ -292,10 +296,10 @@ __global__ void k_mlp_predict_caps(const float *__restrict__ params, const float
 
 cudaError_t launch_predict_caps(const float *params, const float *X, int64_t m, const int64_t *u, float margin,
                                 int32_t min_cap, int32_t *pred_cap, cudaStream_t st, const int64_t *arp,
-                                const int64_t *S, int64_t u_min) {
+                                const int64_t *S, int64_t u_min, int64_t u_max) {
     if (m <= 0) return cudaSuccess;
-    k_mlp_predict_caps<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(params, X, m, u, arp, S, u_min, margin, min_cap,
-                                                                     pred_cap);
+    k_mlp_predict_caps<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(params, X, m, u, arp, S, u_min, u_max, margin,
+                                                                     min_cap, pred_cap);
     return cudaGetLastError();
 }
 

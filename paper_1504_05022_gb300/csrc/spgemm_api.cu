@@ -518,10 +518,11 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             SPG_TRY(p->alloc_n(&X, m * SPGEMM_MLP_FEATURES, LIFE_SYMBOLIC));
             SPG_TRY(p->alloc_n(&p->pred_cap, m, LIFE_SYMBOLIC));
             p->time_begin(SPGEMM_K_OTHER);
-            SPG_TRY(launch_row_features(p->A, p->B, X, p->st, p->S, BIN_MERGE_MIN_U));
+            SPG_TRY(launch_row_features(p->A, p->B, X, p->st, p->S, BIN_MERGE_MIN_U, p->dense_min_u));
             SPG_TRY(launch_predict_caps(predictor_params(o.predictor), X, m, nullptr,
                                         (float)(o.predictor_margin > 0 ? o.predictor_margin : 1.0),
-                                        o.initial_cap, p->pred_cap, p->st, p->A.rp, p->S, BIN_MERGE_MIN_U));
+                                        o.initial_cap, p->pred_cap, p->st, p->A.rp, p->S, BIN_MERGE_MIN_U,
+                                        p->dense_min_u));
             p->time_end();
             p->count(SPGEMM_K_OTHER, 2);
         }
