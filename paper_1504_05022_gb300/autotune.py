@@ -55,13 +55,16 @@ SPACE = {
     "merge_miss": [4096, 2048, 8192],
     "initial_cap": [256, 512, 1024],
     "predictor_margin": [None, 1.15, 1.5, 2.0],  # None = the margin stored with the weights
+    "dense_min_u": [0, 16384, 4096, -1],  # 0 = ncols(B) / 8, -1 = no dense-slice rows
+    "dense_span": [0, 16384, 10912],      # 0 = the widest slice shared memory holds
 }
 POLICY_PARAMS = {
     "hybrid": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "merge_miss",
-               "initial_cap"],
+               "initial_cap", "dense_min_u", "dense_span"],
     "learned": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "merge_miss",
-                "predictor_margin"],
-    "upper_bound": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above"],
+                "predictor_margin", "dense_min_u", "dense_span"],
+    "upper_bound": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "dense_min_u",
+                    "dense_span"],
 }
 MEMORY_SLACK = 1.05
 
