@@ -145,9 +145,10 @@ typedef struct spgemm_opts {
                                 kernels instead of the merge kernel: B's columns are cut into
                                 slices that fit shared memory as fp64 sums, one CTA per (row,
                                 slice), after a pass that counts the columns of every slice.
-                                0 = ncols(B) / 8; negative = never.  Off with
-                                SPGEMM_MERGE_PATH, SPGEMM_LONG_ROWS_LEVEL1 and when B needs more
-                                than 16 slices */
+                                0 = a bin-37 row is dense when 8 u_i >= the width of the column
+                                range its products can reach (first to last column of the B rows
+                                it selects); negative = never.  Off with SPGEMM_MERGE_PATH,
+                                SPGEMM_LONG_ROWS_LEVEL1 and when B needs more than 16 slices */
     int32_t dense_span;      /* widest dense slice in columns (0 = the widest that fits shared
                                 memory, at least 1,024) */
     int32_t reserved[1];

@@ -47,6 +47,53 @@ cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cud
     return cudaGetLastError();
 }
 
+// ---- which bin-37 rows are dense ----
+// One warp per row: u_i from the stage-1 prefix, and for u_i > 512 the row's column
+// range [lo, hi) (first and last column of every touched B row).  The row is dense when
+// u_i >= dmin (dmin > 0), else when 8 u_i >= hi - lo: its products cover at least an
+// eighth of the columns they can reach, so the dense accumulator's O(hi - lo) clearing
+// and write-out are small beside them.
+__global__ void k_dense_mark(DevCSR A, DevCSR B, const int64_t *__restrict__ S, int64_t dmin, uint8_t *flag,
+                             int32_t *lo, int32_t *hi) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= A.nrows) return;
+    const int64_t a0 = A.rp[row], a1 = A.rp[row + 1];
+    const int64_t u = S[a1] - S[a0];
+    if (u <= BIN_MERGE_MIN_U) {
+        if (lane == 0) flag[row] = 0;
+        return;
+    }
+    int32_t cmin = INT32_MAX, cmax = -1;
+    for (int64_t e = a0 + lane; e < a1; e += 32) {
+        const int32_t k = A.col[e];
+        const int64_t rs = B.rp[k], re = B.rp[k + 1];
+        if (re > rs) {
+            cmin = min(cmin, B.col[rs]);
+            cmax = max(cmax, B.col[re - 1]);
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        cmin = min(cmin, __shfl_xor_sync(SPG_FULL, cmin, d));
+        cmax = max(cmax, __shfl_xor_sync(SPG_FULL, cmax, d));
+    }
+    if (lane == 0) {
+        const int64_t span = (int64_t)cmax - cmin + 1;  // u > 0, so some B row is not empty
+        flag[row] = (uint8_t)(dmin > 0 ? u >= dmin : 8 * u >= span);
+        lo[row] = cmin;
+        hi[row] = cmax + 1;
+    }
+}
+
+cudaError_t launch_dense_mark(const DevCSR &A, const DevCSR &B, const int64_t *S, int64_t dmin, uint8_t *flag,
+                              int32_t *lo, int32_t *hi, cudaStream_t st) {
+    if (A.nrows <= 0) return cudaSuccess;
+    const int64_t threads = A.nrows * 32;
+    k_dense_mark<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, B, S, dmin, flag, lo, hi);
+    return cudaGetLastError();
+}
+
 // ---- selection of the dense rows among the bin-37 rows ----
 // Bucket g = 63 - floor(log2 u) (the leading zeros of u) for a dense row, so that
 // larger rows come first; DENSE_BUCKETS for the others.  order[0..nd) lists the
@@ -55,12 +102,13 @@ cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cud
 constexpr int DENSE_BUCKETS = 64;
 
 __global__ void k_dense_select_count(const int32_t *bin_rows, int64_t m, const BinSummary *summary, const int64_t *u,
-                                     int64_t dmin, int32_t *cls_of, int32_t *count) {
+                                     const uint8_t *flag, int32_t *cls_of, int32_t *count) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n37 = summary->bin_count[BIN_MERGE];
     if (j >= n37) return;
-    const int64_t uu = u[bin_rows[m - n37 + j]];
-    const int g = uu >= dmin ? __clzll((long long)uu) : DENSE_BUCKETS;
+    const int32_t row = bin_rows[m - n37 + j];
+    const int64_t uu = u[row];
+    const int g = flag[row] ? __clzll((long long)uu) : DENSE_BUCKETS;
     cls_of[j] = g;
     atomicAdd(&count[g], 1);
 }
@@ -78,30 +126,38 @@ __global__ void k_dense_select_starts(const int32_t *count, int32_t *start, int3
 }
 
 __global__ void k_dense_select_scatter(const int32_t *bin_rows, int64_t m, const BinSummary *summary,
-                                       const int32_t *cls_of, const int32_t *start, int32_t *cursor, int32_t *order,
-                                       int32_t *rows) {
+                                       const int32_t *cls_of, const int32_t *start, int32_t *cursor,
+                                       const int32_t *lo, const int32_t *hi, int32_t *order, int32_t *rows,
+                                       int32_t *rlo, int32_t *rhi) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n37 = summary->bin_count[BIN_MERGE];
     if (j >= n37) return;
     const int g = cls_of[j];
     const int32_t pos = start[g] + atomicAdd(&cursor[g], 1);
     order[pos] = (int32_t)j;
-    if (g < DENSE_BUCKETS) rows[pos] = bin_rows[m - n37 + j];
+    if (g < DENSE_BUCKETS) {
+        const int32_t row = bin_rows[m - n37 + j];
+        rows[pos] = row;
+        rlo[pos] = lo[row];
+        rhi[pos] = hi[row];
+    }
 }
 
 int64_t dense_select_scratch(int64_t m) { return 3 * (DENSE_BUCKETS + 1) + m; }
 
 cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *summary, const int64_t *u,
-                                int64_t dmin, int32_t *scratch, int32_t *order, int32_t *rows, cudaStream_t st) {
+                                const uint8_t *flag, const int32_t *lo, const int32_t *hi, int32_t *scratch,
+                                int32_t *order, int32_t *rows, int32_t *rlo, int32_t *rhi, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     int32_t *count = scratch, *start = count + DENSE_BUCKETS + 1, *cursor = start + DENSE_BUCKETS + 1,
             *cls_of = cursor + DENSE_BUCKETS + 1;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t) * (DENSE_BUCKETS + 1), st);
     if (e != cudaSuccess) return e;
     const unsigned g = (unsigned)((m + 255) / 256);
-    k_dense_select_count<<<g, 256, 0, st>>>(bin_rows, m, summary, u, dmin, cls_of, count);
+    k_dense_select_count<<<g, 256, 0, st>>>(bin_rows, m, summary, u, flag, cls_of, count);
     k_dense_select_starts<<<1, 32, 0, st>>>(count, start, cursor, summary);
-    k_dense_select_scatter<<<g, 256, 0, st>>>(bin_rows, m, summary, cls_of, start, cursor, order, rows);
+    k_dense_select_scatter<<<g, 256, 0, st>>>(bin_rows, m, summary, cls_of, start, cursor, lo, hi, order, rows, rlo,
+                                              rhi);
     return cudaGetLastError();
 }
 
@@ -191,8 +247,13 @@ k_dense_count(DevCSR A, DevCSR B, DenseArgs D, int64_t *err) {
     const int64_t d = b / D.K;
     const int s = (int)(b - d * D.K);
     const int row = D.rows[d];
-    const int64_t lo = (int64_t)s * D.W;
-    const int span = (int)min((int64_t)D.W, B.ncols - lo);
+    // the slice's columns that the row can reach: [lo, lo + span)
+    const int64_t lo = max((int64_t)s * D.W, (int64_t)D.clo[d]);
+    const int span = (int)(min(min((int64_t)(s + 1) * D.W, B.ncols), (int64_t)D.chi[d]) - lo);
+    if (span <= 0) {
+        if (threadIdx.x == 0) D.cnt[b] = 0;
+        return;
+    }
     const int nq = (span + 15) >> 4;  // 16-byte groups of flags
     uint4 *f4 = reinterpret_cast<uint4 *>(dc_flag);
     for (int q = threadIdx.x; q < nq; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
@@ -278,8 +339,9 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
     const int64_t d = b / D.K;
     const int s = (int)(b - d * D.K);
     const int row = D.rows[d];
-    const int64_t lo = (int64_t)s * D.W;
-    const int span = (int)min((int64_t)D.W, B.ncols - lo);
+    // the slice's columns that the row can reach (non-empty: the slice has columns of the row)
+    const int64_t lo = max((int64_t)s * D.W, (int64_t)D.clo[d]);
+    const int span = (int)(min(min((int64_t)(s + 1) * D.W, B.ncols), (int64_t)D.chi[d]) - lo);
     const int nwords = (span + 31) >> 5;
     const int nw4 = dense_nw4(D.W);
     double *V = reinterpret_cast<double *>(df_smem);

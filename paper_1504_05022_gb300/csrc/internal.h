@@ -41,7 +41,7 @@ struct CapPolicy {
     int64_t initial_cap;
     const int32_t *pred_cap;  // learned per-row temporary row sizes (POLICY_LEARNED), may be null
     int64_t cap_max;          // learned: a bin-37 row's home never exceeds the largest shared capacity
-    int64_t dense_min_u;      // bin-37 rows with u_i >= this take no C~ space (dense-slice kernels)
+    const uint8_t *dense;     // per row, 1: a dense-slice row (no C~ space); null: none
 };
 
 // ---- stage 0/1/2 (stage12.cu) ----
@@ -59,21 +59,20 @@ cudaError_t launch_binning(int64_t m, const int64_t *arp, const int64_t *S,
                            BinSummary *summary, cudaStream_t st);
 
 // ---- learned preallocation (predictor.cu) ----
-// Row features (warp per row).  With the stage-1 prefix S, rows with u_i <= u_min or
-// u_i >= u_max are skipped.
+// Row features (warp per row).  With the stage-1 prefix S, rows with u_i <= u_min are
+// skipped, and so are the rows flagged in `skip` (when given).
 cudaError_t launch_row_features(const DevCSR &A, const DevCSR &B, float *X, cudaStream_t st,
-                                const int64_t *S = nullptr, int64_t u_min = 0, int64_t u_max = INT64_MAX);
-// Predicted temporary size per row (0 for rows skipped through arp/S/u_min/u_max).
+                                const int64_t *S = nullptr, int64_t u_min = 0, const uint8_t *skip = nullptr);
+// Predicted temporary size per row (0 for rows skipped through arp/S/u_min/skip).
 cudaError_t launch_predict_caps(const float *params, const float *X, int64_t m, const int64_t *u, float margin,
                                 int32_t min_cap, int32_t *pred_cap, cudaStream_t st, const int64_t *arp = nullptr,
-                                const int64_t *S = nullptr, int64_t u_min = 0, int64_t u_max = INT64_MAX);
+                                const int64_t *S = nullptr, int64_t u_min = 0, const uint8_t *skip = nullptr);
 // Groups the bin-37 items (tail of bin_rows, size read from summary) by launch
-// class; items of rows with u >= dmin go after the last class; scratch: 96 + m
+// class; items of flagged (dense-slice) rows go after the last class; scratch: 96 + m
 // int32; order: item indices grouped by class; counts go to summary->class_count.
 cudaError_t launch_class_partition_tail(const int32_t *bin_rows, int64_t m, BinSummary *summary,
                                         const int32_t *pred_cap, const int32_t *class_cap, int ncls,
-                                        const int64_t *u, int64_t dmin, int32_t *scratch, int32_t *order,
-                                        cudaStream_t st);
+                                        const uint8_t *dense, int32_t *scratch, int32_t *order, cudaStream_t st);
 const float *predictor_params(const void *pred);
 
 // ---- stage 3 ----
@@ -164,6 +163,8 @@ constexpr int DENSE_MAX_SLICES = 16;
 struct DenseArgs {
     const int32_t *items;  // dense items (indices into MergeItems), larger rows first
     const int32_t *rows;   // their rows of A
+    const int32_t *clo;    // and the column range [clo, chi) that each row's products can reach
+    const int32_t *chi;
     int64_t n;             // number of dense items
     int K;                 // column slices of B
     int W;                 // slice width (a multiple of 32); slice s holds columns [s W, (s + 1) W)
@@ -172,11 +173,16 @@ struct DenseArgs {
     int32_t *soff;         // n K offsets of the slices inside their row of C
 };
 cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cudaStream_t st);
+// per row: flag (1 = dense-slice row: bin 37, and u_i >= dmin if dmin > 0, else 8 u_i >= the
+// width of its column range) and, for bin-37 rows, the column range [lo, hi)
+cudaError_t launch_dense_mark(const DevCSR &A, const DevCSR &B, const int64_t *S, int64_t dmin, uint8_t *flag,
+                              int32_t *lo, int32_t *hi, cudaStream_t st);
 int64_t dense_select_scratch(int64_t m);
-// order[0..nd) = items of the bin-37 rows with u >= dmin (larger first), order[nd..n37) = the rest;
-// rows[0..nd) = the rows of the dense items; nd goes to summary->dense_count
+// order[0..nd) = items of the flagged bin-37 rows (larger u first), order[nd..n37) = the rest;
+// rows, rlo, rhi [0..nd) = their rows and column ranges; nd goes to summary->dense_count
 cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *summary, const int64_t *u,
-                                int64_t dmin, int32_t *scratch, int32_t *order, int32_t *rows, cudaStream_t st);
+                                const uint8_t *flag, const int32_t *lo, const int32_t *hi, int32_t *scratch,
+                                int32_t *order, int32_t *rows, int32_t *rlo, int32_t *rhi, cudaStream_t st);
 // counts the columns of every (row, slice) into D.cnt (reads no work-item table, so it
 // may run beside the merge launches)
 cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t *err, cudaStream_t st);

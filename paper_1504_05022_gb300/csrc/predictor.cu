@@ -38,15 +38,16 @@ constexpr int R_XH = 0, R_H1 = MLP_IN, R_H2 = R_H1 + MLP_HID, R_DZ1 = R_H2 + MLP
 
 // One warp per row: the 8 features (log2(1+.) of nnz(a_i*), u_i, min/max/mean/std
 // of the selected B-row lengths, the column span of the selected B rows, ncols(B)).
-__global__ void k_row_features(DevCSR A, DevCSR B, const int64_t *__restrict__ S, int64_t u_min, int64_t u_max,
-                               float *__restrict__ X) {
+__global__ void k_row_features(DevCSR A, DevCSR B, const int64_t *__restrict__ S, int64_t u_min,
+                               const uint8_t *__restrict__ skip, float *__restrict__ X) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= A.nrows) return;
     const int64_t a0 = A.rp[row], a1 = A.rp[row + 1];
-    // with the stage-1 prefix S given, only rows with u_min < u_i < u_max need features (bin 37
-    // without the dense-slice rows)
-    if (S != nullptr && (S[a1] - S[a0] <= u_min || S[a1] - S[a0] >= u_max)) return;
+    // with the stage-1 prefix S given, only rows with u_i > u_min (bin 37) need features, and
+    // not the dense-slice rows
+    if (S != nullptr && S[a1] - S[a0] <= u_min) return;
+    if (skip != nullptr && skip[row]) return;
     double sum_len = 0.0, sg = 0.0, sg2 = 0.0;
     float gmin = 3.4e38f, gmax = -3.4e38f;
     int32_t cmin = INT_MAX, cmax = -1;
@@ -95,10 +96,10 @@ __global__ void k_row_features(DevCSR A, DevCSR B, const int64_t *__restrict__ S
 }
 
 cudaError_t launch_row_features(const DevCSR &A, const DevCSR &B, float *X, cudaStream_t st, const int64_t *S,
-                                int64_t u_min, int64_t u_max) {
+                                int64_t u_min, const uint8_t *skip) {
     if (A.nrows <= 0) return cudaSuccess;
     const int64_t threads = A.nrows * 32;
-    k_row_features<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, B, S, u_min, u_max, X);
+    k_row_features<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, B, S, u_min, skip, X);
     return cudaGetLastError();
 }
 
@@ -268,19 +269,17 @@ __global__ void k_mlp_adam(float *__restrict__ params, const float *__restrict__
 // from the regression head, times `margin`, rounded up to 32.
 __global__ void k_mlp_predict_caps(const float *__restrict__ params, const float *__restrict__ X, int64_t m,
                                    const int64_t *__restrict__ u, const int64_t *__restrict__ arp,
-                                   const int64_t *__restrict__ S, int64_t u_min, int64_t u_max, float margin,
-                                   int32_t min_cap, int32_t *__restrict__ pred_cap) {
+                                   const int64_t *__restrict__ S, int64_t u_min, const uint8_t *__restrict__ skip,
+                                   float margin, int32_t min_cap, int32_t *__restrict__ pred_cap) {
     __shared__ float P[SPGEMM_MLP_NUM_TOTAL];
     for (int t = threadIdx.x; t < SPGEMM_MLP_NUM_TOTAL; t += blockDim.x) P[t] = params[t];
     __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= m) return;
-    if (S != nullptr) {  // outside bin 37, or a dense-slice row: no prediction needed
-        const int64_t us = S[arp[s + 1]] - S[arp[s]];
-        if (us <= u_min || us >= u_max) {
-            pred_cap[s] = 0;
-            return;
-        }
+    // outside bin 37, or a dense-slice row: no prediction needed
+    if ((S != nullptr && S[arp[s + 1]] - S[arp[s]] <= u_min) || (skip != nullptr && skip[s])) {
+        pred_cap[s] = 0;
+        return;
     }
     float xh[MLP_IN], h1[MLP_HID], h2[MLP_HID], o[MLP_OUT];
     mlp_forward_one(P, X + s * MLP_IN, xh, h1, h2, o);
@@ -296,22 +295,22 @@ __global__ void k_mlp_predict_caps(const float *__restrict__ params, const float
 
 cudaError_t launch_predict_caps(const float *params, const float *X, int64_t m, const int64_t *u, float margin,
                                 int32_t min_cap, int32_t *pred_cap, cudaStream_t st, const int64_t *arp,
-                                const int64_t *S, int64_t u_min, int64_t u_max) {
+                                const int64_t *S, int64_t u_min, const uint8_t *skip) {
     if (m <= 0) return cudaSuccess;
-    k_mlp_predict_caps<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(params, X, m, u, arp, S, u_min, u_max, margin,
+    k_mlp_predict_caps<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(params, X, m, u, arp, S, u_min, skip, margin,
                                                                      min_cap, pred_cap);
     return cudaGetLastError();
 }
 
 // Launch-class partition of the bin-37 rows by predicted size: class g holds
 // the rows whose predicted size is at most class_cap[g] (the smallest such g).
-// Rows with u_i >= dmin (the dense-slice rows) go to slot ncls, after the classes.
+// The dense-slice rows go to slot ncls, after the classes.
 // Bin 37 is the last segment of bin_rows; its size is read from the stage-2
 // summary on the device, so no host round trip is needed.  The order inside a
 // class is not fixed (atomics); it only affects scheduling, not C.
 __global__ void k_class_count(const int32_t *bin_rows, int64_t m, const BinSummary *summary,
-                              const int32_t *pred_cap, const int32_t *class_cap, int ncls, const int64_t *u,
-                              int64_t dmin, int32_t *cls_of, int32_t *count) {
+                              const int32_t *pred_cap, const int32_t *class_cap, int ncls, const uint8_t *dense,
+                              int32_t *cls_of, int32_t *count) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n37 = summary->bin_count[BIN_MERGE];
     if (j >= n37) return;
@@ -323,7 +322,7 @@ __global__ void k_class_count(const int32_t *bin_rows, int64_t m, const BinSumma
             g = k;
             break;
         }
-    if (u[row] >= dmin) g = ncls;
+    if (dense != nullptr && dense[row]) g = ncls;
     cls_of[j] = g;
     atomicAdd(&count[g], 1);
 }
@@ -351,14 +350,13 @@ __global__ void k_class_scatter(int64_t m, const BinSummary *summary, const int3
 
 cudaError_t launch_class_partition_tail(const int32_t *bin_rows, int64_t m, BinSummary *summary,
                                         const int32_t *pred_cap, const int32_t *class_cap, int ncls,
-                                        const int64_t *u, int64_t dmin, int32_t *scratch, int32_t *order,
-                                        cudaStream_t st) {
+                                        const uint8_t *dense, int32_t *scratch, int32_t *order, cudaStream_t st) {
     if (m <= 0 || ncls > 31) return m <= 0 ? cudaSuccess : cudaErrorInvalidValue;
     int32_t *count = scratch, *start = scratch + 32, *cursor = scratch + 64, *cls_of = scratch + 96;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t) * 32, st);
     if (e != cudaSuccess) return e;
     const unsigned g = (unsigned)((m + 255) / 256);
-    k_class_count<<<g, 256, 0, st>>>(bin_rows, m, summary, pred_cap, class_cap, ncls, u, dmin, cls_of, count);
+    k_class_count<<<g, 256, 0, st>>>(bin_rows, m, summary, pred_cap, class_cap, ncls, dense, cls_of, count);
     k_class_starts<<<1, 32, 0, st>>>(count, ncls, start, cursor, summary);
     k_class_scatter<<<g, 256, 0, st>>>(m, summary, cls_of, start, cursor, order);
     return cudaGetLastError();

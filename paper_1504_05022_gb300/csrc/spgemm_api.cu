@@ -155,14 +155,18 @@ struct spgemm_plan {
     int capmax = 0, batch = 0, wide_above = 2048, bm_words = 0, bm_miss = 0, bm_two = 0;
     // dense column slices for the longest bin-37 rows (off when dense_K == 0)
     int dense_K = 0, dense_W = 0;
-    int64_t dense_min_u = INT64_MAX;
+    int64_t dense_min_u = 0;              // > 0: absolute threshold on u_i; 0: the row's column range
     int64_t dense_n = 0;                  // dense bin-37 rows
+    uint8_t *dense_flag = nullptr;        // per row: 1 = dense-slice row (symbolic only)
+    int32_t *dense_lo = nullptr, *dense_hi = nullptr;  // per row: column range (symbolic only)
     int32_t *dense_order = nullptr;       // bin-37 items: the dense ones (larger first), then the rest
     int32_t *dense_rows = nullptr;        // rows of the dense items
+    int32_t *dense_clo = nullptr, *dense_chi = nullptr;  // and their column ranges
     int32_t *dense_bnd = nullptr;         // per B row, K + 1 slice boundaries (K > 1)
     int32_t *dense_cnt = nullptr, *dense_soff = nullptr;
     DenseArgs dense_args() const {
-        return DenseArgs{dense_order, dense_rows, dense_n, dense_K, dense_W, dense_bnd, dense_cnt, dense_soff};
+        return DenseArgs{dense_order, dense_rows, dense_clo, dense_chi, dense_n, dense_K, dense_W, dense_bnd,
+                         dense_cnt, dense_soff};
     }
     // batched plans: the pairs and the concatenation offsets
     int64_t npairs = 0;
@@ -311,7 +315,7 @@ static void merge_limits(spgemm_plan *p) {
     // CTAs per SM run that way.  B's columns are cut into equal slices of a multiple of 32
     p->dense_K = 0;
     p->dense_W = 0;
-    p->dense_min_u = INT64_MAX;
+    p->dense_min_u = 0;
     if (p->opts.dense_min_u >= 0 && p->opts.merge_kernel != SPGEMM_MERGE_PATH &&
         p->opts.long_rows == SPGEMM_LONG_ROWS_SPLIT && p->B.ncols > 0) {
         const int64_t n = p->B.ncols;
@@ -328,8 +332,7 @@ static void merge_limits(spgemm_plan *p) {
             const int64_t w = ((n + k0 - 1) / k0 + 31) & ~int64_t(31);
             p->dense_W = (int)w;
             p->dense_K = (int)((n + w - 1) / w);
-            p->dense_min_u = p->opts.dense_min_u > 0 ? (int64_t)p->opts.dense_min_u
-                                                     : std::max<int64_t>(BIN_MERGE_MIN_U + 1, n / 8);
+            p->dense_min_u = p->opts.dense_min_u > 0 ? (int64_t)p->opts.dense_min_u : 0;
         }
     }
     // learned launch classes: 256, 512, ..., 8192, the largest capacity, and "beyond it"
@@ -512,17 +515,26 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
         p->time_end();
         p->count(SPGEMM_K_BOUND, 3);
         merge_limits(p);
+        if (p->dense_K > 0) {
+            // which bin-37 rows go to the dense-slice kernels, and their column ranges
+            SPG_TRY(p->alloc_n(&p->dense_flag, m, LIFE_SYMBOLIC));
+            SPG_TRY(p->alloc_n(&p->dense_lo, m, LIFE_SYMBOLIC));
+            SPG_TRY(p->alloc_n(&p->dense_hi, m, LIFE_SYMBOLIC));
+            SPG_TRY(launch_dense_mark(p->A, p->B, p->S, p->dense_min_u, p->dense_flag, p->dense_lo, p->dense_hi,
+                                      p->st));
+            p->count(SPGEMM_K_OTHER);
+        }
         if (o.alloc_policy == SPGEMM_ALLOC_LEARNED) {
             // features and predicted temporary sizes of every row (used for bin 37)
             float *X = nullptr;
             SPG_TRY(p->alloc_n(&X, m * SPGEMM_MLP_FEATURES, LIFE_SYMBOLIC));
             SPG_TRY(p->alloc_n(&p->pred_cap, m, LIFE_SYMBOLIC));
             p->time_begin(SPGEMM_K_OTHER);
-            SPG_TRY(launch_row_features(p->A, p->B, X, p->st, p->S, BIN_MERGE_MIN_U, p->dense_min_u));
+            SPG_TRY(launch_row_features(p->A, p->B, X, p->st, p->S, BIN_MERGE_MIN_U, p->dense_flag));
             SPG_TRY(launch_predict_caps(predictor_params(o.predictor), X, m, nullptr,
                                         (float)(o.predictor_margin > 0 ? o.predictor_margin : 1.0),
                                         o.initial_cap, p->pred_cap, p->st, p->A.rp, p->S, BIN_MERGE_MIN_U,
-                                        p->dense_min_u));
+                                        p->dense_flag));
             p->time_end();
             p->count(SPGEMM_K_OTHER, 2);
         }
@@ -542,7 +554,7 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             pol.initial_cap = o.initial_cap;
             pol.pred_cap = p->pred_cap;
             pol.cap_max = p->capmax;
-            pol.dense_min_u = p->dense_min_u;
+            pol.dense = p->dense_flag;
             p->time_begin(SPGEMM_K_BIN);
             SPG_TRY(launch_binning(m, p->A.rp, p->S, p->S + nnzA, pol, p->u, p->bin, p->nnzc, p->bin_rows,
                                    p->ctil_rp, hist, capp, p->d_summary, p->st));
@@ -557,8 +569,7 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             SPG_TRY(p->alloc_n(&scratch, 96 + m, LIFE_SYMBOLIC));
             SPG_TRY(p->alloc_n(&p->class_order, m, LIFE_NUMERIC));
             SPG_TRY(launch_class_partition_tail(p->bin_rows, m, p->d_summary, p->pred_cap, ccap,
-                                                NUM_LAUNCH_CLASSES, p->u, p->dense_min_u, scratch,
-                                                p->class_order, p->st));
+                                                NUM_LAUNCH_CLASSES, p->dense_flag, scratch, p->class_order, p->st));
             p->count(SPGEMM_K_OTHER, 3);
         }
         if (p->dense_K > 0) {
@@ -567,8 +578,10 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             SPG_TRY(p->alloc_n(&scratch, dense_select_scratch(m), LIFE_SYMBOLIC));
             SPG_TRY(p->alloc_n(&p->dense_order, m));
             SPG_TRY(p->alloc_n(&p->dense_rows, m));
-            SPG_TRY(launch_dense_select(p->bin_rows, m, p->d_summary, p->u, p->dense_min_u, scratch, p->dense_order,
-                                        p->dense_rows, p->st));
+            SPG_TRY(p->alloc_n(&p->dense_clo, m));
+            SPG_TRY(p->alloc_n(&p->dense_chi, m));
+            SPG_TRY(launch_dense_select(p->bin_rows, m, p->d_summary, p->u, p->dense_flag, p->dense_lo, p->dense_hi,
+                                        scratch, p->dense_order, p->dense_rows, p->dense_clo, p->dense_chi, p->st));
             p->count(SPGEMM_K_OTHER, 3);
         }
         SPG_TRY(p->d2h(&p->h_summary, p->d_summary, sizeof(BinSummary)));
@@ -595,6 +608,8 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
         SPG_TRY(p->alloc_n(&p->ctil_val, p->h_summary.sum_cap, LIFE_NUMERIC));
         p->bytes_ctilde += p->h_summary.sum_cap * 12;
         p->release_temps(LIFE_SYMBOLIC);
+        p->dense_flag = nullptr;
+        p->dense_lo = p->dense_hi = nullptr;
     }
     return SPGEMM_OK;
 fail:

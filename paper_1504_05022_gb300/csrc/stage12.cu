@@ -103,7 +103,7 @@ SPG_DEV int bin_of(int64_t u) {
 // 0..36, the predicted size (never above u_i) for bin 37.  Bin-37 rows computed
 // by the dense-slice kernels take none in every policy.
 SPG_DEV int64_t cap_of(int64_t u, int b, int64_t i, const CapPolicy &P) {
-    if (b == BIN_MERGE && u >= P.dense_min_u) return 0;  // written straight into C
+    if (b == BIN_MERGE && P.dense != nullptr && P.dense[i]) return 0;  // written straight into C
     if (P.policy == POLICY_UPPER_BOUND) return u;
     if (P.policy == POLICY_LEARNED && P.pred_cap != nullptr && b == BIN_MERGE) {
         int64_t c = P.pred_cap[i];

@@ -44,6 +44,20 @@ def _products(A, B):
     return cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]
 
 
+def _col_range(A, B):
+    """Per row of A*B: first and last-plus-one column of the B rows it selects."""
+    blen = np.diff(B.row_ptr)
+    col = B.col.astype(np.int64)
+    first = np.where(blen > 0, col[np.minimum(B.row_ptr[:-1], max(B.nnz - 1, 0))], np.iinfo(np.int64).max)
+    last = np.where(blen > 0, col[np.maximum(B.row_ptr[1:] - 1, 0)], -1)
+    lo = np.full(A.nrows, np.iinfo(np.int64).max)
+    hi = np.full(A.nrows, -1)
+    rows = np.repeat(np.arange(A.nrows), np.diff(A.row_ptr))
+    np.minimum.at(lo, rows, first[A.col])
+    np.maximum.at(hi, rows, last[A.col])
+    return lo, hi + 1
+
+
 def _policy_opts(policy):
     from paper_1504_05022_gb300.predictor import Predictor
     if policy == "learned":
@@ -64,8 +78,11 @@ def test_dense_slices_parity(spg, oracle_mod, span, slices, policy, dmin):
     _check(oracle_mod, A, A, C, label=f"dense {span}/{policy}/{dmin}")
     st = plan.stats()
     u = _products(A, A)
-    thr = dmin if dmin > 0 else max(513, A.ncols // 8)
-    expect = int((u >= thr).sum())
+    if dmin > 0:
+        expect = int((u >= dmin).sum())
+    else:  # 8 u_i >= the width of the row's reachable column range
+        lo, hi = _col_range(A, A)
+        expect = int(((u > 512) & (8 * u >= hi - lo)).sum())
     assert st["rows_dense"] == expect > 0
     assert st["dense_slices"] == slices
     plan.check()
