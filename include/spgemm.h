@@ -148,7 +148,7 @@ typedef struct spgemm_opts {
                                 0 = a bin-37 row is dense when 8 u_i >= the width of the column
                                 range its products can reach (first to last column of the B rows
                                 it selects); negative = never.  Off with SPGEMM_MERGE_PATH,
-                                SPGEMM_LONG_ROWS_LEVEL1 and when B needs more than 16 slices */
+                                SPGEMM_LONG_ROWS_LEVEL1 and when B needs more than 64 slices */
     int32_t dense_span;      /* widest dense slice in columns (0 = the widest that fits shared
                                 memory, at least 1,024) */
     int32_t reserved[1];

@@ -159,7 +159,7 @@ cudaError_t launch_level1_sizes(const MergeItems &it, const int32_t *work, int64
 
 // ---- dense column slices for the longest bin-37 rows (dense.cu) ----
 constexpr int32_t ITEM_DENSE = -2;  // MergeItems.child of a row computed by the dense-slice kernels
-constexpr int DENSE_MAX_SLICES = 16;
+constexpr int DENSE_MAX_SLICES = 64;
 struct DenseArgs {
     const int32_t *items;  // dense items (indices into MergeItems), larger rows first
     const int32_t *rows;   // their rows of A
