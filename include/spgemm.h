@@ -145,13 +145,13 @@ typedef struct spgemm_opts {
                                 kernels instead of the merge kernel: B's columns are cut into
                                 slices that fit shared memory as fp64 sums, one CTA per (row,
                                 slice), after a pass that counts the columns of every slice.
-                                0 = a bin-37 row is dense when 8 u_i >= the width of the column
-                                range its products can reach (first to last column of the B rows
-                                it selects); negative = never.  Off with SPGEMM_MERGE_PATH,
+                                0 = a bin-37 row is dense when dense_span_div * u_i >= the width of
+                                the column range its products can reach (first to last column of
+                                the B rows it selects); negative = never.  Off with SPGEMM_MERGE_PATH,
                                 SPGEMM_LONG_ROWS_LEVEL1 and when B needs more than 64 slices */
     int32_t dense_span;      /* widest dense slice in columns (0 = the widest that fits shared
                                 memory, at least 1,024) */
-    int32_t reserved[1];
+    int32_t dense_span_div;  /* with dense_min_u = 0: the divisor of the rule above (0 = 8) */
     const void *predictor;   /* spgemm_predictor* for SPGEMM_ALLOC_LEARNED, else NULL; it must
                                 not be freed before spgemm_symbolic (or spgemm_galerkin) has
                                 returned, since its weights are read by that call's kernels */

@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
                 ("record_timing", c_i32), ("merge_batch", c_i32), ("smem_cap_max", c_i32),
                 ("heap_block", c_i32), ("long_rows", c_i32), ("wave_mproducts", c_i32), ("heap_max_u", c_i32),
                 ("merge_wide_above", c_i32), ("merge_kernel", c_i32), ("merge_miss", c_i32),
-                ("dense_min_u", c_i32), ("dense_span", c_i32), ("reserved", c_i32 * 1),
+                ("dense_min_u", c_i32), ("dense_span", c_i32), ("dense_span_div", c_i32),
                 ("predictor", c_ptr),
                 ("predictor_margin", c_f64)]
 

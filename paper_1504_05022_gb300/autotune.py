@@ -57,14 +57,15 @@ SPACE = {
     "predictor_margin": [None, 1.15, 1.5, 2.0],  # None = the margin stored with the weights
     "dense_min_u": [0, 16384, 4096, -1],  # 0 = ncols(B) / 8, -1 = no dense-slice rows
     "dense_span": [0, 16384, 10912],      # 0 = the widest slice shared memory holds
+    "dense_span_div": [0, 16, 4],         # 0 = 8: dense when 8 u_i >= the row's column range
 }
 POLICY_PARAMS = {
     "hybrid": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "merge_miss",
-               "initial_cap", "dense_min_u", "dense_span"],
+               "initial_cap", "dense_min_u", "dense_span", "dense_span_div"],
     "learned": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "merge_miss",
-                "predictor_margin", "dense_min_u", "dense_span"],
+                "predictor_margin", "dense_min_u", "dense_span", "dense_span_div"],
     "upper_bound": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "dense_min_u",
-                    "dense_span"],
+                    "dense_span", "dense_span_div"],
 }
 MEMORY_SLACK = 1.05
 

@@ -50,11 +50,11 @@ cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cud
 // ---- which bin-37 rows are dense ----
 // One warp per row: u_i from the stage-1 prefix, and for u_i > 512 the row's column
 // range [lo, hi) (first and last column of every touched B row).  The row is dense when
-// u_i >= dmin (dmin > 0), else when 8 u_i >= hi - lo: its products cover at least an
-// eighth of the columns they can reach, so the dense accumulator's O(hi - lo) clearing
+// u_i >= dmin (dmin > 0), else when div u_i >= hi - lo: its products cover at least a
+// div-th of the columns they can reach, so the dense accumulator's O(hi - lo) clearing
 // and write-out are small beside them.
-__global__ void k_dense_mark(DevCSR A, DevCSR B, const int64_t *__restrict__ S, int64_t dmin, uint8_t *flag,
-                             int32_t *lo, int32_t *hi) {
+__global__ void k_dense_mark(DevCSR A, DevCSR B, const int64_t *__restrict__ S, int64_t dmin, int div,
+                             uint8_t *flag, int32_t *lo, int32_t *hi) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= A.nrows) return;
@@ -80,17 +80,18 @@ __global__ void k_dense_mark(DevCSR A, DevCSR B, const int64_t *__restrict__ S, 
     }
     if (lane == 0) {
         const int64_t span = (int64_t)cmax - cmin + 1;  // u > 0, so some B row is not empty
-        flag[row] = (uint8_t)(dmin > 0 ? u >= dmin : 8 * u >= span);
+        flag[row] = (uint8_t)(dmin > 0 ? u >= dmin : (int64_t)div * u >= span);
         lo[row] = cmin;
         hi[row] = cmax + 1;
     }
 }
 
-cudaError_t launch_dense_mark(const DevCSR &A, const DevCSR &B, const int64_t *S, int64_t dmin, uint8_t *flag,
-                              int32_t *lo, int32_t *hi, cudaStream_t st) {
+cudaError_t launch_dense_mark(const DevCSR &A, const DevCSR &B, const int64_t *S, int64_t dmin, int div,
+                              uint8_t *flag, int32_t *lo, int32_t *hi, cudaStream_t st) {
     if (A.nrows <= 0) return cudaSuccess;
+    if (div < 1) return cudaErrorInvalidValue;
     const int64_t threads = A.nrows * 32;
-    k_dense_mark<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, B, S, dmin, flag, lo, hi);
+    k_dense_mark<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, B, S, dmin, div, flag, lo, hi);
     return cudaGetLastError();
 }
 

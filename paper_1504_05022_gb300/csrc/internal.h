@@ -173,10 +173,10 @@ struct DenseArgs {
     int32_t *soff;         // n K offsets of the slices inside their row of C
 };
 cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cudaStream_t st);
-// per row: flag (1 = dense-slice row: bin 37, and u_i >= dmin if dmin > 0, else 8 u_i >= the
+// per row: flag (1 = dense-slice row: bin 37, and u_i >= dmin if dmin > 0, else div u_i >= the
 // width of its column range) and, for bin-37 rows, the column range [lo, hi)
-cudaError_t launch_dense_mark(const DevCSR &A, const DevCSR &B, const int64_t *S, int64_t dmin, uint8_t *flag,
-                              int32_t *lo, int32_t *hi, cudaStream_t st);
+cudaError_t launch_dense_mark(const DevCSR &A, const DevCSR &B, const int64_t *S, int64_t dmin, int div,
+                              uint8_t *flag, int32_t *lo, int32_t *hi, cudaStream_t st);
 int64_t dense_select_scratch(int64_t m);
 // order[0..nd) = items of the flagged bin-37 rows (larger u first), order[nd..n37) = the rest;
 // rows, rlo, rhi [0..nd) = their rows and column ranges; nd goes to summary->dense_count

@@ -520,8 +520,9 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             SPG_TRY(p->alloc_n(&p->dense_flag, m, LIFE_SYMBOLIC));
             SPG_TRY(p->alloc_n(&p->dense_lo, m, LIFE_SYMBOLIC));
             SPG_TRY(p->alloc_n(&p->dense_hi, m, LIFE_SYMBOLIC));
-            SPG_TRY(launch_dense_mark(p->A, p->B, p->S, p->dense_min_u, p->dense_flag, p->dense_lo, p->dense_hi,
-                                      p->st));
+            SPG_TRY(launch_dense_mark(p->A, p->B, p->S, p->dense_min_u,
+                                      o.dense_span_div > 0 ? o.dense_span_div : 8, p->dense_flag, p->dense_lo,
+                                      p->dense_hi, p->st));
             p->count(SPGEMM_K_OTHER);
         }
         if (o.alloc_policy == SPGEMM_ALLOC_LEARNED) {
