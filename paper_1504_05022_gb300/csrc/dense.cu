@@ -530,26 +530,13 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
     // column order: consecutive threads take consecutive columns, so a warp's stores
     // land in one contiguous run of C
     const int64_t o = c_rp[row] + D.soff[b];
-    constexpr int WU = 4;  // columns per thread in flight
-    for (int x0 = threadIdx.x; x0 < span; x0 += NT * WU) {
-        uint32_t wd[WU];
-        int32_t rk[WU];
-        double vx[WU];
-#pragma unroll
-        for (int k = 0; k < WU; ++k) {
-            const int x = x0 + k * NT;
-            wd[k] = x < span ? Bm[x >> 5] : 0u;  // the same word for the whole warp
-            rk[k] = x < span ? Rd[x >> 5] : 0;
-            vx[k] = x < span ? V[x] : 0.0;
-        }
-#pragma unroll
-        for (int k = 0; k < WU; ++k) {
-            const int x = x0 + k * NT;
-            if ((wd[k] >> (x & 31)) & 1u) {
-                const int64_t pos = o + rk[k] + __popc(wd[k] & ((1u << (x & 31)) - 1u));
-                c_col[pos] = (int32_t)(lo + x);
-                c_val[pos] = vx[k];
-            }
+    for (int x = threadIdx.x; x < span; x += NT) {
+        const uint32_t wd = Bm[x >> 5];  // the same word for the whole warp
+        if (wd == 0u) continue;
+        if ((wd >> (x & 31)) & 1u) {
+            const int64_t pos = o + Rd[x >> 5] + __popc(wd & ((1u << (x & 31)) - 1u));
+            c_col[pos] = (int32_t)(lo + x);
+            c_val[pos] = V[x];
         }
     }
 }

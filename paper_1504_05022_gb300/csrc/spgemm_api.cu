@@ -164,6 +164,7 @@ struct spgemm_plan {
     int32_t *dense_clo = nullptr, *dense_chi = nullptr;  // and their column ranges
     int32_t *dense_bnd = nullptr;         // per B row, K + 1 slice boundaries (K > 1)
     int32_t *dense_cnt = nullptr, *dense_soff = nullptr;
+    cudaEvent_t dense_count_done = nullptr;  // the counts' stream reached the end of the counting pass
     DenseArgs dense_args() const {
         return DenseArgs{dense_order, dense_rows, dense_clo, dense_chi, dense_n, dense_K, dense_W, dense_bnd,
                          dense_cnt, dense_soff};
@@ -263,6 +264,11 @@ struct spgemm_plan {
         return cudaSuccess;
     }
     void release() {
+        if (dense_count_done) {
+            cudaStreamWaitEvent(st, dense_count_done, 0);
+            cudaEventDestroy(dense_count_done);
+            dense_count_done = nullptr;
+        }
         for (spgemm_plan *w : waves) {
             if (w) {
                 w->release();
@@ -856,6 +862,36 @@ fail:
     return status;
 }
 
+// Dense-slice rows: their column counts, launched first in stage 3 on their own
+// stream (unless every kernel is timed), beside the heap, ESC and merge kernels; the
+// event joins them before the row sizes are finalised.
+static spgemm_status launch_dense_counts(spgemm_plan *p) {
+    spgemm_status status = SPGEMM_OK;
+    if (p->dense_n == 0 || p->h_summary.bin_count[BIN_MERGE] == 0) return SPGEMM_OK;
+    {
+        cudaStream_t ds = p->st;
+        if (!p->opts.record_timing) {
+            ds = aux_stream(p->device, DENSE_AUX);
+            if (ds == nullptr) return SPGEMM_ERR_CUDA;
+            cudaEvent_t go = nullptr;
+            SPG_TRY(cudaEventCreateWithFlags(&go, cudaEventDisableTiming));
+            cudaError_t e = cudaEventRecord(go, p->st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, go, 0);
+            cudaEventDestroy(go);
+            SPG_TRY(e);
+            SPG_TRY(cudaEventCreateWithFlags(&p->dense_count_done, cudaEventDisableTiming));
+        }
+        p->time_begin(SPGEMM_K_MERGE);
+        SPG_TRY(launch_dense_count(p->A, p->B, p->dense_args(), p->d_err, ds));
+        p->time_end();
+        p->count(SPGEMM_K_MERGE);
+        if (p->dense_count_done) SPG_TRY(cudaEventRecord(p->dense_count_done, ds));
+    }
+    return SPGEMM_OK;
+fail:
+    return status;
+}
+
 // Bin group 5: the merge kernel over all bin-37 rows.  Plain policies start
 // every row at the initial capacity and go through the progressive rounds.  The
 // learned policy launches each predicted size class with homes of the predicted
@@ -871,29 +907,9 @@ spgemm_status run_bin37(spgemm_plan *p) {
     int32_t *ovf_count = nullptr;
     const int capmax = p->capmax;
     const bool learned = p->opts.alloc_policy == SPGEMM_ALLOC_LEARNED;
-    cudaEvent_t dense_done = nullptr;
+    cudaEvent_t dense_done = p->dense_count_done;
+    p->dense_count_done = nullptr;
     {
-        if (p->dense_n > 0) {
-            // dense-slice rows: their column counts now (on their own stream, beside the merge
-            // launches, unless every kernel is timed), their values once C exists
-            cudaStream_t ds = p->st;
-            if (!p->opts.record_timing) {
-                ds = aux_stream(p->device, DENSE_AUX);
-                if (ds == nullptr) return SPGEMM_ERR_CUDA;
-                cudaEvent_t go = nullptr;
-                SPG_TRY(cudaEventCreateWithFlags(&go, cudaEventDisableTiming));
-                cudaError_t e = cudaEventRecord(go, p->st);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, go, 0);
-                cudaEventDestroy(go);
-                SPG_TRY(e);
-                SPG_TRY(cudaEventCreateWithFlags(&dense_done, cudaEventDisableTiming));
-            }
-            p->time_begin(SPGEMM_K_MERGE);
-            SPG_TRY(launch_dense_count(p->A, p->B, p->dense_args(), p->d_err, ds));
-            p->time_end();
-            p->count(SPGEMM_K_MERGE);
-            if (dense_done) SPG_TRY(cudaEventRecord(dense_done, ds));
-        }
         SPG_TRY(reserve_items(p, n37));
         p->n_items = n37;
         SPG_TRY(p->alloc_n(&ovf_count, 1, LIFE_NUMERIC));
@@ -1060,7 +1076,9 @@ extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
     const int64_t m = p->A.nrows;
     StageArgs a = stage_args(p);
     {
-        // ---- stage 3: bin groups 3 (heap) and 4 (bitonic ESC) ----
+        // ---- stage 3: the dense-slice rows' counts, then bin groups 3 (heap) and 4 (bitonic ESC) ----
+        status = launch_dense_counts(p);
+        if (status != SPGEMM_OK) goto fail;
         SPG_TRY(launch_short_bins(p, a, true));
         // ---- stage 3: bin group 5 (merge, progressive) ----
         status = run_bin37(p);
