@@ -515,6 +515,11 @@ def run_batch(args, world, device):
         "compare": res,
         "clocks": main_clocks,
     }
+    c_bytes = int(arrays["row_nnz"].astype(np.int64).sum()) * 12 + 8 * (int(arrays["u"].shape[0]) + len(pairs))
+    out["memory"]["c_bytes"] = c_bytes
+    out["memory"]["comparison"] = memory_comparison(
+        pairs, c_bytes, "batched_" + head, main,
+        {k: v for k, v in res.items() if isinstance(v, dict) and "peak_bytes" in v})
     return out, pairs
 
 
@@ -648,9 +653,28 @@ def run_ours(args, rank, world, device):
         "compare": {p: brief(m) for p, m in cmp.items()},
         "clocks": main_m["clocks"],
     }
+    out["memory"]["comparison"] = memory_comparison(pairs, out["memory"]["c_bytes"], head, main_m, cmp)
     if chain is not None:
         out["compare"].update(chain)
     return out
+
+
+def memory_comparison(pairs, c_bytes, head, main_m, cmp):
+    """Global memory of the allocation methods, as the paper compares them for C = A*A: the
+    precise method needs the inputs and C only (its nnz(C) comes from a symbolic pre-pass);
+    the others add their temporaries, so each policy's figure is the inputs plus the plan's
+    measured device high-water mark (temporaries and C)."""
+    inputs = 0
+    for A, B in pairs:
+        inputs += A.nnz * 12 + (A.nrows + 1) * 4
+        if B is not None and B is not A:
+            inputs += B.nnz * 12 + (B.nrows + 1) * 4
+    precise = inputs + int(c_bytes)
+    mem = {"unit": "bytes, inputs included", "precise": precise}
+    for name, m in [(head, main_m)] + list(cmp.items()):
+        mem[name] = inputs + int(m["peak_bytes"])
+    mem["ratio_to_precise"] = {k: v / precise for k, v in mem.items() if k not in ("unit", "precise")}
+    return mem
 
 
 def run_e2e(args, spg, pairs, dev, stream, opts, world=1):

@@ -325,7 +325,9 @@ constexpr int DENSE_LONG = DENSE_LONG_MIN;
 
 __host__ __device__ inline int dense_nw4(int W) { return ((W + 31) / 32 + 4) & ~3; }
 
-template <int NT, int MINB>
+// REPLAY: values-only replay; C's columns are already in place, so the flags, the bitmap
+// and the column-order write-out give way to one pass over the slice's known entries.
+template <int NT, int MINB, bool REPLAY>
 __global__ void __launch_bounds__(NT, MINB)
 k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_col, double *c_val, int64_t *err) {
     constexpr int WIN = DENSE_FILL_WIN;
@@ -353,7 +355,8 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
         double2 *v2 = reinterpret_cast<double2 *>(V);
         for (int x = threadIdx.x; x < (span + 1) >> 1; x += NT) v2[x] = make_double2(0.0, 0.0);
         uint4 *f4 = reinterpret_cast<uint4 *>(flag);  // whole 32-column words, as read below
-        for (int q = threadIdx.x; q < 2 * nwords; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (!REPLAY)
+            for (int q = threadIdx.x; q < 2 * nwords; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
     }
     __syncthreads();
     bool bad = false;
@@ -429,7 +432,7 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
                             continue;
                         }
                         atomicAdd(&V[x], a * v[u]);
-                        fl[x] = 1;
+                        if (!REPLAY) fl[x] = 1;
                     }
                 }
             }
@@ -488,7 +491,7 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
                             continue;
                         }
                         V[x] += a * v0[u];
-                        fl[x] = 1;
+                        if (!REPLAY) fl[x] = 1;
                     }
                 }
                 if (j1 != j0) __syncthreads();  // the next part may add into the same columns
@@ -506,6 +509,17 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
             }
         }
         __syncthreads();  // the window's tables are reused
+    }
+    if (REPLAY) {
+        // the slice's entries of C, in place since the product: their values
+        const int64_t o = c_rp[row] + D.soff[b];
+        for (int t = threadIdx.x; t < expected; t += NT) {
+            const int x = (int)(c_col[o + t] - lo);
+            if ((unsigned)x < (unsigned)span) c_val[o + t] = V[x];
+            else bad = true;  // C's columns were changed since the product
+        }
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch((unsigned long long *)err, 6ull);
+        return;
     }
     // flags -> bitmap (32 columns per word), then its rank directory
     for (int w = threadIdx.x; w < nwords; w += NT) {
@@ -582,13 +596,15 @@ cudaError_t launch_dense_rows(const MergeItems &it, const DenseArgs &D, cudaStre
 }
 
 cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs &D, const int64_t *c_rp,
-                              int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st) {
+                              int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st, bool replay) {
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
     const int smem = dense_fill_smem_bytes(D.W);
     // two CTAs per SM when two slices fit the SM's shared memory (64 registers a thread)
-    auto kern = smem <= dense_fill_max_dynamic(2) ? k_dense_fill<DENSE_FILL_NT, 2> : k_dense_fill<DENSE_FILL_NT, 1>;
+    const bool two = smem <= dense_fill_max_dynamic(2);
+    auto kern = replay ? (two ? k_dense_fill<DENSE_FILL_NT, 2, true> : k_dense_fill<DENSE_FILL_NT, 1, true>)
+                       : (two ? k_dense_fill<DENSE_FILL_NT, 2, false> : k_dense_fill<DENSE_FILL_NT, 1, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -188,9 +188,10 @@ cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *
 cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t *err, cudaStream_t st);
 // slice offsets inside the rows, and the dense items' lengths in the work-item table
 cudaError_t launch_dense_rows(const MergeItems &it, const DenseArgs &D, cudaStream_t st);
-// accumulates every (row, slice) and writes it into C at c_rp[row] + soff
+// accumulates every (row, slice) and writes it into C at c_rp[row] + soff; replay: values
+// only, into the entries whose columns are already in C
 cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs &D, const int64_t *c_rp,
-                              int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st);
+                              int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st, bool replay = false);
 int dense_fill_smem_bytes(int W);
 int dense_fill_static_smem();
 int dense_fill_max_dynamic(int per_sm);

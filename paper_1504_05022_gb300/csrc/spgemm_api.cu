@@ -1552,7 +1552,7 @@ extern "C" spgemm_status spgemm_numeric_replay(spgemm_plan *p) {
         }
         if (p->dense_n > 0)
             SPG_TRY(launch_dense_fill(p->A, p->B, p->dense_args(), p->C.row_ptr, p->C.col_idx, p->C.val, p->d_err,
-                                      p->st));
+                                      p->st, true));
     }
     return SPGEMM_OK;
 fail:
