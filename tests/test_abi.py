@@ -82,3 +82,38 @@ def test_argument_errors_without_gpu(lib):
     assert lib.spgemm_symbolic(ctypes.byref(A), ctypes.byref(B), None, None, None, None) == 1
     assert lib.spgemm_numeric(None, None) == 1
     assert lib.spgemm_free(None) == 0
+
+
+def test_every_field_offset_matches_the_c_compiler(tmp_path):
+    """Compiles a C program against include/spgemm.h that prints sizeof and offsetof of every
+    field of the public structs, and compares them with the ctypes mirror."""
+    import shutil
+    from paper_1504_05022_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirror = {"spgemm_csr_in": _lib.CsrIn, "spgemm_csr_out": _lib.CsrOut, "spgemm_opts": _lib.Opts,
+              "spgemm_stats": _lib.Stats, "spgemm_plan_arrays": _lib.PlanArrays}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "spgemm.h"', "int main(void) {"]
+    for cname, cls in mirror.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line:
+            continue
+        cname, what, value = line.split()
+        cls = mirror[cname]
+        if what == "size":
+            assert ctypes.sizeof(cls) == int(value), cname
+        else:
+            assert getattr(cls, what).offset == int(value), (cname, what)
+        seen += 1
+    assert seen == sum(len(c._fields_) + 1 for c in mirror.values())
