@@ -179,7 +179,7 @@ def algorithmic_bytes(A, B, u, rows_sel, row_nnz):
     return int(la.sum()) * 28 + int(u[rows_sel].sum()) * 12 + int(row_nnz[rows_sel].sum()) * 12
 
 
-def policy_opts(policy, tuned_workload=None):
+def policy_opts(policy, tuned_workload=None, value_type="f64"):
     """Library options of a policy name: 'hybrid' = the paper's plain path (256-entry start,
     x2 relaunches), 'upper_bound', 'learned' = trained predictor (committed weights).  With
     tuned_workload, the autotuner's parameters for that workload and policy are applied
@@ -187,7 +187,7 @@ def policy_opts(policy, tuned_workload=None):
     pred = None
     if policy == "learned":
         from paper_1504_05022_gb300.predictor import Predictor
-        pred = Predictor.load()
+        pred = Predictor.load(dtype=value_type)
         opts = pred.opts()
     else:
         opts = {"alloc_policy": policy}
@@ -211,15 +211,18 @@ def tuned_params(args, policy):
     return autotune.load(args.workload, policy)
 
 
-def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=False, tuned=False):
+def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=False, tuned=False,
+            value_type="f64"):
     """W warm-up steps, then K timed steps (CUDA events on the launching stream, L2 flushed
-    between steps outside the events).  Returns the per-step figures."""
+    between steps outside the events).  Returns the per-step figures.  value_type "f32": the
+    same product in single precision (values rounded to float, the float library)."""
     import torch
-    opts, keep = policy_opts(policy, args.workload if tuned and args.tuned else None)
+    opts, keep = policy_opts(policy, args.workload if tuned and args.tuned else None, value_type)
     timing_opts = dict(opts, record_timing=True)  # per-kernel split, taken in one extra untimed step
-    Ad = [spg.CSR.from_host(A, device=dev, rowptr_dtype=torch.int32) for A, _ in pairs]
-    Bd = [spg.CSR.from_host(B, device=dev, rowptr_dtype=torch.int32) if B is not None and B is not A else None
-          for A, B in pairs]
+    vdt = torch.float32 if value_type == "f32" else torch.float64
+    Ad = [spg.CSR.from_host(A, device=dev, rowptr_dtype=torch.int32, dtype=vdt) for A, _ in pairs]
+    Bd = [spg.CSR.from_host(B, device=dev, rowptr_dtype=torch.int32, dtype=vdt)
+          if B is not None and B is not A else None for A, B in pairs]
 
     def step(o=opts):
         prev = None
@@ -619,6 +622,9 @@ def run_ours(args, rank, world, device):
     others = [p for p in ("hybrid", "upper_bound") if p != head] if not args.single_policy else []
     main_m = measure(args, spg, pairs, dev, stream, head, flush, world, sample_clocks=True, tuned=True)
     cmp = {p: measure(args, spg, pairs, dev, stream, p, flush, world) for p in others}
+    if not args.single_policy:
+        # the same product in single precision (the paper's SpSGEMM), same policy and parameters
+        cmp[head + "_f32"] = measure(args, spg, pairs, dev, stream, head, flush, world, tuned=True, value_type="f32")
     e2e_opts, e2e_keep = policy_opts(head, args.workload if args.tuned else None)  # keeps the predictor alive
     e2e = run_e2e(args, spg, pairs, dev, stream, e2e_opts, world)
     chain = galerkin_graph(args, spg, dev, stream, flush, e2e_opts, world) if args.workload == "galerkin64" else None
@@ -653,7 +659,8 @@ def run_ours(args, rank, world, device):
         "compare": {p: brief(m) for p, m in cmp.items()},
         "clocks": main_m["clocks"],
     }
-    out["memory"]["comparison"] = memory_comparison(pairs, out["memory"]["c_bytes"], head, main_m, cmp)
+    out["memory"]["comparison"] = memory_comparison(pairs, out["memory"]["c_bytes"], head, main_m,
+                                                    {k: m for k, m in cmp.items() if not k.endswith("_f32")})
     if chain is not None:
         out["compare"].update(chain)
     return out

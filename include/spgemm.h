@@ -43,6 +43,15 @@ typedef enum spgemm_status {
     SPGEMM_ERR_INTERNAL = 7     /* an internal consistency check failed */
 } spgemm_status;
 
+/* Value type of A, B and C.  The default library (libspgemm.so) computes in double; the
+   single-precision library (libspgemm_f32.so, built from the same sources with SPGEMM_FLOAT
+   defined) has the same entry points with float values (the paper's SpSGEMM). */
+#ifdef SPGEMM_FLOAT
+typedef float spgemm_value_t;
+#else
+typedef double spgemm_value_t;
+#endif
+
 /*
  * Input matrix in CSR format (Section 2.1): row_ptr has nrows+1 entries with
  * row_ptr[0] = 0 and row_ptr[nrows] = nnz; row i holds col_idx/val entries
@@ -60,7 +69,7 @@ typedef struct spgemm_csr_in {
     const void *row_ptr;
     int32_t rowptr_bits;
     const int32_t *col_idx;
-    const double *val;
+    const spgemm_value_t *val;
 } spgemm_csr_in;
 
 /*
@@ -76,7 +85,7 @@ typedef struct spgemm_csr_out {
     int64_t nnz;
     int64_t *row_ptr;
     int32_t *col_idx;
-    double *val;
+    spgemm_value_t *val;
 } spgemm_csr_out;
 
 /* Memory pre-allocation policy for the temporary matrix C~ (Section 3.1). */

@@ -1,8 +1,10 @@
-"""Builds the CUDA library libspgemm.so in-tree for sm_103a with nvcc.
+"""Builds the CUDA libraries in-tree for sm_103a with nvcc.
 
-Each .cu translation unit is compiled in parallel, then linked into one shared
-object under paper_1504_05022_gb300/_build/.  No CMake, no torch extension
-machinery: the library is a plain C ABI (include/spgemm.h)."""
+libspgemm.so computes in double, libspgemm_f32.so (the same sources with SPGEMM_FLOAT
+defined: the same C ABI with float values) in single precision.  Each .cu translation
+unit of both is compiled in parallel, then linked into one shared object each under
+paper_1504_05022_gb300/_build/.  No CMake, no torch extension machinery: the libraries
+are a plain C ABI (include/spgemm.h)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -17,6 +19,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libspgemm.so")
+LIB_F32 = os.path.join(BUILD, "libspgemm_f32.so")
+# value type -> (library, object directory, extra nvcc flags)
+VARIANTS = {"f64": (LIB, BUILD, []), "f32": (LIB_F32, os.path.join(BUILD, "f32"), ["-DSPGEMM_FLOAT"])}
 
 SOURCES = ["stage12.cu", "heap.cu", "esc.cu", "merge.cu", "merge_bm.cu", "dense.cu", "arrange.cu", "predictor.cu", "replay.cu", "batched.cu",
            "spgemm_api.cu", "noalloc.cu"]
@@ -47,19 +52,24 @@ def _digest() -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link libspgemm.so if any source changed; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "stamp.txt")
-    dig = _digest() + repr(tuple(extra_flags))
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
-        with open(stamp) as f:
-            if f.read() == dig:
-                return LIB
+    """Compile and link both libraries where a source changed; returns libspgemm.so's path."""
     nvcc = _nvcc()
-    flags = _flags(extra_flags)
+    todo = []
+    for name, (lib, odir, vflags) in VARIANTS.items():
+        os.makedirs(odir, exist_ok=True)
+        stamp = os.path.join(odir, "stamp.txt" if name == "f64" else "stamp_f32.txt")
+        dig = _digest() + repr(tuple(extra_flags) + tuple(vflags))
+        if not force and os.path.exists(lib) and os.path.exists(stamp):
+            with open(stamp) as f:
+                if f.read() == dig:
+                    continue
+        todo.append((lib, odir, _flags(list(extra_flags) + vflags), stamp, dig))
+    if not todo:
+        return LIB
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+    def compile_one(job):
+        src, odir, flags = job
+        obj = os.path.join(odir, src.replace(".cu", ".o"))
         cmd = [nvcc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -68,16 +78,19 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(r.stdout, r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xlinker", "--no-undefined"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    with open(stamp, "w") as f:
-        f.write(dig)
+    jobs = [(src, odir, flags) for (_, odir, flags, _, _) in todo for src in SOURCES]
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for k, (lib, odir, flags, stamp, dig) in enumerate(todo):
+        mine = objs[k * len(SOURCES):(k + 1) * len(SOURCES)]
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + mine + ["-Xlinker", "--no-undefined"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
+        with open(stamp, "w") as f:
+            f.write(dig)
     return LIB
 
 

@@ -1,7 +1,8 @@
 """ctypes mirror of include/spgemm.h (argument marshalling only).
 
-Loads paper_1504_05022_gb300/_build/libspgemm.so.  If the library is missing the
-import fails loudly: there is no CPU fallback."""
+Loads paper_1504_05022_gb300/_build/libspgemm.so (double values) or libspgemm_f32.so
+(float values, the same entry points).  If a library is missing the call fails loudly:
+there is no CPU fallback."""
 from __future__ import annotations
 
 import ctypes
@@ -90,29 +91,38 @@ SIGNATURES = {
 
 MLP_FEATURES, MLP_HIDDEN, MLP_CLASSES, MLP_NUM_PARAMS, MLP_NUM_TOTAL = 8, 32, 16, 1905, 1921
 
-_lib = None
+_lib = None          # the double-precision library, once loaded
+_libs = {}           # value type ("f64", "f32") -> loaded library
+VALUE_TYPES = ("f64", "f32")
 
 
-def lib_path() -> str:
-    return _build.LIB
+def lib_path(dtype: str = "f64") -> str:
+    return _build.LIB_F32 if dtype == "f32" else _build.LIB
 
 
-def load(build_if_missing: bool = True):
-    """Returns the loaded library.  Builds it first when missing and a compiler exists."""
+def load(build_if_missing: bool = True, dtype: str = "f64"):
+    """Returns the loaded library for the value type ("f64": libspgemm.so, "f32":
+    libspgemm_f32.so).  Builds the libraries first when missing and a compiler exists."""
     global _lib
-    if _lib is not None:
+    if dtype not in VALUE_TYPES:
+        raise ValueError(f"value type must be one of {VALUE_TYPES}")
+    if dtype == "f64" and _lib is not None:
         return _lib
-    path = lib_path()
+    if dtype in _libs:
+        return _libs[dtype]
+    path = lib_path(dtype)
     if not os.path.exists(path):
         if not build_if_missing:
-            raise ImportError(f"libspgemm.so not built ({path}); run __graft_entry__.build()")
+            raise ImportError(f"{os.path.basename(path)} not built ({path}); run __graft_entry__.build()")
         _build.build()
     lib = ctypes.CDLL(path)
     for name, (args, res) in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = res
-    _lib = lib
+    _libs[dtype] = lib
+    if dtype == "f64":
+        _lib = lib
     return lib
 
 

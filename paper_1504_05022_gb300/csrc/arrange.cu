@@ -27,7 +27,7 @@ constexpr int ARR_NT = 256;
 
 __global__ void __launch_bounds__(ARR_NT)
 k_arrange_short(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows, const uint8_t *__restrict__ bin,
-                const int64_t *__restrict__ c_rp, int32_t *__restrict__ c_col, double *__restrict__ c_val) {
+                const int64_t *__restrict__ c_rp, int32_t *__restrict__ c_col, val_t *__restrict__ c_val) {
     const int64_t wg = ((int64_t)blockIdx.x * ARR_NT + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wg >= nrows) return;
@@ -66,7 +66,7 @@ k_arrange_short(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows, co
 
 cudaError_t launch_arrange_short(const StageArgs &a, const int32_t *rows, int64_t nrows,
                                  const uint8_t *bin, const int64_t *c_rp, int32_t *c_col,
-                                 double *c_val, cudaStream_t st) {
+                                 val_t *c_val, cudaStream_t st) {
     if (nrows <= 0) return cudaSuccess;
     const int64_t threads = nrows * 32;
     k_arrange_short<<<(unsigned)((threads + ARR_NT - 1) / ARR_NT), ARR_NT, 0, st>>>(a, rows, nrows, bin, c_rp,
@@ -79,7 +79,7 @@ cudaError_t launch_arrange_short(const StageArgs &a, const int32_t *rows, int64_
 // Rows of the dense-slice kernels are already in C.
 __global__ void __launch_bounds__(ARR_NT)
 k_arrange_long(MergeItems it, const int64_t *__restrict__ c_rp, int32_t *__restrict__ c_col,
-               double *__restrict__ c_val) {
+               val_t *__restrict__ c_val) {
     constexpr int LEAF_BUF = 128, STACK = 64;
     __shared__ int leaves[LEAF_BUF];
     __shared__ int stack[STACK];
@@ -114,7 +114,7 @@ k_arrange_long(MergeItems it, const int64_t *__restrict__ c_rp, int32_t *__restr
             const int x = leaves[l];
             const int64_t n = it.len[x];
             const int32_t *sc = it.home_col[x];
-            const double *sv = it.home_val[x];
+            const val_t *sv = it.home_val[x];
             for (int64_t t = threadIdx.x; t < n; t += ARR_NT) {
                 c_col[o + t] = sc[t];
                 c_val[o + t] = sv[t];
@@ -126,7 +126,7 @@ k_arrange_long(MergeItems it, const int64_t *__restrict__ c_rp, int32_t *__restr
 }
 
 cudaError_t launch_arrange_long(const MergeItems &it, int64_t n37, const int64_t *c_rp, int32_t *c_col,
-                                double *c_val, cudaStream_t st) {
+                                val_t *c_val, cudaStream_t st) {
     if (n37 <= 0) return cudaSuccess;
     k_arrange_long<<<(unsigned)n37, ARR_NT, 0, st>>>(it, c_rp, c_col, c_val);
     return cudaGetLastError();

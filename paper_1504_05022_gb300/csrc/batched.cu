@@ -46,8 +46,8 @@ __global__ void k_concat_rp(const PairDesc *d, int64_t npairs, const int64_t *mo
 
 // Entries of the concatenated A (columns shifted into the pair's block) and B.
 __global__ void k_concat_entries(const PairDesc *d, int64_t npairs, const int64_t *annz_off, const int64_t *bnnz_off,
-                                 int64_t annz, int64_t bnnz, int32_t *a_col, double *a_val, int32_t *b_col,
-                                 double *b_val, int values_only) {
+                                 int64_t annz, int64_t bnnz, int32_t *a_col, val_t *a_val, int32_t *b_col,
+                                 val_t *b_val, int values_only) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < annz) {
         const int i = find_pair(annz_off, npairs, t);
@@ -65,8 +65,8 @@ __global__ void k_concat_entries(const PairDesc *d, int64_t npairs, const int64_
 
 cudaError_t launch_concat(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *koff,
                           const int64_t *annz_off, const int64_t *bnnz_off, int64_t M, int64_t K, int64_t annz,
-                          int64_t bnnz, int64_t *a_rp, int32_t *a_col, double *a_val, int64_t *b_rp, int32_t *b_col,
-                          double *b_val, bool values_only, cudaStream_t st) {
+                          int64_t bnnz, int64_t *a_rp, int32_t *a_col, val_t *a_val, int64_t *b_rp, int32_t *b_col,
+                          val_t *b_val, bool values_only, cudaStream_t st) {
     if (npairs <= 0) return cudaSuccess;
     if (!values_only) {
         const int64_t rmax = (M > K ? M : K) + 1;

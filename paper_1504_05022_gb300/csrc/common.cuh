@@ -6,6 +6,8 @@
 #include <climits>
 #include <cuda_runtime.h>
 
+#include "internal.h"
+
 #define SPG_DEV __device__ __forceinline__
 #define SPG_FULL 0xffffffffu
 
@@ -199,7 +201,7 @@ SPG_DEV int bitmap_pos(const uint32_t *Bm, const int32_t *Rd, int x) {
 // that a chunk to its left still has to read.  Every thread of the block must
 // call it; it ends with a barrier.
 template <int NT, int IPT>
-SPG_DEV void merge_inplace_rtl(int32_t *xk, double *xv, int nx, const int32_t *yk, const double *yv,
+SPG_DEV void merge_inplace_rtl(int32_t *xk, val_t *xv, int nx, const int32_t *yk, const val_t *yv,
                                int ny) {
     if (ny == 0) return;
     const int n = nx + ny;
@@ -207,7 +209,7 @@ SPG_DEV void merge_inplace_rtl(int32_t *xk, double *xv, int nx, const int32_t *y
     for (int hi = n; hi > 0; hi -= CH) {
         const int lo = hi > CH ? hi - CH : 0;
         int32_t rk[IPT];
-        double rv[IPT];
+        val_t rv[IPT];
         const int d0 = lo + threadIdx.x * IPT;
         int cnt = 0;
         if (d0 < hi) {
@@ -234,8 +236,8 @@ SPG_DEV void merge_inplace_rtl(int32_t *xk, double *xv, int nx, const int32_t *y
 
 // Out-of-place stable merge of a and b into out (na + nb entries).  All threads call.
 template <int NT>
-SPG_DEV void merge_into(const int32_t *ak, const double *av, int na, const int32_t *bk,
-                        const double *bv, int nb, int32_t *ok, double *ov) {
+SPG_DEV void merge_into(const int32_t *ak, const val_t *av, int na, const int32_t *bk,
+                        const val_t *bv, int nb, int32_t *ok, val_t *ov) {
     const int n = na + nb;
     const int ipt = (n + NT - 1) / NT;
     const int d0 = threadIdx.x * ipt;

@@ -175,7 +175,7 @@ constexpr int DENSE_UN = 4;
 
 template <int NT, int WIN, bool VALS, typename F>
 SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int row, int s, int64_t *wbs,
-                          int32_t *wlen, int64_t *cscan, double *wa, int64_t *scan64, F f) {
+                          int32_t *wlen, int64_t *cscan, val_t *wa, int64_t *scan64, F f) {
     constexpr int NW = NT / 32;
     const int lane = lane_id(), wid = warp_id();
     const int64_t a0 = A.rp[row], a1 = A.rp[row + 1];
@@ -329,12 +329,12 @@ __host__ __device__ inline int dense_nw4(int W) { return ((W + 31) / 32 + 4) & ~
 // and the column-order write-out give way to one pass over the slice's known entries.
 template <int NT, int MINB, bool REPLAY>
 __global__ void __launch_bounds__(NT, MINB)
-k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_col, double *c_val, int64_t *err) {
+k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_col, val_t *c_val, int64_t *err) {
     constexpr int WIN = DENSE_FILL_WIN;
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char df_smem[];
     __shared__ int64_t wbs[WIN], cscan[WIN], scan64[NT / 32 + 1];
-    __shared__ double wa[WIN];
+    __shared__ val_t wa[WIN];
     __shared__ int32_t wlen[WIN], lidx[WIN], scan32[NT / 32 + 1];
     const int64_t b = blockIdx.x;
     const int expected = D.cnt[b];
@@ -347,13 +347,15 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
     const int span = (int)(min(min((int64_t)(s + 1) * D.W, B.ncols), (int64_t)D.chi[d]) - lo);
     const int nwords = (span + 31) >> 5;
     const int nw4 = dense_nw4(D.W);
-    double *V = reinterpret_cast<double *>(df_smem);
+    val_t *V = reinterpret_cast<val_t *>(df_smem);
     uint8_t *flag = reinterpret_cast<uint8_t *>(V + D.W);
     uint32_t *Bm = reinterpret_cast<uint32_t *>(flag + D.W);  // D.W is a multiple of 32
     int32_t *Rd = reinterpret_cast<int32_t *>(Bm + nw4);
     {
-        double2 *v2 = reinterpret_cast<double2 *>(V);
-        for (int x = threadIdx.x; x < (span + 1) >> 1; x += NT) v2[x] = make_double2(0.0, 0.0);
+        // V's first span sums, in whole 16-byte groups (W sums fill a multiple of 16 bytes)
+        uint4 *z4 = reinterpret_cast<uint4 *>(V);
+        const int nz = (int)((span * sizeof(val_t) + 15) / 16);
+        for (int q = threadIdx.x; q < nz; q += NT) z4[q] = make_uint4(0u, 0u, 0u, 0u);
         uint4 *f4 = reinterpret_cast<uint4 *>(flag);  // whole 32-column words, as read below
         if (!REPLAY)
             for (int q = threadIdx.x; q < 2 * nwords; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
@@ -413,10 +415,10 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
                 const int64_t off = (c - cscan[t]) * DENSE_CH;
                 const int64_t p0 = wbs[t] + off;
                 const int n = (int)min((int64_t)DENSE_CH, (int64_t)wlen[t] - off);
-                const double a = wa[t];
+                const val_t a = wa[t];
                 for (int i = lane; i < n; i += 32 * DENSE_UN) {
                     int32_t cc[DENSE_UN];
-                    double v[DENSE_UN];
+                    val_t v[DENSE_UN];
 #pragma unroll
                     for (int u = 0; u < DENSE_UN; ++u)
                         if (i + 32 * u < n) cc[u] = __ldg(B.col + p0 + i + 32 * u);
@@ -446,9 +448,9 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
             constexpr int RND = NT * DENSE_UN;
             // rounds r0 (being added), r1 and r2 (loading); part index nlong: no round
             int32_t c0[DENSE_UN], c1[DENSE_UN], c2[DENSE_UN];
-            double v0[DENSE_UN], v1[DENSE_UN], v2[DENSE_UN];
+            val_t v0[DENSE_UN], v1[DENSE_UN], v2[DENSE_UN];
             int j0 = 0, o0 = 0, j1, o1, j2, o2;
-            auto load = [&](int32_t (&cc)[DENSE_UN], double (&vv)[DENSE_UN], int j, int i0) {
+            auto load = [&](int32_t (&cc)[DENSE_UN], val_t (&vv)[DENSE_UN], int j, int i0) {
                 if (j >= nlong) return;
                 const int t = lidx[j];
                 const int64_t p0 = wbs[t] + i0;
@@ -481,7 +483,7 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
                 {
                     const int t = lidx[j0];
                     const int n = wlen[t] - o0;
-                    const double a = wa[t];
+                    const val_t a = wa[t];
 #pragma unroll
                     for (int u = 0; u < DENSE_UN; ++u) {
                         if ((int)threadIdx.x + NT * u >= n) continue;
@@ -562,7 +564,7 @@ constexpr int DENSE_COUNT_NT = 256;
 constexpr int DENSE_FILL_NT = DENSE_FILL_THREADS;
 
 int dense_fill_smem_bytes(int W) {
-    return (int)((sizeof(double) + 1) * (size_t)W + 2 * sizeof(int32_t) * (size_t)dense_nw4(W));
+    return (int)((sizeof(val_t) + 1) * (size_t)W + 2 * sizeof(int32_t) * (size_t)dense_nw4(W));
 }
 
 // Largest dynamic shared memory of a fill CTA when `per_sm` of them share an SM
@@ -573,7 +575,7 @@ int dense_fill_max_dynamic(int per_sm) {
 }
 
 int dense_fill_static_smem() {
-    return (int)(DENSE_FILL_WIN * (2 * sizeof(int64_t) + sizeof(double) + 2 * sizeof(int32_t)) +
+    return (int)(DENSE_FILL_WIN * (2 * sizeof(int64_t) + sizeof(val_t) + 2 * sizeof(int32_t)) +
                  (DENSE_FILL_NT / 32 + 1) * 12 + 64);
 }
 
@@ -596,7 +598,7 @@ cudaError_t launch_dense_rows(const MergeItems &it, const DenseArgs &D, cudaStre
 }
 
 cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs &D, const int64_t *c_rp,
-                              int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st, bool replay) {
+                              int32_t *c_col, val_t *c_val, int64_t *err, cudaStream_t st, bool replay) {
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;

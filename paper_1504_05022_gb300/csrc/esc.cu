@@ -23,16 +23,16 @@ __global__ void __launch_bounds__(ESC_WARPS * 32)
 k_esc(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows) {
     constexpr int N = 32 * E;
     __shared__ int32_t sk[ESC_WARPS][N];
-    __shared__ double sv[ESC_WARPS][N];
+    __shared__ val_t sv[ESC_WARPS][N];
     __shared__ int64_t sbs[ESC_WARPS][32];
     __shared__ int32_t soff[ESC_WARPS][33];
-    __shared__ double sa[ESC_WARPS][32];
+    __shared__ val_t sa[ESC_WARPS][32];
     const int lane = lane_id(), w = warp_id();
     const int64_t t = (int64_t)blockIdx.x * ESC_WARPS + w;
     if (t >= nrows) return;  // whole warp leaves together
     const int row = rows[t];
     int32_t *wk = sk[w];
-    double *wv = sv[w];
+    val_t *wv = sv[w];
 
     // ---- expand ----
     int filled = 0;
@@ -41,7 +41,7 @@ k_esc(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows) {
         const int64_t p = base + lane;
         int32_t len = 0;
         int64_t bs = 0;
-        double av = 0.0;
+        val_t av = 0.0;
         if (p < a1) {
             const int32_t j = a.A.col[p];
             bs = a.B.rp[j];
@@ -74,7 +74,7 @@ k_esc(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows) {
     __syncwarp();
 
     int32_t key[E];
-    double val[E];
+    val_t val[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         key[e] = wk[lane * E + e];
@@ -92,7 +92,7 @@ k_esc(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int32_t pk = __shfl_xor_sync(SPG_FULL, key[e], lj);
-                    const double pv = __shfl_xor_sync(SPG_FULL, val[e], lj);
+                    const val_t pv = __shfl_xor_sync(SPG_FULL, val[e], lj);
                     const bool up = ((lane * E + e) & k) == 0;
                     const bool take = (lower == up) ? (pk < key[e]) : (pk > key[e]);
                     if (take) {
@@ -111,7 +111,7 @@ k_esc(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows) {
                             const int32_t tk = key[e];
                             key[e] = key[e2];
                             key[e2] = tk;
-                            const double tv = val[e];
+                            const val_t tv = val[e];
                             val[e] = val[e2];
                             val[e2] = tv;
                         }
@@ -129,18 +129,18 @@ k_esc(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows) {
     int32_t prev_last = __shfl_up_sync(SPG_FULL, last, 1);
     const bool cont = (lane > 0) && (prev_last == first);
     // R = running sum of the run that ends this lane; flag = a run starts in this lane
-    double R = val[E - 1];
+    val_t R = val[E - 1];
     bool f = !((first == last) && cont);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const double Rn = __shfl_up_sync(SPG_FULL, R, d);
+        const val_t Rn = __shfl_up_sync(SPG_FULL, R, d);
         const bool fn = __shfl_up_sync(SPG_FULL, (int)f, d) != 0;
         if (lane >= d && !f) {
             R += Rn;
             f = fn;
         }
     }
-    const double carry = __shfl_up_sync(SPG_FULL, R, 1);
+    const val_t carry = __shfl_up_sync(SPG_FULL, R, 1);
     if (cont) {
 #pragma unroll
         for (int e = 0; e < E; ++e)

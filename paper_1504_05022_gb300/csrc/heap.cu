@@ -15,8 +15,8 @@ namespace spg {
 template <int NT>
 __global__ void __launch_bounds__(NT)
 k_heap(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows, int slots) {
-    extern __shared__ double heap_smem[];
-    double *hv = heap_smem;
+    extern __shared__ val_t heap_smem[];
+    val_t *hv = heap_smem;
     int32_t *hk = reinterpret_cast<int32_t *>(heap_smem + (size_t)slots * NT);
     const int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (t >= nrows) return;
@@ -28,7 +28,7 @@ k_heap(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows, int slots) 
     const int64_t a0 = a.A.rp[row], a1 = a.A.rp[row + 1];
     for (int64_t p = a0; p < a1; ++p) {
         const int32_t j = a.A.col[p];
-        const double av = a.A.val[p];
+        const val_t av = a.A.val[p];
         const int64_t b0 = a.B.rp[j], b1 = a.B.rp[j + 1];
         for (int64_t q = b0; q < b1 && n < slots; ++q) {
             HK(n) = a.B.col[q];
@@ -40,7 +40,7 @@ k_heap(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows, int slots) 
     for (int s = n / 2 - 1; s >= 0; --s) {
         int c = s;
         const int32_t k = HK(c);
-        const double v = HV(c);
+        const val_t v = HV(c);
         while (true) {
             int l = 2 * c + 1;
             if (l >= n) break;
@@ -58,11 +58,11 @@ k_heap(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows, int slots) 
     int hn = n, rs = n;
     while (hn > 0) {
         const int32_t key = HK(0);
-        const double val = HV(0);
+        const val_t val = HV(0);
         --hn;
         if (hn > 0) {
             const int32_t k = HK(hn);
-            const double v = HV(hn);
+            const val_t v = HV(hn);
             int c = 0;
             while (true) {
                 int l = 2 * c + 1;
@@ -99,7 +99,7 @@ k_heap(StageArgs a, const int32_t *__restrict__ rows, int64_t nrows, int slots) 
 cudaError_t launch_heap(const StageArgs &a, const int32_t *rows, int64_t nrows, int slots, int nt,
                         cudaStream_t st) {
     if (nrows <= 0) return cudaSuccess;
-    const size_t smem = (size_t)slots * nt * (sizeof(double) + sizeof(int32_t));
+    const size_t smem = (size_t)slots * nt * (sizeof(val_t) + sizeof(int32_t));
     const unsigned grid = (unsigned)((nrows + nt - 1) / nt);
     auto go = [&](auto kern) -> cudaError_t {
         if (smem > 48 * 1024) {

@@ -7,6 +7,14 @@
 
 namespace spg {
 
+// Value type of A, B and C: double in the default build, float in the single-precision
+// build (compiled with SPGEMM_FLOAT, the same entry points).
+#ifdef SPGEMM_FLOAT
+using val_t = float;
+#else
+using val_t = double;
+#endif
+
 constexpr int NUM_BINS = 38;
 constexpr int BIN_HEAP_LO = 2, BIN_HEAP_HI = 32;  // bin group 3 (Section 4.1)
 constexpr int BIN_ESC_LO = 33, BIN_ESC_HI = 36;   // bin group 4
@@ -20,7 +28,7 @@ struct DevCSR {
     int64_t nrows, ncols, nnz;
     const int64_t *rp;
     const int32_t *col;
-    const double *val;
+    const val_t *val;
 };
 
 // Host-visible summary written by stage 2 (copied back in one transfer).
@@ -80,7 +88,7 @@ struct StageArgs {
     DevCSR A, B;
     const int64_t *ctil_rp;
     int32_t *ctil_col;
-    double *ctil_val;
+    val_t *ctil_val;
     int32_t *nnzc;
 };
 
@@ -99,10 +107,10 @@ struct MergeItems {
     int32_t *clo;        // first column of the item's range
     int32_t *chi;        // end of the range (exclusive); INT32_MAX = unbounded
     int32_t **src_col;   // sorted sequence to reload when the item (re)starts
-    double **src_val;
+    val_t **src_val;
     int32_t *src_len;
     int32_t **home_col;  // where the item's sequence is written
-    double **home_val;
+    val_t **home_val;
     int64_t *home_cap;
     int32_t *len;        // final length (leaves)
     int64_t *ck_entry;   // checkpoint: A-entry index relative to the row start
@@ -118,12 +126,12 @@ struct MergeLaunch {
     int batch;               // products per batch
     int level1;              // 1: level-1 mode (global result + shared level-1 sequence)
     int32_t *pool_col;       // per-work-item homes of capacity pool_cap (may be null)
-    double *pool_val;
+    val_t *pool_val;
     int64_t pool_cap;
     const int64_t *g_off;    // level-1: per-work-item offset of two global buffers
     const int64_t *g_cap;    //          and their capacity
     int32_t *g_col;
-    double *g_val;
+    val_t *g_val;
     int32_t *ovf_list;       // items that overflowed
     int32_t *ovf_count;
     int64_t *err;            // device error word
@@ -145,11 +153,11 @@ int merge_batch_limit(int cap, int wide_above);
 int merge_max_cap(int batch, int smem_limit, int wide_above);
 cudaError_t launch_merge(const StageArgs &a, const MergeItems &it, const MergeLaunch &L, cudaStream_t st);
 cudaError_t launch_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
-                              double *ctil_val, const MergeItems &it, cudaStream_t st);
+                              val_t *ctil_val, const MergeItems &it, cudaStream_t st);
 // splits the items listed in ovf (count n) into children first_new + 2i, first_new + 2i + 1;
 // right child i gets slot i of the pool (n slots of pool_cap entries)
 cudaError_t launch_split(const int32_t *ovf, int64_t n, int64_t first_new, const MergeItems &it,
-                         int32_t *pool_col, double *pool_val, int64_t pool_cap, cudaStream_t st);
+                         int32_t *pool_col, val_t *pool_val, int64_t pool_cap, cudaStream_t st);
 // nnz(c_i) of every bin-37 row = summed lengths of its leaves
 cudaError_t launch_finalize37(int64_t n37, const MergeItems &it, int32_t *nnzc, int64_t *err, cudaStream_t st);
 // level-1 buffer sizing: per work item cap = min(u_row, ncols_B) (two buffers each)
@@ -191,7 +199,7 @@ cudaError_t launch_dense_rows(const MergeItems &it, const DenseArgs &D, cudaStre
 // accumulates every (row, slice) and writes it into C at c_rp[row] + soff; replay: values
 // only, into the entries whose columns are already in C
 cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs &D, const int64_t *c_rp,
-                              int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st, bool replay = false);
+                              int32_t *c_col, val_t *c_val, int64_t *err, cudaStream_t st, bool replay = false);
 int dense_fill_smem_bytes(int W);
 int dense_fill_static_smem();
 int dense_fill_max_dynamic(int per_sm);
@@ -205,7 +213,7 @@ struct ReplayLeaves {
 };
 constexpr int NUM_REPLAY_CLASSES = 3;
 cudaError_t launch_replay(const StageArgs &a, ReplayLeaves lv, const int32_t *order, int64_t n, int cap,
-                          int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st);
+                          int32_t *c_col, val_t *c_val, int64_t *err, cudaStream_t st);
 cudaError_t launch_replay_leaves(int64_t n37, const MergeItems &it, const int64_t *c_rp, const int32_t *class_cap,
                                  int ncls, int32_t *count, int32_t *start, int32_t *cursor, const ReplayLeaves &lv,
                                  int32_t *order, int64_t *err, bool scatter, cudaStream_t st);
@@ -214,7 +222,7 @@ cudaError_t launch_replay_leaves(int64_t n37, const MergeItems &it, const int64_
 struct PairDesc {
     const void *a_rp, *b_rp;
     const int32_t *a_col, *b_col;
-    const double *a_val, *b_val;
+    const val_t *a_val, *b_val;
     int32_t a_bits, b_bits;
     int64_t m, k, n;             // A_i is m x k, B_i is k x n
     int64_t moff, koff;          // row offset of A_i and B_i in the concatenation
@@ -223,8 +231,8 @@ struct PairDesc {
 };
 cudaError_t launch_concat(const PairDesc *d, int64_t npairs, const int64_t *moff, const int64_t *koff,
                           const int64_t *annz_off, const int64_t *bnnz_off, int64_t M, int64_t K, int64_t annz,
-                          int64_t bnnz, int64_t *a_rp, int32_t *a_col, double *a_val, int64_t *b_rp, int32_t *b_col,
-                          double *b_val, bool values_only, cudaStream_t st);
+                          int64_t bnnz, int64_t *a_rp, int32_t *a_col, val_t *a_val, int64_t *b_rp, int32_t *b_col,
+                          val_t *b_val, bool values_only, cudaStream_t st);
 cudaError_t launch_gather_first(const PairDesc *d, int64_t npairs, const int64_t *c_rp, int64_t M, int64_t *out,
                                 cudaStream_t st);
 cudaError_t launch_pair_products(const PairDesc *d, int64_t npairs, int64_t *prod, int64_t *clow,
@@ -237,8 +245,8 @@ cudaError_t launch_row_scan(int64_t m, const int32_t *nnzc, int64_t *c_rp, int64
                             cudaStream_t st);
 cudaError_t launch_arrange_short(const StageArgs &a, const int32_t *rows, int64_t nrows,
                                  const uint8_t *bin, const int64_t *c_rp, int32_t *c_col,
-                                 double *c_val, cudaStream_t st);
+                                 val_t *c_val, cudaStream_t st);
 cudaError_t launch_arrange_long(const MergeItems &it, int64_t n37, const int64_t *c_rp, int32_t *c_col,
-                                double *c_val, cudaStream_t st);
+                                val_t *c_val, cudaStream_t st);
 
 }  // namespace spg

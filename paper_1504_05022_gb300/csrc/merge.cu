@@ -37,7 +37,7 @@ constexpr int MERGE_MAX_IPT = 4;   // products per thread per batch: batch <= NT
 constexpr int MERGE_TN_MAX = 2048; // pending-set capacity
 
 struct MergeSmem {
-    double *Rv, *Nv, *Sav, *Sbv, *wa;
+    val_t *Rv, *Nv, *Sav, *Sbv, *wa;
     int64_t *wbs, *wscan;
     int32_t *Rk, *Nk, *Sak, *Sbk, *pf, *runoff;
 };
@@ -55,11 +55,11 @@ __host__ __device__ inline size_t merge_layout(int cap, int kb, int W, unsigned 
         return base ? base + o : nullptr;
     };
     unsigned char *p;
-    p = take(sizeof(double) * cap);       if (s) s->Rv = (double *)p;
-    p = take(sizeof(double) * tn);        if (s) s->Nv = (double *)p;
-    p = take(sizeof(double) * kb);        if (s) s->Sav = (double *)p;
-    p = take(sizeof(double) * kb);        if (s) s->Sbv = (double *)p;
-    p = take(sizeof(double) * W);         if (s) s->wa = (double *)p;
+    p = take(sizeof(val_t) * cap);       if (s) s->Rv = (val_t *)p;
+    p = take(sizeof(val_t) * tn);        if (s) s->Nv = (val_t *)p;
+    p = take(sizeof(val_t) * kb);        if (s) s->Sav = (val_t *)p;
+    p = take(sizeof(val_t) * kb);        if (s) s->Sbv = (val_t *)p;
+    p = take(sizeof(val_t) * W);         if (s) s->wa = (val_t *)p;
     p = take(sizeof(int64_t) * W);        if (s) s->wbs = (int64_t *)p;
     p = take(sizeof(int64_t) * (W + 1));  if (s) s->wscan = (int64_t *)p;
     p = take(sizeof(int32_t) * cap);      if (s) s->Rk = (int32_t *)p;
@@ -96,8 +96,8 @@ int merge_max_cap(int batch, int smem_limit, int wide_above) {
 // levels.  Runs 2p and 2p+1 are merged into the same range of dk/dv.  All threads
 // call; ends with a barrier.
 template <int NT>
-SPG_DEV void merge_level(const int32_t *sk, const double *sv, const int32_t *runoff, int nr0, int stride, int n,
-                         int32_t *dk, double *dv) {
+SPG_DEV void merge_level(const int32_t *sk, const val_t *sv, const int32_t *runoff, int nr0, int stride, int n,
+                         int32_t *dk, val_t *dv) {
     const int ipt = (n + NT - 1) / NT;
     int d = threadIdx.x * ipt;
     const int dend = min(n, d + ipt);
@@ -133,7 +133,7 @@ SPG_DEV void merge_level(const int32_t *sk, const double *sv, const int32_t *run
 // Fuses runs of equal keys of the sorted k/v[0..n) into ok/ov (in order, sums
 // taken left to right).  Returns the number of distinct keys.  All threads call.
 template <int NT>
-SPG_DEV int compress_runs(const int32_t *k, const double *v, int n, int32_t *ok, double *ov,
+SPG_DEV int compress_runs(const int32_t *k, const val_t *v, int n, int32_t *ok, val_t *ov,
                           int32_t *scan32) {
     const int ipt = (n + NT - 1) / NT;
     const int q0 = threadIdx.x * ipt;
@@ -146,7 +146,7 @@ SPG_DEV int compress_runs(const int32_t *k, const double *v, int n, int32_t *ok,
     for (int q = q0; q < q1; ++q) {
         if (q == 0 || k[q] != k[q - 1]) {
             const int32_t key = k[q];
-            double s = v[q];
+            val_t s = v[q];
             for (int r = q + 1; r < n && k[r] == key; ++r) s += v[r];
             ok[o] = key;
             ov[o] = s;
@@ -161,8 +161,8 @@ SPG_DEV int compress_runs(const int32_t *k, const double *v, int n, int32_t *ok,
 // memory (ny), Z global.  Streams X through the batch buffers in tiles; each
 // step consumes every key <= a limit from both inputs.  Returns |Z|.
 template <int NT>
-SPG_DEV int64_t union_stream(const int32_t *xk, const double *xv, int64_t nx, const int32_t *yk,
-                             const double *yv, int ny, int32_t *zk, double *zv, const MergeSmem &s,
+SPG_DEV int64_t union_stream(const int32_t *xk, const val_t *xv, int64_t nx, const int32_t *yk,
+                             const val_t *yv, int ny, int32_t *zk, val_t *zv, const MergeSmem &s,
                              int kb, int32_t *scan32) {
     const int T = kb / 2;
     int64_t xa = 0, zo = 0;
@@ -215,7 +215,7 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
     // reload the item's sequence (empty for a fresh row; half of the parent's for a split child)
     {
         const int32_t *sc = it.src_col[j];
-        const double *sv = it.src_val[j];
+        const val_t *sv = it.src_val[j];
         for (int t = threadIdx.x; t < rlen; t += NT) {
             s.Rk[t] = sc[t];
             s.Rv[t] = sv[t];
@@ -224,7 +224,7 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
     // where this launch writes the item: its home if large enough, else a fresh
     // slot; without a pool the item's capacity is that of its home
     int32_t *dst_col = it.home_col[j];
-    double *dst_val = it.home_val[j];
+    val_t *dst_val = it.home_val[j];
     int64_t dst_cap = it.home_cap[j];
     int cap = L.cap;
     if (!L.level1 && dst_cap < cap) {
@@ -238,7 +238,7 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
     }
     // level-1 global sequence: ping-pong between g0 and g1
     int32_t *g0k = nullptr, *g1k = nullptr;
-    double *g0v = nullptr, *g1v = nullptr;
+    val_t *g0v = nullptr, *g1v = nullptr;
     int64_t glen = 0;
     if (L.level1) {
         const int64_t go = L.g_off[w], gc = L.g_cap[w];
@@ -293,7 +293,7 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
                     }
                     glen = union_stream<NT>(g0k, g0v, glen, s.Rk, s.Rv, rlen, g1k, g1v, s, kb, scan32);
                     int32_t *tk = g0k; g0k = g1k; g1k = tk;
-                    double *tv = g0v; g0v = g1v; g1v = tv;
+                    val_t *tv = g0v; g0v = g1v; g1v = tv;
                     rlen = 0;
                     avail = cap;
                 } else if (avail < (kb >> 2) || avail <= 0) {
@@ -317,7 +317,7 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
             const int q0 = threadIdx.x * ipt;
             const int cnt = max(0, min(ipt, nb - q0));
             int32_t key[MERGE_MAX_IPT];
-            double val[MERGE_MAX_IPT];
+            val_t val[MERGE_MAX_IPT];
             if (cnt > 0) {
                 // all addresses first, then all loads: one L2 round trip per batch, not IPT
                 int te[MERGE_MAX_IPT], to[MERGE_MAX_IPT];  // window entry and offset in its B range
@@ -396,11 +396,11 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
             if (nnew > 0) {
                 // (3) pairwise merge-path merges of the runs, then fuse equal columns
                 int32_t *ck = s.Sbk, *okk = s.Sak;
-                double *cv = s.Sbv, *ovv = s.Sav;
+                val_t *cv = s.Sbv, *ovv = s.Sav;
                 for (int stride = 1; stride < nruns; stride *= 2) {
                     merge_level<NT>(ck, cv, s.runoff, nruns, stride, nnew, okk, ovv);
                     int32_t *tk = ck; ck = okk; okk = tk;
-                    double *tv = cv; cv = ovv; ovv = tv;
+                    val_t *tv = cv; cv = ovv; ovv = tv;
                 }
                 const int nn = compress_runs<NT>(ck, cv, nnew, okk, ovv, scan32);
                 // (4) in-place merges into N, and N into R
@@ -441,7 +441,7 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
     }
     int64_t final_len;
     int32_t *fin_col;
-    double *fin_val;
+    val_t *fin_val;
     int64_t fin_cap;
     if (L.level1) {
         glen = union_stream<NT>(g0k, g0v, glen, s.Rk, s.Rv, rlen, g1k, g1v, s, kb, scan32);
@@ -480,7 +480,7 @@ k_merge(StageArgs a, MergeItems it, MergeLaunch L) {
 }
 
 __global__ void k_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
-                             double *ctil_val, MergeItems it) {
+                             val_t *ctil_val, MergeItems it) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n37) return;
     const int row = rows37[j];
@@ -501,7 +501,7 @@ __global__ void k_merge_init(const int32_t *rows37, int64_t n37, const int64_t *
 }
 
 cudaError_t launch_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
-                              double *ctil_val, const MergeItems &it, cudaStream_t st) {
+                              val_t *ctil_val, const MergeItems &it, cudaStream_t st) {
     if (n37 <= 0) return cudaSuccess;
     k_merge_init<<<(unsigned)((n37 + 255) / 256), 256, 0, st>>>(rows37, n37, ctil_rp, ctil_col, ctil_val, it);
     return cudaGetLastError();
@@ -513,7 +513,7 @@ cudaError_t launch_merge_init(const int32_t *rows37, int64_t n37, const int64_t 
 // already sits at the start; the right child gets slot i of `pool`, and
 // k_split_copy moves the right half there, so no two items share memory.
 __global__ void k_split(const int32_t *ovf, int64_t n, int64_t first_new, MergeItems it, int32_t *pool_col,
-                        double *pool_val, int64_t pool_cap) {
+                        val_t *pool_val, int64_t pool_cap) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int p = ovf[i];
@@ -555,9 +555,9 @@ __global__ void k_split_copy(const int32_t *ovf, int64_t first_new, MergeItems i
     const int plen = it.src_len[p];
     const int mid = plen / 2;
     const int32_t *sc = it.src_col[p] + mid;
-    const double *sv = it.src_val[p] + mid;
+    const val_t *sv = it.src_val[p] + mid;
     int32_t *dc = it.home_col[r];
-    double *dv = it.home_val[r];
+    val_t *dv = it.home_val[r];
     for (int t = threadIdx.x; t < plen - mid; t += blockDim.x) {
         dc[t] = sc[t];
         dv[t] = sv[t];
@@ -565,7 +565,7 @@ __global__ void k_split_copy(const int32_t *ovf, int64_t first_new, MergeItems i
 }
 
 cudaError_t launch_split(const int32_t *ovf, int64_t n, int64_t first_new, const MergeItems &it,
-                         int32_t *pool_col, double *pool_val, int64_t pool_cap, cudaStream_t st) {
+                         int32_t *pool_col, val_t *pool_val, int64_t pool_cap, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ovf, n, first_new, it, pool_col, pool_val, pool_cap);
     k_split_copy<<<(unsigned)n, 256, 0, st>>>(ovf, first_new, it);

@@ -37,7 +37,7 @@ namespace spg {
 constexpr int BM_IPT = 4;          // products per thread per batch: batch <= NT * 4
 
 struct BmSmem {
-    double *Rv, *Mv, *wa;
+    val_t *Rv, *Mv, *wa;
     int64_t *wbs, *wscan;
     int32_t *Rk, *Mk;
 };
@@ -208,9 +208,9 @@ __host__ __device__ inline size_t bm_layout(int cap, int nwords, int miss, int W
     };
     const int nw4 = (nwords + 4) & ~3;
     unsigned char *p;
-    p = take(sizeof(double) * cap);            if (s) s->Rv = (double *)p;
-    p = take(sizeof(double) * miss);           if (s) s->Mv = (double *)p;
-    p = take(sizeof(double) * W);              if (s) s->wa = (double *)p;
+    p = take(sizeof(val_t) * cap);            if (s) s->Rv = (val_t *)p;
+    p = take(sizeof(val_t) * miss);           if (s) s->Mv = (val_t *)p;
+    p = take(sizeof(val_t) * W);              if (s) s->wa = (val_t *)p;
     p = take(sizeof(int64_t) * W);             if (s) s->wbs = (int64_t *)p;
     p = take(sizeof(int64_t) * (W + 1));       if (s) s->wscan = (int64_t *)p;
     p = take(sizeof(int32_t) * cap);           if (s) s->Rk = (int32_t *)p;
@@ -249,7 +249,7 @@ SPG_DEV int bm_merge_misses(const BmSmem &s, Index &ix, int rlen, int nm, int32_
     for (int hi = rlen; hi > 0; hi -= CH) {
         const int base = hi > CH ? hi - CH : 0;
         int32_t kk[4];
-        double vv[4];
+        val_t vv[4];
         int np[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {  // entry base + q*NT + thread: consecutive lanes, consecutive words
@@ -318,7 +318,7 @@ k_merge_bm(StageArgs a, MergeItems it, MergeLaunch L) {
     // where this launch writes the item: its home if large enough, else a fresh
     // slot; without a pool the item's capacity is that of its home
     int32_t *dst_col = it.home_col[j];
-    double *dst_val = it.home_val[j];
+    val_t *dst_val = it.home_val[j];
     int64_t dst_cap = it.home_cap[j];
     int cap = L.cap;
     if (dst_cap < cap) {
@@ -346,7 +346,7 @@ k_merge_bm(StageArgs a, MergeItems it, MergeLaunch L) {
     bool bad = false;
     {
         const int32_t *sc = it.src_col[j];
-        const double *sv = it.src_val[j];
+        const val_t *sv = it.src_val[j];
         for (int t = threadIdx.x; t < rlen; t += NT) {
             const int32_t c = sc[t];
             if ((unsigned)(c - lo) >= (unsigned)span) bad = true;  // cannot happen: items hold their own columns
@@ -406,7 +406,7 @@ k_merge_bm(StageArgs a, MergeItems it, MergeLaunch L) {
             // registers: consecutive lanes read consecutive B entries (coalesced)
             int cnt = need > (int)threadIdx.x ? min(BM_IPT, (need - (int)threadIdx.x + NT - 1) / NT) : 0;
             int32_t key[BM_IPT];
-            double val[BM_IPT];
+            val_t val[BM_IPT];
             {
                 int te[BM_IPT], to[BM_IPT];
 #pragma unroll

@@ -19,7 +19,7 @@ constexpr int REPLAY_IPT = 4;
 template <int NT>
 __global__ void __launch_bounds__(NT, 2048 / NT / 2)
 k_replay(StageArgs a, ReplayLeaves lv, const int32_t *__restrict__ order, int32_t *__restrict__ c_col,
-         double *__restrict__ c_val, int64_t *err) {
+         val_t *__restrict__ c_val, int64_t *err) {
     extern __shared__ __align__(16) unsigned char rsmem[];
     __shared__ int64_t scan64[NT / 32 + 1];
     constexpr int W = NT;
@@ -33,8 +33,8 @@ k_replay(StageArgs a, ReplayLeaves lv, const int32_t *__restrict__ order, int32_
         if (threadIdx.x == 0) atomicExch((unsigned long long *)err, 4ull);
         return;
     }
-    double *Rv = reinterpret_cast<double *>(rsmem);
-    double *wa = Rv + lv.cap;
+    val_t *Rv = reinterpret_cast<val_t *>(rsmem);
+    val_t *wa = Rv + lv.cap;
     int64_t *wbs = reinterpret_cast<int64_t *>(wa + W);
     int64_t *wscan = wbs + W;
     int32_t *Rk = reinterpret_cast<int32_t *>(wscan + W + 1);
@@ -72,7 +72,7 @@ k_replay(StageArgs a, ReplayLeaves lv, const int32_t *__restrict__ order, int32_
             const int q0 = threadIdx.x * ipt;
             const int cnt = max(0, min(ipt, nb - q0));
             int32_t key[REPLAY_IPT];
-            double val[REPLAY_IPT];
+            val_t val[REPLAY_IPT];
             if (cnt > 0) {
                 int te[REPLAY_IPT], to[REPLAY_IPT];
                 int64_t pos = p0 + q0;
@@ -115,7 +115,7 @@ k_replay(StageArgs a, ReplayLeaves lv, const int32_t *__restrict__ order, int32_
 template <int NT>
 __global__ void __launch_bounds__(NT, 2048 / NT / 2)
 k_replay_bm(StageArgs a, ReplayLeaves lv, const int32_t *__restrict__ order, int nwords_max,
-            int32_t *__restrict__ c_col, double *__restrict__ c_val, int64_t *err) {
+            int32_t *__restrict__ c_col, val_t *__restrict__ c_val, int64_t *err) {
     extern __shared__ __align__(16) unsigned char rsmem[];
     __shared__ int64_t scan64[NT / 32 + 1];
     __shared__ int32_t scan32[NT / 32 + 1];
@@ -133,8 +133,8 @@ k_replay_bm(StageArgs a, ReplayLeaves lv, const int32_t *__restrict__ order, int
         if (threadIdx.x == 0) atomicExch((unsigned long long *)err, 4ull);
         return;
     }
-    double *Rv = reinterpret_cast<double *>(rsmem);
-    double *wa = Rv + lv.cap;
+    val_t *Rv = reinterpret_cast<val_t *>(rsmem);
+    val_t *wa = Rv + lv.cap;
     int64_t *wbs = reinterpret_cast<int64_t *>(wa + W);
     int64_t *wscan = wbs + W;
     int32_t *Rd = reinterpret_cast<int32_t *>(wscan + W + 1 + 1);  // 16-byte aligned (W is a multiple of 32)
@@ -182,7 +182,7 @@ k_replay_bm(StageArgs a, ReplayLeaves lv, const int32_t *__restrict__ order, int
             if (cnt > 0) {
                 int te[REPLAY_IPT], to[REPLAY_IPT];
                 int32_t key[REPLAY_IPT];
-                double val[REPLAY_IPT];
+                val_t val[REPLAY_IPT];
 #pragma unroll
                 for (int k = 0; k < REPLAY_IPT; ++k) {
                     if (k < cnt) {
@@ -220,18 +220,18 @@ int replay_threads(int cap) { return cap <= 1024 ? 128 : (cap <= 4096 ? 256 : 51
 
 int replay_bm_smem_bytes(int cap, int nwords_max) {
     const int W = replay_threads(cap);
-    return (int)(sizeof(double) * (cap + W) + sizeof(int64_t) * (2 * W + 2) +
+    return (int)(sizeof(val_t) * (cap + W) + sizeof(int64_t) * (2 * W + 2) +
                  sizeof(int32_t) * ((nwords_max + 4) & ~3) + sizeof(uint32_t) * nwords_max + 64);
 }
 
 int replay_smem_bytes(int cap) {
     const int W = replay_threads(cap);
-    return (int)(sizeof(double) * (cap + W) + sizeof(int64_t) * (2 * W + 1) + sizeof(int32_t) * cap + 64);
+    return (int)(sizeof(val_t) * (cap + W) + sizeof(int64_t) * (2 * W + 1) + sizeof(int32_t) * cap + 64);
 }
 
 template <int NT>
 static cudaError_t launch_replay_nt(const StageArgs &a, const ReplayLeaves &lv, const int32_t *order, int64_t n,
-                                   int32_t *c_col, double *c_val, int64_t *err, int smem, cudaStream_t st) {
+                                   int32_t *c_col, val_t *c_val, int64_t *err, int smem, cudaStream_t st) {
     auto kern = k_replay<NT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -241,7 +241,7 @@ static cudaError_t launch_replay_nt(const StageArgs &a, const ReplayLeaves &lv, 
 
 template <int NT>
 static cudaError_t launch_replay_bm_nt(const StageArgs &a, const ReplayLeaves &lv, const int32_t *order, int64_t n,
-                                      int nwords, int32_t *c_col, double *c_val, int64_t *err, int smem,
+                                      int nwords, int32_t *c_col, val_t *c_val, int64_t *err, int smem,
                                       cudaStream_t st) {
     auto kern = k_replay_bm<NT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -251,7 +251,7 @@ static cudaError_t launch_replay_bm_nt(const StageArgs &a, const ReplayLeaves &l
 }
 
 cudaError_t launch_replay(const StageArgs &a, ReplayLeaves lv, const int32_t *order, int64_t n, int cap,
-                          int32_t *c_col, double *c_val, int64_t *err, cudaStream_t st) {
+                          int32_t *c_col, val_t *c_val, int64_t *err, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     lv.cap = cap;
     if (a.B.ncols > 0 && a.B.ncols <= BM_MAX_COLS) {

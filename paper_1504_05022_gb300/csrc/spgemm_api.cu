@@ -110,6 +110,9 @@ struct Timer {
 // Heap-kernel launches: bins 2..32 split into ranges sized to their widest heap.
 const int kHeapRanges[][2] = {{2, 8}, {9, 16}, {17, 24}, {25, 32}};
 
+// Bytes of one stored entry (int32 column + value).
+constexpr int64_t ENTRY_BYTES = sizeof(int32_t) + sizeof(val_t);
+
 // Lifetimes of plan allocations.
 constexpr int LIFE_SYMBOLIC = 0;  // released when spgemm_symbolic returns
 constexpr int LIFE_NUMERIC = 1;   // released when spgemm_numeric returns
@@ -140,7 +143,7 @@ struct spgemm_plan {
     uint8_t *bin = nullptr;
     int32_t *bin_rows = nullptr, *nnzc = nullptr, *ctil_col_i = nullptr;
     int32_t *ctil_col = nullptr;
-    double *ctil_val = nullptr;
+    val_t *ctil_val = nullptr;
     BinSummary *d_summary = nullptr;
     int64_t *d_err = nullptr;
     BinSummary h_summary{};
@@ -176,7 +179,7 @@ struct spgemm_plan {
     int64_t *d_moff = nullptr, *d_koff = nullptr, *d_annz_off = nullptr, *d_bnnz_off = nullptr;
     int64_t *cat_a_rp = nullptr, *cat_b_rp = nullptr;
     int32_t *cat_a_col = nullptr, *cat_b_col = nullptr;
-    double *cat_a_val = nullptr, *cat_b_val = nullptr;
+    val_t *cat_a_val = nullptr, *cat_b_val = nullptr;
     int64_t *split_rp = nullptr;
     std::vector<spgemm_csr_out> batch_out;
     // batched plans in waves: groups of pairs computed one after another, each a
@@ -326,7 +329,7 @@ static void merge_limits(spgemm_plan *p) {
         p->opts.long_rows == SPGEMM_LONG_ROWS_SPLIT && p->B.ncols > 0) {
         const int64_t n = p->B.ncols;
         auto widest = [](int limit) {
-            int w = (int)(limit / 9.25) & ~31;
+            int w = (int)(limit / (sizeof(val_t) + 1.25)) & ~31;
             while (w > 32 && dense_fill_smem_bytes(w) > limit) w -= 32;
             return w;
         };
@@ -613,7 +616,7 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
         // C~ (hybrid: u_i for bins 0..36, 256 for bin 37)
         SPG_TRY(p->alloc_n(&p->ctil_col, p->h_summary.sum_cap, LIFE_NUMERIC));
         SPG_TRY(p->alloc_n(&p->ctil_val, p->h_summary.sum_cap, LIFE_NUMERIC));
-        p->bytes_ctilde += p->h_summary.sum_cap * 12;
+        p->bytes_ctilde += p->h_summary.sum_cap * ENTRY_BYTES;
         p->release_temps(LIFE_SYMBOLIC);
         p->dense_flag = nullptr;
         p->dense_lo = p->dense_hi = nullptr;
@@ -786,7 +789,7 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
                     SPG_TRY(p->alloc_n(&L.pool_col, nwork * (int64_t)cap, LIFE_NUMERIC));
                     SPG_TRY(p->alloc_n(&L.pool_val, nwork * (int64_t)cap, LIFE_NUMERIC));
                     L.pool_cap = cap;
-                    p->bytes_ctilde += nwork * (int64_t)cap * 12;
+                    p->bytes_ctilde += nwork * (int64_t)cap * ENTRY_BYTES;
                 }
                 if (level1) {
                     SPG_TRY(p->alloc_n(&g_cap, nwork, LIFE_NUMERIC));
@@ -800,7 +803,7 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
                     SPG_TRY(p->d2h(&gtot, g_total, sizeof(int64_t)));
                     SPG_TRY(p->alloc_n(&L.g_col, gtot, LIFE_NUMERIC));
                     SPG_TRY(p->alloc_n(&L.g_val, gtot, LIFE_NUMERIC));
-                    p->bytes_ctilde += gtot * 12;
+                    p->bytes_ctilde += gtot * ENTRY_BYTES;
                     L.g_cap = g_cap;
                     L.g_off = g_off;
                     p->stats.rows_level1 += nwork;
@@ -841,10 +844,10 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
             // split every overflowed item at the median column of its sequence
             SPG_TRY(reserve_items(p, p->n_items + 2 * novf));
             int32_t *scol = nullptr;
-            double *sval = nullptr;
+            val_t *sval = nullptr;
             SPG_TRY(p->alloc_n(&scol, novf * (int64_t)capmax, LIFE_NUMERIC));
             SPG_TRY(p->alloc_n(&sval, novf * (int64_t)capmax, LIFE_NUMERIC));
-            p->bytes_ctilde += novf * (int64_t)capmax * 12;
+            p->bytes_ctilde += novf * (int64_t)capmax * ENTRY_BYTES;
             p->time_begin(SPGEMM_K_OTHER);
             SPG_TRY(launch_split(ovf_items, novf, p->n_items, p->items, scol, sval, capmax, p->st));
             p->time_end();
@@ -1031,7 +1034,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 SPG_TRY(p->alloc_n(&L.pool_col, (int64_t)nk * lv[k], LIFE_NUMERIC));
                 SPG_TRY(p->alloc_n(&L.pool_val, (int64_t)nk * lv[k], LIFE_NUMERIC));
                 L.pool_cap = lv[k];
-                p->bytes_ctilde += (int64_t)nk * lv[k] * 12;
+                p->bytes_ctilde += (int64_t)nk * lv[k] * ENTRY_BYTES;
                 p->time_begin(SPGEMM_K_MERGE);
                 SPG_TRY(launch_merge(a, p->items, L, p->st));
                 p->time_end();

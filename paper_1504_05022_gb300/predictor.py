@@ -79,8 +79,9 @@ class Trainer:
 class Predictor:
     """Device copy of a parameter vector, usable as opts.predictor (alloc_policy='learned')."""
 
-    def __init__(self, params, margin: float = 1.0):
-        L = _lib.load()
+    def __init__(self, params, margin: float = 1.0, dtype: str = "f64"):
+        L = self.L = _lib.load(dtype=dtype)
+        self.dtype = dtype  # the value type of the plans it serves ("f64" or "f32")
         host = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
         if host.size != _lib.MLP_NUM_TOTAL:
             raise ValueError(f"expected {_lib.MLP_NUM_TOTAL} parameters, got {host.size}")
@@ -99,13 +100,14 @@ class Predictor:
     def __del__(self):
         try:
             if self.handle:
-                _lib.load().spgemm_predictor_free(ctypes.c_void_p(self.handle))
+                self.L.spgemm_predictor_free(ctypes.c_void_p(self.handle))
                 self.handle = None
         except Exception:
             pass
 
     @classmethod
-    def load(cls, path: str = WEIGHTS, margin: float | None = None) -> "Predictor":
+    def load(cls, path: str = WEIGHTS, margin: float | None = None, dtype: str = "f64") -> "Predictor":
         with open(path) as f:
             d = json.load(f)
-        return cls(np.array(d["params"], dtype=np.float32), d.get("margin", 1.0) if margin is None else margin)
+        return cls(np.array(d["params"], dtype=np.float32), d.get("margin", 1.0) if margin is None else margin,
+                   dtype=dtype)

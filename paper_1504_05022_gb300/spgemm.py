@@ -18,8 +18,8 @@ from . import _lib
 class CSR:
     """A CSR matrix whose arrays are torch tensors on one CUDA device.
 
-    row_ptr: int32 or int64 (nrows+1), col: int32 (nnz), val: float64 (nnz); columns of a row
-    strictly ascending."""
+    row_ptr: int32 or int64 (nrows+1), col: int32 (nnz), val: float64 or float32 (nnz; the
+    product runs in the values' precision); columns of a row strictly ascending."""
 
     row_ptr: torch.Tensor
     col: torch.Tensor
@@ -38,27 +38,35 @@ class CSR:
     def nnz(self) -> int:
         return int(self.col.numel())
 
+    @property
+    def value_type(self) -> str:
+        """"f64" or "f32": which library (double or single precision) computes with it."""
+        return {torch.float64: "f64", torch.float32: "f32"}[self.val.dtype]
+
     @classmethod
-    def from_host(cls, M, device="cuda", rowptr_dtype=torch.int64, pin: bool = False) -> "CSR":
-        """Copies a host CSR (anything with row_ptr/col/val numpy arrays and nrows/ncols)."""
+    def from_host(cls, M, device="cuda", rowptr_dtype=torch.int64, pin: bool = False,
+                  dtype: torch.dtype = torch.float64) -> "CSR":
+        """Copies a host CSR (anything with row_ptr/col/val numpy arrays and nrows/ncols);
+        values are stored as `dtype` (float64 or float32)."""
         rp = torch.from_numpy(np.ascontiguousarray(M.row_ptr)).to(rowptr_dtype)
         col = torch.from_numpy(np.ascontiguousarray(M.col, dtype=np.int32))
-        val = torch.from_numpy(np.ascontiguousarray(M.val, dtype=np.float64))
+        npdt = {torch.float64: np.float64, torch.float32: np.float32}[dtype]
+        val = torch.from_numpy(np.ascontiguousarray(M.val, dtype=npdt))
         if pin:
             rp, col, val = rp.pin_memory(), col.pin_memory(), val.pin_memory()
         return cls(rp.to(device, non_blocking=pin), col.to(device, non_blocking=pin),
                    val.to(device, non_blocking=pin), (int(M.nrows), int(M.ncols)))
 
     def to_host(self):
-        """(row_ptr int64, col int32, val float64) numpy arrays."""
+        """(row_ptr int64, col int32, val float64 or float32) numpy arrays."""
         return (self.row_ptr.to("cpu", torch.int64).numpy(), self.col.cpu().numpy(), self.val.cpu().numpy())
 
     def _c_in(self) -> _lib.CsrIn:
         for t in (self.row_ptr, self.col, self.val):
             if not t.is_cuda or not t.is_contiguous():
                 raise ValueError("CSR arrays must be contiguous CUDA tensors")
-        if self.col.dtype != torch.int32 or self.val.dtype != torch.float64:
-            raise TypeError("col must be int32 and val float64")
+        if self.col.dtype != torch.int32 or self.val.dtype not in (torch.float64, torch.float32):
+            raise TypeError("col must be int32 and val float64 or float32")
         if self.row_ptr.dtype not in (torch.int32, torch.int64):
             raise TypeError("row_ptr must be int32 or int64")
         if self.row_ptr.numel() != self.nrows + 1 or self.val.numel() != self.col.numel():
@@ -72,13 +80,14 @@ class CSR:
 class _PlanHandle:
     """Owns an spgemm_plan*; freed (stream-ordered) when the last reference goes."""
 
-    def __init__(self, ptr: int, stream: torch.cuda.Stream):
+    def __init__(self, ptr: int, stream: torch.cuda.Stream, L):
         self.ptr = ptr
         self.stream = stream
+        self.L = L  # the library (value type) that made the plan
 
     def free(self):
         if self.ptr:
-            _lib.load().spgemm_free(ctypes.c_void_p(self.ptr))
+            self.L.spgemm_free(ctypes.c_void_p(self.ptr))
             self.ptr = 0
 
     def __del__(self):
@@ -100,7 +109,7 @@ class _PlanArray:
 
 
 def _wrap(ptr: int, n: int, dtype: torch.dtype, owner: _PlanHandle, device: int) -> torch.Tensor:
-    typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.float64: "<f8"}[dtype]
+    typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.float64: "<f8", torch.float32: "<f4"}[dtype]
     if n == 0:
         return torch.empty(0, dtype=dtype, device=f"cuda:{device}")
     return torch.as_tensor(_PlanArray(ptr, n, typestr, owner, device), device=f"cuda:{device}")
@@ -143,11 +152,25 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
     return o
 
 
+def _value_type(mats, opts) -> str:
+    """The value type shared by the matrices (and the predictor, if any)."""
+    vts = {m.value_type for m in mats}
+    if len(vts) != 1:
+        raise TypeError("A and B must have the same value type (float64 or float32)")
+    vt = vts.pop()
+    pred = opts.get("predictor")
+    if pred is not None and getattr(pred, "dtype", vt) != vt:
+        raise TypeError(f"the predictor was made for {pred.dtype} values, the matrices hold {vt}")
+    return vt
+
+
 class Plan:
-    """C = A*B split into the symbolic part (stages 1-2) and the numeric part (stages 3-4)."""
+    """C = A*B split into the symbolic part (stages 1-2) and the numeric part (stages 3-4).
+    The precision of the matrices' values (float64 or float32) selects the library."""
 
     def __init__(self, A: CSR, B: CSR, stream: torch.cuda.Stream | None = None, **opts):
-        L = _lib.load()
+        vt = _value_type([A, B], opts)
+        L = self.L = _lib.load(dtype=vt)
         self.A, self.B = A, B  # keep inputs alive until numeric work completes
         self.device = A.val.device.index if A.val.is_cuda else torch.cuda.current_device()
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -160,26 +183,26 @@ class Plan:
             _lib.check(L.spgemm_symbolic(ctypes.byref(a_in), ctypes.byref(b_in), ctypes.byref(self.opts),
                                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(plan),
                                          ctypes.byref(ub)), "spgemm_symbolic")
-        self.handle = _PlanHandle(plan.value, self.stream)
+        self.handle = _PlanHandle(plan.value, self.stream, L)
         self.upper_bound_nnz = int(ub.value)
         self._C = None
 
     def numeric(self) -> CSR:
         if self._C is not None:
             return self._C
-        L = _lib.load()
+        L = self.L
         out = _lib.CsrOut()
         with torch.cuda.device(self.device):
             _lib.check(L.spgemm_numeric(ctypes.c_void_p(self.handle.ptr), ctypes.byref(out)), "spgemm_numeric")
         h = self.handle
         rp = _wrap(out.row_ptr, out.nrows + 1, torch.int64, h, self.device)
         col = _wrap(out.col_idx, out.nnz, torch.int32, h, self.device)
-        val = _wrap(out.val, out.nnz, torch.float64, h, self.device)
+        val = _wrap(out.val, out.nnz, self.A.val.dtype, h, self.device)
         self._C = CSR(rp, col, val, (int(out.nrows), int(out.ncols)))
         return self._C
 
     def stats(self) -> dict:
-        L = _lib.load()
+        L = self.L
         s = _lib.Stats()
         _lib.check(L.spgemm_plan_stats(ctypes.c_void_p(self.handle.ptr), ctypes.byref(s)), "spgemm_plan_stats")
         return {
@@ -198,7 +221,7 @@ class Plan:
         return self._arrays_of(self.handle.ptr)
 
     def _arrays_of(self, ptr: int) -> dict:
-        L = _lib.load()
+        L = self.L
         a = _lib.PlanArrays()
         _lib.check(L.spgemm_plan_arrays_get(ctypes.c_void_p(ptr), ctypes.byref(a)), "spgemm_plan_arrays_get")
         self.stream.synchronize()
@@ -219,11 +242,11 @@ class Plan:
         """Recomputes C's values in place for new values of A and B with the same structure
         (no allocation, no host synchronisation after the first call)."""
         with torch.cuda.device(self.device):
-            _lib.check(_lib.load().spgemm_numeric_replay(ctypes.c_void_p(self.handle.ptr)), "spgemm_numeric_replay")
+            _lib.check(self.L.spgemm_numeric_replay(ctypes.c_void_p(self.handle.ptr)), "spgemm_numeric_replay")
 
     def check(self) -> None:
         """Raises if a device-side consistency check failed (e.g. a replay with changed structure)."""
-        _lib.check(_lib.load().spgemm_plan_check(ctypes.c_void_p(self.handle.ptr)), "spgemm_plan_check")
+        _lib.check(self.L.spgemm_plan_check(ctypes.c_void_p(self.handle.ptr)), "spgemm_plan_check")
 
     def free(self) -> None:
         """Releases the plan now; tensors of C obtained from numeric() become invalid."""
@@ -242,9 +265,9 @@ class BatchPlan(Plan):
     """Many independent C_i = A_i * B_i in one pipeline (block-diagonal concatenation)."""
 
     def __init__(self, As, Bs, stream: torch.cuda.Stream | None = None, **opts):  # noqa: D401
-        L = _lib.load()
         if len(As) != len(Bs) or not As:
             raise ValueError("need as many A as B matrices, at least one")
+        L = self.L = _lib.load(dtype=_value_type(list(As) + list(Bs), opts))
         self.As, self.Bs = list(As), list(Bs)
         self.A, self.B = self.As[0], self.Bs[0]
         self.device = As[0].val.device.index
@@ -260,7 +283,7 @@ class BatchPlan(Plan):
             _lib.check(L.spgemm_batched_symbolic(n, ain, bin_, ctypes.byref(self.opts),
                                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(plan),
                                                  ctypes.byref(ub)), "spgemm_batched_symbolic")
-        self.handle = _PlanHandle(plan.value, self.stream)
+        self.handle = _PlanHandle(plan.value, self.stream, L)
         self.upper_bound_nnz = int(ub.value)
         self._C = None
         self._Cs = None
@@ -268,7 +291,7 @@ class BatchPlan(Plan):
     def numeric(self):
         if self._Cs is not None:
             return self._Cs
-        L = _lib.load()
+        L = self.L
         n = len(self.As)
         outs = (_lib.CsrOut * n)()
         with torch.cuda.device(self.device):
@@ -276,7 +299,7 @@ class BatchPlan(Plan):
         h = self.handle
         self._Cs = [CSR(_wrap(o.row_ptr, o.nrows + 1, torch.int64, h, self.device),
                         _wrap(o.col_idx, o.nnz, torch.int32, h, self.device),
-                        _wrap(o.val, o.nnz, torch.float64, h, self.device), (int(o.nrows), int(o.ncols)))
+                        _wrap(o.val, o.nnz, self.A.val.dtype, h, self.device), (int(o.nrows), int(o.ncols)))
                     for o in outs]
         return self._Cs
 
@@ -284,14 +307,14 @@ class BatchPlan(Plan):
     @property
     def n_waves(self) -> int:
         n = ctypes.c_int64()
-        _lib.check(_lib.load().spgemm_batched_waves(ctypes.c_void_p(self.handle.ptr), ctypes.byref(n)),
+        _lib.check(self.L.spgemm_batched_waves(ctypes.c_void_p(self.handle.ptr), ctypes.byref(n)),
                    "spgemm_batched_waves")
         return int(n.value)
 
     def pair_order(self) -> np.ndarray:
         """Pairs in the order the waves compute them (largest product count first)."""
         order = np.zeros(len(self.As), dtype=np.int64)
-        _lib.check(_lib.load().spgemm_batched_wave_pairs(ctypes.c_void_p(self.handle.ptr),
+        _lib.check(self.L.spgemm_batched_wave_pairs(ctypes.c_void_p(self.handle.ptr),
                                                          order.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
                    "spgemm_batched_wave_pairs")
         return order
@@ -303,7 +326,7 @@ class BatchPlan(Plan):
         nw = self.n_waves
         if nw == 1:
             return super().arrays()
-        L = _lib.load()
+        L = self.L
         parts = []
         for i in range(nw):
             sub = ctypes.c_void_p()
@@ -324,8 +347,10 @@ class ReplayGraph:
     products of a Galerkin chain); launch() recomputes all their results for new input values."""
 
     def __init__(self, plans):
-        L = _lib.load()
         self.plans = list(plans)
+        if len({p.L._name for p in self.plans}) != 1:
+            raise ValueError("the plans of one graph must share a value type")
+        L = self.L = self.plans[0].L
         arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.ptr for p in self.plans])
         g = ctypes.c_void_p()
         with torch.cuda.device(self.plans[0].device):
@@ -333,12 +358,12 @@ class ReplayGraph:
         self.handle = g.value
 
     def launch(self) -> None:
-        _lib.check(_lib.load().spgemm_graph_launch(ctypes.c_void_p(self.handle)), "spgemm_graph_launch")
+        _lib.check(self.L.spgemm_graph_launch(ctypes.c_void_p(self.handle)), "spgemm_graph_launch")
 
     def __del__(self):
         try:
             if self.handle:
-                _lib.load().spgemm_graph_free(ctypes.c_void_p(self.handle))
+                self.L.spgemm_graph_free(ctypes.c_void_p(self.handle))
                 self.handle = None
         except Exception:
             pass

@@ -117,3 +117,14 @@ def test_every_field_offset_matches_the_c_compiler(tmp_path):
             assert getattr(cls, what).offset == int(value), (cname, what)
         seen += 1
     assert seen == sum(len(c._fields_) + 1 for c in mirror.values())
+
+
+def test_single_precision_library_exports_the_same_boundary():
+    from paper_1504_05022_gb300 import _build, _lib
+    _build.build()
+    L32 = _lib.load(dtype="f32")
+    assert L32 is not _lib.load()
+    for name in _declared_functions():
+        assert hasattr(L32, name), name
+    o = _lib.Opts()
+    assert L32.spgemm_opts_init(ctypes.byref(o)) == 0 and o.initial_cap == 256
