@@ -217,7 +217,13 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
     between steps outside the events).  Returns the per-step figures.  value_type "f32": the
     same product in single precision (values rounded to float, the float library)."""
     import torch
-    opts, keep = policy_opts(policy, args.workload if tuned and args.tuned else None, value_type)
+    tw = None
+    if tuned and args.tuned:  # single precision: its own tuned entry when there is one
+        from paper_1504_05022_gb300 import autotune
+        tw = args.workload
+        if value_type == "f32" and autotune.load(args.workload + ":f32", policy):
+            tw = args.workload + ":f32"
+    opts, keep = policy_opts(policy, tw, value_type)
     timing_opts = dict(opts, record_timing=True)  # per-kernel split, taken in one extra untimed step
     vdt = torch.float32 if value_type == "f32" else torch.float64
     Ad = [spg.CSR.from_host(A, device=dev, rowptr_dtype=torch.int32, dtype=vdt) for A, _ in pairs]

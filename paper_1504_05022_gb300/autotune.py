@@ -111,15 +111,17 @@ def apply(opts: dict, params: dict, predictor=None) -> dict:
 class Runner:
     """Times one configuration of the whole product on device-resident inputs."""
 
-    def __init__(self, pairs, device="cuda"):
+    def __init__(self, pairs, device="cuda", value_type="f64"):
         import torch
 
         from .spgemm import CSR
         self.torch = torch
         self.chain = len(pairs) == 2 and pairs[1][1] is None
         self.batched = len(pairs) > 1 and not self.chain
-        self.A = [CSR.from_host(A, device=device, rowptr_dtype=torch.int32) for A, _ in pairs]
-        self.B = [a if B is A else (None if B is None else CSR.from_host(B, device=device, rowptr_dtype=torch.int32))
+        vdt = torch.float32 if value_type == "f32" else torch.float64
+        self.A = [CSR.from_host(A, device=device, rowptr_dtype=torch.int32, dtype=vdt) for A, _ in pairs]
+        self.B = [a if B is A else (None if B is None else CSR.from_host(B, device=device, rowptr_dtype=torch.int32,
+                                                                         dtype=vdt))
                   for a, (A, B) in zip(self.A, pairs)]
         self.stream = torch.cuda.current_stream()
 
@@ -218,19 +220,22 @@ def main():
     ap.add_argument("--rounds", type=int, default=2)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--out", default=TUNED)
+    ap.add_argument("--value-type", default="f64", choices=["f64", "f32"],
+                    help="f32: the single-precision library; stored under '<workload>:f32'")
     args = ap.parse_args()
     if not torch.cuda.is_available():
         raise SystemExit("autotune needs a CUDA device")
     t0 = time.time()
     pairs = workload(args.workload)
-    runner = Runner(pairs)
-    pred = Predictor.load() if args.policy == "learned" else None
+    runner = Runner(pairs, value_type=args.value_type)
+    pred = Predictor.load(dtype=args.value_type) if args.policy == "learned" else None
     rec = tune(runner, args.policy, pred, rounds=args.rounds, reps=args.reps)
     rec["products"] = int(sum(np.diff(B.row_ptr)[A.col].sum() for A, B in pairs if B is not None))
     rec["device"] = torch.cuda.get_device_name()
     rec["tuning_seconds"] = round(time.time() - t0, 1)
     doc = json.load(open(args.out)) if os.path.exists(args.out) else {}
-    doc.setdefault(args.workload, {})[args.policy] = rec
+    key = args.workload + (":f32" if args.value_type == "f32" else "")
+    doc.setdefault(key, {})[args.policy] = rec
     with open(args.out, "w") as f:
         json.dump(doc, f, indent=1, sort_keys=True)
     print(json.dumps(rec))
