@@ -805,6 +805,60 @@ def _cpu_baseline_batch(pairs, budget_s):
                       f"median of {len(times)} passes", "ms_per_pass": t * 1e3}
 
 
+def run_merge_micro(args):
+    """The merge evaluation of Section 4.3: 2^25 keys in groups of two ascending runs of
+    length l, merged by the ranking merge, merge path and bitonic merge (one CTA per group,
+    best of 64-1024 threads), with no value, 32-bit and 64-bit values.  CUDA-event time of
+    one launch, median of 5 after a warm-up; merged elements per second."""
+    import torch
+
+    import paper_1504_05022_gb300 as spg
+    spg.load_library()
+    n = 1 << 25
+    gen_ = torch.Generator(device="cuda").manual_seed(0)
+    out = []
+    for vb in (0, 4, 8):
+        for lg in range(5, 14):
+            l = 1 << lg
+            if 2 * l * (4 + vb) > 200 * 1024:
+                continue
+            keys = torch.randint(0, 1 << 30, (n // (2 * l), 2, l), device="cuda", dtype=torch.int32, generator=gen_)
+            keys = keys.sort(dim=2).values.reshape(-1).contiguous()
+            vals = None
+            if vb == 4:
+                vals = torch.arange(n, device="cuda", dtype=torch.int32)
+            elif vb == 8:
+                vals = torch.arange(n, device="cuda", dtype=torch.float64)
+            row = {"value_bytes": vb, "l": l}
+            for method in ("ranking", "merge_path", "bitonic"):
+                best = None
+                for threads in (64, 128, 256, 512, 1024):
+                    spg.merge_micro(keys, l, method=method, threads=threads, vals=vals)
+                    ts = []
+                    for _ in range(5):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        spg.merge_micro(keys, l, method=method, threads=threads, vals=vals)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                    ms = float(np.median(ts))
+                    if best is None or ms < best[0]:
+                        best = (ms, threads)
+                row[method] = {"gelem_s": n / (best[0] * 1e-3) / 1e9, "ms": best[0], "threads": best[1]}
+            row["fastest"] = max(("ranking", "merge_path", "bitonic"), key=lambda k: row[k]["gelem_s"])
+            out.append(row)
+            del keys, vals
+    head = next(r for r in out if r["value_bytes"] == 8 and r["l"] == 256)
+    return {"metric": "merge micro-benchmark (Section 4.3): merged elements/s, merge path, l = 256, "
+                      "32-bit keys with 64-bit values", "value": head["merge_path"]["gelem_s"] * 1e9,
+            "unit": "elements/s", "higher_is_better": True, "n_gpus": 1, "dtype": "i32 keys",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": "merge_micro", "elements": n, "ls": sorted({r["l"] for r in out}),
+                       "threads": [64, 128, 256, 512, 1024]},
+            "results": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -819,7 +873,12 @@ def main():
                     help="do not apply the autotuner's parameters to the reported policy")
     ap.add_argument("--merge-kernel", default="auto", choices=["auto", "merge_path", "bitmap"],
                     help="form of the bin-37 kernel for every policy")
+    ap.add_argument("--merge-micro", action="store_true",
+                    help="run the merge evaluation of Section 4.3 instead and print its line")
     args = ap.parse_args()
+    if args.merge_micro:
+        print(json.dumps(run_merge_micro(args)))
+        return
     global MERGE_KERNEL
     MERGE_KERNEL = args.merge_kernel
     rank = int(os.environ.get("RANK", "0"))

@@ -435,6 +435,23 @@ spgemm_status spgemm_mlp_loss_grad(const float *params, const float *X, const in
 spgemm_status spgemm_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t step,
                               float lr, float grad_scale, spgemm_stream_t stream);
 
+/*
+ * The merge evaluation of Section 4.3 ("Evaluating GPU Merge algorithms"): merges groups
+ * of two sorted runs into sorted sequences, with one CTA of `threads` threads (64, 128,
+ * 256, 512 or 1024) per group, in shared memory.  method: 0 ranking merge, 1 merge path,
+ * 2 bitonic merge (the last stage of a bitonic sort).  keys: n int32 device values, in
+ * groups of 2l: keys[g 2l .. g 2l + l) and keys[g 2l + l .. (g + 1) 2l) each ascending.
+ * vals: n device values of value_bytes (0: none and may be NULL, 4 or 8) that move with
+ * their keys.  out_keys, out_vals: n each (out_vals ignored when value_bytes = 0).  l must
+ * be a power of two with 2 l (4 + value_bytes) bytes of shared memory available, and n a
+ * positive multiple of 2 l.  Equal keys: ranking merge and merge path put the first run's
+ * element first; the bitonic network does not keep an order among them.  Enqueued on
+ * `stream`; SPGEMM_ERR_INVALID_ARG for bad arguments.
+ */
+spgemm_status spgemm_merge_micro(int32_t method, int32_t threads, int32_t value_bytes, const int32_t *keys,
+                                 const void *vals, int64_t n, int32_t l, int32_t *out_keys, void *out_vals,
+                                 spgemm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

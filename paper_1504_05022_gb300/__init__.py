@@ -1,10 +1,11 @@
-"""GB300-native CSR SpGEMM (C = A*B, FP64) after Liu & Vinter's four-stage framework.
+"""GB300-native CSR SpGEMM (C = A*B, FP64, and FP32) after Liu & Vinter's four-stage framework.
 
-The compute path is the CUDA library libspgemm.so (C ABI in include/spgemm.h);
+The compute path is the CUDA library libspgemm.so (libspgemm_f32.so for float values;
+C ABI in include/spgemm.h);
 this package only marshals arguments.  Importing it does not touch the GPU; the
 library is loaded on first use and the call fails loudly if it is missing."""
 from ._lib import SpgemmError, load as load_library, lib_path  # noqa: F401
-from .spgemm import CSR, BatchPlan, Plan, ReplayGraph, galerkin, make_opts, spgemm, spgemm_batched  # noqa: F401
+from .spgemm import CSR, BatchPlan, Plan, ReplayGraph, galerkin, make_opts, merge_micro, spgemm, spgemm_batched  # noqa: F401
 
-__all__ = ["CSR", "Plan", "BatchPlan", "ReplayGraph", "spgemm", "spgemm_batched", "galerkin", "make_opts",
+__all__ = ["CSR", "Plan", "BatchPlan", "ReplayGraph", "spgemm", "spgemm_batched", "galerkin", "make_opts", "merge_micro",
            "SpgemmError", "load_library", "lib_path"]

@@ -23,7 +23,7 @@ LIB_F32 = os.path.join(BUILD, "libspgemm_f32.so")
 # value type -> (library, object directory, extra nvcc flags)
 VARIANTS = {"f64": (LIB, BUILD, []), "f32": (LIB_F32, os.path.join(BUILD, "f32"), ["-DSPGEMM_FLOAT"])}
 
-SOURCES = ["stage12.cu", "heap.cu", "esc.cu", "merge.cu", "merge_bm.cu", "dense.cu", "arrange.cu", "predictor.cu", "replay.cu", "batched.cu",
+SOURCES = ["stage12.cu", "heap.cu", "esc.cu", "merge.cu", "merge_bm.cu", "dense.cu", "merge_micro.cu", "arrange.cu", "predictor.cu", "replay.cu", "batched.cu",
            "spgemm_api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

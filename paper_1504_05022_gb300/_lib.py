@@ -80,6 +80,7 @@ SIGNATURES = {
     "spgemm_graph_free": ([c_ptr], c_i32),
     "spgemm_galerkin": ([ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(Opts),
                          c_ptr, ctypes.POINTER(c_ptr), ctypes.POINTER(c_ptr), ctypes.POINTER(CsrOut)], c_i32),
+    "spgemm_merge_micro": ([c_i32, c_i32, c_i32, c_ptr, c_ptr, c_i64, c_i32, c_ptr, c_ptr, c_ptr], c_i32),
     "spgemm_predictor_create": ([c_ptr, c_i64, ctypes.POINTER(c_ptr)], c_i32),
     "spgemm_predictor_free": ([c_ptr], c_i32),
     "spgemm_row_features": ([ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_ptr, c_ptr], c_i32),

@@ -1165,6 +1165,26 @@ fail:
     return status;
 }
 
+extern "C" spgemm_status spgemm_merge_micro(int32_t method, int32_t threads, int32_t value_bytes,
+                                            const int32_t *keys, const void *vals, int64_t n, int32_t l,
+                                            int32_t *out_keys, void *out_vals, spgemm_stream_t stream) {
+    if (method < 0 || method > 2 || !keys || !out_keys || n <= 0 || l < 1 || (l & (l - 1)) != 0)
+        return SPGEMM_ERR_INVALID_ARG;
+    if (threads != 64 && threads != 128 && threads != 256 && threads != 512 && threads != 1024)
+        return SPGEMM_ERR_INVALID_ARG;
+    if (value_bytes != 0 && value_bytes != 4 && value_bytes != 8) return SPGEMM_ERR_INVALID_ARG;
+    if (value_bytes != 0 && (!vals || !out_vals)) return SPGEMM_ERR_INVALID_ARG;
+    if (n % (2 * (int64_t)l) != 0 || n / (2 * (int64_t)l) > INT32_MAX) return SPGEMM_ERR_INVALID_ARG;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (merge_micro_smem(l, value_bytes) > optin - 1024) return SPGEMM_ERR_INVALID_ARG;
+    e = launch_merge_micro(method, threads, value_bytes, keys, vals, n, l, out_keys, out_vals,
+                           reinterpret_cast<cudaStream_t>(stream));
+    return from_cuda(e);
+}
+
 extern "C" spgemm_status spgemm_free(spgemm_plan *p) {
     if (!p) return SPGEMM_OK;
     p->release();

@@ -378,3 +378,29 @@ def galerkin(R: CSR, A: CSR, P: CSR, stream: torch.cuda.Stream | None = None, **
     Ac = p2.numeric()
     p2._keep = p1
     return Ac, p1, p2
+
+
+MERGE_METHODS = {"ranking": 0, "merge_path": 1, "bitonic": 2}
+
+
+def merge_micro(keys: torch.Tensor, l: int, method: str = "merge_path", threads: int = 256,
+                vals: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None):
+    """The merge evaluation of Section 4.3: every group of 2l int32 keys holds two ascending
+    runs of length l, and is merged into one ascending sequence by one CTA of `threads`
+    threads with the ranking merge, merge path or bitonic merge.  vals (4- or 8-byte
+    elements, optional) move with their keys.  Returns (keys, vals or None)."""
+    if keys.dtype != torch.int32 or not keys.is_cuda or not keys.is_contiguous():
+        raise TypeError("keys must be a contiguous int32 CUDA tensor")
+    vb = 0 if vals is None else vals.element_size()
+    if vals is not None and (not vals.is_cuda or not vals.is_contiguous() or vals.numel() != keys.numel()):
+        raise ValueError("vals must be a contiguous CUDA tensor of keys' length")
+    out_k = torch.empty_like(keys)
+    out_v = None if vals is None else torch.empty_like(vals)
+    stream = stream if stream is not None else torch.cuda.current_stream(keys.device)
+    with torch.cuda.device(keys.device):
+        _lib.check(_lib.load().spgemm_merge_micro(
+            MERGE_METHODS[method], int(threads), vb, ctypes.c_void_p(keys.data_ptr()),
+            ctypes.c_void_p(vals.data_ptr() if vals is not None else 0), keys.numel(), int(l),
+            ctypes.c_void_p(out_k.data_ptr()), ctypes.c_void_p(out_v.data_ptr() if out_v is not None else 0),
+            ctypes.c_void_p(stream.cuda_stream)), "spgemm_merge_micro")
+    return out_k, out_v
