@@ -1,6 +1,8 @@
 """Host-side logic of bench.py and the autotuner that needs no GPU: the memory comparison
-against the precise method, the choice of tuned parameters per value type, and the
-algorithmic-byte model of the roofline."""
+against the precise method, the choice of tuned parameters per value type, the
+algorithmic-byte model and the roofline object built from a measurement, the rule that
+profiled DRAM traffic is dropped once its kernels' sources change, and the tuner's
+coordinate descent with its memory slack."""
 import json
 import os
 import sys
@@ -51,3 +53,116 @@ def test_single_precision_tuned_entries(tmp_path, monkeypatch):
     assert autotune.load("x:f32", "learned") is None
     opts = autotune.apply({"alloc_policy": "learned"}, {"dense_span": 16384, "dense_span_div": 0})
     assert opts == {"alloc_policy": "learned", "dense_span": 16384, "dense_span_div": 0}
+
+
+class _Args:
+    workload = "w"
+
+
+def _fake_measurement(A, kms, clocks=None):
+    """A bench measurement record of one product C = A*A: per-row products u, output
+    counts and bins, the per-class kernel times (ms per step) and the launch counts."""
+    blen = np.diff(A.row_ptr)
+    u = np.array([blen[A.col[A.row_ptr[i]:A.row_ptr[i + 1]]].sum() for i in range(A.nrows)], dtype=np.int64)
+    rn = (u + 1) // 2
+    bins = np.where(u > 256, 37, np.where(u > 32, 34, np.where(u > 1, 8, 1)))
+    return {"kms": kms, "st_all": [{"launches": {"merge": 4, "arrange": 1}}],
+            "arrays": [{"u": u, "row_nnz": rn, "bin": bins}], "policy": "learned", "ms_per_step": 5.0,
+            "clocks": clocks}, u, rn, bins
+
+
+def test_roofline_of_the_dominant_class(tmp_path, monkeypatch):
+    """The class with the largest time is reported; its algorithmic bytes count only its own
+    rows (bin 37 for the merge class); the FP64 ceiling follows the sampled SM clock."""
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 5000.0}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    A = gen.rmat(9, 16, seed=4)
+    m, u, rn, bins = _fake_measurement(A, {"merge": 2.0, "arrange": 1.0, "esc": 0.5}, {"sm_mhz": 1000.0})
+    r = bench.roofline(_Args, [(A, A)], m)
+    long_rows = np.nonzero(bins == 37)[0]
+    assert long_rows.size > 0 and long_rows.size < A.nrows
+    want = bench.algorithmic_bytes(A, A, u, long_rows, rn)
+    assert r["kernel"] == "merge" and r["bound"] == "hbm" and r["peak_source"] == "measured"
+    assert r["algorithmic_bytes_per_step"] == want
+    assert abs(r["achieved"] - want / 2e-3 / 1e9) < 1e-9 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12
+    assert r["launches_per_step"] == 4 and r["traffic"] is None
+    f = r["fp64"]
+    assert f["flops_per_step"] == 2 * int(u[long_rows].sum())
+    assert abs(f["peak"] - 608.0) < 1e-9  # 2 FMA x 2 flop x 152 SMs x 1 GHz
+    comp = A.nnz * 12 + (A.nrows + 1) * 4 + int(rn.sum()) * 12 + (A.nrows + 1) * 8
+    assert r["compulsory_bytes_per_step"] == comp
+    # the arrange class: C written and read once (24 B an entry) plus its row pointer
+    m2, _, _, _ = _fake_measurement(A, {"merge": 1.0, "arrange": 3.0})
+    r2 = bench.roofline(_Args, [(A, A)], m2)
+    assert r2["kernel"] == "arrange" and r2["fp64"] is None
+    assert r2["algorithmic_bytes_per_step"] == int(rn.sum()) * 24 + 8 * (A.nrows + 1)
+
+
+def test_roofline_without_measured_peaks_uses_the_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    A = gen.rmat(8, 16, seed=5)
+    m, _, _, _ = _fake_measurement(A, {"merge": 1.0})
+    r = bench.roofline(_Args, [(A, A)], m)
+    assert r["peak"] == 6800.0 and r["peak_source"] == "fallback"
+    assert abs(r["fp64"]["peak"] - 2 * 2 * 152 * 2070e6 / 1e9) < 1e-9  # no clock samples: the maximum clock
+
+
+def test_traffic_only_while_the_kernel_sources_match(tmp_path, monkeypatch):
+    """DRAM traffic from a profile is reported only while the digest of the sources it was
+    taken from matches the sources as they are; after a change it is null."""
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    for f in bench.KERNEL_SOURCES["merge"]:
+        p = tmp_path / f
+        p.parent.mkdir(parents=True, exist_ok=True)
+        p.write_text(f"// {f}\n")
+    (tmp_path / "profiles").mkdir()
+    rec = {"w": {"learned": {"merge": {"bytes_per_step": 12345,
+                                       "source_digest": bench.src_digest(bench.KERNEL_SOURCES["merge"])}}}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    A = gen.rmat(8, 16, seed=6)
+    m, _, _, _ = _fake_measurement(A, {"merge": 1.0})
+    assert bench.roofline(_Args, [(A, A)], m)["traffic"] == 12345
+    (tmp_path / bench.KERNEL_SOURCES["merge"][1]).write_text("// changed\n")
+    assert bench.roofline(_Args, [(A, A)], m)["traffic"] is None
+
+
+class _FakeRunner:
+    """Device time and peak memory of a configuration from a table, for the tuner's logic."""
+
+    def __init__(self, cost):
+        self.cost, self.calls = cost, []
+
+    def time(self, opts, reps=3):
+        self.calls.append(dict(opts))
+        return self.cost(opts)
+
+
+def test_tuner_keeps_faster_configurations_within_the_memory_slack():
+    from paper_1504_05022_gb300 import autotune
+
+    def cost(o):
+        ms, peak = 10.0, 1000
+        if o.get("heap_max_u") == 16:
+            ms -= 2.0                    # faster, same memory: kept
+        if o.get("merge_batch") == 512:
+            ms -= 5.0
+            peak += 1000                 # much faster but twice the memory: refused
+        if o.get("smem_cap_max") == 4096:
+            ms -= 1.0
+            peak += 40                   # faster, within 5% more memory: kept
+        if o.get("merge_miss") == 8192:
+            ms -= 0.05                   # under the 1% threshold: not worth a change
+        return ms, peak
+
+    runner = _FakeRunner(cost)
+    rec = autotune.tune(runner, "upper_bound", rounds=3, reps=1, log=lambda *_: None)
+    best = rec["params"]
+    assert best["heap_max_u"] == 16 and best["smem_cap_max"] == 4096
+    assert best["merge_batch"] == autotune.SPACE["merge_batch"][0]
+    assert rec["default_ms"] == 10.0 and rec["ms"] == 7.0 and rec["default_peak_bytes"] == 1000
+    assert set(best) == set(autotune.POLICY_PARAMS["upper_bound"])
+    # the second round changes nothing, so the search stops there: default + 2 rounds of trials
+    per_round = sum(len(autotune.SPACE[k]) - 1 for k in autotune.POLICY_PARAMS["upper_bound"])
+    assert len(runner.calls) == 1 + 2 * per_round == rec["trials"]
+    assert all(c["alloc_policy"] == "upper_bound" for c in runner.calls)
