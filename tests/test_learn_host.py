@@ -4,14 +4,11 @@ weights judged by the oracle on matrices the training held out (every seed s wit
 The network's forward pass here is the oracle's (FP64); its row sizes are the oracle's exact
 counts, so what is measured is the stored network itself."""
 import json
-import os
 
 import numpy as np
 import pytest
 
 import gen
-
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
