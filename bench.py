@@ -8,7 +8,8 @@ are already resident in device memory.  L2 is flushed (a 512 MB write) between
 timed steps, outside the timed events.
 
 Prints one JSON line.  `--impl reference` times the CPU oracle (the reference arm)
-on the same workload.  Under torchrun each rank runs an independent replica (the
+on the same workload: W untimed steps, then K timed ones, each a pass over the workload
+or over a bounded seeded sample of it.  Under torchrun each rank runs an independent replica (the
 method does not exchange data between problems), and rank 0 reports the
 aggregate.
 """
@@ -735,77 +736,103 @@ def _products(A):
     return blen[A.col].sum()
 
 
-def run_cpu_baseline(args, budget_s=20.0, pairs=None):
-    """The oracle, as it stands, on the host cores: repeated full passes over the workload
-    (or a row sample when a pass is too long), median time, GFLOP/s on the products computed."""
+def oracle_sample(args, pairs, cap_products):
+    """One pass of the oracle over a bounded sample of the workload: the whole workload when
+    it has at most cap_products products, else seeded random rows (or whole pairs of a batch)
+    up to that count.  Returns (step, products, threads, sample description)."""
     import oracle
-    pairs = make_workload(args.workload) if pairs is None else pairs
+    nthreads = oracle.num_threads()
     if args.workload == "batch512":
-        return _cpu_baseline_batch(pairs, budget_s)
+        order = np.random.default_rng(0).permutation(len(pairs))
+        sel, prods = [], 0
+        for i in order:
+            u = _products_ab(*pairs[i])
+            if prods + u > cap_products and sel:
+                continue
+            sel.append(int(i))
+            prods += u
+
+        def step():
+            for i in sel:
+                oracle.spgemm_rows(pairs[i][0], pairs[i][1], None, nthreads=nthreads)
+        return step, prods, nthreads, f"{len(sel)} of {len(pairs)} pairs (seeded random order, products capped)"
     A, B = pairs[0]
     B = A if B is None else B
-    nthreads = oracle.num_threads()
     blen = np.diff(B.row_ptr)
     cs = np.concatenate([[0], np.cumsum(blen[A.col])])
     u = cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]
     total_u = int(u.sum())
     rows = None
     sample = "full workload"
-    # keep one pass under ~budget/3 seconds assuming >= 20M products/s/thread
-    cap_products = int(20e6 * nthreads * budget_s / 3)
+    if len(pairs) == 2 and pairs[1][1] is None:
+        sample = "the chain's first product, A*P"
     if total_u > cap_products:
-        rng = np.random.default_rng(0)
-        perm = rng.permutation(A.nrows)
-        cs = np.cumsum(u[perm])
-        rows = np.sort(perm[: int(np.searchsorted(cs, cap_products)) + 1])
+        perm = np.random.default_rng(0).permutation(A.nrows)
+        cu = np.cumsum(u[perm])
+        rows = np.sort(perm[: int(np.searchsorted(cu, cap_products)) + 1])
         sample = f"{rows.size} of {A.nrows} rows (random, seed 0)"
     prods = total_u if rows is None else int(u[rows].sum())
-    times = []
-    t_start = time.perf_counter()
-    while len(times) < 5 and (time.perf_counter() - t_start) < budget_s:
-        t0 = time.perf_counter()
+
+    def step():
         oracle.spgemm_rows(A, B, rows, nthreads=nthreads)
-        times.append(time.perf_counter() - t0)
-    t = float(np.median(times))
-    # one core, on a smaller row sample (about 80 M products)
-    rng1 = np.random.default_rng(1)
-    perm1 = rng1.permutation(A.nrows)
-    cs1 = np.cumsum(u[perm1])
-    rows1 = np.sort(perm1[: int(np.searchsorted(cs1, 80_000_000)) + 1])
-    t1 = time.perf_counter()
-    oracle.spgemm_rows(A, B, rows1, nthreads=1)
-    t1 = time.perf_counter() - t1
-    return {"value": 2.0 * prods / t / 1e9, "unit": "GFLOP/s", "cores": nthreads, "kind": "oracle",
-            "sample": f"{sample}; {prods} products; median of {len(times)} passes",
-            "ms_per_pass": t * 1e3,
-            "one_core": {"value": 2.0 * int(u[rows1].sum()) / t1 / 1e9, "unit": "GFLOP/s",
-                         "sample": f"{rows1.size} random rows (seed 1), {int(u[rows1].sum())} products, one pass"}}
+    return step, prods, nthreads, sample
 
 
-def _cpu_baseline_batch(pairs, budget_s):
-    """Oracle on a seeded random sample of whole pairs of the batch (bounded product count)."""
+def run_cpu_baseline(args, budget_s=20.0, pairs=None):
+    """The oracle, as it stands, on the host cores: repeated passes over the workload (or a
+    bounded sample of it), median time, GFLOP/s on the products computed."""
     import oracle
-    nthreads = oracle.num_threads()
-    cap_products = int(20e6 * nthreads * budget_s / 3)
-    order = np.random.default_rng(0).permutation(len(pairs))
-    sel, prods = [], 0
-    for i in order:
-        u = _products_ab(*pairs[i])
-        if prods + u > cap_products and sel:
-            continue
-        sel.append(int(i))
-        prods += u
+    pairs = make_workload(args.workload) if pairs is None else pairs
+    # keep one pass under ~budget/3 seconds assuming >= 20M products/s/thread
+    cap_products = int(20e6 * oracle.num_threads() * budget_s / 3)
+    step, prods, nthreads, sample = oracle_sample(args, pairs, cap_products)
     times = []
     t_start = time.perf_counter()
     while len(times) < 5 and (time.perf_counter() - t_start) < budget_s:
         t0 = time.perf_counter()
-        for i in sel:
-            oracle.spgemm_rows(pairs[i][0], pairs[i][1], None, nthreads=nthreads)
+        step()
         times.append(time.perf_counter() - t0)
     t = float(np.median(times))
-    return {"value": 2.0 * prods / t / 1e9, "unit": "GFLOP/s", "cores": nthreads, "kind": "oracle",
-            "sample": f"{len(sel)} of {len(pairs)} pairs (seeded random order, products capped); {prods} products; "
-                      f"median of {len(times)} passes", "ms_per_pass": t * 1e3}
+    out = {"value": 2.0 * prods / t / 1e9, "unit": "GFLOP/s", "cores": nthreads, "kind": "oracle",
+           "sample": f"{sample}; {prods} products; median of {len(times)} passes", "ms_per_pass": t * 1e3}
+    if args.workload != "batch512":
+        # one core, on a smaller row sample (about 80 M products)
+        A, B = pairs[0]
+        B = A if B is None else B
+        blen = np.diff(B.row_ptr)
+        cs = np.concatenate([[0], np.cumsum(blen[A.col])])
+        u = cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]
+        perm1 = np.random.default_rng(1).permutation(A.nrows)
+        cs1 = np.cumsum(u[perm1])
+        rows1 = np.sort(perm1[: int(np.searchsorted(cs1, 80_000_000)) + 1])
+        t1 = time.perf_counter()
+        oracle.spgemm_rows(A, B, rows1, nthreads=1)
+        t1 = time.perf_counter() - t1
+        out["one_core"] = {"value": 2.0 * int(u[rows1].sum()) / t1 / 1e9, "unit": "GFLOP/s",
+                           "sample": f"{rows1.size} random rows (seed 1), {int(u[rows1].sum())} products, one pass"}
+    return out
+
+
+def run_reference(args, total_s=150.0):
+    """The reference arm: the oracle on the host cores, W untimed steps, then exactly K timed
+    steps, each one pass over a bounded sample of the workload sized so that the whole run
+    takes about total_s seconds or less (at >= 20M products/s/thread)."""
+    import oracle
+    pairs = make_workload(args.workload)
+    per_step = min(20.0, total_s / max(1, args.steps + args.warmup))
+    step, prods, nthreads, sample = oracle_sample(args, pairs, int(20e6 * oracle.num_threads() * per_step))
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    total = float(sum(times))
+    value = 2.0 * prods * len(times) / total / 1e9
+    return {"value": value, "unit": "GFLOP/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"{sample}; {prods} products per step; {len(times)} timed steps after {args.warmup} untimed",
+            "ms_per_step": total / len(times) * 1e3}
 
 
 def run_merge_micro(args):
@@ -891,10 +918,10 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = run_cpu_baseline(args, budget_s=max(20.0, 6.0 * (args.steps + args.warmup)))
+        cb = run_reference(args)
         out = {"metric": "FP64 SpGEMM GFLOP/s (2*products/s)", "value": cb["value"], "unit": "GFLOP/s",
                "impl": "reference", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-               "ms_per_step": cb["ms_per_pass"], "higher_is_better": True, "scaling": "weak",
+               "ms_per_step": cb["ms_per_step"], "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
                "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
                "cpu_baseline": cb,

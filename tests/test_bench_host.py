@@ -166,3 +166,41 @@ def test_tuner_keeps_faster_configurations_within_the_memory_slack():
     per_round = sum(len(autotune.SPACE[k]) - 1 for k in autotune.POLICY_PARAMS["upper_bound"])
     assert len(runner.calls) == 1 + 2 * per_round == rec["trials"]
     assert all(c["alloc_policy"] == "upper_bound" for c in runner.calls)
+
+
+class _RefArgs:
+    def __init__(self, workload, steps, warmup):
+        self.workload, self.steps, self.warmup = workload, steps, warmup
+
+
+def test_oracle_sample_is_bounded(oracle_mod):
+    """A pass covers the whole workload when it fits the product cap, otherwise a seeded row
+    sample whose products stay within the cap plus one row."""
+    args = _RefArgs("rmat14x16", 1, 0)
+    pairs = bench.make_workload("rmat14x16")
+    A = pairs[0][0]
+    blen = np.diff(A.row_ptr)
+    u = np.array([blen[A.col[A.row_ptr[i]:A.row_ptr[i + 1]]].sum() for i in range(A.nrows)])
+    _, prods, _, sample = bench.oracle_sample(args, pairs, 10 ** 12)
+    assert prods == int(u.sum()) and sample == "full workload"
+    cap = int(u.sum()) // 10
+    step, prods, _, sample = bench.oracle_sample(args, pairs, cap)
+    assert cap <= prods <= cap + int(u.max()) and "rows (random, seed 0)" in sample
+    step()
+
+
+def test_reference_arm_times_exactly_k_steps_after_w(oracle_mod, monkeypatch):
+    calls = []
+    real = bench.oracle_sample
+
+    def counted(args, pairs, cap):
+        step, prods, n, sample = real(args, pairs, cap)
+
+        def wrapped():
+            calls.append(1)
+            step()
+        return wrapped, prods, n, sample
+    monkeypatch.setattr(bench, "oracle_sample", counted)
+    r = bench.run_reference(_RefArgs("lap2d64", 3, 2))
+    assert len(calls) == 5 and "3 timed steps after 2 untimed" in r["sample"]
+    assert r["value"] > 0 and r["ms_per_step"] > 0 and r["kind"] == "oracle" and r["cores"] >= 1
