@@ -303,6 +303,28 @@ def test_row_counts_match_full_product():
     assert np.array_equal(oracle.row_counts(A, A, rows), np.diff(ref.row_ptr)[rows])
 
 
+
+def test_sampled_rows_and_thread_counts_are_bit_exact():
+    """The full-size checks compare sampled rows: spgemm_rows on a subset (any order, with
+    repeats) must give exactly those rows of the full product, and the result must not
+    depend on the thread count (each row is summed in the same order by one thread)."""
+    import oracle
+    A = gen.rmat(11, 12, seed=8)
+    ref = oracle.spgemm(A, A, nthreads=1)
+    for nt in (2, 5, 0):
+        C = oracle.spgemm(A, A, nthreads=nt)
+        assert np.array_equal(C.row_ptr, ref.row_ptr) and np.array_equal(C.col, ref.col)
+        assert np.array_equal(C.val, ref.val) and np.array_equal(C.den, ref.den)
+    rows = np.array([2047, 0, 17, 17, 1024, 3])
+    off, col, val, den = oracle.spgemm_rows(A, A, rows, nthreads=3)
+    for j, i in enumerate(rows):
+        s, e = ref.row_ptr[i], ref.row_ptr[i + 1]
+        assert np.array_equal(col[off[j]:off[j + 1]], ref.col[s:e])
+        assert np.array_equal(val[off[j]:off[j + 1]], ref.val[s:e])
+        assert np.array_equal(den[off[j]:off[j + 1]], ref.den[s:e])
+    with pytest.raises(ValueError):
+        oracle.spgemm_rows(A, A, np.array([A.nrows]))
+
 def _galerkin_oracle(A, P):
     import oracle
     R = gen.transpose(P)
