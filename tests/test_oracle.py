@@ -22,7 +22,7 @@ import numpy as np
 import pytest
 
 import gen
-from tests.helpers import (REL_TOL, assert_csr_equal, csr_pattern, csr_to_dense, dense,
+from tests.helpers import (REL_TOL, csr_pattern, csr_to_dense, dense,
                            load_golden, pattern)
 
 
