@@ -212,15 +212,14 @@ __global__ void k_mlp_fwd_bwd(const float *__restrict__ params, const float *__r
 // over all samples.  Blocks 0..31: layer 1, 32..63: layer 2, 64..80: layer 3.
 __global__ void k_mlp_grad_reduce(const float *__restrict__ rec, int64_t n, float *__restrict__ grad) {
     const int b = blockIdx.x;
-    int layer, o, nin, din, ain, gw, gb;
-    if (b < MLP_HID) {
-        layer = 1; o = b; nin = MLP_IN; din = R_DZ1; ain = R_XH; gw = OFF_W1; gb = OFF_B1;
-    } else if (b < 2 * MLP_HID) {
-        layer = 2; o = b - MLP_HID; nin = MLP_HID; din = R_DZ2; ain = R_H1; gw = OFF_W2; gb = OFF_B2;
-    } else {
-        layer = 3; o = b - 2 * MLP_HID; nin = MLP_HID; din = R_DOUT; ain = R_H2; gw = OFF_W3; gb = OFF_B3;
+    int o, nin, din, ain, gw, gb;
+    if (b < MLP_HID) {  // layer 1
+        o = b; nin = MLP_IN; din = R_DZ1; ain = R_XH; gw = OFF_W1; gb = OFF_B1;
+    } else if (b < 2 * MLP_HID) {  // layer 2
+        o = b - MLP_HID; nin = MLP_HID; din = R_DZ2; ain = R_H1; gw = OFF_W2; gb = OFF_B2;
+    } else {  // layer 3
+        o = b - 2 * MLP_HID; nin = MLP_HID; din = R_DOUT; ain = R_H2; gw = OFF_W3; gb = OFF_B3;
     }
-    (void)layer;
     float acc[MLP_HID + 1];
 #pragma unroll
     for (int i = 0; i <= MLP_HID; ++i) acc[i] = 0.f;

@@ -734,7 +734,6 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
     spgemm_status status = SPGEMM_OK;
     if (nwork <= 0) return SPGEMM_OK;
     StageArgs a = stage_args(p);
-    const int batch = p->batch;
     const int capmax = p->capmax;
     const bool use_level1 = p->opts.long_rows == SPGEMM_LONG_ROWS_LEVEL1;
     const bool learned = p->opts.alloc_policy == SPGEMM_ALLOC_LEARNED;
