@@ -88,3 +88,23 @@ def test_value_types_are_checked_before_any_call():
         _value_type([_M("f64"), _M("f32")], {})
     with pytest.raises(TypeError):
         _value_type([_M("f32"), _M("f32")], {"predictor": _P("f64")})
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the built library the binding raises instead of computing
+    anything itself; a nonzero status becomes an exception naming it."""
+    from paper_1504_05022_gb300 import _build, _lib
+    _build.build()
+    with pytest.raises(_lib.SpgemmError, match="SPGEMM_ERR_UNSORTED"):
+        _lib.check(3, "probe")
+    _lib.check(0, "probe")
+    with pytest.raises(ValueError):
+        _lib.load(dtype="f16")
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "_libs", {})
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "libspgemm.so"))
+    monkeypatch.setattr(_build, "LIB_F32", str(tmp_path / "libspgemm_f32.so"))
+    with pytest.raises(ImportError, match="not built"):
+        _lib.load(build_if_missing=False)
+    with pytest.raises(ImportError, match="not built"):
+        _lib.load(build_if_missing=False, dtype="f32")
