@@ -374,3 +374,47 @@ def test_aggregation_generators_agree():
         assert np.array_equal(gen.agg_P2(g, 3).col, gen.agg_P(g).col)
     assert [(P.nrows, P.ncols) for P in gen.galerkin_levels(32, 3)] == \
         [(32 ** 3, 16 ** 3), (16 ** 3, 8 ** 3), (8 ** 3, 4 ** 3)]
+
+
+def _hierarchy(A, Ps):
+    import oracle
+    out = []
+    for P in Ps:
+        AP = oracle.spgemm(A, P)
+        APm = gen.HostCSR(A.nrows, P.ncols, AP.row_ptr, AP.col, AP.val)
+        Ac = oracle.spgemm(gen.transpose(P), APm)
+        A = gen.HostCSR(Ac.nrows, Ac.ncols, Ac.row_ptr, Ac.col, Ac.val)
+        out.append(A)
+    return out
+
+
+def _offsets(M, h, dim):
+    rows = np.repeat(np.arange(M.nrows), np.diff(M.row_ptr))
+    d = [((M.col // h ** k) % h) - ((rows // h ** k) % h) for k in range(dim)]
+    return np.stack(d, 1)
+
+
+def test_galerkin_hierarchies_closed_form():
+    """Every level of the piecewise-constant hierarchies, every entry.  Aggregation keeps the
+    stencil shape and maps its values by a recursion that does not depend on the boundary
+    (a block's own couplings and the couplings across a block face are the same for every
+    block): 2D 9-point (diagonal d, edge e, corner c) -> (4d + 8e + 4c, 2e + 2c, c) from
+    (8, -1, -1); 3D 7-point (diagonal d, face f) -> (8d + 24f, 4f) from (6, -1)."""
+    g, (d, e, c) = 32, (8.0, -1.0, -1.0)
+    for lvl, A in enumerate(_hierarchy(gen.lap2d9(g), gen.galerkin_levels(g, 2))):
+        h = g >> (lvl + 1)
+        d, e, c = 4 * d + 8 * e + 4 * c, 2 * e + 2 * c, c
+        off = _offsets(A, h, 2)
+        kind = np.abs(off).sum(1)
+        assert A.nnz == (3 * h - 2) ** 2 and np.abs(off).max() == 1
+        assert np.all(A.val[kind == 0] == d) and np.all(A.val[kind == 1] == e) and np.all(A.val[kind == 2] == c)
+    assert (d, e, c) == (92.0, -22.0, -1.0)  # the 4 x 4 level: interior row sum 92 - 4*22 - 4 = 0
+    g, (d, f) = 16, (6.0, -1.0)
+    for lvl, A in enumerate(_hierarchy(gen.lap3d7(g), gen.galerkin_levels(g, 3))):
+        h = g >> (lvl + 1)
+        d, f = 8 * d + 24 * f, 4 * f
+        off = _offsets(A, h, 3)
+        kind = np.abs(off).sum(1)
+        assert A.nnz == 7 * h ** 3 - 6 * h ** 2 and kind.max() == 1
+        assert np.all(A.val[kind == 0] == d) and np.all(A.val[kind == 1] == f)
+    assert (d, f) == (96.0, -16.0)  # the 4 x 4 x 4 level
