@@ -399,7 +399,8 @@ def test_galerkin_hierarchies_closed_form():
     stencil shape and maps its values by a recursion that does not depend on the boundary
     (a block's own couplings and the couplings across a block face are the same for every
     block): 2D 9-point (diagonal d, edge e, corner c) -> (4d + 8e + 4c, 2e + 2c, c) from
-    (8, -1, -1); 3D 7-point (diagonal d, face f) -> (8d + 24f, 4f) from (6, -1)."""
+    (8, -1, -1); 3D 7-point (diagonal d, face f) -> (8d + 24f, 4f) from (6, -1); 3D 27-point
+    below."""
     g, (d, e, c) = 32, (8.0, -1.0, -1.0)
     for lvl, A in enumerate(_hierarchy(gen.lap2d9(g), gen.galerkin_levels(g, 2))):
         h = g >> (lvl + 1)
@@ -418,3 +419,17 @@ def test_galerkin_hierarchies_closed_form():
         assert A.nnz == 7 * h ** 3 - 6 * h ** 2 and kind.max() == 1
         assert np.all(A.val[kind == 0] == d) and np.all(A.val[kind == 1] == f)
     assert (d, f) == (96.0, -16.0)  # the 4 x 4 x 4 level
+    # 3D 27-point: (diagonal d, face f, edge e, corner c) -> (8d + 24f + 24e + 8c, 4f + 8e + 4c,
+    # 2e + 2c, c) from (26, -1, -1, -1); the first level is the (152, -16, -4, -1) operator
+    g, (d, f, e, c) = 16, (26.0, -1.0, -1.0, -1.0)
+    for lvl, A in enumerate(_hierarchy(gen.lap3d27(g), gen.galerkin_levels(g, 3))):
+        h = g >> (lvl + 1)
+        d, f, e, c = 8 * d + 24 * f + 24 * e + 8 * c, 4 * f + 8 * e + 4 * c, 2 * e + 2 * c, c
+        off = _offsets(A, h, 3)
+        kind = np.abs(off).sum(1)
+        assert A.nnz == (3 * h - 2) ** 3 and np.abs(off).max() == 1
+        for k, want in enumerate((d, f, e, c)):
+            assert np.all(A.val[kind == k] == want), (lvl, k)
+        if lvl == 0:
+            assert (d, f, e, c) == (152.0, -16.0, -4.0, -1.0)
+    assert (d, f, e, c) == (728.0, -100.0, -10.0, -1.0)  # interior row sum 728 - 600 - 120 - 8 = 0
