@@ -52,3 +52,21 @@ def test_autotune_apply_and_load(tmp_path, monkeypatch):
     monkeypatch.setattr(autotune, "TUNED", str(f))
     assert autotune.load("w", "hybrid") == {"heap_block": 64}
     assert autotune.load("w", "learned") is None and autotune.load("x", "hybrid") is None
+
+
+def test_rmat_headline_recipe():
+    """The R-MAT 2^16 x 16 input of the headline product: its size after merging duplicates,
+    its product count, first-level quadrant shares near (a, b, c, d) = (.57, .19, .19, .05)
+    (duplicates, most frequent in the dense quadrant, lower its share a little) and values in
+    (-1, 1)."""
+    A = gen.rmat(16, 16, seed=1)
+    assert A.nrows == A.ncols == 1 << 16
+    assert A.nnz == 955_117
+    assert int(np.diff(A.row_ptr)[A.col].astype(np.int64).sum()) == 402_077_751
+    rows = np.repeat(np.arange(A.nrows), np.diff(A.row_ptr))
+    h = A.nrows // 2
+    q = [np.mean((rows < h) & (A.col < h)), np.mean((rows < h) & (A.col >= h)),
+         np.mean((rows >= h) & (A.col < h)), np.mean((rows >= h) & (A.col >= h))]
+    assert abs(q[0] - 0.57) < 0.03 and abs(q[1] - 0.19) < 0.015 and abs(q[2] - 0.19) < 0.015
+    assert abs(q[3] - 0.05) < 0.01
+    assert A.val.min() > -1.0 and A.val.max() < 1.0
