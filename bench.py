@@ -1,11 +1,13 @@
 """Benchmark: FP64 CSR SpGEMM throughput (GFLOP/s = 2 * products / s) on one GB300.
 
-Default workload: C = A*A, A = R-MAT with 2^16 rows/cols, 16 samples/row
-(a,b,c,d = .57,.19,.19,.05, duplicates merged, values U(-1,1), seed 1).  A step is
-one full pass of the four-stage framework (symbolic + numeric: stages 1-4,
-including the size read-backs and allocations the method needs) on inputs that
-are already resident in device memory.  L2 is flushed (a 512 MB write) between
-timed steps, outside the timed events.
+Default workload: C = A*A, A = R-MAT with 2^20 rows/cols, 8 samples/row
+(a,b,c,d = .57,.19,.19,.05, duplicates merged, values U(-1,1), seed 1), under the learned
+preallocation; the same product is also timed under the paper's plain (hybrid) form and
+the upper-bound policy, and the 512-pair batch is timed batched against 512 sequential
+plain calls (`compare.batch512`).  A step is one full pass of the four-stage framework
+(symbolic + numeric: stages 1-4, including the size read-backs and allocations the method
+needs) on inputs that are already resident in device memory.  L2 is flushed (a 512 MB
+write) between timed steps, outside the timed events.  Step times are medians.
 
 Prints one JSON line.  `--impl reference` times the CPU oracle (the reference arm)
 on the same workload: W untimed steps, then K timed ones, each a pass over the workload
@@ -293,7 +295,7 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
     st_all = [p.stats() for p in plans]
     arrays = [p.arrays() for p in plans]
     sum_u = sum(p.upper_bound_nnz for p in plans)
-    value, ms_step = job_gflops(sum_u, float(np.mean(times)), world, dev)
+    value, ms_step = job_gflops(sum_u, float(np.median(times)), world, dev)
     res = {"policy": policy, "ms_per_step": ms_step, "value": value,
            "kms": kms, "launches": launches, "wall_s": t_wall,
            "st_all": st_all, "arrays": arrays, "sum_u": sum_u, "nnz_C": int(st_all[-1]["nnz_c"]),
@@ -326,7 +328,7 @@ def job_gflops(products, ms, world, device):
 def time_steps(args, stream, flush, step):
     """W untimed warm-up calls of step(), then K calls each bracketed by CUDA events on
     `stream`, L2 flushed (512 MB write) before each, outside the events.  step() returns an
-    object kept alive until the next call.  Returns this rank's mean milliseconds per step."""
+    object kept alive until the next call.  Returns this rank's median milliseconds per step."""
     import torch
     keep = None
     for _ in range(args.warmup):
@@ -346,7 +348,7 @@ def time_steps(args, stream, flush, step):
         if k < args.steps - 1:
             del keep
             keep = None
-    return float(np.mean(times)), keep
+    return float(np.median(times)), keep
 
 
 def galerkin_graph(args, spg, dev, stream, flush, opts, world):
@@ -393,111 +395,160 @@ def galerkin_graph(args, spg, dev, stream, flush, opts, world):
             "nnz_Ac": nnz_ac}
 
 
-def run_batch(args, world, device):
-    """512 independent products: one batched pipeline (block-diagonal concatenation) under the
-    learned and the plain policy, 512 sequential plain calls, and the batched plan's
-    values-only replay captured in a CUDA graph."""
-    pairs = make_workload("batch512")  # generated by spawned workers before CUDA is touched
-    import torch
+class BatchRig:
+    """The 512 batched pairs on the device, and the two ways of computing them that the metric
+    compares: one batched pipeline (block-diagonal concatenation, in waves) and 512 sequential
+    plain calls."""
 
-    import paper_1504_05022_gb300 as spg
-    spg.load_library()
-    dev = torch.device(f"cuda:{device}")
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    As = [spg.CSR.from_host(A, device=dev, rowptr_dtype=torch.int32) for A, _ in pairs]
-    Bs = [spg.CSR.from_host(B, device=dev, rowptr_dtype=torch.int32) for _, B in pairs]
-    products = int(sum(_products_ab(A, B) for A, B in pairs))
-    res = {}
+    def __init__(self, args, world, device, pairs=None):
+        # generated by spawned workers (pair i depends only on seed i)
+        self.pairs = make_workload("batch512") if pairs is None else pairs
+        import torch
 
-    def batched(policy, clocks=False, wave_mproducts=0, tuned=False):
+        import paper_1504_05022_gb300 as spg
+        spg.load_library()
+        self.spg, self.args, self.world = spg, args, world
+        self.dev = torch.device(f"cuda:{device}")
+        torch.cuda.set_device(self.dev)
+        self.stream = torch.cuda.current_stream(self.dev)
+        self.flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=self.dev)
+        self.As = [spg.CSR.from_host(A, device=self.dev, rowptr_dtype=torch.int32) for A, _ in self.pairs]
+        self.Bs = [spg.CSR.from_host(B, device=self.dev, rowptr_dtype=torch.int32) for _, B in self.pairs]
+        self.products = int(sum(_products_ab(A, B) for A, B in self.pairs))
+
+    def batched(self, policy, clocks=False, wave_mproducts=0, tuned=False):
+        """One BatchPlan per step.  Returns (figures, the last step's plan, objects to keep alive)."""
+        import torch
+        args, spg = self.args, self.spg
         opts, keep = policy_opts(policy, "batch512" if tuned and args.tuned else None)
         opts = dict(opts, wave_mproducts=wave_mproducts)
 
         def step(o=opts):
-            bp = spg.BatchPlan(As, Bs, stream=stream, **o)
+            bp = spg.BatchPlan(self.As, self.Bs, stream=self.stream, **o)
             bp.numeric()
             return bp
-        clk = ClockSampler(dev.index) if clocks else None
+        clk = ClockSampler(self.dev.index) if clocks else None
         if clk:
             clk.__enter__()
             clk.wait_first_sample()
-        ms, bp = time_steps(args, stream, flush, step)
-        value, ms = job_gflops(products, ms, world, dev)
+        ms, bp = time_steps(args, self.stream, self.flush, step)
+        value, ms = job_gflops(self.products, ms, self.world, self.dev)
         if clk:
             clk.__exit__(None, None, None)
         st = bp.stats()
-        flush.fill_(-1.0)
+        self.flush.fill_(-1.0)
         torch.cuda.synchronize()
         tp = step(dict(opts, record_timing=True))  # once more with CUDA events around every kernel
         torch.cuda.synchronize()
         kms = tp.stats()["kernel_ms"]
         del tp
-        out = {"value": value, "ms_per_step": ms,
+        out = {"value": value, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
                "peak_bytes": int(st["peak_bytes"]), "held_bytes_after": int(st["held_bytes"]),
                "launches_per_step": int(sum(st["launches"].values())), "kms": kms,
                "rows_bin37": int(st["bin_count"][37]), "rows_fallback": int(st["rows_fallback"]),
-               "merge_rounds": int(st["merge_rounds"]), "waves": bp.n_waves,
-               "clocks": clk.summary() if clk else None}
+               "merge_rounds": int(st["merge_rounds"]), "item_rounds": int(st["item_rounds"]),
+               "waves": bp.n_waves, "clocks": clk.summary() if clk else None}
         return out, bp, keep
 
-    def sequential(policy):
+    def sequential(self, policy):
+        """The 512 pairs as 512 plain calls, one after another, on one stream."""
+        args, spg = self.args, self.spg
         opts, keep = policy_opts(policy)
-        stats = {}
 
         def step():
             plans = []
-            for A, B in zip(As, Bs):
-                p = spg.Plan(A, B, stream=stream, **opts)
+            for A, B in zip(self.As, self.Bs):
+                p = spg.Plan(A, B, stream=self.stream, **opts)
                 p.numeric()
                 plans.append(p)
             return plans
-        ms, plans = time_steps(args, stream, flush, step)
-        value, ms = job_gflops(products, ms, world, dev)
+        ms, plans = time_steps(args, self.stream, self.flush, step)
+        value, ms = job_gflops(self.products, ms, self.world, self.dev)
         held, peak, launches = 0, 0, 0
         for p in plans:  # results stay resident, so call i peaks on top of results 0..i-1
             st = p.stats()
             peak = max(peak, held + st["peak_bytes"])
             held += st["held_bytes"]
             launches += sum(st["launches"].values())
-        stats.update({"value": value, "ms_per_step": ms,
-                      "peak_bytes": int(peak), "launches_per_step": int(launches)})
         del plans, keep
-        return stats
+        return {"value": value, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                "peak_bytes": int(peak), "launches_per_step": int(launches)}
 
+    def replay_graph(self, policy):
+        """Values-only replay (structure reused) of the batched plan, captured in one CUDA graph."""
+        import torch
+        args, spg = self.args, self.spg
+        opts, keep_g = policy_opts(policy, "batch512" if args.tuned else None)
+        gstream = torch.cuda.Stream(self.dev)  # a graph is captured from a created stream, not the legacy one
+        torch.cuda.synchronize()
+        gp = spg.BatchPlan(self.As, self.Bs, stream=gstream, **opts)
+        gp.numeric()
+        g = spg.ReplayGraph([gp])
+        ms_g, _ = time_steps(args, gstream, self.flush, g.launch)
+        v_g, ms_g = job_gflops(self.products, ms_g, self.world, self.dev)
+        gp.check()
+        del g, gp, keep_g
+        torch.cuda.synchronize()
+        return {"value": v_g, "ms_per_step": ms_g,
+                "note": "values-only replay (structure reused) of the batched plan, one CUDA graph"}
+
+    def release(self):
+        import torch
+        del self.As, self.Bs, self.flush
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+
+def batch_compare(args, world, device):
+    """The batched half of the metric on the 512-pair workload, for the default line: the batched
+    learned pipeline against 512 sequential calls of the paper's plain form (hybrid)."""
+    rig = BatchRig(args, world, device)
+    head = "learned" if _weights_exist() else "hybrid"
+    main, bp, keep = rig.batched(head, tuned=True)
+    del bp, keep
+    main.pop("clocks", None)
+    seq = rig.sequential("hybrid")
+    out = {"workload": "batch512", "description": WORKLOADS["batch512"], "products_per_step": rig.products,
+           "batched_" + head: main, "sequential_hybrid": seq,
+           "speedup_batched_over_sequential": main["value"] / seq["value"],
+           "peak_ratio_batched_to_sequential": main["peak_bytes"] / seq["peak_bytes"]}
+    rig.release()
+    return out
+
+
+def _weights_exist():
+    from paper_1504_05022_gb300.predictor import WEIGHTS
+    return os.path.exists(WEIGHTS)
+
+
+def run_batch(args, world, device):
+    """512 independent products: one batched pipeline (block-diagonal concatenation) under the
+    learned and the plain policy, 512 sequential plain calls, and the batched plan's
+    values-only replay captured in a CUDA graph."""
+    import torch
+    rig = BatchRig(args, world, device)
+    pairs = rig.pairs
+    res = {}
     head = args.policy
-    main, bp, keep = batched(head, clocks=True, tuned=True)
+    main, bp, keep = rig.batched(head, clocks=True, tuned=True)
     arrays = bp.arrays()
     order = bp.pair_order()
     del bp
     torch.cuda.synchronize()
     for p in ("hybrid",):
         if p != head:
-            r, b2, k2 = batched(p)
+            r, b2, k2 = rig.batched(p)
             del b2, k2
             res["batched_" + p] = r
     torch.cuda.synchronize()
-    r, b2, k2 = batched(head, wave_mproducts=-1, tuned=True)  # one wave: fewer launches, more memory
+    r, b2, k2 = rig.batched(head, wave_mproducts=-1, tuned=True)  # one wave: fewer launches, more memory
     del b2, k2
     res[f"batched_{head}_one_wave"] = r
     torch.cuda.synchronize()
-    res["sequential_hybrid"] = sequential("hybrid")
+    res["sequential_hybrid"] = rig.sequential("hybrid")
     torch.cuda.synchronize()
-    # values-only replay of the whole batch in one CUDA graph
-    opts, keep_g = policy_opts(head, "batch512" if args.tuned else None)
-    gstream = torch.cuda.Stream(dev)  # a graph is captured from a created stream, not the legacy one
-    torch.cuda.synchronize()
-    gp = spg.BatchPlan(As, Bs, stream=gstream, **opts)
-    gp.numeric()
-    g = spg.ReplayGraph([gp])
-    ms_g, _ = time_steps(args, gstream, flush, g.launch)
-    v_g, ms_g = job_gflops(products, ms_g, world, dev)
-    gp.check()
-    res["graph_replay"] = {"value": v_g, "ms_per_step": ms_g,
-                           "note": "values-only replay (structure reused) of the batched plan, one CUDA graph"}
-    del g, gp, keep_g
-    torch.cuda.synchronize()
+    res["graph_replay"] = rig.replay_graph(head)
+    products = rig.products
     m = {"policy": head, "kms": main["kms"], "st_all": [{"launches": {}}], "arrays": [arrays],
          "ms_per_step": main["ms_per_step"]}
     cat_a = _Cat([pairs[i][0] for i in order])  # rows in the order of the plan's arrays
@@ -533,6 +584,7 @@ def run_batch(args, world, device):
     out["memory"]["comparison"] = memory_comparison(
         pairs, c_bytes, "batched_" + head, main,
         {k: v for k, v in res.items() if isinstance(v, dict) and "peak_bytes" in v})
+    rig.release()
     return out, pairs
 
 
@@ -673,7 +725,7 @@ def run_ours(args, rank, world, device):
                                                     {k: m for k, m in cmp.items() if not k.endswith("_f32")})
     if chain is not None:
         out["compare"].update(chain)
-    return out
+    return out, pairs
 
 
 def memory_comparison(pairs, c_bytes, head, main_m, cmp):
@@ -694,14 +746,19 @@ def memory_comparison(pairs, c_bytes, head, main_m, cmp):
     return mem
 
 
+STAGE_BYTES = 1 << 30  # pinned staging buffer for results larger than this
+
+
 def run_e2e(args, spg, pairs, dev, stream, opts, world=1):
-    """Same metric through the public API with host buffers: pinned host -> device copies of
-    the inputs, the product, and a device -> host read of the whole result, all timed."""
+    """Same metric through the public API with host buffers: every step copies A from pinned
+    host memory to the device, computes C = A*A and reads every byte of C (row pointers,
+    columns, values) back to the host.  A result of at most STAGE_BYTES lands in pinned host
+    arrays; a larger one streams through one pinned staging buffer of STAGE_BYTES in chunks,
+    each chunk overwriting the previous one (the host keeps no copy), so a run pins a bounded
+    amount of host memory whatever the size of C."""
     import torch
     if len(pairs) != 1 or pairs[0][1] is not pairs[0][0]:
         return None
-    if pairs[0][0].nnz > 50_000_000:
-        return {"value": None, "unit": "GFLOP/s", "note": "skipped: the result would need > 40 GB of pinned host memory"}
     A = pairs[0][0]
     hp = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
           for x in (A.row_ptr.astype(np.int32), A.col, A.val)]
@@ -709,26 +766,46 @@ def run_e2e(args, spg, pairs, dev, stream, opts, world=1):
     reps = max(3, min(args.steps, 10))
     times, d2h = [], 0
     out_host = None
+    staging = None
+
+    def read_back(C):
+        nonlocal out_host, staging
+        srcs = (C.row_ptr, C.col, C.val)
+        total = sum(t.numel() * t.element_size() for t in srcs)
+        if total <= STAGE_BYTES:
+            if out_host is None or out_host[1].numel() != C.nnz:
+                out_host = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in srcs]
+            for h, d in zip(out_host, srcs):
+                h.copy_(d, non_blocking=True)
+            return total, "pinned host arrays"
+        if staging is None:
+            staging = torch.empty(STAGE_BYTES, dtype=torch.uint8).pin_memory()
+        for d in srcs:
+            b = d.view(torch.uint8)
+            for off in range(0, b.numel(), STAGE_BYTES):
+                n = min(STAGE_BYTES, b.numel() - off)
+                staging[:n].copy_(b[off:off + n], non_blocking=True)
+        return total, f"streamed through one {STAGE_BYTES >> 20} MiB pinned staging buffer"
+
+    how = None
     for k in range(reps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rp, col, val = (t.to(dev, non_blocking=True) for t in hp)
         Ad = spg.CSR(rp, col, val, (A.nrows, A.ncols))
         C = spg.Plan(Ad, Ad, stream=stream, **opts).numeric()
-        if out_host is None or out_host[1].numel() != C.nnz:
-            out_host = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in (C.row_ptr, C.col, C.val)]
-        for h, d in zip(out_host, (C.row_ptr, C.col, C.val)):
-            h.copy_(d, non_blocking=True)
+        d2h, how = read_back(C)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        d2h = sum(t.numel() * t.element_size() for t in out_host)
         del C, Ad
         if k > 0:
             times.append(dt)
+    del staging, out_host
     u_sum = int(_products(A))
     value, ms = job_gflops(u_sum, float(np.median(times)) * 1e3, world, dev)
     return {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms, "steps": reps,
+            "note": f"median of {reps} steps after 1 untimed; A copied from pinned host memory, C {how}"}
 
 
 def _products(A):
@@ -836,7 +913,7 @@ def run_reference(args, total_s=150.0):
 
 
 def run_merge_micro(args):
-    """The merge evaluation of Section 4.3: 2^25 keys in groups of two ascending runs of
+    """The merge evaluation of Section 4.2: 2^25 keys in groups of two ascending runs of
     length l, merged by the ranking merge, merge path and bitonic merge (one CTA per group,
     best of 64-1024 threads), with no value, 32-bit and 64-bit values.  CUDA-event time of
     one launch, median of 5 after a warm-up; merged elements per second."""
@@ -880,7 +957,7 @@ def run_merge_micro(args):
             out.append(row)
             del keys, vals
     head = next(r for r in out if r["value_bytes"] == 8 and r["l"] == 256)
-    return {"metric": "merge micro-benchmark (Section 4.3): merged elements/s, merge path, l = 256, "
+    return {"metric": "merge micro-benchmark (Section 4.2): merged elements/s, merge path, l = 256, "
                       "32-bit keys with 64-bit values", "value": head["merge_path"]["gelem_s"] * 1e9,
             "unit": "elements/s", "higher_is_better": True, "n_gpus": 1, "dtype": "i32 keys",
             "data": "synthetic (seeded generator)",
@@ -895,16 +972,18 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat16x16", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="rmat20x8", choices=list(WORKLOADS))
     ap.add_argument("--policy", default="learned", choices=["hybrid", "upper_bound", "learned"])
     ap.add_argument("--single-policy", action="store_true", help="do not also time the plain hybrid path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch-compare", action="store_true",
+                    help="R-MAT 2^20 line: do not also time the 512-pair batch (batched against sequential calls)")
     ap.add_argument("--no-tuned", dest="tuned", action="store_false",
                     help="do not apply the autotuner's parameters to the reported policy")
     ap.add_argument("--merge-kernel", default="auto", choices=["auto", "merge_path", "bitmap"],
                     help="form of the bin-37 kernel for every policy")
     ap.add_argument("--merge-micro", action="store_true",
-                    help="run the merge evaluation of Section 4.3 instead and print its line")
+                    help="run the merge evaluation of Section 4.2 instead and print its line")
     args = ap.parse_args()
     if args.merge_micro:
         print(json.dumps(run_merge_micro(args)))
@@ -938,7 +1017,10 @@ def main():
     if args.workload == "batch512":
         out, pairs = run_batch(args, world, local)
     else:
-        out = run_ours(args, rank, world, local)
+        out, pairs = run_ours(args, rank, world, local)
+        if args.workload == "rmat20x8" and not args.no_batch_compare and not args.single_policy:
+            # the batched half of the metric: 512 pairs, batched pipeline against sequential plain calls
+            out["compare"]["batch512"] = batch_compare(args, world, local)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = run_cpu_baseline(args, pairs=pairs)

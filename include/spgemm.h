@@ -234,6 +234,9 @@ typedef struct spgemm_stats {
                                    this is C plus the O(rows) tables that values-only replay uses */
     int64_t rows_dense;         /* bin-37 rows computed by the dense-slice kernels */
     int64_t dense_slices;       /* column slices of B used by them (0 when none) */
+    int64_t item_rounds;        /* bin-37 work items summed over every launch of the bin-37 merge
+                                   kernel: a row counts once per progressive round it runs in, and
+                                   each half of a split row counts on its own */
 } spgemm_stats;
 
 /* Copies the plan's counters into *out.  Timings are read after synchronising
@@ -436,7 +439,7 @@ spgemm_status spgemm_mlp_adam(float *params, const float *grad, float *m, float 
                               float lr, float grad_scale, spgemm_stream_t stream);
 
 /*
- * The merge evaluation of Section 4.3 ("Evaluating GPU Merge algorithms"): merges groups
+ * The merge evaluation of Section 4.2 ("Evaluating GPU Merge algorithms"): merges groups
  * of two sorted runs into sorted sequences, with one CTA of `threads` threads (64, 128,
  * 256, 512 or 1024) per group, in shared memory.  method: 0 ranking merge, 1 merge path,
  * 2 bitonic merge (the last stage of a bitonic sort).  keys: n int32 device values, in

@@ -204,7 +204,7 @@ int dense_fill_smem_bytes(int W);
 int dense_fill_static_smem();
 int dense_fill_max_dynamic(int per_sm);
 
-// ---- the merge evaluation of Section 4.3 (merge_micro.cu) ----
+// ---- the merge evaluation of Section 4.2 (merge_micro.cu) ----
 // method 0 ranking merge, 1 merge path, 2 bitonic merge; groups of 2l keys (two sorted runs)
 int merge_micro_smem(int l, int value_bytes);
 cudaError_t launch_merge_micro(int method, int threads, int value_bytes, const int32_t *keys, const void *vals,

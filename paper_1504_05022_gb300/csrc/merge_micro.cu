@@ -1,4 +1,4 @@
-// The merge evaluation of Section 4.3 ("Evaluating GPU Merge algorithms"): merging two
+// The merge evaluation of Section 4.2 ("Evaluating GPU Merge algorithms"): merging two
 // sorted sequences of length l into one of length 2l, many independent groups (the paper
 // uses 2^25 elements in all), with 32-bit keys and no value, a 32-bit value or a 64-bit
 // value.  Three of the paper's five algorithms, each in shared memory on one CTA per group:

@@ -813,6 +813,7 @@ spgemm_status run_progressive(spgemm_plan *p, const int32_t *work_in, int64_t wo
                 p->time_end();
                 p->count(SPGEMM_K_MERGE);
                 p->stats.merge_rounds += 1;
+                p->stats.item_rounds += nwork;
                 int32_t n = 0;
                 SPG_TRY(p->d2h(&n, ovf_count, sizeof(int32_t)));
                 novf = n;
@@ -994,6 +995,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 p->time_end();
                 p->count(SPGEMM_K_MERGE);
                 p->stats.merge_rounds += 1;
+                p->stats.item_rounds += cnt;
                 if (concurrent) {
                     cudaEvent_t done = nullptr;
                     SPG_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
@@ -1039,6 +1041,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 p->time_end();
                 p->count(SPGEMM_K_MERGE);
                 p->stats.merge_rounds += 1;
+                p->stats.item_rounds += nk;
             }
             if (stale) SPG_TRY(p->d2h(hc.data(), counts, sizeof(int32_t) * (nlv + 1)));
             status = run_progressive(p, lists[nlv - 1], 0, hc[nlv - 1], capmax, false, ovf_count);
@@ -1213,6 +1216,7 @@ extern "C" spgemm_status spgemm_plan_stats(spgemm_plan *p, spgemm_stats *out) {
         out->nnz_ctilde += ws.nnz_ctilde;
         out->nnz_c += ws.nnz_c;
         out->merge_rounds += ws.merge_rounds;
+        out->item_rounds += ws.item_rounds;
         out->rows_relaunched += ws.rows_relaunched;
         out->rows_level1 += ws.rows_level1;
         out->rows_split += ws.rows_split;

@@ -210,7 +210,7 @@ class Plan:
             "merge_rounds": s.merge_rounds, "rows_relaunched": s.rows_relaunched, "rows_level1": s.rows_level1,
             "rows_split": s.rows_split,
             "rows_fallback": s.rows_fallback, "bytes_ctilde": s.bytes_ctilde, "peak_bytes": s.peak_bytes, "held_bytes": s.held_bytes,
-            "rows_dense": s.rows_dense, "dense_slices": s.dense_slices,
+            "rows_dense": s.rows_dense, "dense_slices": s.dense_slices, "item_rounds": s.item_rounds,
             "launches": dict(zip(_lib.KERNELS, list(s.launches))),
             "kernel_ms": dict(zip(_lib.KERNELS, [float(x) for x in s.kernel_ms])),
         }
@@ -385,7 +385,7 @@ MERGE_METHODS = {"ranking": 0, "merge_path": 1, "bitonic": 2}
 
 def merge_micro(keys: torch.Tensor, l: int, method: str = "merge_path", threads: int = 256,
                 vals: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None):
-    """The merge evaluation of Section 4.3: every group of 2l int32 keys holds two ascending
+    """The merge evaluation of Section 4.2: every group of 2l int32 keys holds two ascending
     runs of length l, and is merged into one ascending sequence by one CTA of `threads`
     threads with the ranking merge, merge path or bitonic merge.  vals (4- or 8-byte
     elements, optional) move with their keys.  Returns (keys, vals or None)."""

@@ -100,7 +100,19 @@ def test_batched_replay(spg, oracle_mod):
         _check(oracle_mod, A2, B2, C, f"batched replay {i}")
 
 
-def test_galerkin_graph_exact(spg):
+def _int_values(M, seed, lo=-3, hi=4):
+    """M with new small nonzero integer values drawn from the seed (same structure), so every
+    product and sum is exact in FP64."""
+    rng = np.random.default_rng(seed)
+    v = rng.integers(lo, hi, size=M.nnz).astype(np.float64)
+    v[v == 0] = 5.0
+    return gen.HostCSR(M.nrows, M.ncols, M.row_ptr, M.col, v)
+
+
+def test_galerkin_graph_exact(spg, oracle_mod):
+    """R*(A*P) on the 27-point 32^3 operator, then its values-only replay from one CUDA graph for
+    new integer values of R, A and P (the same structure): each replay equals the oracle's
+    R*(A*P) of those values exactly."""
     g = 32
     A, P = gen.lap3d27(g), gen.agg_P(g)
     R = gen.transpose(P)
@@ -113,14 +125,18 @@ def test_galerkin_graph_exact(spg):
     assert Ac.nnz == (3 * (g // 2) - 2) ** 3
     assert set(np.unique(val).tolist()) == {152.0, -16.0, -4.0, -1.0}
     graph = spg.ReplayGraph([p1, p2])
-    for scale in (2.0, -3.0):
-        Ad.val.copy_(torch.from_numpy(A.val * scale))
+    for k in range(3):
+        A2, P2, R2 = _int_values(A, 100 + k), _int_values(P, 200 + k), _int_values(R, 300 + k)
+        for Md, M2 in ((Ad, A2), (Pd, P2), (Rd, R2)):
+            Md.val.copy_(torch.from_numpy(M2.val))
         s.synchronize()
         graph.launch()
         s.synchronize()
+        AP = oracle_mod.spgemm(A2, P2)
+        ref = oracle_mod.spgemm(R2, gen.HostCSR(AP.nrows, AP.ncols, AP.row_ptr, AP.col, AP.val))
         rp2, col2, val2 = Ac.to_host()
-        assert np.array_equal(rp2, rp) and np.array_equal(col2, col)
-        assert np.array_equal(val2, val * scale)          # integers: exact
+        assert np.array_equal(rp2, ref.row_ptr) and np.array_equal(col2, ref.col)
+        assert np.array_equal(val2, ref.val), f"replay {k}"    # integers: exact
     p2.check()
 
 

@@ -140,3 +140,40 @@ def test_value_types_must_match(spg):
         spg.Plan(A64, A32)
     with pytest.raises(TypeError):
         spg.Plan(A32, A32, **Predictor.load().opts())  # a double-precision predictor
+
+
+@pytest.mark.parametrize("stencil,g,dim", [("lap2d9", 256, 2), ("lap3d7", 32, 3), ("lap3d27", 32, 3)])
+@pytest.mark.parametrize("policy", ["hybrid", "learned"])
+def test_f32_galerkin_hierarchy_exact(spg, oracle_mod, stencil, g, dim, policy):
+    """The single-precision Galerkin products of the paper's AMG setting (Section 5.2 reports
+    them in both precisions): a piecewise-constant aggregation hierarchy A_{l+1} = P_l^T (A_l P_l)
+    down to a 4^dim grid, each level fed by the previous one on the device.  Every value of
+    every level is an integer below 2^24, so each level equals the oracle's exactly."""
+    from paper_1504_05022_gb300.predictor import Predictor
+    A = getattr(gen, stencil)(g)
+    Ps = gen.galerkin_levels(g, dim)
+    opts = Predictor.load(dtype="f32").opts() if policy == "learned" else {"alloc_policy": policy}
+    s = torch.cuda.Stream()
+    cur = spg.CSR.from_host(A, dtype=torch.float32)
+    levels, keep = [], []
+    with torch.cuda.stream(s):
+        for P in Ps:
+            Pd = spg.CSR.from_host(P, dtype=torch.float32)
+            Rd = spg.CSR.from_host(gen.transpose(P), dtype=torch.float32)
+            cur, p1, p2 = spg.galerkin(Rd, cur, Pd, stream=s, **opts)
+            levels.append(cur)
+            keep += [Pd, Rd, p1, p2]
+    s.synchronize()
+    ref = A
+    for lvl, (P, Ac) in enumerate(zip(Ps, levels)):
+        AP = oracle_mod.spgemm(ref, P)
+        Rc = oracle_mod.spgemm(gen.transpose(P), gen.HostCSR(AP.nrows, AP.ncols, AP.row_ptr, AP.col, AP.val))
+        assert np.abs(Rc.val).max() < 2 ** 24
+        rp, col, val = Ac.to_host()
+        assert Ac.val.dtype == torch.float32
+        assert np.array_equal(rp, Rc.row_ptr) and np.array_equal(col, Rc.col), f"level {lvl}"
+        assert np.array_equal(val.astype(np.float64), Rc.val), f"level {lvl}"
+        ref = gen.HostCSR(Rc.nrows, Rc.ncols, Rc.row_ptr, Rc.col, Rc.val)
+    assert levels[-1].shape == (4 ** dim, 4 ** dim)
+    for p in keep[2::4] + keep[3::4]:
+        p.check()

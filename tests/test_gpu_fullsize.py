@@ -1,8 +1,8 @@
 """Full-size parity at the benchmark's largest configurations, in the launch configuration
-bench.py times (learned policy with the committed weights and tuned parameters): every row
-pointer of C against the oracle's row counts, and every entry of sampled rows (random rows,
-the longest rows, random rows of bin 37) against the oracle's rows (structure exact, values
-within 1e-12 * sum |a b|)."""
+bench.py times (learned policy with the committed weights and tuned parameters): every entry
+of C against the oracle (structure exact, values within 1e-12 * sum |a b|).  The oracle
+computes C block of rows by block of rows (about 200 M products each), so the host never
+holds all of it; each block is compared with the GPU's rows on the device."""
 import multiprocessing as mp
 import os
 
@@ -38,27 +38,25 @@ def _products(A, B):
     return cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]
 
 
-def _sample_rows(u, bins, rng, n_random=1500, n_long=20, n_bin37=300):
-    m = u.shape[0]
-    rows = [rng.choice(m, min(n_random, m), replace=False), np.argsort(u)[-n_long:]]
-    b37 = np.nonzero(bins == 37)[0]
-    if b37.size:
-        rows.append(rng.choice(b37, min(n_bin37, b37.size), replace=False))
-    return np.unique(np.concatenate(rows))
-
-
-def _check_rows(oracle_mod, A, B, C, rows, label):
+def _check_all_rows(oracle_mod, A, B, C, label, block_products=200_000_000):
+    """Every row of C against the oracle, in row blocks of about block_products products."""
+    u = _products(A, B)
+    cu = np.cumsum(u)
     rp = C.row_ptr.cpu().numpy()
-    starts, ends = rp[rows], rp[rows + 1]
-    idx = np.concatenate([np.arange(s, e, dtype=np.int64) for s, e in zip(starts, ends)])
-    it = torch.from_numpy(idx).to(C.col.device)
-    gc = C.col[it].cpu().numpy()
-    gv = C.val[it].cpu().numpy()
-    off, col, val, den = oracle_mod.spgemm_rows(A, B, rows)
-    assert np.array_equal(np.diff(off), ends - starts), label
-    assert np.array_equal(gc, col), label
-    bad = np.abs(gv - val) > REL_TOL * den
-    assert not bad.any(), f"{label}: {int(bad.sum())} values outside the tolerance"
+    dev = C.col.device
+    r0 = 0
+    while r0 < A.nrows:
+        r1 = int(np.searchsorted(cu, (cu[r0 - 1] if r0 else 0) + block_products, side="right"))
+        r1 = min(A.nrows, max(r1, r0 + 1))
+        off, col, val, den = oracle_mod.spgemm_rows(A, B, np.arange(r0, r1, dtype=np.int64))
+        where = f"{label}, rows {r0}..{r1 - 1}"
+        assert np.array_equal(np.diff(rp[r0:r1 + 1]), np.diff(off)), f"{where}: row sizes differ"
+        s, e = int(rp[r0]), int(rp[r1])
+        assert torch.equal(C.col[s:e], torch.from_numpy(col).to(dev)), f"{where}: columns differ"
+        err = (C.val[s:e] - torch.from_numpy(val).to(dev)).abs()
+        bad = int((err > REL_TOL * torch.from_numpy(den).to(dev)).sum())
+        assert bad == 0, f"{where}: {bad} values outside the tolerance"
+        r0 = r1
 
 
 def test_config4_rmat20x8_full_size(spg, oracle_mod):
@@ -70,13 +68,11 @@ def test_config4_rmat20x8_full_size(spg, oracle_mod):
     torch.cuda.synchronize()
     u = _products(A, A)
     assert plan.upper_bound_nnz == int(u.sum())
-    counts = oracle_mod.row_counts(A, A)
-    assert np.array_equal(np.diff(C.row_ptr.cpu().numpy()), counts)
-    assert C.nnz == int(counts.sum()) > 2**31          # int64 row pointers are needed
-    rows = _sample_rows(u, plan.arrays()["bin"], np.random.default_rng(4))
-    _check_rows(oracle_mod, A, A, C, rows, "R-MAT 2^20 x 8")
+    assert C.nnz > 2**31                                 # int64 row pointers are needed
+    _check_all_rows(oracle_mod, A, A, C, "R-MAT 2^20 x 8")
     st = plan.stats()
     assert st["rows_split"] > 0                          # hub rows took the long-row path
+    assert st["rows_dense"] > 0                          # and the dense-slice kernels
     del keep
 
 
@@ -93,11 +89,5 @@ def test_config5_batch512_full_size(spg, oracle_mod):
     assert plan.upper_bound_nnz == sum(int(_products(A, B).sum()) for A, B in pairs)
     for i, ((A, B), C) in enumerate(zip(pairs, Cs)):
         assert C.shape == (A.nrows, B.ncols)
-        assert np.array_equal(np.diff(C.row_ptr.cpu().numpy()), oracle_mod.row_counts(A, B)), f"pair {i}"
-    rng = np.random.default_rng(9)
-    for i in rng.choice(len(pairs), 12, replace=False):
-        A, B = pairs[i]
-        u = _products(A, B)
-        rows = _sample_rows(u, np.where(u > 512, 37, 0), rng, n_random=300, n_long=5, n_bin37=100)
-        _check_rows(oracle_mod, A, B, Cs[i], rows, f"pair {i}")
+        _check_all_rows(oracle_mod, A, B, C, f"pair {i}")
     del keep

@@ -1,4 +1,4 @@
-"""GPU tests of the merge evaluation of Section 4.3 (spgemm_merge_micro): every method merges
+"""GPU tests of the merge evaluation of Section 4.2 (spgemm_merge_micro): every method merges
 every group of two ascending runs into the sorted group, with values moving with their keys,
 for run lengths from 1 to 4,096, every CTA size and every value width.  Keys within a group
 are distinct, so the expected output is unique; with repeated keys the keys must still come
