@@ -99,7 +99,15 @@ typedef enum spgemm_alloc_policy {
     /* Rows are sized from a learned prediction of nnz(c_i) (see
        spgemm_predictor_*); a row whose result exceeds its prediction falls back
        to the exact path, so C is unchanged. */
-    SPGEMM_ALLOC_LEARNED = 2
+    SPGEMM_ALLOC_LEARNED = 2,
+    /* The precise method (Section 3.1): a counting pass first computes nnz(c_i) of every
+       row -- a warp sort of the row's columns for u_i <= 512, the dense column-slice count for
+       longer rows -- then C is allocated exactly and every row is computed straight into it
+       (heap / bitonic ESC for u_i <= 512, the dense column slices for the rest): no temporary
+       matrix C~ and no relaunch, at the price of a second pass over the products.  B's columns
+       must fit 64 shared-memory slices (about 1.4 million columns in double, twice as many in
+       float); a wider B returns SPGEMM_ERR_SHAPE. */
+    SPGEMM_ALLOC_PRECISE = 3
 } spgemm_alloc_policy;
 
 /* Rows whose result outgrows the largest shared-memory capacity (bin 37). */
@@ -351,6 +359,49 @@ spgemm_status spgemm_graph_free(spgemm_graph *graph);
 spgemm_status spgemm_galerkin(const spgemm_csr_in *R, const spgemm_csr_in *A, const spgemm_csr_in *P,
                               const spgemm_opts *opts, spgemm_stream_t stream, spgemm_plan **plan_ap,
                               spgemm_plan **plan_rap, spgemm_csr_out *Ac);
+
+/*
+ * Products sized on the device (not in the paper): the whole of C = A * B -- stages 1 to 4 --
+ * enqueued with every size the method needs (bin counts, nnz(c_i), nnz(C)) kept in device
+ * memory and none read back, so that the product can be enqueued again and again or captured
+ * in a CUDA graph, for inputs whose structure changes from one run to the next.  It follows
+ * the precise method (SPGEMM_ALLOC_PRECISE: count, then compute every row straight into C),
+ * and each stage-3 launch is a persistent kernel: a fixed grid of as many CTAs as the SMs
+ * hold, striding over a bin whose rows are listed on the device (warps and threads over the
+ * rows of bins 2..36, a work counter over the (row, slice) items of bin 37).
+ *
+ * spgemm_dplan_create allocates everything at once for inputs of the given sizes: A and B
+ * (or the npairs pairs of spgemm_dplan_batched_create, computed as one block-diagonal
+ * product) are borrowed device matrices whose sizes (nrows, ncols, nnz, rowptr_bits) are
+ * fixed, while their row pointers, columns and values may change between runs.  C gets room
+ * for c_capacity entries; *C receives its device arrays (row_ptr with nrows + 1 entries, col
+ * and val with c_capacity entries; C->nnz = -1 until a result is read).  C's arrays may be
+ * the B of a later plan on the same stream (B.nnz = c_capacity), which chains two products.
+ * Options: as for spgemm_symbolic; the allocation policy is always the precise method.
+ *
+ * spgemm_dplan_run enqueues the product on the plan's stream: no allocation, no host
+ * synchronisation.  If nnz(C) exceeds c_capacity, nothing is written to C's columns and
+ * values, and spgemm_dplan_result returns SPGEMM_ERR_OOM.  spgemm_dplan_result synchronises
+ * the stream, reads nnz(C) and the device error word, and describes C (npairs descriptors for
+ * a batched plan: each C_i with its own int64 row pointers starting at 0, its columns and
+ * values views into the concatenated C).  spgemm_dplan_graph_create captures one run of each
+ * of plans[0..n) in order (all on one created, non-default stream) into a CUDA graph; it runs
+ * each plan once before the capture.  spgemm_graph_launch and spgemm_graph_free apply.
+ * Errors: as spgemm_symbolic; SPGEMM_ERR_SHAPE also when B is too wide for the precise method.
+ */
+typedef struct spgemm_dplan spgemm_dplan;
+spgemm_status spgemm_dplan_create(const spgemm_csr_in *A, const spgemm_csr_in *B, int64_t c_capacity,
+                                  const spgemm_opts *opts, spgemm_stream_t stream, spgemm_dplan **out,
+                                  spgemm_csr_out *C);
+spgemm_status spgemm_dplan_batched_create(int64_t npairs, const spgemm_csr_in *A, const spgemm_csr_in *B,
+                                          int64_t c_capacity, const spgemm_opts *opts, spgemm_stream_t stream,
+                                          spgemm_dplan **out, spgemm_csr_out *C);
+spgemm_status spgemm_dplan_run(spgemm_dplan *plan);
+spgemm_status spgemm_dplan_result(spgemm_dplan *plan, spgemm_csr_out *C_out);
+spgemm_status spgemm_dplan_graph_create(spgemm_dplan *const *plans, int64_t n, spgemm_graph **out);
+spgemm_status spgemm_dplan_free(spgemm_dplan *plan);
+/* Device bytes the plan holds (all of it allocated by spgemm_dplan_create). */
+spgemm_status spgemm_dplan_bytes(spgemm_dplan *plan, int64_t *bytes);
 
 /*
  * Allocation-free row-pointer scan (no counterpart in the paper).

@@ -16,7 +16,7 @@ STATUS = {
     0: "SPGEMM_OK", 1: "SPGEMM_ERR_INVALID_ARG", 2: "SPGEMM_ERR_SHAPE", 3: "SPGEMM_ERR_UNSORTED",
     4: "SPGEMM_ERR_OOM", 5: "SPGEMM_ERR_CUDA", 6: "SPGEMM_ERR_TIMEOUT", 7: "SPGEMM_ERR_INTERNAL",
 }
-POLICY = {"hybrid": 0, "upper_bound": 1, "learned": 2}
+POLICY = {"hybrid": 0, "upper_bound": 1, "learned": 2, "precise": 3}
 LONG_ROWS = {"split": 0, "level1": 1}
 KERNELS = ["bound", "bin", "heap", "esc", "merge", "scan", "arrange", "other"]
 NUM_BINS = 38
@@ -80,6 +80,15 @@ SIGNATURES = {
     "spgemm_graph_free": ([c_ptr], c_i32),
     "spgemm_galerkin": ([ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(Opts),
                          c_ptr, ctypes.POINTER(c_ptr), ctypes.POINTER(c_ptr), ctypes.POINTER(CsrOut)], c_i32),
+    "spgemm_dplan_create": ([ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_i64, ctypes.POINTER(Opts), c_ptr,
+                             ctypes.POINTER(c_ptr), ctypes.POINTER(CsrOut)], c_i32),
+    "spgemm_dplan_batched_create": ([c_i64, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_i64, ctypes.POINTER(Opts),
+                                     c_ptr, ctypes.POINTER(c_ptr), ctypes.POINTER(CsrOut)], c_i32),
+    "spgemm_dplan_run": ([c_ptr], c_i32),
+    "spgemm_dplan_result": ([c_ptr, ctypes.POINTER(CsrOut)], c_i32),
+    "spgemm_dplan_graph_create": ([ctypes.POINTER(c_ptr), c_i64, ctypes.POINTER(c_ptr)], c_i32),
+    "spgemm_dplan_free": ([c_ptr], c_i32),
+    "spgemm_dplan_bytes": ([c_ptr, ctypes.POINTER(c_i64)], c_i32),
     "spgemm_merge_micro": ([c_i32, c_i32, c_i32, c_ptr, c_ptr, c_i64, c_i32, c_ptr, c_ptr, c_ptr], c_i32),
     "spgemm_predictor_create": ([c_ptr, c_i64, ctypes.POINTER(c_ptr)], c_i32),
     "spgemm_predictor_free": ([c_ptr], c_i32),

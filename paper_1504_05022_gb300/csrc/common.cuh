@@ -17,6 +17,21 @@ namespace spg {
 constexpr int32_t KEY_PAD = INT_MAX;
 
 SPG_DEV int lane_id() { return threadIdx.x & 31; }
+
+// The rows of a RowSet: host-known, or a range of `rows` whose ends are read here.
+SPG_DEV void rowset_range(const RowSet &R, const int32_t *&rows, int64_t &n) {
+    if (R.dev_lo != nullptr) {
+        const int64_t lo = *R.dev_lo;
+        rows = R.rows + lo;
+        n = *R.dev_hi - lo;
+    } else {
+        rows = R.rows;
+        n = R.n;
+    }
+}
+
+// True when a gate word is set: the launch must write nothing.
+SPG_DEV bool gated(const int64_t *gate) { return gate != nullptr && *gate != 0; }
 SPG_DEV int warp_id() { return threadIdx.x >> 5; }
 
 template <typename T>

@@ -238,13 +238,25 @@ SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, 
 // Shared memory: one flag byte per column of the slice (a plain store of 1 per
 // product: every writer stores the same value, so no atomics are needed).
 
+// The next (item, slice) of a CTA: blockIdx.x, then + gridDim.x (a grid that covers the
+// items takes one each), or, with a work counter, the counter's next ticket (a persistent
+// grid over a count read on the device).  All threads call it; its barrier ends the
+// previous item's use of shared memory.
+SPG_DEV int64_t dense_next(unsigned long long *counter, int64_t cur, bool first, int64_t *s_b) {
+    __syncthreads();
+    if (counter == nullptr) return first ? (int64_t)blockIdx.x : cur + gridDim.x;
+    if (threadIdx.x == 0) *s_b = (int64_t)atomicAdd(counter, 1ull);
+    __syncthreads();
+    return *s_b;
+}
+
+SPG_DEV int64_t dense_items(const DenseArgs &D) { return (D.dev_n != nullptr ? *D.dev_n : D.n) * (int64_t)D.K; }
+
 template <int NT>
-__global__ void __launch_bounds__(NT)
-k_dense_count(DevCSR A, DevCSR B, DenseArgs D, int64_t *err) {
+SPG_DEV void dense_count_item(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t b, int64_t *err) {
     extern __shared__ __align__(16) uint8_t dc_flag[];
     __shared__ int64_t wbs[NT], cscan[NT], scan64[NT / 32 + 1];
     __shared__ int32_t wlen[NT], scan32[NT / 32 + 1];
-    const int64_t b = blockIdx.x;
     const int64_t d = b / D.K;
     const int s = (int)(b - d * D.K);
     const int row = D.rows[d];
@@ -288,6 +300,16 @@ k_dense_count(DevCSR A, DevCSR B, DenseArgs D, int64_t *err) {
     if (threadIdx.x == 0) D.cnt[b] = n;
 }
 
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_dense_count(DevCSR A, DevCSR B, DenseArgs D, int64_t *err) {
+    __shared__ int64_t s_b;
+    unsigned long long *q = D.dev_n != nullptr ? D.queue : nullptr;
+    const int64_t nb = dense_items(D);
+    for (int64_t b = dense_next(q, 0, true, &s_b); b < nb; b = dense_next(q, b, false, &s_b))
+        dense_count_item<NT>(A, B, D, b, err);
+}
+
 // One thread per dense item: the slices' offsets inside the row and the row's length.
 __global__ void k_dense_rows(MergeItems it, DenseArgs D) {
     const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -324,16 +346,15 @@ __host__ __device__ inline int dense_nw4(int W) { return ((W + 31) / 32 + 4) & ~
 
 // REPLAY: values-only replay; C's columns are already in place, so the flags, the bitmap
 // and the column-order write-out give way to one pass over the slice's known entries.
-template <int NT, int MINB, bool REPLAY>
-__global__ void __launch_bounds__(NT, MINB)
-k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_col, val_t *c_val, int64_t *err) {
+template <int NT, bool REPLAY>
+SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t b, const int64_t *c_rp,
+                             int32_t *c_col, val_t *c_val, int64_t *err) {
     constexpr int WIN = DENSE_FILL_WIN;
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char df_smem[];
     __shared__ int64_t wbs[WIN], cscan[WIN], scan64[NT / 32 + 1];
     __shared__ val_t wa[WIN];
     __shared__ int32_t wlen[WIN], lidx[WIN], scan32[NT / 32 + 1];
-    const int64_t b = blockIdx.x;
     const int expected = D.cnt[b];
     if (expected == 0) return;
     const int64_t d = b / D.K;
@@ -554,6 +575,32 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
     }
 }
 
+template <int NT, int MINB, bool REPLAY>
+__global__ void __launch_bounds__(NT, MINB)
+k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_col, val_t *c_val, int64_t *err,
+             const int64_t *gate) {
+    __shared__ int64_t s_b;
+    if (gated(gate)) return;
+    unsigned long long *q = D.dev_n != nullptr ? D.queue + 1 : nullptr;
+    const int64_t nb = dense_items(D);
+    for (int64_t b = dense_next(q, 0, true, &s_b); b < nb; b = dense_next(q, b, false, &s_b))
+        dense_fill_item<NT, REPLAY>(A, B, D, b, c_rp, c_col, c_val, err);
+}
+
+// One thread per dense item (precise method): the slices' offsets inside the row and the
+// row's size nnz(c_i), the sum of its slices' counts.
+__global__ void k_dense_rowsum(DenseArgs D, int32_t *nnzc) {
+    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = D.dev_n != nullptr ? *D.dev_n : D.n;
+    if (d >= n) return;
+    int32_t acc = 0;
+    for (int s = 0; s < D.K; ++s) {
+        D.soff[d * D.K + s] = acc;
+        acc += D.cnt[d * D.K + s];
+    }
+    nnzc[D.rows[d]] = acc;
+}
+
 constexpr int DENSE_COUNT_NT = 256;
 constexpr int DENSE_FILL_NT = 512;  // 1,024-thread CTAs measured slower (the atomics' unit saturates)
 
@@ -581,7 +628,21 @@ cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs
     auto kern = k_dense_count<DENSE_COUNT_NT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)nb, DENSE_COUNT_NT, smem, st>>>(A, B, D, err);
+    int64_t grid = nb;
+    if (D.dev_n != nullptr) {  // persistent grid over the items counted on the device
+        if (D.queue == nullptr) return cudaErrorInvalidValue;
+        e = cudaMemsetAsync(D.queue, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+        grid = persistent_blocks((const void *)kern, DENSE_COUNT_NT, smem, nb);
+        if (grid <= 0) return cudaErrorInvalidValue;
+    }
+    kern<<<(unsigned)grid, DENSE_COUNT_NT, smem, st>>>(A, B, D, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_rowsum(const DenseArgs &D, int32_t *nnzc, cudaStream_t st) {
+    if (D.n <= 0) return cudaSuccess;
+    k_dense_rowsum<<<(unsigned)((D.n + 127) / 128), 128, 0, st>>>(D, nnzc);
     return cudaGetLastError();
 }
 
@@ -592,7 +653,8 @@ cudaError_t launch_dense_rows(const MergeItems &it, const DenseArgs &D, cudaStre
 }
 
 cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs &D, const int64_t *c_rp,
-                              int32_t *c_col, val_t *c_val, int64_t *err, cudaStream_t st, bool replay) {
+                              int32_t *c_col, val_t *c_val, int64_t *err, cudaStream_t st, bool replay,
+                              const int64_t *gate) {
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
@@ -605,7 +667,15 @@ cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs 
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)nb, DENSE_FILL_NT, smem, st>>>(A, B, D, c_rp, c_col, c_val, err);
+    int64_t grid = nb;
+    if (D.dev_n != nullptr) {  // persistent grid over the items counted on the device
+        if (D.queue == nullptr) return cudaErrorInvalidValue;
+        e = cudaMemsetAsync(D.queue + 1, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+        grid = persistent_blocks((const void *)kern, DENSE_FILL_NT, smem, nb);
+        if (grid <= 0) return cudaErrorInvalidValue;
+    }
+    kern<<<(unsigned)grid, DENSE_FILL_NT, smem, st>>>(A, B, D, c_rp, c_col, c_val, err, gate);
     return cudaGetLastError();
 }
 

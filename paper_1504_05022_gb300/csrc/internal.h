@@ -21,7 +21,7 @@ constexpr int BIN_ESC_LO = 33, BIN_ESC_HI = 36;   // bin group 4
 constexpr int BIN_MERGE = 37;                     // bin group 5
 constexpr int64_t BIN_MERGE_MIN_U = 512;          // bin 37 holds the rows with u_i > 512 (Algorithm 3)
 
-enum AllocPolicy { POLICY_HYBRID = 0, POLICY_UPPER_BOUND = 1, POLICY_LEARNED = 2 };
+enum AllocPolicy { POLICY_HYBRID = 0, POLICY_UPPER_BOUND = 1, POLICY_LEARNED = 2, POLICY_PRECISE = 3 };
 
 // CSR with int64 row pointers (int32 inputs are widened once per call).
 struct DevCSR {
@@ -42,7 +42,24 @@ struct BinSummary {
     int64_t pad;
     int64_t class_count[NUM_LAUNCH_CLASSES];  // learned: bin-37 rows per launch class
     int64_t dense_count;                      // bin-37 rows computed by the dense-slice kernels
+    int64_t bin_start[NUM_BINS + 1];          // offsets of the bins in bin_rows (for launches sized on the device)
 };
+
+// Rows of one stage-3 launch.  With dev_lo == nullptr they are rows[0..n), n known on the
+// host.  Otherwise they are rows[*dev_lo .. *dev_hi), both ends read on the device, so the
+// launch needs no read-back: it runs a fixed (persistent) grid that strides over the range,
+// and n is only an upper bound of its length (it caps the grid).
+struct RowSet {
+    const int32_t *rows;
+    int64_t n;
+    const int64_t *dev_lo = nullptr;
+    const int64_t *dev_hi = nullptr;
+};
+inline RowSet host_rows(const int32_t *rows, int64_t n) { return RowSet{rows, n, nullptr, nullptr}; }
+
+// Blocks of a persistent launch of `kern` (NT threads, smem dynamic bytes): as many as are
+// resident on all SMs at once, at most `cap` (> 0).
+int persistent_blocks(const void *kern, int nt, size_t smem, int64_t cap);
 
 struct CapPolicy {
     int policy;
@@ -90,12 +107,17 @@ struct StageArgs {
     int32_t *ctil_col;
     val_t *ctil_val;
     int32_t *nnzc;
+    const int64_t *gate = nullptr;  // when set and *gate != 0, the kernels write nothing (C too small)
 };
 
 cudaError_t launch_heap(const StageArgs &a, const int32_t *rows, int64_t nrows, int slots, int nt,
                         cudaStream_t st);
+cudaError_t launch_heap_set(const StageArgs &a, const RowSet &R, int slots, int nt, cudaStream_t st);
 cudaError_t launch_esc(const StageArgs &a, const int32_t *rows, int64_t nrows, int bin,
                        cudaStream_t st);
+// count_only: nnz(c_i) of every row into a.nnzc and nothing else (the counting pass of the
+// precise method, Section 3.1); bin 32 stands for any u_i <= 32
+cudaError_t launch_esc_set(const StageArgs &a, const RowSet &R, int bin, bool count_only, cudaStream_t st);
 
 // Bin-37 work items.  Item j < n37 is the j-th row of bin 37 with the full
 // column range.  An item whose sequence outgrows the largest shared-memory
@@ -179,6 +201,9 @@ struct DenseArgs {
     const int32_t *bnd;    // K > 1: per B row, K + 1 offsets of the slices' first entries in the row
     int32_t *cnt;          // n K columns per (row, slice)
     int32_t *soff;         // n K offsets of the slices inside their row of C
+    const int64_t *dev_n = nullptr;  // when set: the number of dense items is *dev_n (<= n), read on
+                                     // the device; the kernels run persistent grids over (item, slice)
+    unsigned long long *queue = nullptr;  // with dev_n: two work counters (count, fill), zeroed by the launchers
 };
 cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cudaStream_t st);
 // per row: flag (1 = dense-slice row: bin 37, and u_i >= dmin if dmin > 0, else div u_i >= the
@@ -196,10 +221,13 @@ cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *
 cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t *err, cudaStream_t st);
 // slice offsets inside the rows, and the dense items' lengths in the work-item table
 cudaError_t launch_dense_rows(const MergeItems &it, const DenseArgs &D, cudaStream_t st);
+// precise method: slice offsets inside the rows, and nnz(c_i) of every dense row into nnzc
+cudaError_t launch_dense_rowsum(const DenseArgs &D, int32_t *nnzc, cudaStream_t st);
 // accumulates every (row, slice) and writes it into C at c_rp[row] + soff; replay: values
 // only, into the entries whose columns are already in C
 cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs &D, const int64_t *c_rp,
-                              int32_t *c_col, val_t *c_val, int64_t *err, cudaStream_t st, bool replay = false);
+                              int32_t *c_col, val_t *c_val, int64_t *err, cudaStream_t st, bool replay = false,
+                              const int64_t *gate = nullptr);
 int dense_fill_smem_bytes(int W);
 int dense_fill_static_smem();
 int dense_fill_max_dynamic(int per_sm);
@@ -252,6 +280,11 @@ cudaError_t launch_row_scan(int64_t m, const int32_t *nnzc, int64_t *c_rp, int64
 cudaError_t launch_arrange_short(const StageArgs &a, const int32_t *rows, int64_t nrows,
                                  const uint8_t *bin, const int64_t *c_rp, int32_t *c_col,
                                  val_t *c_val, cudaStream_t st);
+cudaError_t launch_arrange_short_set(const StageArgs &a, const RowSet &R, const uint8_t *bin, const int64_t *c_rp,
+                                     int32_t *c_col, val_t *c_val, cudaStream_t st);
+// *gate = 1, *err = 8 and every c_rp[0..m] = 0 (C empty) when the result of m rows (c_rp[m]
+// entries) exceeds cap entries, else *gate = 0
+cudaError_t launch_gate(int64_t *c_rp, int64_t m, int64_t cap, int64_t *gate, int64_t *err, cudaStream_t st);
 cudaError_t launch_arrange_long(const MergeItems &it, int64_t n37, const int64_t *c_rp, int32_t *c_col,
                                 val_t *c_val, cudaStream_t st);
 

@@ -146,6 +146,11 @@ struct spgemm_plan {
     val_t *ctil_val = nullptr;
     BinSummary *d_summary = nullptr;
     int64_t *d_err = nullptr;
+    // products sized on the device: stage-2 scratch and dense-selection scratch kept with the
+    // plan, and the work counters of the persistent dense kernels
+    int32_t *d_hist = nullptr, *d_select = nullptr;
+    int64_t *d_capp = nullptr;
+    unsigned long long *d_queue = nullptr;
     BinSummary h_summary{};
     int64_t bin_start[NUM_BINS + 1] = {0};
     // bin 37 work items
@@ -294,8 +299,11 @@ struct spgemm_plan {
     }
 };
 
-// Largest shared-memory result capacity of the merge kernel for the plan's batch size.
+// Largest shared-memory result capacity of the merge kernel for the plan's batch size, and
+// the dense column slices (always sized for the precise method, which computes every bin-37
+// row with them).
 static void merge_limits(spgemm_plan *p) {
+    const bool force_dense = p->opts.alloc_policy == SPGEMM_ALLOC_PRECISE;
     // leave room for the kernel's static shared memory
     const int smem_limit = (p->smem_optin > 0 ? p->smem_optin : 227 * 1024) - 1024;
     int batch = p->opts.merge_batch > 0 ? p->opts.merge_batch : 2048;
@@ -325,8 +333,9 @@ static void merge_limits(spgemm_plan *p) {
     p->dense_K = 0;
     p->dense_W = 0;
     p->dense_min_u = 0;
-    if (p->opts.dense_min_u >= 0 && p->opts.merge_kernel != SPGEMM_MERGE_PATH &&
-        p->opts.long_rows == SPGEMM_LONG_ROWS_SPLIT && p->B.ncols > 0) {
+    if ((force_dense || (p->opts.dense_min_u >= 0 && p->opts.merge_kernel != SPGEMM_MERGE_PATH &&
+                         p->opts.long_rows == SPGEMM_LONG_ROWS_SPLIT)) &&
+        p->B.ncols > 0) {
         const int64_t n = p->B.ncols;
         auto widest = [](int limit) {
             int w = (int)(limit / (sizeof(val_t) + 1.25)) & ~31;
@@ -342,6 +351,7 @@ static void merge_limits(spgemm_plan *p) {
             p->dense_W = (int)w;
             p->dense_K = (int)((n + w - 1) / w);
             p->dense_min_u = p->opts.dense_min_u > 0 ? (int64_t)p->opts.dense_min_u : 0;
+            if (force_dense) p->dense_min_u = BIN_MERGE_MIN_U + 1;  // every bin-37 row
         }
     }
     // learned launch classes: 256, 512, ..., 8192, the largest capacity, and "beyond it"
@@ -410,10 +420,19 @@ StageArgs stage_args(spgemm_plan *p) {
     return a;
 }
 
+// Rows of bins lo..hi: host-known from the stage-2 summary, or (dev) a range of bin_rows whose
+// ends the kernels read from the device copy of the summary.
+RowSet bin_range(const spgemm_plan *p, int lo, int hi, bool dev) {
+    if (dev)
+        return RowSet{p->bin_rows, p->A.nrows, &p->d_summary->bin_start[lo], &p->d_summary->bin_start[hi + 1]};
+    return host_rows(p->bin_rows + p->bin_start[lo], p->bin_start[hi + 1] - p->bin_start[lo]);
+}
+
 // Stage 3, bins 2..36 (bin groups 3 and 4): the heap kernel for bins 2..heap_max_u
 // (one launch per range, sized to the range's widest heap), the bitonic ESC kernel
-// with 32 slots for the rest of bins up to 32, and ESC for bins 33..36.
-cudaError_t launch_short_bins(spgemm_plan *p, const StageArgs &a, bool account) {
+// with 32 slots for the rest of bins up to 32, and ESC for bins 33..36.  With dev the
+// bin sizes are read on the device (persistent grids; every launch is made).
+cudaError_t launch_short_bins(spgemm_plan *p, const StageArgs &a, bool account, bool dev = false) {
     cudaError_t e = cudaSuccess;
     const int hmax = (p->opts.heap_max_u >= 2 && p->opts.heap_max_u <= 32) ? p->opts.heap_max_u : 32;
     const int heap_nt = p->opts.heap_block > 0 ? p->opts.heap_block : 128;
@@ -429,21 +448,18 @@ cudaError_t launch_short_bins(spgemm_plan *p, const StageArgs &a, bool account) 
     for (auto &r : kHeapRanges) {
         const int lo = r[0], hi = std::min(r[1], hmax);
         if (lo > hi) continue;
-        const int64_t s0 = p->bin_start[lo], s1 = p->bin_start[hi + 1];
-        if (s1 > s0 && run(SPGEMM_K_HEAP, [&] { return launch_heap(a, p->bin_rows + s0, s1 - s0, hi, heap_nt, p->st); }) !=
-                           cudaSuccess)
+        const RowSet R = bin_range(p, lo, hi, dev);
+        if (R.n > 0 && run(SPGEMM_K_HEAP, [&] { return launch_heap_set(a, R, hi, heap_nt, p->st); }) != cudaSuccess)
             return e;
     }
     if (hmax < 32) {
-        const int64_t s0 = p->bin_start[hmax + 1], s1 = p->bin_start[33];
-        if (s1 > s0 && run(SPGEMM_K_ESC, [&] { return launch_esc(a, p->bin_rows + s0, s1 - s0, 32, p->st); }) !=
-                           cudaSuccess)
+        const RowSet R = bin_range(p, hmax + 1, 32, dev);
+        if (R.n > 0 && run(SPGEMM_K_ESC, [&] { return launch_esc_set(a, R, 32, false, p->st); }) != cudaSuccess)
             return e;
     }
     for (int b = BIN_ESC_LO; b <= BIN_ESC_HI; ++b) {
-        const int64_t s0 = p->bin_start[b], s1 = p->bin_start[b + 1];
-        if (s1 > s0 && run(SPGEMM_K_ESC, [&] { return launch_esc(a, p->bin_rows + s0, s1 - s0, b, p->st); }) !=
-                           cudaSuccess)
+        const RowSet R = bin_range(p, b, b, dev);
+        if (R.n > 0 && run(SPGEMM_K_ESC, [&] { return launch_esc_set(a, R, b, false, p->st); }) != cudaSuccess)
             return e;
     }
     return cudaSuccess;
@@ -456,7 +472,7 @@ static spgemm_status plan_begin(const spgemm_opts *opts, spgemm_stream_t stream,
     *out = nullptr;
     spgemm_opts o;
     if (opts) o = *opts; else spgemm_opts_init(&o);
-    if (o.alloc_policy < 0 || o.alloc_policy > 2 || o.initial_cap < 1) return SPGEMM_ERR_INVALID_ARG;
+    if (o.alloc_policy < 0 || o.alloc_policy > 3 || o.initial_cap < 1) return SPGEMM_ERR_INVALID_ARG;
     if (o.alloc_policy == SPGEMM_ALLOC_LEARNED && o.predictor == nullptr) return SPGEMM_ERR_INVALID_ARG;
     spgemm_plan *p = new (std::nothrow) spgemm_plan();
     if (!p) return SPGEMM_ERR_OOM;
@@ -524,6 +540,10 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
         p->time_end();
         p->count(SPGEMM_K_BOUND, 3);
         merge_limits(p);
+        if (o.alloc_policy == SPGEMM_ALLOC_PRECISE && p->dense_K == 0 && p->B.ncols > 0) {
+            status = SPGEMM_ERR_SHAPE;  // B too wide for the column slices of the precise method
+            goto fail;
+        }
         if (p->dense_K > 0) {
             // which bin-37 rows go to the dense-slice kernels, and their column ranges
             SPG_TRY(p->alloc_n(&p->dense_flag, m, LIFE_SYMBOLIC));
@@ -1071,12 +1091,15 @@ fail:
 
 }  // namespace
 
+static spgemm_status run_precise(spgemm_plan *p, spgemm_csr_out *C_out);
+
 extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
     if (!p || !C_out || p->wave_mode) return SPGEMM_ERR_INVALID_ARG;
     if (p->numeric_done) {
         *C_out = p->C;
         return SPGEMM_OK;
     }
+    if (p->opts.alloc_policy == SPGEMM_ALLOC_PRECISE) return run_precise(p, C_out);
     spgemm_status status = SPGEMM_OK;
     const int64_t m = p->A.nrows;
     StageArgs a = stage_args(p);
@@ -1493,6 +1516,11 @@ fail:
 static spgemm_status prepare_replay(spgemm_plan *p) {
     spgemm_status status = SPGEMM_OK;
     const int64_t n37 = p->h_summary.bin_count[BIN_MERGE];
+    if (p->opts.alloc_policy == SPGEMM_ALLOC_PRECISE) {
+        // every bin-37 row is a dense-slice row, replayed by the fill kernel
+        p->replay_ready = true;
+        return SPGEMM_OK;
+    }
     // rows finished with a level-1 sequence can be longer than any shared-memory slice
     if (p->stats.rows_level1 > 0) return SPGEMM_ERR_INVALID_ARG;
     {
@@ -1683,5 +1711,465 @@ extern "C" spgemm_status spgemm_galerkin(const spgemm_csr_in *R, const spgemm_cs
     }
     *plan_ap = p1;
     *plan_rap = p2;
+    return SPGEMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The precise method (Section 3.1): count every row, allocate C exactly, compute
+// every row straight into it.  The same passes serve the products sized on the
+// device (spgemm_dplan_*), with the bin sizes read by the kernels.
+// ---------------------------------------------------------------------------
+
+// The dense-slice arguments of a plan; with dev, the number of items is read on the device
+// (the plan's bin-37 count) and the kernels take work from the plan's counters.
+static DenseArgs dense_args_of(const spgemm_plan *p, bool dev) {
+    DenseArgs D = p->dense_args();
+    if (dev) {
+        D.n = p->A.nrows;  // every row may be in bin 37: the arrays hold n K entries
+        D.dev_n = &p->d_summary->dense_count;
+        D.queue = p->d_queue;
+    }
+    return D;
+}
+
+// Counting pass: nnz(c_i) of bins 2..36 by a warp sort of their columns, and of bin 37 by the
+// dense-slice count; bins 0 and 1 were sized by stage 2.
+static cudaError_t precise_count(spgemm_plan *p, bool dev) {
+    StageArgs a = stage_args(p);
+    const bool acc = !dev;
+    auto run = [&](int kind, auto &&launch) -> cudaError_t {
+        if (acc) p->time_begin(kind);
+        cudaError_t e = launch();
+        if (acc) {
+            p->time_end();
+            p->count(kind);
+        }
+        return e;
+    };
+    cudaError_t e;
+    const RowSet r32 = bin_range(p, BIN_HEAP_LO, BIN_HEAP_HI, dev);
+    if (r32.n > 0 && (e = run(SPGEMM_K_ESC, [&] { return launch_esc_set(a, r32, 32, true, p->st); })) != cudaSuccess)
+        return e;
+    for (int b = BIN_ESC_LO; b <= BIN_ESC_HI; ++b) {
+        const RowSet R = bin_range(p, b, b, dev);
+        if (R.n > 0 && (e = run(SPGEMM_K_ESC, [&] { return launch_esc_set(a, R, b, true, p->st); })) != cudaSuccess)
+            return e;
+    }
+    if (p->dense_K > 0 && (dev || p->dense_n > 0)) {
+        const DenseArgs D = dense_args_of(p, dev);
+        if ((e = run(SPGEMM_K_MERGE, [&] { return launch_dense_count(p->A, p->B, D, p->d_err, p->st); })) != cudaSuccess)
+            return e;
+        if ((e = run(SPGEMM_K_OTHER, [&] { return launch_dense_rowsum(D, p->nnzc, p->st); })) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Fill pass: every row computed straight into C (whose row pointers exist); nothing is
+// written when the gate word is set.
+static cudaError_t precise_fill(spgemm_plan *p, bool dev, const int64_t *gate) {
+    StageArgs a = stage_args(p);
+    a.ctil_rp = p->C.row_ptr;
+    a.ctil_col = p->C.col_idx;
+    a.ctil_val = p->C.val;
+    a.gate = gate;
+    cudaError_t e = launch_short_bins(p, a, !dev, dev);
+    if (e != cudaSuccess) return e;
+    // bin 1: the single product of each row
+    const RowSet r1 = bin_range(p, 1, 1, dev);
+    if (!dev) p->time_begin(SPGEMM_K_ARRANGE);
+    e = launch_arrange_short_set(a, r1, p->bin, p->C.row_ptr, p->C.col_idx, p->C.val, p->st);
+    if (!dev) {
+        p->time_end();
+        if (r1.n > 0) p->count(SPGEMM_K_ARRANGE);
+    }
+    if (e != cudaSuccess) return e;
+    if (p->dense_K > 0 && (dev || p->dense_n > 0)) {
+        if (!dev) p->time_begin(SPGEMM_K_MERGE);
+        e = launch_dense_fill(p->A, p->B, dense_args_of(p, dev), p->C.row_ptr, p->C.col_idx, p->C.val, p->d_err, p->st,
+                              false, gate);
+        if (!dev) {
+            p->time_end();
+            p->count(SPGEMM_K_MERGE);
+        }
+    }
+    return e;
+}
+
+static spgemm_status run_precise(spgemm_plan *p, spgemm_csr_out *C_out) {
+    spgemm_status status = SPGEMM_OK;
+    const int64_t m = p->A.nrows;
+    {
+        SPG_TRY(precise_count(p, false));
+        SPG_TRY(p->alloc_n(&p->C.row_ptr, m + 1));
+        p->time_begin(SPGEMM_K_SCAN);
+        SPG_TRY(launch_row_scan(m, p->nnzc, p->C.row_ptr, p->scan_partial, p->st));
+        p->time_end();
+        p->count(SPGEMM_K_SCAN, 3);
+        int64_t both[2] = {0, 0};
+        SPG_TRY(p->d2h2(both, p->C.row_ptr + m, p->d_err));  // nnz(C), the one size the method reads back
+        if (both[1] != 0) {
+            status = SPGEMM_ERR_INTERNAL;
+            goto fail;
+        }
+        const int64_t nnzC = both[0];
+        SPG_TRY(p->alloc_n(&p->C.col_idx, nnzC));
+        SPG_TRY(p->alloc_n(&p->C.val, nnzC));
+        SPG_TRY(precise_fill(p, false, nullptr));
+        p->C.nrows = m;
+        p->C.ncols = p->B.ncols;
+        p->C.nnz = nnzC;
+        p->stats.nnz_c = nnzC;
+        p->stats.bytes_ctilde = p->bytes_ctilde;
+        p->numeric_done = true;
+        p->release_temps(LIFE_NUMERIC);
+        *C_out = p->C;
+    }
+    return SPGEMM_OK;
+fail:
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// Products sized on the device: the precise method with every size kept in device
+// memory, enqueued without allocation or read-back (capturable in a CUDA graph).
+// ---------------------------------------------------------------------------
+
+struct spgemm_dplan {
+    spgemm_plan *p = nullptr;
+    spgemm_csr_in A_in{}, B_in{};  // the borrowed inputs (int32 row pointers are widened each run)
+    int64_t *a_rp64 = nullptr, *b_rp64 = nullptr;
+    int64_t c_cap = 0;
+    int64_t *gate = nullptr;
+    int64_t *d_first = nullptr;     // batched: first entry of each C_i in the concatenated C
+    int64_t nnz_cat_a = 0, nnz_cat_b = 0;
+};
+
+// Allocates every buffer of a device-sized plan whose A and B (DevCSR sizes) are set.
+static spgemm_status dplan_buffers(spgemm_dplan *d) {
+    spgemm_plan *p = d->p;
+    spgemm_status status = SPGEMM_OK;
+    const int64_t m = p->A.nrows, nnzA = p->A.nnz;
+    const int64_t nblk = bin_blocks(m);
+    {
+        merge_limits(p);
+        if (p->dense_K == 0 && p->B.ncols > 0) return SPGEMM_ERR_SHAPE;
+        SPG_TRY(p->alloc_n(&p->d_summary, 1));
+        SPG_TRY(p->alloc_n(&p->d_err, 1));
+        SPG_TRY(p->alloc_n(&d->gate, 1));
+        SPG_TRY(p->alloc_n(&p->d_queue, 2));
+        SPG_TRY(p->alloc_n(&p->S, nnzA + 1));
+        SPG_TRY(p->alloc_n(&p->scan_partial, std::max(bound_partial_size(nnzA), bin_blocks(m) + 1) + 1));
+        SPG_TRY(p->alloc_n(&p->u, m));
+        SPG_TRY(p->alloc_n(&p->bin, m));
+        SPG_TRY(p->alloc_n(&p->nnzc, m));
+        SPG_TRY(p->alloc_n(&p->bin_rows, m));
+        SPG_TRY(p->alloc_n(&p->ctil_rp, m + 1));
+        SPG_TRY(p->alloc_n(&p->d_hist, (int64_t)NUM_BINS * nblk));
+        SPG_TRY(p->alloc_n(&p->d_capp, nblk));
+        if (p->dense_K > 0) {
+            SPG_TRY(p->alloc_n(&p->dense_flag, m));
+            SPG_TRY(p->alloc_n(&p->dense_lo, m));
+            SPG_TRY(p->alloc_n(&p->dense_hi, m));
+            SPG_TRY(p->alloc_n(&p->d_select, dense_select_scratch(m)));
+            SPG_TRY(p->alloc_n(&p->dense_order, m));
+            SPG_TRY(p->alloc_n(&p->dense_rows, m));
+            SPG_TRY(p->alloc_n(&p->dense_clo, m));
+            SPG_TRY(p->alloc_n(&p->dense_chi, m));
+            if (p->dense_K > 1) SPG_TRY(p->alloc_n(&p->dense_bnd, p->B.nrows * (p->dense_K + 1)));
+            SPG_TRY(p->alloc_n(&p->dense_cnt, m * p->dense_K));
+            SPG_TRY(p->alloc_n(&p->dense_soff, m * p->dense_K));
+        }
+        SPG_TRY(p->alloc_n(&p->C.row_ptr, m + 1));
+        SPG_TRY(p->alloc_n(&p->C.col_idx, d->c_cap));
+        SPG_TRY(p->alloc_n(&p->C.val, d->c_cap));
+        SPG_TRY(cudaStreamSynchronize(p->st));  // the buffers exist before any capture
+        p->C.nrows = m;
+        p->C.ncols = p->B.ncols;
+        p->C.nnz = -1;
+    }
+    return SPGEMM_OK;
+fail:
+    return status;
+}
+
+// One product, stages 1-4, every size on the device.
+static cudaError_t dplan_enqueue(spgemm_dplan *d) {
+    spgemm_plan *p = d->p;
+    const int64_t m = p->A.nrows;
+    cudaError_t e;
+#define DP_TRY(x)                            \
+    do {                                     \
+        if ((e = (x)) != cudaSuccess) return e; \
+    } while (0)
+    DP_TRY(cudaMemsetAsync(p->d_summary, 0, sizeof(BinSummary), p->st));
+    DP_TRY(cudaMemsetAsync(p->d_err, 0, sizeof(int64_t), p->st));
+    if (p->npairs > 0) {
+        DP_TRY(launch_concat(p->d_pairs, p->npairs, p->d_moff, p->d_koff, p->d_annz_off, p->d_bnnz_off, p->A.nrows,
+                             p->B.nrows, p->A.nnz, p->B.nnz, p->cat_a_rp, p->cat_a_col, p->cat_a_val, p->cat_b_rp,
+                             p->cat_b_col, p->cat_b_val, false, p->st));
+    } else {
+        if (d->a_rp64)
+            DP_TRY(launch_widen_rowptr(static_cast<const int32_t *>(d->A_in.row_ptr), d->a_rp64, m + 1, p->st));
+        if (d->b_rp64 && d->b_rp64 != d->a_rp64)
+            DP_TRY(launch_widen_rowptr(static_cast<const int32_t *>(d->B_in.row_ptr), d->b_rp64, p->B.nrows + 1,
+                                       p->st));
+    }
+    // stage 1 and the column ranges of the bin-37 rows (all of them dense-slice rows)
+    DP_TRY(launch_bound(p->A, p->B, p->S, p->scan_partial, p->st));
+    if (p->dense_K > 0)
+        DP_TRY(launch_dense_mark(p->A, p->B, p->S, p->dense_min_u, 8, p->dense_flag, p->dense_lo, p->dense_hi, p->st));
+    // stage 2: bins (no C~ to size)
+    CapPolicy pol{};
+    pol.policy = POLICY_PRECISE;
+    pol.initial_cap = 1;
+    pol.dense = p->dense_flag;
+    DP_TRY(launch_binning(m, p->A.rp, p->S, p->S + p->A.nnz, pol, p->u, p->bin, p->nnzc, p->bin_rows, p->ctil_rp,
+                          p->d_hist, p->d_capp, p->d_summary, p->st));
+    if (p->dense_K > 0) {
+        DP_TRY(launch_dense_select(p->bin_rows, m, p->d_summary, p->u, p->dense_flag, p->dense_lo, p->dense_hi,
+                                   p->d_select, p->dense_order, p->dense_rows, p->dense_clo, p->dense_chi, p->st));
+        if (p->dense_K > 1) DP_TRY(launch_dense_bounds(p->B, p->dense_K, p->dense_W, p->dense_bnd, p->st));
+    }
+    // stage 3, counting pass; stage 4, row pointers; then the fill pass straight into C
+    DP_TRY(precise_count(p, true));
+    DP_TRY(launch_row_scan(m, p->nnzc, p->C.row_ptr, p->scan_partial, p->st));
+    DP_TRY(launch_gate(p->C.row_ptr, m, d->c_cap, d->gate, p->d_err, p->st));
+    DP_TRY(precise_fill(p, true, d->gate));
+    if (p->npairs > 0) {
+        DP_TRY(launch_split_out(p->d_pairs, p->npairs, p->C.row_ptr, m, p->split_rp, p->st));
+        DP_TRY(launch_gather_first(p->d_pairs, p->npairs, p->C.row_ptr, m, d->d_first, p->st));
+    }
+#undef DP_TRY
+    return cudaSuccess;
+}
+
+static spgemm_status dplan_begin(const spgemm_opts *opts, spgemm_stream_t stream, int64_t c_cap, spgemm_dplan **out) {
+    *out = nullptr;
+    if (c_cap < 0) return SPGEMM_ERR_INVALID_ARG;
+    spgemm_opts o;
+    if (opts) o = *opts; else spgemm_opts_init(&o);
+    o.alloc_policy = SPGEMM_ALLOC_PRECISE;
+    o.predictor = nullptr;
+    o.record_timing = 0;
+    o.check_inputs = 0;
+    spgemm_dplan *d = new (std::nothrow) spgemm_dplan();
+    if (!d) return SPGEMM_ERR_OOM;
+    spgemm_status st = plan_begin(&o, stream, &d->p);
+    if (st != SPGEMM_OK) {
+        delete d;
+        return st;
+    }
+    d->c_cap = c_cap;
+    *out = d;
+    return SPGEMM_OK;
+}
+
+extern "C" spgemm_status spgemm_dplan_free(spgemm_dplan *d) {
+    if (!d) return SPGEMM_OK;
+    if (d->p) spgemm_free(d->p);
+    delete d;
+    return SPGEMM_OK;
+}
+
+extern "C" spgemm_status spgemm_dplan_create(const spgemm_csr_in *A_in, const spgemm_csr_in *B_in, int64_t c_cap,
+                                             const spgemm_opts *opts, spgemm_stream_t stream, spgemm_dplan **out,
+                                             spgemm_csr_out *C) {
+    if (!out || !C) return SPGEMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    spgemm_status status = check_in(A_in);
+    if (status != SPGEMM_OK) return status;
+    status = check_in(B_in);
+    if (status != SPGEMM_OK) return status;
+    if (A_in->ncols != B_in->nrows) return SPGEMM_ERR_SHAPE;
+    spgemm_dplan *d = nullptr;
+    status = dplan_begin(opts, stream, c_cap, &d);
+    if (status != SPGEMM_OK) return status;
+    spgemm_plan *p = d->p;
+    {
+        d->A_in = *A_in;
+        d->B_in = *B_in;
+        auto side = [&](const spgemm_csr_in *M, DevCSR &D, int64_t **rp64) -> cudaError_t {
+            D = DevCSR{M->nrows, M->ncols, M->nnz, static_cast<const int64_t *>(M->row_ptr), M->col_idx, M->val};
+            if (M->rowptr_bits == 64) return cudaSuccess;
+            cudaError_t e = p->alloc_n(rp64, M->nrows + 1);
+            D.rp = *rp64;
+            return e;
+        };
+        SPG_TRY(side(A_in, p->A, &d->a_rp64));
+        if (B_in->row_ptr == A_in->row_ptr && B_in->rowptr_bits == A_in->rowptr_bits) {
+            p->B = DevCSR{B_in->nrows, B_in->ncols, B_in->nnz, p->A.rp, B_in->col_idx, B_in->val};
+            d->b_rp64 = d->a_rp64;
+        } else {
+            SPG_TRY(side(B_in, p->B, &d->b_rp64));
+        }
+        status = dplan_buffers(d);
+        if (status != SPGEMM_OK) goto fail;
+    }
+    *C = p->C;
+    *out = d;
+    return SPGEMM_OK;
+fail:
+    cudaStreamSynchronize(p->st);
+    spgemm_dplan_free(d);
+    return status;
+}
+
+extern "C" spgemm_status spgemm_dplan_batched_create(int64_t npairs, const spgemm_csr_in *A, const spgemm_csr_in *B,
+                                                     int64_t c_cap, const spgemm_opts *opts, spgemm_stream_t stream,
+                                                     spgemm_dplan **out, spgemm_csr_out *C) {
+    if (!out || !C || npairs < 1 || !A || !B) return SPGEMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::vector<PairDesc> hd((size_t)npairs);
+    std::vector<int64_t> moff(npairs), koff(npairs), aoff(npairs), boff(npairs);
+    int64_t M = 0, K = 0, N = 0, annz = 0, bnnz = 0;
+    for (int64_t i = 0; i < npairs; ++i) {
+        spgemm_status st = check_in(&A[i]);
+        if (st != SPGEMM_OK) return st;
+        st = check_in(&B[i]);
+        if (st != SPGEMM_OK) return st;
+        if (A[i].ncols != B[i].nrows) return SPGEMM_ERR_SHAPE;
+        PairDesc &q = hd[i];
+        q.a_rp = A[i].row_ptr;
+        q.b_rp = B[i].row_ptr;
+        q.a_col = A[i].col_idx;
+        q.b_col = B[i].col_idx;
+        q.a_val = A[i].val;
+        q.b_val = B[i].val;
+        q.a_bits = A[i].rowptr_bits;
+        q.b_bits = B[i].rowptr_bits;
+        q.m = A[i].nrows;
+        q.k = A[i].ncols;
+        q.n = B[i].ncols;
+        q.moff = moff[i] = M;
+        q.koff = koff[i] = K;
+        q.annz_off = aoff[i] = annz;
+        q.bnnz_off = boff[i] = bnnz;
+        q.annz = A[i].nnz;
+        q.bnnz = B[i].nnz;
+        M += q.m;
+        K += q.k;
+        N = std::max(N, q.n);
+        annz += q.annz;
+        bnnz += q.bnnz;
+    }
+    if (M > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return SPGEMM_ERR_SHAPE;
+    spgemm_dplan *d = nullptr;
+    spgemm_status status = dplan_begin(opts, stream, c_cap, &d);
+    if (status != SPGEMM_OK) return status;
+    spgemm_plan *p = d->p;
+    {
+        p->npairs = npairs;
+        p->h_pairs = hd;
+        SPG_TRY(p->alloc_n(&p->d_pairs, npairs));
+        SPG_TRY(p->alloc_n(&p->d_moff, npairs));
+        SPG_TRY(p->alloc_n(&p->d_koff, npairs));
+        SPG_TRY(p->alloc_n(&p->d_annz_off, npairs));
+        SPG_TRY(p->alloc_n(&p->d_bnnz_off, npairs));
+        SPG_TRY(cudaMemcpyAsync(p->d_pairs, hd.data(), sizeof(PairDesc) * npairs, cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(cudaMemcpyAsync(p->d_moff, moff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(cudaMemcpyAsync(p->d_koff, koff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(cudaMemcpyAsync(p->d_annz_off, aoff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(cudaMemcpyAsync(p->d_bnnz_off, boff.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, p->st));
+        SPG_TRY(cudaStreamSynchronize(p->st));  // pageable sources
+        SPG_TRY(p->alloc_n(&p->cat_a_rp, M + 1));
+        SPG_TRY(p->alloc_n(&p->cat_b_rp, K + 1));
+        SPG_TRY(p->alloc_n(&p->cat_a_col, annz));
+        SPG_TRY(p->alloc_n(&p->cat_a_val, annz));
+        SPG_TRY(p->alloc_n(&p->cat_b_col, bnnz));
+        SPG_TRY(p->alloc_n(&p->cat_b_val, bnnz));
+        SPG_TRY(p->alloc_n(&p->split_rp, M + npairs));
+        SPG_TRY(p->alloc_n(&d->d_first, npairs + 1));
+        p->A = DevCSR{M, K, annz, p->cat_a_rp, p->cat_a_col, p->cat_a_val};
+        p->B = DevCSR{K, N, bnnz, p->cat_b_rp, p->cat_b_col, p->cat_b_val};
+        status = dplan_buffers(d);
+        if (status != SPGEMM_OK) goto fail;
+    }
+    *C = p->C;
+    *out = d;
+    return SPGEMM_OK;
+fail:
+    cudaStreamSynchronize(p->st);
+    spgemm_dplan_free(d);
+    return status;
+}
+
+extern "C" spgemm_status spgemm_dplan_run(spgemm_dplan *d) {
+    if (!d || !d->p) return SPGEMM_ERR_INVALID_ARG;
+    return from_cuda(dplan_enqueue(d));
+}
+
+extern "C" spgemm_status spgemm_dplan_result(spgemm_dplan *d, spgemm_csr_out *C_out) {
+    if (!d || !d->p || !C_out) return SPGEMM_ERR_INVALID_ARG;
+    spgemm_plan *p = d->p;
+    const int64_t m = p->A.nrows;
+    int64_t both[2] = {0, 0};
+    cudaError_t e = p->d2h2(both, p->C.row_ptr + m, p->d_err);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (both[1] == 8) return SPGEMM_ERR_OOM;  // nnz(C) exceeded the capacity: C was left empty
+    if (both[1] != 0) return SPGEMM_ERR_INTERNAL;
+    p->C.nnz = both[0];
+    if (p->npairs == 0) {
+        *C_out = p->C;
+        return SPGEMM_OK;
+    }
+    const int64_t np = p->npairs;
+    std::vector<int64_t> first(np + 1);
+    e = cudaMemcpy(first.data(), d->d_first, sizeof(int64_t) * (np + 1), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return from_cuda(e);
+    for (int64_t i = 0; i < np; ++i) {
+        const PairDesc &q = p->h_pairs[i];
+        spgemm_csr_out &c = C_out[i];
+        c.nrows = q.m;
+        c.ncols = q.n;
+        c.nnz = first[i + 1] - first[i];
+        c.row_ptr = p->split_rp + q.moff + i;
+        c.col_idx = p->C.col_idx + first[i];
+        c.val = p->C.val + first[i];
+    }
+    return SPGEMM_OK;
+}
+
+extern "C" spgemm_status spgemm_dplan_bytes(spgemm_dplan *d, int64_t *bytes) {
+    if (!d || !d->p || !bytes) return SPGEMM_ERR_INVALID_ARG;
+    *bytes = d->p->bytes_held;
+    return SPGEMM_OK;
+}
+
+extern "C" spgemm_status spgemm_dplan_graph_create(spgemm_dplan *const *plans, int64_t n, spgemm_graph **out) {
+    if (!plans || n < 1 || !out) return SPGEMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int64_t i = 0; i < n; ++i)
+        if (!plans[i] || !plans[i]->p) return SPGEMM_ERR_INVALID_ARG;
+    cudaStream_t st = plans[0]->p->st;
+    if (st == nullptr) return SPGEMM_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+    for (int64_t i = 0; i < n; ++i) {
+        if (plans[i]->p->st != st) return SPGEMM_ERR_INVALID_ARG;
+        // one run outside the capture sets the kernels' attributes
+        spgemm_status s = from_cuda(dplan_enqueue(plans[i]));
+        if (s != SPGEMM_OK) return s;
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    spgemm_graph *g = new (std::nothrow) spgemm_graph();
+    if (!g) return SPGEMM_ERR_OOM;
+    g->st = st;
+    g->graph = nullptr;
+    g->exec = nullptr;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    spgemm_status status = e == cudaSuccess ? SPGEMM_OK : from_cuda(e);
+    for (int64_t i = 0; status == SPGEMM_OK && i < n; ++i) status = from_cuda(dplan_enqueue(plans[i]));
+    e = cudaStreamEndCapture(st, &g->graph);
+    if (status == SPGEMM_OK && e != cudaSuccess) status = from_cuda(e);
+    if (status == SPGEMM_OK) {
+        e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+        if (e != cudaSuccess) status = from_cuda(e);
+    }
+    if (status != SPGEMM_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return status;
+    }
+    *out = g;
     return SPGEMM_OK;
 }

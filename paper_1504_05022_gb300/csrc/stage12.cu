@@ -13,7 +13,30 @@
 #include "internal.h"
 #include "scan.cuh"
 
+#include <mutex>
+#include <vector>
+
 namespace spg {
+
+int persistent_blocks(const void *kern, int nt, size_t smem, int64_t cap) {
+    static std::mutex mu;
+    static std::vector<int> sms;  // SM count per device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    int nsm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if ((int)sms.size() <= dev) sms.resize(dev + 1, 0);
+        if (sms[dev] == 0 && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        nsm = sms[dev];
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t g = (int64_t)nsm * per_sm;
+    return (int)(cap > 0 && cap < g ? cap : g);
+}
 
 __global__ void k_widen_rowptr(const int32_t *in, int64_t *out, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -101,8 +124,10 @@ SPG_DEV int bin_of(int64_t u) {
 // Size of row i in C~.  Hybrid (Algorithm 3): u_i for bins 0..36, a fixed
 // initial size (256) for bin 37.  Upper bound: u_i.  Learned: u_i for bins
 // 0..36, the predicted size (never above u_i) for bin 37.  Bin-37 rows computed
-// by the dense-slice kernels take none in every policy.
+// by the dense-slice kernels take none in every policy, and the precise method
+// has no C~ at all.
 SPG_DEV int64_t cap_of(int64_t u, int b, int64_t i, const CapPolicy &P) {
+    if (P.policy == POLICY_PRECISE) return 0;  // counted first, then computed straight into C
     if (b == BIN_MERGE && P.dense != nullptr && P.dense[i]) return 0;  // written straight into C
     if (P.policy == POLICY_UPPER_BOUND) return u;
     if (P.policy == POLICY_LEARNED && P.pred_cap != nullptr && b == BIN_MERGE) {
@@ -192,6 +217,7 @@ k_bin_scan(int64_t m, int32_t *hist, int64_t nblk, int64_t *cap_partial, int64_t
     }
     __syncthreads();
     if (threadIdx.x < NUM_BINS) summary->bin_count[threadIdx.x] = bstart[threadIdx.x + 1] - bstart[threadIdx.x];
+    if (threadIdx.x <= NUM_BINS) summary->bin_start[threadIdx.x] = bstart[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(BIN_NT)

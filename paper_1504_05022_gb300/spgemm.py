@@ -380,6 +380,122 @@ def galerkin(R: CSR, A: CSR, P: CSR, stream: torch.cuda.Stream | None = None, **
     return Ac, p1, p2
 
 
+class _DPlanHandle(_PlanHandle):
+    """Owns an spgemm_dplan*."""
+
+    def free(self):
+        if self.ptr:
+            self.L.spgemm_dplan_free(ctypes.c_void_p(self.ptr))
+            self.ptr = 0
+
+
+class DevicePlan:
+    """C = A*B (or a batch of C_i = A_i*B_i) with every size kept on the device: the precise
+    method (count, then compute every row straight into C) with persistent per-bin kernels.
+    run() enqueues the whole product -- stages 1-4 -- without allocating or synchronising, so
+    it can run again on new contents of the same input arrays (structure included) and be
+    captured in a CUDA graph (DeviceGraph).  C has room for `capacity` entries; result()
+    synchronises, reads nnz(C) and returns C (a list of C_i for a batch), raising
+    SpgemmError(SPGEMM_ERR_OOM) if the product outgrew the capacity."""
+
+    def __init__(self, A, B, capacity: int, stream: torch.cuda.Stream | None = None, **opts):
+        batched = isinstance(A, (list, tuple))
+        mats = (list(A) + list(B)) if batched else [A, B]
+        L = self.L = _lib.load(dtype=_value_type(mats, opts))
+        self.inputs = mats  # borrowed by every run
+        first = mats[0]
+        self.device = first.val.device.index
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.opts = make_opts(**{k: v for k, v in opts.items() if k != "alloc_policy"})
+        self.capacity = int(capacity)
+        self.dtype = first.val.dtype
+        plan = ctypes.c_void_p()
+        c = _lib.CsrOut()
+        with torch.cuda.device(self.device):
+            if batched:
+                n = len(A)
+                ain = (_lib.CsrIn * n)(*[a._c_in() for a in A])
+                bin_ = (_lib.CsrIn * n)(*[b._c_in() for b in B])
+                rc = L.spgemm_dplan_batched_create(n, ain, bin_, self.capacity, ctypes.byref(self.opts),
+                                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(plan),
+                                                   ctypes.byref(c))
+            else:
+                a_in, b_in = A._c_in(), B._c_in()
+                rc = L.spgemm_dplan_create(ctypes.byref(a_in), ctypes.byref(b_in), self.capacity,
+                                           ctypes.byref(self.opts), ctypes.c_void_p(self.stream.cuda_stream),
+                                           ctypes.byref(plan), ctypes.byref(c))
+            _lib.check(rc, "spgemm_dplan_create")
+        self.handle = _DPlanHandle(plan.value, self.stream, L)
+        self.npairs = len(A) if batched else 0
+        self.shape = (int(c.nrows), int(c.ncols))
+        h = self.handle
+        self._rp = _wrap(c.row_ptr, c.nrows + 1, torch.int64, h, self.device)
+        self._col = _wrap(c.col_idx, self.capacity, torch.int32, h, self.device)
+        self._val = _wrap(c.val, self.capacity, self.dtype, h, self.device)
+
+    def run(self) -> None:
+        with torch.cuda.device(self.device):
+            _lib.check(self.L.spgemm_dplan_run(ctypes.c_void_p(self.handle.ptr)), "spgemm_dplan_run")
+
+    def as_input(self) -> CSR:
+        """C's arrays as the input of a later plan on the same stream (its entries beyond nnz(C)
+        are never read): chains two products on the device."""
+        return CSR(self._rp, self._col, self._val, self.shape)
+
+    def result(self):
+        n = max(1, self.npairs)
+        outs = (_lib.CsrOut * n)()
+        _lib.check(self.L.spgemm_dplan_result(ctypes.c_void_p(self.handle.ptr), outs), "spgemm_dplan_result")
+        h = self.handle
+        cs = [CSR(_wrap(o.row_ptr, o.nrows + 1, torch.int64, h, self.device),
+                  _wrap(o.col_idx, o.nnz, torch.int32, h, self.device),
+                  _wrap(o.val, o.nnz, self.dtype, h, self.device), (int(o.nrows), int(o.ncols))) for o in outs]
+        return cs if self.npairs else cs[0]
+
+    @property
+    def held_bytes(self) -> int:
+        b = ctypes.c_int64()
+        _lib.check(self.L.spgemm_dplan_bytes(ctypes.c_void_p(self.handle.ptr), ctypes.byref(b)), "spgemm_dplan_bytes")
+        return int(b.value)
+
+
+class DeviceGraph:
+    """One CUDA graph holding a full run (stages 1-4, every size on the device) of each of
+    several DevicePlans sharing one created stream, in order -- a whole batch, or both products
+    of a Galerkin chain R*(A*P).  launch() recomputes everything from the inputs' current
+    contents."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        L = self.L = self.plans[0].L
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.ptr for p in self.plans])
+        g = ctypes.c_void_p()
+        with torch.cuda.device(self.plans[0].device):
+            _lib.check(L.spgemm_dplan_graph_create(arr, len(self.plans), ctypes.byref(g)), "spgemm_dplan_graph_create")
+        self.handle = g.value
+
+    def launch(self) -> None:
+        _lib.check(self.L.spgemm_graph_launch(ctypes.c_void_p(self.handle)), "spgemm_graph_launch")
+
+    def __del__(self):
+        try:
+            if self.handle:
+                self.L.spgemm_graph_free(ctypes.c_void_p(self.handle))
+                self.handle = None
+        except Exception:
+            pass
+
+
+def galerkin_device(R: CSR, A: CSR, P: CSR, cap_ap: int, cap_ac: int, stream: torch.cuda.Stream, **opts):
+    """Ac = R*(A*P) as two DevicePlans chained on `stream` and one CUDA graph of both:
+    returns (plan_ap, plan_rap, graph); graph.launch() recomputes the chain from the current
+    contents of R, A and P, and plan_rap.result() is Ac."""
+    p1 = DevicePlan(A, P, cap_ap, stream=stream, **opts)
+    p2 = DevicePlan(R, p1.as_input(), cap_ac, stream=stream, **opts)
+    p2._keep = p1
+    return p1, p2, DeviceGraph([p1, p2])
+
+
 MERGE_METHODS = {"ranking": 0, "merge_path": 1, "bitonic": 2}
 
 

@@ -22,12 +22,18 @@ def test_memory_comparison_against_the_precise_method():
     c_bytes = 1000
     mem = bench.memory_comparison([(A, A)], c_bytes, "learned", {"peak_bytes": 5000},
                                   {"hybrid": {"peak_bytes": 9000}})
-    assert mem["precise"] == inputs + c_bytes
+    assert mem["inputs_plus_C"] == inputs + c_bytes and "precise" not in mem
     assert mem["learned"] == inputs + 5000 and mem["hybrid"] == inputs + 9000
     assert mem["ratio_to_precise"]["hybrid"] == (inputs + 9000) / (inputs + c_bytes)
+    # the measured precise policy, when it ran, is the denominator
+    mem1 = bench.memory_comparison([(A, A)], c_bytes, "learned", {"peak_bytes": 5000},
+                                   {"hybrid": {"peak_bytes": 9000}, "precise": {"peak_bytes": 1500}})
+    assert mem1["precise"] == inputs + 1500 and mem1["precise_source"].startswith("measured")
+    assert mem1["ratio_to_precise"]["hybrid"] == (inputs + 9000) / (inputs + 1500)
+    assert mem1["ratio_to_precise"]["inputs_plus_C"] == (inputs + c_bytes) / (inputs + 1500)
     B = gen.erdos_renyi(A.ncols, 3, seed=2, ncols=50)
     mem2 = bench.memory_comparison([(A, B)], c_bytes, "learned", {"peak_bytes": 0}, {})
-    assert mem2["precise"] == inputs + B.nnz * 12 + (B.nrows + 1) * 4 + c_bytes
+    assert mem2["inputs_plus_C"] == inputs + B.nnz * 12 + (B.nrows + 1) * 4 + c_bytes
 
 
 def test_algorithmic_bytes_model():

@@ -65,8 +65,9 @@ def test_make_opts_sets_every_field():
         handle = 777
     assert make_opts(alloc_policy="learned", predictor=_Pred()).predictor == 777
     assert make_opts(merge_kernel="merge_path").merge_kernel == 1
+    assert make_opts(alloc_policy="precise").alloc_policy == 3
     with pytest.raises(KeyError):
-        make_opts(alloc_policy="precise")
+        make_opts(alloc_policy="exact")
     with pytest.raises(KeyError):
         make_opts(long_rows="level2")
 
