@@ -449,7 +449,8 @@ int64_t spgemm_rowptr_scan_noalloc_max_rows(void);
  * min, max, mean and standard deviation of log2(1 + nnz(b_k*)) over the stored
  * a_ik, log2(1 + column span of the selected non-empty B rows), log2(1 + ncols(B)).
  * With SPGEMM_ALLOC_LEARNED, a bin-37 row gets a temporary row of
- * max(256, 32*ceil(margin * (2^reg - 1) / 32)) entries (at most u_i) and starts in
+ * s = max(256, 32*ceil(margin * (2^reg - 1) / 32)) entries -- or u_i entries when
+ * u_i <= margin * s, a bound it can never outgrow at little extra space -- and starts in
  * the shared-memory class that fits it; a row whose result outgrows that size
  * continues on the exact progressive path, so C does not depend on the prediction.
  */

@@ -265,7 +265,8 @@ __global__ void k_mlp_adam(float *__restrict__ params, const float *__restrict__
 }
 
 // Plan-side prediction for every row: predicted home size (>= min_cap, <= u_i)
-// from the regression head, times `margin`, rounded up to 32.
+// from the regression head, times `margin`, rounded up to 32; u_i itself when it is
+// within a factor `margin` of that size.
 __global__ void k_mlp_predict_caps(const float *__restrict__ params, const float *__restrict__ X, int64_t m,
                                    const int64_t *__restrict__ u, const int64_t *__restrict__ arp,
                                    const int64_t *__restrict__ S, int64_t u_min, const uint8_t *__restrict__ skip,
@@ -275,8 +276,10 @@ __global__ void k_mlp_predict_caps(const float *__restrict__ params, const float
     __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= m) return;
+    // the row's bound u_i (Algorithm 2), when known
+    const int64_t uu = S != nullptr ? S[arp[s + 1]] - S[arp[s]] : (u != nullptr ? u[s] : -1);
     // outside bin 37, or a dense-slice row: no prediction needed
-    if ((S != nullptr && S[arp[s + 1]] - S[arp[s]] <= u_min) || (skip != nullptr && skip[s])) {
+    if ((S != nullptr && uu <= u_min) || (skip != nullptr && skip[s])) {
         pred_cap[s] = 0;
         return;
     }
@@ -287,7 +290,12 @@ __global__ void k_mlp_predict_caps(const float *__restrict__ params, const float
     double c = ceil(nnz * (double)margin / 32.0) * 32.0;
     int64_t cap = (int64_t)c;
     if (cap < min_cap) cap = min_cap;
-    if (u != nullptr && cap > u[s]) cap = u[s];
+    if (uu >= 0) {
+        // a bound within a factor `margin` of the sized prediction is taken instead: the row
+        // can then never outgrow its slot, for at most `margin` times the prediction's space
+        if ((double)uu <= (double)cap * (double)margin) cap = uu;
+        if (cap > uu) cap = uu;
+    }
     if (cap > INT32_MAX) cap = INT32_MAX;
     pred_cap[s] = (int32_t)cap;
 }
