@@ -234,9 +234,53 @@ SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, 
     }
 }
 
+// ---- the column bitmap of a (row, slice) ----
+// Sets bit x - lo of Bm for every column x of the row's products in the slice.  The 32
+// lanes of an access read consecutive entries of one B row (ascending columns), so lanes
+// whose columns share a word are neighbours: an OR over each such run of lanes leaves one
+// shared atomic per word touched instead of one per product.  Ends with a barrier.
+
+SPG_DEV void bitmap_set_warp(uint32_t *Bm, int x, bool ok) {
+    const int lane = lane_id();
+    const int w = ok ? (x >> 5) : -1 - lane;  // invalid lanes form runs of their own
+    uint32_t bits = ok ? (1u << (x & 31)) : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t nb = __shfl_down_sync(SPG_FULL, bits, d);
+        const int nw = __shfl_down_sync(SPG_FULL, w, d);
+        if (lane + d < 32 && nw == w) bits |= nb;
+    }
+    const int pw = __shfl_up_sync(SPG_FULL, w, 1);
+    if (ok && (lane == 0 || pw != w)) atomicOr(&Bm[w], bits);
+}
+
+template <int NT>
+SPG_DEV bool dense_bitmap(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int row, int s, int64_t lo,
+                          int span, uint32_t *Bm, int64_t *wbs, int32_t *wlen, int64_t *cscan, int64_t *scan64) {
+    const int nq = (((span + 31) >> 5) + 3) >> 2;  // 16-byte groups of bitmap words
+    uint4 *b4 = reinterpret_cast<uint4 *>(Bm);
+    for (int q = threadIdx.x; q < nq; q += NT) b4[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    bool bad = false;
+    dense_expand<NT, NT, false>(A, B, D, row, s, wbs, wlen, cscan, nullptr, scan64,
+                            [&](const int64_t *p, const bool *ok, int) {
+        int32_t c[DENSE_UN];
+#pragma unroll
+        for (int u = 0; u < DENSE_UN; ++u)
+            if (ok[u]) c[u] = __ldg(B.col + p[u]);
+#pragma unroll
+        for (int u = 0; u < DENSE_UN; ++u) {
+            const int x = ok[u] ? (int)(c[u] - lo) : 0;
+            const bool in = ok[u] && (unsigned)x < (unsigned)span;
+            if (ok[u] && !in) bad = true;  // cannot happen: the slice boundaries select the columns
+            bitmap_set_warp(Bm, x, in);
+        }
+    });
+    return bad;
+}
+
 // ---- pass 1: the number of columns of every (row, slice) ----
-// Shared memory: one flag byte per column of the slice (a plain store of 1 per
-// product: every writer stores the same value, so no atomics are needed).
+// Shared memory: the slice's column bitmap (one bit per column), then its popcount.
 
 // The next (item, slice) of a CTA: blockIdx.x, then + gridDim.x (a grid that covers the
 // items takes one each), or, with a work counter, the counter's next ticket (a persistent
@@ -252,49 +296,29 @@ SPG_DEV int64_t dense_next(unsigned long long *counter, int64_t cur, bool first,
 
 SPG_DEV int64_t dense_items(const DenseArgs &D) { return (D.dev_n != nullptr ? *D.dev_n : D.n) * (int64_t)D.K; }
 
+// The columns of slice s that row d of the dense items can reach: [lo, lo + span).
+SPG_DEV int dense_span(const DevCSR &B, const DenseArgs &D, int64_t d, int s, int64_t &lo) {
+    lo = max((int64_t)s * D.W, (int64_t)D.clo[d]);
+    return (int)(min(min((int64_t)(s + 1) * D.W, B.ncols), (int64_t)D.chi[d]) - lo);
+}
+
 template <int NT>
 SPG_DEV void dense_count_item(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t b, int64_t *err) {
-    extern __shared__ __align__(16) uint8_t dc_flag[];
+    extern __shared__ __align__(16) uint32_t dc_bm[];
     __shared__ int64_t wbs[NT], cscan[NT], scan64[NT / 32 + 1];
     __shared__ int32_t wlen[NT], scan32[NT / 32 + 1];
     const int64_t d = b / D.K;
     const int s = (int)(b - d * D.K);
-    const int row = D.rows[d];
-    // the slice's columns that the row can reach: [lo, lo + span)
-    const int64_t lo = max((int64_t)s * D.W, (int64_t)D.clo[d]);
-    const int span = (int)(min(min((int64_t)(s + 1) * D.W, B.ncols), (int64_t)D.chi[d]) - lo);
+    int64_t lo;
+    const int span = dense_span(B, D, d, s, lo);
     if (span <= 0) {
         if (threadIdx.x == 0) D.cnt[b] = 0;
         return;
     }
-    const int nq = (span + 15) >> 4;  // 16-byte groups of flags
-    uint4 *f4 = reinterpret_cast<uint4 *>(dc_flag);
-    for (int q = threadIdx.x; q < nq; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
-    __syncthreads();
-    bool bad = false;
-    volatile uint8_t *fl = dc_flag;
-    dense_expand<NT, NT, false>(A, B, D, row, s, wbs, wlen, cscan, nullptr, scan64,
-                            [&](const int64_t *p, const bool *ok, int) {
-        int32_t c[DENSE_UN];
-#pragma unroll
-        for (int u = 0; u < DENSE_UN; ++u)
-            if (ok[u]) c[u] = __ldg(B.col + p[u]);
-#pragma unroll
-        for (int u = 0; u < DENSE_UN; ++u) {
-            if (!ok[u]) continue;
-            const int x = (int)(c[u] - lo);
-            if ((unsigned)x >= (unsigned)span) {  // cannot happen: the slice boundaries select the columns
-                bad = true;
-                continue;
-            }
-            fl[x] = 1;
-        }
-    });
+    const bool bad = dense_bitmap<NT>(A, B, D, D.rows[d], s, lo, span, dc_bm, wbs, wlen, cscan, scan64);
+    const int nw = (span + 31) >> 5;
     int n = 0;
-    for (int q = threadIdx.x; q < nq; q += NT) {
-        const uint4 v = f4[q];
-        n += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-    }
+    for (int w = threadIdx.x; w < nw; w += NT) n += __popc(dc_bm[w]);
     n = block_reduce_sum<NT, int>(n, scan32);
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch((unsigned long long *)err, 5ull);
     if (threadIdx.x == 0) D.cnt[b] = n;
@@ -329,58 +353,34 @@ __global__ void k_dense_rows(MergeItems it, DenseArgs D) {
 }
 
 // ---- pass 2: the values, written into C ----
-// Shared memory: W fp64 sums, W flag bytes, then the flags as a bitmap and its
-// rank directory for the write-out.
+// Shared memory: the slice's column bitmap Bm and its rank directory Rd (Rd[w] = set bits
+// in the words before w), then a compact buffer V of vcap sums.  A product's column x has
+// the position Rd[x >> 5] + popc(bits of its word below x) among the slice's columns, so
+// V holds one sum per column of the result, in column order: clearing and writing out
+// cost the slice's entries, not its width.  When a slice has more entries than V holds,
+// its word range is cut into pieces of at most vcap entries (the rank directory gives
+// the cuts) and the products are gone through once per piece.
 //
-// The columns of one B row are distinct, so while the whole CTA works on a single
-// B-row part no two threads add into the same sum and plain adds suffice; parts of
-// at least DENSE_LONG products are done that way, one after another (a barrier
-// between two parts), each product one fused multiply-add.  The shorter parts are
-// shared out to the warps in chunks and added with shared fp64 atomics, before the
-// long ones.  (A compare-and-swap loop around a fused multiply-add, one FP64
-// instruction per product instead of two, measured twice as slow as atomicAdd.)
+// The columns of one B row are distinct, so while the whole CTA works on a single B-row
+// part no two threads add into the same sum and plain adds suffice; parts of at least
+// DENSE_LONG products are done that way, one after another (a barrier between two
+// parts), each product one fused multiply-add.  The shorter parts are shared out to the
+// warps in chunks and added with shared fp64 atomics, before the long ones.
 constexpr int DENSE_FILL_WIN = 512;  // A entries per window
-constexpr int DENSE_LONG = 512;  // 256 and 1,024 measured slower
+constexpr int DENSE_LONG = 512;
 
 __host__ __device__ inline int dense_nw4(int W) { return ((W + 31) / 32 + 4) & ~3; }
 
-// REPLAY: values-only replay; C's columns are already in place, so the flags, the bitmap
-// and the column-order write-out give way to one pass over the slice's known entries.
-template <int NT, bool REPLAY>
-SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t b, const int64_t *c_rp,
-                             int32_t *c_col, val_t *c_val, int64_t *err) {
+// The product loop of a fill: every product of row `row` in slice s whose column offset x
+// lies in [x0, x1) is passed to add(x, a * b) (short parts, by the warps) or add_plain
+// (long parts, the whole CTA on one part).  Ends with a barrier.
+template <int NT, typename Fa, typename Fp>
+SPG_DEV bool dense_products(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int row, int s, int64_t lo,
+                            int x0, int x1, int64_t *wbs, int64_t *cscan, val_t *wa, int32_t *wlen, int32_t *lidx,
+                            int64_t *scan64, Fa add, Fp add_plain) {
     constexpr int WIN = DENSE_FILL_WIN;
     constexpr int NW = NT / 32;
-    extern __shared__ __align__(16) unsigned char df_smem[];
-    __shared__ int64_t wbs[WIN], cscan[WIN], scan64[NT / 32 + 1];
-    __shared__ val_t wa[WIN];
-    __shared__ int32_t wlen[WIN], lidx[WIN], scan32[NT / 32 + 1];
-    const int expected = D.cnt[b];
-    if (expected == 0) return;
-    const int64_t d = b / D.K;
-    const int s = (int)(b - d * D.K);
-    const int row = D.rows[d];
-    // the slice's columns that the row can reach (non-empty: the slice has columns of the row)
-    const int64_t lo = max((int64_t)s * D.W, (int64_t)D.clo[d]);
-    const int span = (int)(min(min((int64_t)(s + 1) * D.W, B.ncols), (int64_t)D.chi[d]) - lo);
-    const int nwords = (span + 31) >> 5;
-    const int nw4 = dense_nw4(D.W);
-    val_t *V = reinterpret_cast<val_t *>(df_smem);
-    uint8_t *flag = reinterpret_cast<uint8_t *>(V + D.W);
-    uint32_t *Bm = reinterpret_cast<uint32_t *>(flag + D.W);  // D.W is a multiple of 32
-    int32_t *Rd = reinterpret_cast<int32_t *>(Bm + nw4);
-    {
-        // V's first span sums, in whole 16-byte groups (W sums fill a multiple of 16 bytes)
-        uint4 *z4 = reinterpret_cast<uint4 *>(V);
-        const int nz = (int)((span * sizeof(val_t) + 15) / 16);
-        for (int q = threadIdx.x; q < nz; q += NT) z4[q] = make_uint4(0u, 0u, 0u, 0u);
-        uint4 *f4 = reinterpret_cast<uint4 *>(flag);  // whole 32-column words, as read below
-        if (!REPLAY)
-            for (int q = threadIdx.x; q < 2 * nwords; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
-    }
-    __syncthreads();
     bool bad = false;
-    volatile uint8_t *fl = flag;
     const int lane = lane_id(), wid = warp_id();
     const int64_t a0 = A.rp[row], a1 = A.rp[row + 1];
     const int K1 = D.K + 1;
@@ -415,7 +415,7 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
         const int64_t tc = ptot & ((int64_t(1) << 40) - 1);
         const int nlong = (int)(ptot >> 40);
         __syncthreads();
-        // short parts: the warps' contiguous chunk ranges, shared fp64 atomics
+        // short parts: the warps' contiguous chunk ranges
         {
             const int64_t c0 = tc * wid / NW, c1 = tc * (wid + 1) / NW;
             int t = 0;
@@ -433,7 +433,7 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
                 const int64_t off = (c - cscan[t]) * DENSE_CH;
                 const int64_t p0 = wbs[t] + off;
                 const int n = (int)min((int64_t)DENSE_CH, (int64_t)wlen[t] - off);
-                const val_t a = wa[t];
+                const val_t av = wa[t];
                 for (int i = lane; i < n; i += 32 * DENSE_UN) {
                     int32_t cc[DENSE_UN];
                     val_t v[DENSE_UN];
@@ -447,12 +447,8 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
                     for (int u = 0; u < DENSE_UN; ++u) {
                         if (i + 32 * u >= n) continue;
                         const int x = (int)(cc[u] - lo);
-                        if ((unsigned)x >= (unsigned)span) {  // cannot happen: the slice boundaries select the columns
-                            bad = true;
-                            continue;
-                        }
-                        atomicAdd(&V[x], a * v[u]);
-                        if (!REPLAY) fl[x] = 1;
+                        if (x < x0 || x >= x1) continue;
+                        if (!add(x, av * v[u])) bad = true;
                     }
                 }
             }
@@ -464,7 +460,6 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
         // barrier between two parts)
         if (nlong > 0) {
             constexpr int RND = NT * DENSE_UN;
-            // rounds r0 (being added), r1 and r2 (loading); part index nlong: no round
             int32_t c0[DENSE_UN], c1[DENSE_UN], c2[DENSE_UN];
             val_t v0[DENSE_UN], v1[DENSE_UN], v2[DENSE_UN];
             int j0 = 0, o0 = 0, j1, o1, j2, o2;
@@ -501,17 +496,13 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
                 {
                     const int t = lidx[j0];
                     const int n = wlen[t] - o0;
-                    const val_t a = wa[t];
+                    const val_t av = wa[t];
 #pragma unroll
                     for (int u = 0; u < DENSE_UN; ++u) {
                         if ((int)threadIdx.x + NT * u >= n) continue;
                         const int x = (int)(c0[u] - lo);
-                        if ((unsigned)x >= (unsigned)span) {
-                            bad = true;
-                            continue;
-                        }
-                        V[x] += a * v0[u];
-                        if (!REPLAY) fl[x] = 1;
+                        if (x < x0 || x >= x1) continue;
+                        if (!add_plain(x, av * v0[u])) bad = true;
                     }
                 }
                 if (j1 != j0) __syncthreads();  // the next part may add into the same columns
@@ -530,61 +521,120 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
         }
         __syncthreads();  // the window's tables are reused
     }
+    return bad;
+}
+
+// REPLAY: values-only replay; C's columns are already in place, so the bitmap is built
+// from the slice's known entries of C and only the values are written.
+template <int NT, bool REPLAY>
+SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t b, const int64_t *c_rp,
+                             int32_t *c_col, val_t *c_val, int64_t *err, int vcap) {
+    constexpr int WIN = DENSE_FILL_WIN;
+    extern __shared__ __align__(16) unsigned char df_smem[];
+    __shared__ int64_t wbs[WIN], cscan[WIN], scan64[NT / 32 + 1];
+    __shared__ val_t wa[WIN];
+    __shared__ int32_t wlen[WIN], lidx[WIN], scan32[NT / 32 + 1];
+    const int expected = D.cnt[b];
+    if (expected == 0) return;
+    const int64_t d = b / D.K;
+    const int s = (int)(b - d * D.K);
+    const int row = D.rows[d];
+    // the slice's columns that the row can reach (non-empty: the slice has columns of the row)
+    int64_t lo;
+    const int span = dense_span(B, D, d, s, lo);
+    const int nwords = (span + 31) >> 5;
+    const int nw4 = dense_nw4(D.W);
+    uint32_t *Bm = reinterpret_cast<uint32_t *>(df_smem);
+    int32_t *Rd = reinterpret_cast<int32_t *>(Bm + nw4);
+    val_t *V = reinterpret_cast<val_t *>(Rd + nw4);
+    const int64_t o = c_rp[row] + D.soff[b];  // the slice's first entry in C
+    bool bad = false;
+    // ---- the slice's columns: bitmap and rank directory ----
     if (REPLAY) {
-        // the slice's entries of C, in place since the product: their values
-        const int64_t o = c_rp[row] + D.soff[b];
-        for (int t = threadIdx.x; t < expected; t += NT) {
-            const int x = (int)(c_col[o + t] - lo);
-            if ((unsigned)x < (unsigned)span) c_val[o + t] = V[x];
-            else bad = true;  // C's columns were changed since the product
+        uint4 *b4 = reinterpret_cast<uint4 *>(Bm);
+        for (int q = threadIdx.x; q < (nwords + 3) >> 2; q += NT) b4[q] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        for (int t0 = 0; t0 < expected; t0 += NT) {  // whole warps: the bitmap update is warp-wide
+            const int t = t0 + (int)threadIdx.x;
+            const int x = t < expected ? (int)(c_col[o + t] - lo) : 0;
+            const bool in = t < expected && (unsigned)x < (unsigned)span;
+            if (t < expected && !in) bad = true;  // C's columns were changed since the product
+            bitmap_set_warp(Bm, x, in);
         }
-        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch((unsigned long long *)err, 6ull);
-        return;
+        __syncthreads();
+    } else {
+        bad = dense_bitmap<NT>(A, B, D, row, s, lo, span, Bm, wbs, wlen, cscan, scan64);
     }
-    // flags -> bitmap (32 columns per word), then its rank directory
-    for (int w = threadIdx.x; w < nwords; w += NT) {
-        const uint4 *f4 = reinterpret_cast<const uint4 *>(flag + 32 * w);
-        const uint4 lo4 = f4[0], hi4 = f4[1];
-        const uint32_t q[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
-        uint32_t m = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            // byte j of q[k] (0 or 1) is column 4k + j
-            const uint32_t y = q[k];
-            m |= ((y & 1u) | ((y >> 7) & 2u) | ((y >> 14) & 4u) | ((y >> 21) & 8u)) << (4 * k);
-        }
-        Bm[w] = m;
-    }
-    __syncthreads();
     const int tot = bitmap_rank<NT>(Bm, Rd, nwords, scan32);
     if (__syncthreads_or(bad || tot != expected)) {  // the counting pass saw other columns: cannot happen
         if (threadIdx.x == 0) atomicExch((unsigned long long *)err, 6ull);
         return;
     }
-    // column order: consecutive threads take consecutive columns, so a warp's stores
-    // land in one contiguous run of C
-    const int64_t o = c_rp[row] + D.soff[b];
-    for (int x = threadIdx.x; x < span; x += NT) {
-        const uint32_t wd = Bm[x >> 5];  // the same word for the whole warp
-        if (wd == 0u) continue;
-        if ((wd >> (x & 31)) & 1u) {
-            const int64_t pos = o + Rd[x >> 5] + __popc(wd & ((1u << (x & 31)) - 1u));
-            c_col[pos] = (int32_t)(lo + x);
-            c_val[pos] = V[x];
+    auto rank_at = [&](int w) { return w < nwords ? Rd[w] : tot; };
+    // ---- pieces of at most vcap entries, each summed in V and written out ----
+    for (int w0 = 0; w0 < nwords;) {
+        // the last word end w1 with rank_at(w1) - Rd[w0] <= vcap (a word holds <= 32 <= vcap entries)
+        const int e0 = Rd[w0];
+        int lo_ = w0 + 1, hi = nwords;
+        while (lo_ < hi) {
+            const int mid = (lo_ + hi + 1) >> 1;
+            if (rank_at(mid) - e0 <= vcap) lo_ = mid; else hi = mid - 1;
         }
+        const int w1 = lo_;
+        const int n = rank_at(w1) - e0;
+        const int x0 = w0 << 5, x1 = min(span, w1 << 5);
+        for (int k = threadIdx.x; k < n; k += NT) V[k] = val_t(0);
+        __syncthreads();
+        auto pos_of = [&](int x) {
+            const uint32_t wd = Bm[x >> 5];
+            return ((wd >> (x & 31)) & 1u) ? Rd[x >> 5] + __popc(wd & ((1u << (x & 31)) - 1u)) - e0 : -1;
+        };
+        bad = dense_products<NT>(
+            A, B, D, row, s, lo, x0, x1, wbs, cscan, wa, wlen, lidx, scan64,
+            [&](int x, val_t v) {
+                const int q = pos_of(x);
+                if (q < 0) return false;  // a column the bitmap does not hold: cannot happen
+                atomicAdd(&V[q], v);
+                return true;
+            },
+            [&](int x, val_t v) {
+                const int q = pos_of(x);
+                if (q < 0) return false;
+                V[q] += v;
+                return true;
+            });
+        if (__syncthreads_or(bad)) {
+            if (threadIdx.x == 0) atomicExch((unsigned long long *)err, 6ull);
+            return;
+        }
+        // write-out: the sums in column order (contiguous), and the columns word by word
+        for (int k = threadIdx.x; k < n; k += NT) c_val[o + e0 + k] = V[k];
+        if (!REPLAY) {
+            for (int w = w0 + (int)threadIdx.x; w < w1; w += NT) {
+                uint32_t bits = Bm[w];
+                int64_t q = o + Rd[w];
+                while (bits) {
+                    const int t = __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    c_col[q++] = (int32_t)(lo + ((int64_t)w << 5) + t);
+                }
+            }
+        }
+        __syncthreads();  // V is reused by the next piece
+        w0 = w1;
     }
 }
 
 template <int NT, int MINB, bool REPLAY>
 __global__ void __launch_bounds__(NT, MINB)
 k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_col, val_t *c_val, int64_t *err,
-             const int64_t *gate) {
+             const int64_t *gate, int vcap) {
     __shared__ int64_t s_b;
     if (gated(gate)) return;
     unsigned long long *q = D.dev_n != nullptr ? D.queue + 1 : nullptr;
     const int64_t nb = dense_items(D);
     for (int64_t b = dense_next(q, 0, true, &s_b); b < nb; b = dense_next(q, b, false, &s_b))
-        dense_fill_item<NT, REPLAY>(A, B, D, b, c_rp, c_col, c_val, err);
+        dense_fill_item<NT, REPLAY>(A, B, D, b, c_rp, c_col, c_val, err, vcap);
 }
 
 // One thread per dense item (precise method): the slices' offsets inside the row and the
@@ -602,10 +652,14 @@ __global__ void k_dense_rowsum(DenseArgs D, int32_t *nnzc) {
 }
 
 constexpr int DENSE_COUNT_NT = 256;
-constexpr int DENSE_FILL_NT = 512;  // 1,024-thread CTAs measured slower (the atomics' unit saturates)
+constexpr int DENSE_FILL_NT = 512;
+
+// Bytes of a fill CTA's bitmap and rank directory for slices of W columns.
+static int dense_index_bytes(int W) { return (int)(2 * sizeof(int32_t) * (size_t)dense_nw4(W)); }
 
 int dense_fill_smem_bytes(int W) {
-    return (int)((sizeof(val_t) + 1) * (size_t)W + 2 * sizeof(int32_t) * (size_t)dense_nw4(W));
+    // the index, and room for at least one word's entries in V
+    return dense_index_bytes(W) + 32 * (int)sizeof(val_t);
 }
 
 // Largest dynamic shared memory of a fill CTA when `per_sm` of them share an SM
@@ -624,7 +678,7 @@ cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
-    const int smem = D.W;  // flag bytes (a multiple of 32)
+    const int smem = (int)(sizeof(uint32_t) * dense_nw4(D.W));  // the slice's bitmap
     auto kern = k_dense_count<DENSE_COUNT_NT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -658,11 +712,11 @@ cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs 
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
-    const int smem = dense_fill_smem_bytes(D.W);
-    // two CTAs per SM when two slices fit the SM's shared memory (64 registers a thread)
-    const bool two = smem <= dense_fill_max_dynamic(2);
-    auto kern = replay ? (two ? k_dense_fill<DENSE_FILL_NT, 2, true> : k_dense_fill<DENSE_FILL_NT, 1, true>)
-                       : (two ? k_dense_fill<DENSE_FILL_NT, 2, false> : k_dense_fill<DENSE_FILL_NT, 1, false>);
+    // the index, then as many sums as the rest of one CTA's shared memory holds
+    const int smem = dense_fill_max_dynamic(1) & ~15;
+    const int vcap = (smem - dense_index_bytes(D.W)) / (int)sizeof(val_t);
+    if (vcap < 32) return cudaErrorInvalidValue;
+    auto kern = replay ? k_dense_fill<DENSE_FILL_NT, 1, true> : k_dense_fill<DENSE_FILL_NT, 1, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -675,7 +729,7 @@ cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs 
         grid = persistent_blocks((const void *)kern, DENSE_FILL_NT, smem, nb);
         if (grid <= 0) return cudaErrorInvalidValue;
     }
-    kern<<<(unsigned)grid, DENSE_FILL_NT, smem, st>>>(A, B, D, c_rp, c_col, c_val, err, gate);
+    kern<<<(unsigned)grid, DENSE_FILL_NT, smem, st>>>(A, B, D, c_rp, c_col, c_val, err, gate, vcap);
     return cudaGetLastError();
 }
 

@@ -190,6 +190,7 @@ cudaError_t launch_level1_sizes(const MergeItems &it, const int32_t *work, int64
 // ---- dense column slices for the longest bin-37 rows (dense.cu) ----
 constexpr int32_t ITEM_DENSE = -2;  // MergeItems.child of a row computed by the dense-slice kernels
 constexpr int DENSE_MAX_SLICES = 64;
+constexpr int DENSE_W_MAX = 131072;  // widest slice: its bitmap and rank directory take 32 KB
 struct DenseArgs {
     const int32_t *items;  // dense items (indices into MergeItems), larger rows first
     const int32_t *rows;   // their rows of A

@@ -326,10 +326,9 @@ static void merge_limits(spgemm_plan *p) {
     if (p->opts.smem_cap_max > 0) capmax = std::min(capmax, std::max(256, p->opts.smem_cap_max));
     p->batch = batch;
     p->capmax = capmax;
-    // dense column slices: by default the widest slice that fits shared memory (one fill
-    // CTA per SM; fill CTAs are bound by the SM's shared fp64 atomics, so two narrower
-    // ones per SM are no faster); dense_span narrows it, and slices narrow enough for two
-    // CTAs per SM run that way.  B's columns are cut into equal slices of a multiple of 32
+    // dense column slices: B's columns cut into equal slices of at most DENSE_W_MAX columns
+    // (a multiple of 32); a fill CTA holds the slice's bitmap and rank directory and a
+    // compact buffer of sums, one per column of the result; dense_span narrows the slices
     p->dense_K = 0;
     p->dense_W = 0;
     p->dense_min_u = 0;
@@ -337,16 +336,10 @@ static void merge_limits(spgemm_plan *p) {
                          p->opts.long_rows == SPGEMM_LONG_ROWS_SPLIT)) &&
         p->B.ncols > 0) {
         const int64_t n = p->B.ncols;
-        auto widest = [](int limit) {
-            int w = (int)(limit / (sizeof(val_t) + 1.25)) & ~31;
-            while (w > 32 && dense_fill_smem_bytes(w) > limit) w -= 32;
-            return w;
-        };
-        const int w1 = widest(std::min(smem_limit - dense_fill_static_smem(), dense_fill_max_dynamic(1)));
-        int wmax = w1;
-        if (p->opts.dense_span > 0) wmax = std::min(w1, std::max(1024, p->opts.dense_span & ~31));
+        int wmax = DENSE_W_MAX;
+        if (p->opts.dense_span > 0) wmax = std::min(wmax, std::max(1024, p->opts.dense_span & ~31));
         const int64_t k0 = (n + wmax - 1) / wmax;
-        if (wmax >= 32 && k0 <= DENSE_MAX_SLICES) {
+        if (k0 <= DENSE_MAX_SLICES && dense_fill_smem_bytes(wmax) <= dense_fill_max_dynamic(1)) {
             const int64_t w = ((n + k0 - 1) / k0 + 31) & ~int64_t(31);
             p->dense_W = (int)w;
             p->dense_K = (int)((n + w - 1) / w);
