@@ -107,36 +107,27 @@ cudaError_t launch_gate(int64_t *c_rp, int64_t m, int64_t cap, int64_t *gate, in
 }
 
 // One CTA per bin-37 row: its leaves (column slices) are visited in column order
-// by a depth-first walk of the split tree (left child first) and copied back to back.
+// (a walk of the split tree, left child first) and copied back to back.
 // Rows of the dense-slice kernels are already in C.
 __global__ void __launch_bounds__(ARR_NT)
 k_arrange_long(MergeItems it, const int64_t *__restrict__ c_rp, int32_t *__restrict__ c_col,
                val_t *__restrict__ c_val) {
-    constexpr int LEAF_BUF = 128, STACK = 64;
+    constexpr int LEAF_BUF = 128;
     __shared__ int leaves[LEAF_BUF];
-    __shared__ int stack[STACK];
-    __shared__ int sp, nleaves;
+    __shared__ int nleaves, cursor;
     const int j = blockIdx.x;
     if (it.child[j] == ITEM_DENSE) return;  // written into C by the dense-slice kernel
     int64_t o = c_rp[it.row[j]];
-    if (threadIdx.x == 0) {
-        sp = 0;
-        stack[sp++] = j;
-    }
+    if (threadIdx.x == 0) cursor = split_first_leaf(it, j);
     __syncthreads();
     while (true) {
         if (threadIdx.x == 0) {
-            int n = 0;
-            while (sp > 0 && n < LEAF_BUF) {
-                const int x = stack[--sp];
-                const int c = it.child[x];
-                if (c < 0) {
-                    leaves[n++] = x;
-                } else if (sp + 2 <= STACK) {
-                    stack[sp++] = c + 1;
-                    stack[sp++] = c;
-                }
+            int n = 0, x = cursor;
+            while (x >= 0 && n < LEAF_BUF) {
+                leaves[n++] = x;
+                x = split_next_leaf(it, j, x);
             }
+            cursor = x;
             nleaves = n;
         }
         __syncthreads();

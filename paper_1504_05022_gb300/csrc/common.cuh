@@ -30,6 +30,22 @@ SPG_DEV void rowset_range(const RowSet &R, const int32_t *&rows, int64_t &n) {
     }
 }
 
+// Walks of a row's split tree in column order (left child first), without a stack, so a
+// tree of any depth is walked: the first leaf under x, and the leaf after x under root
+// (-1 after the last).  Leaves are the items with child < 0.
+SPG_DEV int split_first_leaf(const MergeItems &it, int x) {
+    while (it.child[x] >= 0) x = it.child[x];
+    return x;
+}
+SPG_DEV int split_next_leaf(const MergeItems &it, int root, int x) {
+    while (x != root) {
+        const int p = it.parent[x];
+        if (x == it.child[p]) return split_first_leaf(it, x + 1);  // a left child: its right sibling
+        x = p;
+    }
+    return -1;
+}
+
 // True when a gate word is set: the launch must write nothing.
 SPG_DEV bool gated(const int64_t *gate) { return gate != nullptr && *gate != 0; }
 SPG_DEV int warp_id() { return threadIdx.x >> 5; }

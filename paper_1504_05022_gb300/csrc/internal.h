@@ -138,6 +138,7 @@ struct MergeItems {
     int64_t *ck_entry;   // checkpoint: A-entry index relative to the row start
     int64_t *ck_off;     //             and offset inside that entry's full B row
     int32_t *child;      // -1 for a leaf, else the left child (the right one is child + 1)
+    int32_t *parent;     // the item it was split from; -1 for a row's own item
 };
 
 struct MergeLaunch {

@@ -498,6 +498,7 @@ __global__ void k_merge_init(const int32_t *rows37, int64_t n37, const int64_t *
     it.ck_entry[j] = 0;
     it.ck_off[j] = 0;
     it.child[j] = -1;
+    it.parent[j] = -1;
 }
 
 cudaError_t launch_merge_init(const int32_t *rows37, int64_t n37, const int64_t *ctil_rp, int32_t *ctil_col,
@@ -530,6 +531,7 @@ __global__ void k_split(const int32_t *ovf, int64_t n, int64_t first_new, MergeI
         it.ck_entry[q] = it.ck_entry[p];
         it.ck_off[q] = it.ck_off[p];
         it.child[q] = -1;
+        it.parent[q] = p;
     }
     it.src_col[l] = it.src_col[p];
     it.src_val[l] = it.src_val[p];
@@ -572,25 +574,10 @@ cudaError_t launch_split(const int32_t *ovf, int64_t n, int64_t first_new, const
     return cudaGetLastError();
 }
 
-// Sum of the leaf lengths under item j (its column slices); -1 if the split
-// tree is deeper than the walk's stack (a split tree is at most ~31 deep).
+// Sum of the leaf lengths under item j (its column slices).
 SPG_DEV int64_t leaf_total(const MergeItems &it, int j) {
-    constexpr int STACK = 64;
-    int stack[STACK];
-    int sp = 0;
     int64_t tot = 0;
-    stack[sp++] = j;
-    while (sp > 0) {
-        const int x = stack[--sp];
-        const int c = it.child[x];
-        if (c < 0) {
-            tot += it.len[x];
-        } else {
-            if (sp + 2 > STACK) return -1;
-            stack[sp++] = c + 1;
-            stack[sp++] = c;
-        }
-    }
+    for (int x = split_first_leaf(it, j); x >= 0; x = split_next_leaf(it, j, x)) tot += it.len[x];
     return tot;
 }
 

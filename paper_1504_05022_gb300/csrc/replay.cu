@@ -284,24 +284,9 @@ __global__ void k_replay_leaves(int64_t n37, MergeItems it, const int64_t *c_rp,
                                 int32_t *order, int64_t *err) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n37) return;
-    constexpr int STACK = 64;
-    int stack[STACK];
-    int sp = 0;
     int64_t off = c_rp[it.row[j]];
-    stack[sp++] = (int)j;
-    while (sp > 0) {
-        const int x = stack[--sp];
-        const int c = it.child[x];
-        if (c == ITEM_DENSE) continue;  // replayed by the dense-slice kernel
-        if (c >= 0) {
-            if (sp + 2 > STACK) {
-                atomicExch((unsigned long long *)err, 2ull);
-                return;
-            }
-            stack[sp++] = c + 1;
-            stack[sp++] = c;
-            continue;
-        }
+    for (int x = split_first_leaf(it, (int)j); x >= 0; x = split_next_leaf(it, (int)j, x)) {
+        if (it.child[x] == ITEM_DENSE) continue;  // replayed by the dense-slice kernel
         const int len = it.len[x];
         int g = ncls - 1;
         for (int k = 0; k < ncls; ++k)

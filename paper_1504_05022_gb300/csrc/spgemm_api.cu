@@ -721,6 +721,7 @@ cudaError_t reserve_items(spgemm_plan *p, int64_t need) {
     if ((e = grow_array(p, &it.ck_entry, n, nc)) != cudaSuccess) return e;
     if ((e = grow_array(p, &it.ck_off, n, nc)) != cudaSuccess) return e;
     if ((e = grow_array(p, &it.child, n, nc)) != cudaSuccess) return e;
+    if ((e = grow_array(p, &it.parent, n, nc)) != cudaSuccess) return e;
     p->items_cap = nc;
     return cudaSuccess;
 }
