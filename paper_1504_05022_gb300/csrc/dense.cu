@@ -169,7 +169,8 @@ cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *
 // lanes read a chunk's entries 32 at a time (coalesced, one B row per access, so
 // the 32 columns of an access are distinct), DENSE_UN accesses in flight.
 // f(p, ok, t) gets DENSE_UN entry positions p[] of B, which of them are valid,
-// and the window slot t of their A entry.  Ends with a barrier.
+// and the window slot t of their A entry; every lane of a warp makes the same calls
+// (so f may use warp-wide intrinsics).  Ends with a barrier.
 constexpr int DENSE_CH = 256;
 constexpr int DENSE_UN = 4;
 
@@ -219,7 +220,9 @@ SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, 
             const int64_t off = (c - cscan[t]) * DENSE_CH;
             const int64_t p0 = wbs[t] + off;
             const int n = (int)min((int64_t)DENSE_CH, (int64_t)wlen[t] - off);
-            for (int i = lane; i < n; i += 32 * DENSE_UN) {
+            // the trip count is the same for every lane (f may be warp-collective)
+            for (int i0 = 0; i0 < n; i0 += 32 * DENSE_UN) {
+                const int i = i0 + lane;
                 int64_t p[DENSE_UN];
                 bool ok[DENSE_UN];
 #pragma unroll
