@@ -173,6 +173,9 @@ typedef struct spgemm_opts {
                                 not be freed before spgemm_symbolic (or spgemm_galerkin) has
                                 returned, since its weights are read by that call's kernels */
     double predictor_margin; /* predicted size is multiplied by this before rounding up */
+    int32_t dense_pred_min;  /* learned policy: a bin-37 row whose predicted nnz(c_i) is at least this
+                                is computed by the dense-slice kernels (the network's choice of
+                                kernel as well as of size); 0 = off */
 } spgemm_opts;
 
 /* Fills *opts with the defaults (hybrid policy, initial_cap 256, no checks). */

@@ -16,7 +16,12 @@ measured device time, over the parameters the library exposes for that choice:
 * merge_miss   - entries of the bitmap merge kernel's miss buffer (how often new
                  columns are merged into the result);
 * initial_cap  - the first bin-37 row size of the plain (hybrid) policy;
-* predictor_margin - the safety factor of the learned policy.
+* predictor_margin - the safety factor of the learned policy;
+* dense_min_u, dense_span_div - which bin-37 rows the dense column slices take;
+* dense_span   - the slices' width (and with it their form: one sum per column of a
+                 narrow slice, or a bitmap with compact sums for a wide one);
+* dense_pred_min - the learned policy's choice of kernel: rows predicted at least this
+                 long go to the dense column slices.
 
 A configuration is kept only if it is faster and its peak device memory stays
 within 5% of the default configuration's, so tuning never buys time with memory.
@@ -55,15 +60,17 @@ SPACE = {
     "merge_miss": [4096, 2048, 8192],
     "initial_cap": [256, 512, 1024],
     "predictor_margin": [None, 1.15, 1.5, 2.0],  # None = the margin stored with the weights
-    "dense_min_u": [0, 16384, 4096, -1],  # 0 = ncols(B) / 8, -1 = no dense-slice rows
-    "dense_span": [0, 16384, 10912],      # 0 = the widest slice shared memory holds
-    "dense_span_div": [0, 16, 4],         # 0 = 8: dense when 8 u_i >= the row's column range
+    "dense_min_u": [0, 16384, 4096, -1],  # 0 = the rule of dense_span_div, -1 = no dense-slice rows
+    "dense_span": [0, 21856, 16384, 10912],  # 0 = 131,072-column slices (bitmap, compact sums); narrow
+                                             # enough for a sum per column: the single-pass form
+    "dense_span_div": [0, 16, 4, 64],     # 0 = 8: dense when 8 u_i >= the row's column range
+    "dense_pred_min": [0, 12288, 6144, 3072],  # learned: predicted nnz(c_i) that sends a row to the slices
 }
 POLICY_PARAMS = {
     "hybrid": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "merge_miss",
                "initial_cap", "dense_min_u", "dense_span", "dense_span_div"],
     "learned": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "merge_miss",
-                "predictor_margin", "dense_min_u", "dense_span", "dense_span_div"],
+                "predictor_margin", "dense_min_u", "dense_span", "dense_span_div", "dense_pred_min"],
     "upper_bound": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "dense_min_u",
                     "dense_span", "dense_span_div"],
 }

@@ -1,22 +1,23 @@
 // Stage 3, bin group 5, for the rows whose products cover a large part of B's
-// column range (u_i >= a threshold of the order of ncols(B)): a dense
-// accumulator over column slices instead of the merge of Section 4.1.
+// column range (and, in the precise method, for every bin-37 row): an accumulator
+// over column slices instead of the merge of Section 4.1.
 //
-// B's columns are cut into K slices of W columns (W a multiple of 32, K W >=
-// ncols).  A slice of a row is one CTA.  Its shared memory holds W fp64 sums and
-// W flag bytes; every product of the row whose column falls in the slice adds
-// into its column's sum (a shared fp64 atomic) and stores 1 into its column's
-// flag.  There are no misses, no merges and no capacity to outgrow: the cost is
-// the products plus O(W) to clear the slice and to write it out in column order.
-// The part of each B row that falls in slice s is read from a table of per-row
-// slice boundaries, built once per call, and is cut into chunks of consecutive
-// entries that the warps share out.
+// B's columns are cut into K slices of W columns (W a multiple of 32, at most
+// DENSE_W_MAX, K W >= ncols).  A slice of a row is one CTA.  The counting pass marks
+// the columns of the row's products in the slice in a shared bitmap and counts its
+// bits.  The fill pass marks them again, ranks the bitmap (set bits before each word),
+// and adds every product into a compact buffer of sums, one per column of the result,
+// at its column's rank: clearing and writing out cost the slice's entries, not its
+// width, and the sums come out in column order.  There are no misses, no merges and no
+// capacity to outgrow (a slice with more entries than the buffer is done in pieces).
+// The part of each B row that falls in slice s is read from a table of per-row slice
+// boundaries, built once per call, and is cut into chunks of consecutive entries that
+// the warps share out.
 //
-// The rows' sizes are counted first (the same expansion with only the flags), so
-// the dense rows need no temporary space at all: their sizes go into the row
-// counts of C with the other rows', and the values are written straight into C
-// once its row pointers exist.  The same launch recomputes the values for a
-// values-only replay.
+// Because the rows are counted first, they need no temporary space at all: their sizes
+// go into the row counts of C with the other rows', and the values are written
+// straight into C once its row pointers exist.  The same launch recomputes the values
+// for a values-only replay.
 #include "internal.h"
 #include "common.cuh"
 
@@ -529,7 +530,12 @@ SPG_DEV bool dense_products(const DevCSR &A, const DevCSR &B, const DenseArgs &D
 
 // REPLAY: values-only replay; C's columns are already in place, so the bitmap is built
 // from the slice's known entries of C and only the values are written.
-template <int NT, bool REPLAY>
+// WIDE: the single-pass form for slices narrow enough to hold one sum per column of the
+// slice (W sums, W flag bytes, then the flags as a bitmap with its rank directory for the
+// write-out): every product adds into its column's sum and marks its flag in one pass,
+// and the write-out walks the slice's columns.  It reads the products once instead of
+// twice, which pays where slices are dense (products well above their width).
+template <int NT, bool REPLAY, bool WIDE>
 SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t b, const int64_t *c_rp,
                              int32_t *c_col, val_t *c_val, int64_t *err, int vcap) {
     constexpr int WIN = DENSE_FILL_WIN;
@@ -547,11 +553,82 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
     const int span = dense_span(B, D, d, s, lo);
     const int nwords = (span + 31) >> 5;
     const int nw4 = dense_nw4(D.W);
+    const int64_t o = c_rp[row] + D.soff[b];  // the slice's first entry in C
+    bool bad = false;
+    if constexpr (WIDE) {
+        val_t *V = reinterpret_cast<val_t *>(df_smem);
+        uint8_t *flag = reinterpret_cast<uint8_t *>(V + D.W);
+        uint32_t *Bm = reinterpret_cast<uint32_t *>(flag + D.W);  // D.W is a multiple of 32
+        int32_t *Rd = reinterpret_cast<int32_t *>(Bm + nw4);
+        {
+            // V's first span sums, in whole 16-byte groups (W sums fill a multiple of 16 bytes)
+            uint4 *z4 = reinterpret_cast<uint4 *>(V);
+            const int nz = (int)((span * sizeof(val_t) + 15) / 16);
+            for (int q = threadIdx.x; q < nz; q += NT) z4[q] = make_uint4(0u, 0u, 0u, 0u);
+            uint4 *f4 = reinterpret_cast<uint4 *>(flag);  // whole 32-column words, as read below
+            if (!REPLAY)
+                for (int q = threadIdx.x; q < 2 * nwords; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        volatile uint8_t *fl = flag;
+        bad = dense_products<NT>(
+            A, B, D, row, s, lo, 0, span, wbs, cscan, wa, wlen, lidx, scan64,
+            [&](int x, val_t v) {
+                atomicAdd(&V[x], v);
+                if (!REPLAY) fl[x] = 1;
+                return true;
+            },
+            [&](int x, val_t v) {
+                V[x] += v;
+                if (!REPLAY) fl[x] = 1;
+                return true;
+            });
+        if (REPLAY) {
+            // the slice's entries of C, in place since the product: their values
+            for (int t = threadIdx.x; t < expected; t += NT) {
+                const int x = (int)(c_col[o + t] - lo);
+                if ((unsigned)x < (unsigned)span) c_val[o + t] = V[x];
+                else bad = true;  // C's columns were changed since the product
+            }
+            if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch((unsigned long long *)err, 6ull);
+            return;
+        }
+        // flags -> bitmap (32 columns per word), then its rank directory
+        for (int w = threadIdx.x; w < nwords; w += NT) {
+            const uint4 *f4 = reinterpret_cast<const uint4 *>(flag + 32 * w);
+            const uint4 lo4 = f4[0], hi4 = f4[1];
+            const uint32_t q[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+            uint32_t m = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                // byte j of q[k] (0 or 1) is column 4k + j
+                const uint32_t y = q[k];
+                m |= ((y & 1u) | ((y >> 7) & 2u) | ((y >> 14) & 4u) | ((y >> 21) & 8u)) << (4 * k);
+            }
+            Bm[w] = m;
+        }
+        __syncthreads();
+        const int tot = bitmap_rank<NT>(Bm, Rd, nwords, scan32);
+        if (__syncthreads_or(bad || tot != expected)) {  // the counting pass saw other columns: cannot happen
+            if (threadIdx.x == 0) atomicExch((unsigned long long *)err, 6ull);
+            return;
+        }
+        // column order: consecutive threads take consecutive columns, so a warp's stores
+        // land in one contiguous run of C
+        for (int x = threadIdx.x; x < span; x += NT) {
+            const uint32_t wd = Bm[x >> 5];  // the same word for the whole warp
+            if (wd == 0u) continue;
+            if ((wd >> (x & 31)) & 1u) {
+                const int64_t pos = o + Rd[x >> 5] + __popc(wd & ((1u << (x & 31)) - 1u));
+                c_col[pos] = (int32_t)(lo + x);
+                c_val[pos] = V[x];
+            }
+        }
+        return;
+    }
     uint32_t *Bm = reinterpret_cast<uint32_t *>(df_smem);
     int32_t *Rd = reinterpret_cast<int32_t *>(Bm + nw4);
     val_t *V = reinterpret_cast<val_t *>(Rd + nw4);
-    const int64_t o = c_rp[row] + D.soff[b];  // the slice's first entry in C
-    bool bad = false;
     // ---- the slice's columns: bitmap and rank directory ----
     if (REPLAY) {
         uint4 *b4 = reinterpret_cast<uint4 *>(Bm);
@@ -628,7 +705,7 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
     }
 }
 
-template <int NT, int MINB, bool REPLAY>
+template <int NT, int MINB, bool REPLAY, bool WIDE>
 __global__ void __launch_bounds__(NT, MINB)
 k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_col, val_t *c_val, int64_t *err,
              const int64_t *gate, int vcap) {
@@ -637,7 +714,7 @@ k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_co
     unsigned long long *q = D.dev_n != nullptr ? D.queue + 1 : nullptr;
     const int64_t nb = dense_items(D);
     for (int64_t b = dense_next(q, 0, true, &s_b); b < nb; b = dense_next(q, b, false, &s_b))
-        dense_fill_item<NT, REPLAY>(A, B, D, b, c_rp, c_col, c_val, err, vcap);
+        dense_fill_item<NT, REPLAY, WIDE>(A, B, D, b, c_rp, c_col, c_val, err, vcap);
 }
 
 // One thread per dense item (precise method): the slices' offsets inside the row and the
@@ -664,6 +741,9 @@ int dense_fill_smem_bytes(int W) {
     // the index, and room for at least one word's entries in V
     return dense_index_bytes(W) + 32 * (int)sizeof(val_t);
 }
+
+// The single-pass form: one sum and one flag byte per column of the slice, and the index.
+int dense_fill_wide_bytes(int W) { return (int)((sizeof(val_t) + 1) * (size_t)W) + dense_index_bytes(W); }
 
 // Largest dynamic shared memory of a fill CTA when `per_sm` of them share an SM
 // (228 KB per SM, 1 KB of it reserved per CTA, at most 227 KB per CTA).
@@ -715,11 +795,14 @@ cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs 
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
+    // slices narrow enough for one sum per column take the single-pass form; the others hold
     // the index, then as many sums as the rest of one CTA's shared memory holds
-    const int smem = dense_fill_max_dynamic(1) & ~15;
+    const bool wide = dense_fill_wide_bytes(D.W) <= dense_fill_max_dynamic(1);
+    const int smem = wide ? dense_fill_wide_bytes(D.W) : dense_fill_max_dynamic(1) & ~15;
     const int vcap = (smem - dense_index_bytes(D.W)) / (int)sizeof(val_t);
     if (vcap < 32) return cudaErrorInvalidValue;
-    auto kern = replay ? k_dense_fill<DENSE_FILL_NT, 1, true> : k_dense_fill<DENSE_FILL_NT, 1, false>;
+    auto kern = wide ? (replay ? k_dense_fill<DENSE_FILL_NT, 1, true, true> : k_dense_fill<DENSE_FILL_NT, 1, false, true>)
+                     : (replay ? k_dense_fill<DENSE_FILL_NT, 1, true, false> : k_dense_fill<DENSE_FILL_NT, 1, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

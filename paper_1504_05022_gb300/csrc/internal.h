@@ -88,10 +88,13 @@ cudaError_t launch_binning(int64_t m, const int64_t *arp, const int64_t *S,
 // skipped, and so are the rows flagged in `skip` (when given).
 cudaError_t launch_row_features(const DevCSR &A, const DevCSR &B, float *X, cudaStream_t st,
                                 const int64_t *S = nullptr, int64_t u_min = 0, const uint8_t *skip = nullptr);
-// Predicted temporary size per row (0 for rows skipped through arp/S/u_min/skip).
+// Predicted temporary size per row (0 for rows skipped through arp/S/u_min/skip).  With
+// promote_min > 0, a row whose predicted nnz(c_i) is at least promote_min is flagged in
+// skip (a dense-slice row) instead.
 cudaError_t launch_predict_caps(const float *params, const float *X, int64_t m, const int64_t *u, float margin,
                                 int32_t min_cap, int32_t *pred_cap, cudaStream_t st, const int64_t *arp = nullptr,
-                                const int64_t *S = nullptr, int64_t u_min = 0, const uint8_t *skip = nullptr);
+                                const int64_t *S = nullptr, int64_t u_min = 0, uint8_t *skip = nullptr,
+                                int64_t promote_min = 0);
 // Groups the bin-37 items (tail of bin_rows, size read from summary) by launch
 // class; items of flagged (dense-slice) rows go after the last class; scratch: 96 + m
 // int32; order: item indices grouped by class; counts go to summary->class_count.
@@ -231,6 +234,7 @@ cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs 
                               int32_t *c_col, val_t *c_val, int64_t *err, cudaStream_t st, bool replay = false,
                               const int64_t *gate = nullptr);
 int dense_fill_smem_bytes(int W);
+int dense_fill_wide_bytes(int W);  // the single-pass form (fits for narrow slices only)
 int dense_fill_static_smem();
 int dense_fill_max_dynamic(int per_sm);
 

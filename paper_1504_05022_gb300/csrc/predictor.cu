@@ -269,8 +269,9 @@ __global__ void k_mlp_adam(float *__restrict__ params, const float *__restrict__
 // within a factor `margin` of that size.
 __global__ void k_mlp_predict_caps(const float *__restrict__ params, const float *__restrict__ X, int64_t m,
                                    const int64_t *__restrict__ u, const int64_t *__restrict__ arp,
-                                   const int64_t *__restrict__ S, int64_t u_min, const uint8_t *__restrict__ skip,
-                                   float margin, int32_t min_cap, int32_t *__restrict__ pred_cap) {
+                                   const int64_t *__restrict__ S, int64_t u_min, uint8_t *__restrict__ skip,
+                                   float margin, int32_t min_cap, int32_t *__restrict__ pred_cap,
+                                   int64_t promote_min) {
     __shared__ float P[SPGEMM_MLP_NUM_TOTAL];
     for (int t = threadIdx.x; t < SPGEMM_MLP_NUM_TOTAL; t += blockDim.x) P[t] = params[t];
     __syncthreads();
@@ -287,6 +288,12 @@ __global__ void k_mlp_predict_caps(const float *__restrict__ params, const float
     mlp_forward_one(P, X + s * MLP_IN, xh, h1, h2, o);
     float reg = fminf(fmaxf(o[MLP_CLS], 0.f), 30.f);
     double nnz = exp2((double)reg) - 1.0;
+    if (promote_min > 0 && skip != nullptr && nnz >= (double)promote_min) {
+        // the network's choice of kernel: a row this long goes to the dense-slice kernels
+        skip[s] = 1;
+        pred_cap[s] = 0;
+        return;
+    }
     double c = ceil(nnz * (double)margin / 32.0) * 32.0;
     int64_t cap = (int64_t)c;
     if (cap < min_cap) cap = min_cap;
@@ -302,10 +309,10 @@ __global__ void k_mlp_predict_caps(const float *__restrict__ params, const float
 
 cudaError_t launch_predict_caps(const float *params, const float *X, int64_t m, const int64_t *u, float margin,
                                 int32_t min_cap, int32_t *pred_cap, cudaStream_t st, const int64_t *arp,
-                                const int64_t *S, int64_t u_min, const uint8_t *skip) {
+                                const int64_t *S, int64_t u_min, uint8_t *skip, int64_t promote_min) {
     if (m <= 0) return cudaSuccess;
     k_mlp_predict_caps<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(params, X, m, u, arp, S, u_min, skip, margin,
-                                                                     min_cap, pred_cap);
+                                                                     min_cap, pred_cap, promote_min);
     return cudaGetLastError();
 }
 

@@ -557,7 +557,7 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             SPG_TRY(launch_predict_caps(predictor_params(o.predictor), X, m, nullptr,
                                         (float)(o.predictor_margin > 0 ? o.predictor_margin : 1.0),
                                         o.initial_cap, p->pred_cap, p->st, p->A.rp, p->S, BIN_MERGE_MIN_U,
-                                        p->dense_flag));
+                                        p->dense_flag, p->dense_K > 0 ? (int64_t)o.dense_pred_min : 0));
             p->time_end();
             p->count(SPGEMM_K_OTHER, 2);
         }

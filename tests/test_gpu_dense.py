@@ -198,3 +198,47 @@ def test_dense_off_for_merge_path_and_level1(spg, oracle_mod):
         plan, C, _ = _run(spg, A, A, **kw)
         assert plan.stats()["rows_dense"] == 0, kw
         _check(oracle_mod, A, A, C, label=str(kw))
+
+
+@pytest.mark.parametrize("policy", ["hybrid", "precise"])
+@pytest.mark.parametrize("span", [0, 16384])
+def test_dense_compact_form_and_replay(spg, oracle_mod, policy, span):
+    """Slices too wide for one sum per column (R-MAT 2^15 x 16: one slice of 32,768 columns, or
+    two of 16,384 in the single-pass form): the bitmap, rank directory and compact sums; then a
+    values-only replay of the same plan."""
+    A = gen.rmat(15, 16, seed=64)
+    Ad = spg.CSR.from_host(A)
+    plan = spg.Plan(Ad, Ad, alloc_policy=policy, dense_span=span)
+    C = plan.numeric()
+    torch.cuda.synchronize()
+    _check(oracle_mod, A, A, C, label=f"compact {policy}/{span}")
+    st = plan.stats()
+    assert st["rows_dense"] > 0 and st["dense_slices"] == (1 if span == 0 else 2)
+    rng = np.random.default_rng(65)
+    A2 = gen.HostCSR(A.nrows, A.ncols, A.row_ptr, A.col, rng.uniform(-1, 1, A.nnz))
+    Ad.val.copy_(torch.from_numpy(A2.val))
+    plan.replay()
+    torch.cuda.synchronize()
+    plan.check()
+    _check(oracle_mod, A2, A2, C, label=f"compact replay {policy}/{span}")
+
+
+def test_learned_kernel_choice_sends_long_rows_to_the_slices(spg, oracle_mod):
+    """With dense_pred_min, the rows the network predicts to be long are computed by the
+    dense-slice kernels instead of the merge kernel; C is unchanged."""
+    from paper_1504_05022_gb300.predictor import Predictor
+    A = gen.rmat(14, 8, seed=66)
+    Ad = spg.CSR.from_host(A)
+    pred = Predictor.load()
+    base = spg.Plan(Ad, Ad, **pred.opts())
+    C0 = base.numeric()
+    torch.cuda.synchronize()
+    st0 = base.stats()
+    plan = spg.Plan(Ad, Ad, dense_pred_min=1024, **pred.opts())
+    C = plan.numeric()
+    torch.cuda.synchronize()
+    _check(oracle_mod, A, A, C, label="learned kernel choice")
+    st = plan.stats()
+    assert st["rows_dense"] > st0["rows_dense"]
+    assert st["item_rounds"] < st0["item_rounds"]
+    plan.check()

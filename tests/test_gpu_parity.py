@@ -231,7 +231,7 @@ def test_config2_rmat16_full(spg, oracle_mod, dense):
     check(oracle_mod, A, A, C, label=f"cfg2 dense={dense}")
     st = plan.stats()
     if dense:
-        assert st["rows_dense"] > 0 and st["dense_slices"] >= 3 and st["merge_rounds"] >= 1
+        assert st["rows_dense"] > 0 and st["dense_slices"] >= 1 and st["merge_rounds"] >= 1
     else:
         assert st["merge_rounds"] >= 3 and st["rows_split"] > 0 and st["rows_dense"] == 0
     assert all(st["bin_count"][b] > 0 for b in (0, 1, 2, 33, 34, 35, 36, 37))
