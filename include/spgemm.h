@@ -105,8 +105,8 @@ typedef enum spgemm_alloc_policy {
        longer rows -- then C is allocated exactly and every row is computed straight into it
        (heap / bitonic ESC for u_i <= 512, the dense column slices for the rest): no temporary
        matrix C~ and no relaunch, at the price of a second pass over the products.  B's columns
-       must fit 64 shared-memory slices (about 1.4 million columns in double, twice as many in
-       float); a wider B returns SPGEMM_ERR_SHAPE. */
+       must fit 64 slices of 131,072 columns (8,388,608 columns); a wider B returns
+       SPGEMM_ERR_SHAPE. */
     SPGEMM_ALLOC_PRECISE = 3
 } spgemm_alloc_policy;
 

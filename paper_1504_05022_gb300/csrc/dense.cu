@@ -248,6 +248,12 @@ SPG_DEV void bitmap_set_warp(uint32_t *Bm, int x, bool ok) {
     const int lane = lane_id();
     const int w = ok ? (x >> 5) : -1 - lane;  // invalid lanes form runs of their own
     uint32_t bits = ok ? (1u << (x & 31)) : 0u;
+    // sparse columns (no two neighbours in one word): one atomic per lane, no combining
+    const bool shared_word = lane > 0 && __shfl_up_sync(SPG_FULL, w, 1) == w;
+    if (!__any_sync(SPG_FULL, shared_word)) {
+        if (ok) atomicOr(&Bm[w], bits);
+        return;
+    }
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const uint32_t nb = __shfl_down_sync(SPG_FULL, bits, d);
@@ -797,12 +803,15 @@ cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs 
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
     // slices narrow enough for one sum per column take the single-pass form; the others hold
     // the index, then as many sums as the rest of one CTA's shared memory holds
+    // (two CTAs per SM when two single-pass slices fit an SM's shared memory)
     const bool wide = dense_fill_wide_bytes(D.W) <= dense_fill_max_dynamic(1);
+    const bool two = wide && dense_fill_wide_bytes(D.W) <= dense_fill_max_dynamic(2);
     const int smem = wide ? dense_fill_wide_bytes(D.W) : dense_fill_max_dynamic(1) & ~15;
     const int vcap = (smem - dense_index_bytes(D.W)) / (int)sizeof(val_t);
     if (vcap < 32) return cudaErrorInvalidValue;
-    auto kern = wide ? (replay ? k_dense_fill<DENSE_FILL_NT, 1, true, true> : k_dense_fill<DENSE_FILL_NT, 1, false, true>)
-                     : (replay ? k_dense_fill<DENSE_FILL_NT, 1, true, false> : k_dense_fill<DENSE_FILL_NT, 1, false, false>);
+    auto kern = !wide ? (replay ? k_dense_fill<DENSE_FILL_NT, 1, true, false> : k_dense_fill<DENSE_FILL_NT, 1, false, false>)
+                : two ? (replay ? k_dense_fill<DENSE_FILL_NT, 2, true, true> : k_dense_fill<DENSE_FILL_NT, 2, false, true>)
+                      : (replay ? k_dense_fill<DENSE_FILL_NT, 1, true, true> : k_dense_fill<DENSE_FILL_NT, 1, false, true>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

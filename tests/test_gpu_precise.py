@@ -113,7 +113,7 @@ def test_precise_replay(spg, oracle_mod):
 
 def test_precise_rejects_too_wide_b(spg):
     A = gen.erdos_renyi(64, 4, seed=39, ncols=64)
-    B = gen.erdos_renyi(64, 4, seed=40, ncols=3_000_000)
+    B = gen.erdos_renyi(64, 4, seed=40, ncols=9_000_000)  # beyond 64 slices of 131,072 columns
     with pytest.raises(spg.SpgemmError, match="SHAPE"):
         spg.Plan(spg.CSR.from_host(A), spg.CSR.from_host(B), alloc_policy="precise")
 
