@@ -584,30 +584,35 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             p->time_end();
             p->count(SPGEMM_K_BIN, nblk > 0 ? 3 : 1);
         }
-        if (o.alloc_policy == SPGEMM_ALLOC_LEARNED) {
-            // group the bin-37 rows by the shared-memory class their predicted size needs
-            int32_t *ccap = nullptr, *scratch = nullptr;
-            SPG_TRY(p->alloc_n(&ccap, NUM_LAUNCH_CLASSES));
-            SPG_TRY(cudaMemcpyAsync(ccap, p->class_caps, sizeof(p->class_caps), cudaMemcpyHostToDevice, p->st));
-            SPG_TRY(p->alloc_n(&scratch, 96 + m, LIFE_SYMBOLIC));
-            SPG_TRY(p->alloc_n(&p->class_order, m, LIFE_NUMERIC));
-            SPG_TRY(launch_class_partition_tail(p->bin_rows, m, p->d_summary, p->pred_cap, ccap,
-                                                NUM_LAUNCH_CLASSES, p->dense_flag, scratch, p->class_order, p->st));
-            p->count(SPGEMM_K_OTHER, 3);
-        }
-        if (p->dense_K > 0) {
-            // the bin-37 rows for the dense-slice kernels, larger first, then the others
-            int32_t *scratch = nullptr;
-            SPG_TRY(p->alloc_n(&scratch, dense_select_scratch(m), LIFE_SYMBOLIC));
-            SPG_TRY(p->alloc_n(&p->dense_order, m));
-            SPG_TRY(p->alloc_n(&p->dense_rows, m));
-            SPG_TRY(p->alloc_n(&p->dense_clo, m));
-            SPG_TRY(p->alloc_n(&p->dense_chi, m));
-            SPG_TRY(launch_dense_select(p->bin_rows, m, p->d_summary, p->u, p->dense_flag, p->dense_lo, p->dense_hi,
-                                        scratch, p->dense_order, p->dense_rows, p->dense_clo, p->dense_chi, p->st));
-            p->count(SPGEMM_K_OTHER, 3);
-        }
+        // the bin sizes first: without bin-37 rows the learned launch classes and the slice
+        // selection have nothing to do, and their launches are skipped
         SPG_TRY(p->d2h(&p->h_summary, p->d_summary, sizeof(BinSummary)));
+        if (p->h_summary.bin_count[BIN_MERGE] > 0 && (o.alloc_policy == SPGEMM_ALLOC_LEARNED || p->dense_K > 0)) {
+            if (o.alloc_policy == SPGEMM_ALLOC_LEARNED) {
+                // group the bin-37 rows by the shared-memory class their predicted size needs
+                int32_t *ccap = nullptr, *scratch = nullptr;
+                SPG_TRY(p->alloc_n(&ccap, NUM_LAUNCH_CLASSES));
+                SPG_TRY(cudaMemcpyAsync(ccap, p->class_caps, sizeof(p->class_caps), cudaMemcpyHostToDevice, p->st));
+                SPG_TRY(p->alloc_n(&scratch, 96 + m, LIFE_SYMBOLIC));
+                SPG_TRY(p->alloc_n(&p->class_order, m, LIFE_NUMERIC));
+                SPG_TRY(launch_class_partition_tail(p->bin_rows, m, p->d_summary, p->pred_cap, ccap,
+                                                    NUM_LAUNCH_CLASSES, p->dense_flag, scratch, p->class_order, p->st));
+                p->count(SPGEMM_K_OTHER, 3);
+            }
+            if (p->dense_K > 0) {
+                // the bin-37 rows for the dense-slice kernels, larger first, then the others
+                int32_t *scratch = nullptr;
+                SPG_TRY(p->alloc_n(&scratch, dense_select_scratch(m), LIFE_SYMBOLIC));
+                SPG_TRY(p->alloc_n(&p->dense_order, m));
+                SPG_TRY(p->alloc_n(&p->dense_rows, m));
+                SPG_TRY(p->alloc_n(&p->dense_clo, m));
+                SPG_TRY(p->alloc_n(&p->dense_chi, m));
+                SPG_TRY(launch_dense_select(p->bin_rows, m, p->d_summary, p->u, p->dense_flag, p->dense_lo, p->dense_hi,
+                                            scratch, p->dense_order, p->dense_rows, p->dense_clo, p->dense_chi, p->st));
+                p->count(SPGEMM_K_OTHER, 3);
+            }
+            SPG_TRY(p->d2h(&p->h_summary, p->d_summary, sizeof(BinSummary)));  // class and slice counts
+        }
         p->bin_start[0] = 0;
         for (int b = 0; b < NUM_BINS; ++b) p->bin_start[b + 1] = p->bin_start[b] + p->h_summary.bin_count[b];
         for (int b = 0; b < NUM_BINS; ++b) p->stats.bin_count[b] = p->h_summary.bin_count[b];
