@@ -249,7 +249,8 @@ SPG_DEV void bitmap_set_warp(uint32_t *Bm, int x, bool ok) {
     const int w = ok ? (x >> 5) : -1 - lane;  // invalid lanes form runs of their own
     uint32_t bits = ok ? (1u << (x & 31)) : 0u;
     // sparse columns (no two neighbours in one word): one atomic per lane, no combining
-    const bool shared_word = lane > 0 && __shfl_up_sync(SPG_FULL, w, 1) == w;
+    const int prev_w = __shfl_up_sync(SPG_FULL, w, 1);  // every lane takes part in the shuffle
+    const bool shared_word = lane > 0 && prev_w == w;
     if (!__any_sync(SPG_FULL, shared_word)) {
         if (ok) atomicOr(&Bm[w], bits);
         return;
