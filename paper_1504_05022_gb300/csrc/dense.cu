@@ -164,27 +164,26 @@ cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *
 }
 
 // ---- the product expansion shared by the count and fill kernels ----
-// Walks the A entries of `row` in windows of WIN (<= NT).  For each window, the part of
-// every selected B row inside slice s is cut into chunks of DENSE_CH consecutive
-// entries; warp w takes the w-th contiguous range of the window's chunks, and its
-// lanes read a chunk's entries 32 at a time (coalesced, one B row per access, so
-// the 32 columns of an access are distinct), DENSE_UN accesses in flight.
-// f(p, ok, t) gets DENSE_UN entry positions p[] of B, which of them are valid,
-// and the window slot t of their A entry; every lane of a warp makes the same calls
-// (so f may use warp-wide intrinsics).  Ends with a barrier.
+// Walks the A entries of `row` in windows of WIN (<= NT).  For each window, the parts of
+// the selected B rows inside slice s form one flat sequence of products (an exclusive scan
+// of the part lengths); the threads take consecutive products, DENSE_UN per thread in
+// flight, and find each product's part by a binary search of the scan.  Consecutive lanes
+// read consecutive entries of one B row (coalesced, distinct ascending columns) however
+// short the parts are: the slices of a wide B cut most rows into parts of a few entries,
+// which a part-per-warp walk would leave mostly idle.
+// f(p, ok) gets DENSE_UN entry positions p[] of B and which of them are valid; every lane
+// of a warp makes the same calls (so f may use warp-wide intrinsics).  Ends with a barrier.
 constexpr int DENSE_CH = 256;
 constexpr int DENSE_UN = 4;
 
-template <int NT, int WIN, bool VALS, typename F>
+template <int NT, int WIN, typename F>
 SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int row, int s, int64_t *wbs,
-                          int32_t *wlen, int64_t *cscan, val_t *wa, int64_t *scan64, F f) {
-    constexpr int NW = NT / 32;
-    const int lane = lane_id(), wid = warp_id();
+                          int64_t *cscan, int64_t *scan64, F f) {
     const int64_t a0 = A.rp[row], a1 = A.rp[row + 1];
     const int K1 = D.K + 1;
     for (int64_t e = a0; e < a1; e += WIN) {
         const int nW = (int)min((int64_t)WIN, a1 - e);
-        int64_t nch = 0;
+        int64_t len = 0;
         if (threadIdx.x < nW) {
             const int32_t k = A.col[e + threadIdx.x];
             const int64_t rs = B.rp[k];
@@ -198,41 +197,27 @@ SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, 
                 be = B.rp[k + 1];
             }
             wbs[threadIdx.x] = bs;
-            wlen[threadIdx.x] = (int32_t)(be - bs);  // a B row has at most ncols < 2^31 entries
-            if (VALS) wa[threadIdx.x] = A.val[e + threadIdx.x];
-            nch = (be - bs + DENSE_CH - 1) / DENSE_CH;
+            len = be - bs;
         }
-        int64_t tc;
-        const int64_t ex = block_exclusive_scan<NT, int64_t, false>(nch, scan64, tc);
+        int64_t tot;
+        const int64_t ex = block_exclusive_scan<NT, int64_t, false>(len, scan64, tot);
         if (threadIdx.x < nW) cscan[threadIdx.x] = ex;
         __syncthreads();
-        const int64_t c0 = tc * wid / NW, c1 = tc * (wid + 1) / NW;
-        int t = 0;
-        if (c0 < c1) {  // the entry of chunk c0: the last one whose first chunk is <= c0
-            int lo = 0, hi = nW - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (cscan[mid] <= c0) lo = mid; else hi = mid - 1;
-            }
-            t = lo;
-        }
-        for (int64_t c = c0; c < c1; ++c) {
-            while (t + 1 < nW && cscan[t + 1] <= c) ++t;  // warp-uniform: skips entries without chunks
-            const int64_t off = (c - cscan[t]) * DENSE_CH;
-            const int64_t p0 = wbs[t] + off;
-            const int n = (int)min((int64_t)DENSE_CH, (int64_t)wlen[t] - off);
-            // the trip count is the same for every lane (f may be warp-collective)
-            for (int i0 = 0; i0 < n; i0 += 32 * DENSE_UN) {
-                const int i = i0 + lane;
-                int64_t p[DENSE_UN];
-                bool ok[DENSE_UN];
+        // the trip count is the same for every lane (f may be warp-collective)
+        for (int64_t q0 = 0; q0 < tot; q0 += (int64_t)NT * DENSE_UN) {
+            int64_t p[DENSE_UN];
+            bool ok[DENSE_UN];
 #pragma unroll
-                for (int u = 0; u < DENSE_UN; ++u) {
-                    ok[u] = i + 32 * u < n;
-                    p[u] = p0 + i + 32 * u;
+            for (int u = 0; u < DENSE_UN; ++u) {
+                const int64_t q = q0 + (int64_t)u * NT + threadIdx.x;
+                ok[u] = q < tot;
+                p[u] = 0;
+                if (ok[u]) {
+                    const int t = find_segment_i64(cscan, nW, q);  // the last part starting at or before q
+                    p[u] = wbs[t] + (q - cscan[t]);
                 }
-                f(p, ok, t);
             }
+            f(p, ok);
         }
         __syncthreads();  // the window's tables are reused
     }
@@ -267,14 +252,13 @@ SPG_DEV void bitmap_set_warp(uint32_t *Bm, int x, bool ok) {
 
 template <int NT>
 SPG_DEV bool dense_bitmap(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int row, int s, int64_t lo,
-                          int span, uint32_t *Bm, int64_t *wbs, int32_t *wlen, int64_t *cscan, int64_t *scan64) {
+                          int span, uint32_t *Bm, int64_t *wbs, int64_t *cscan, int64_t *scan64) {
     const int nq = (((span + 31) >> 5) + 3) >> 2;  // 16-byte groups of bitmap words
     uint4 *b4 = reinterpret_cast<uint4 *>(Bm);
     for (int q = threadIdx.x; q < nq; q += NT) b4[q] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     bool bad = false;
-    dense_expand<NT, NT, false>(A, B, D, row, s, wbs, wlen, cscan, nullptr, scan64,
-                            [&](const int64_t *p, const bool *ok, int) {
+    dense_expand<NT, NT>(A, B, D, row, s, wbs, cscan, scan64, [&](const int64_t *p, const bool *ok) {
         int32_t c[DENSE_UN];
 #pragma unroll
         for (int u = 0; u < DENSE_UN; ++u)
@@ -313,11 +297,13 @@ SPG_DEV int dense_span(const DevCSR &B, const DenseArgs &D, int64_t d, int s, in
     return (int)(min(min((int64_t)(s + 1) * D.W, B.ncols), (int64_t)D.chi[d]) - lo);
 }
 
-template <int NT>
+// FLAGS: narrow slices count with one flag byte per column (a plain store of 1 per product:
+// every writer stores the same value, so no atomics are needed); wide ones with the bitmap.
+template <int NT, bool FLAGS>
 SPG_DEV void dense_count_item(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t b, int64_t *err) {
     extern __shared__ __align__(16) uint32_t dc_bm[];
     __shared__ int64_t wbs[NT], cscan[NT], scan64[NT / 32 + 1];
-    __shared__ int32_t wlen[NT], scan32[NT / 32 + 1];
+    __shared__ int32_t scan32[NT / 32 + 1];
     const int64_t d = b / D.K;
     const int s = (int)(b - d * D.K);
     int64_t lo;
@@ -326,23 +312,52 @@ SPG_DEV void dense_count_item(const DevCSR &A, const DevCSR &B, const DenseArgs 
         if (threadIdx.x == 0) D.cnt[b] = 0;
         return;
     }
-    const bool bad = dense_bitmap<NT>(A, B, D, D.rows[d], s, lo, span, dc_bm, wbs, wlen, cscan, scan64);
-    const int nw = (span + 31) >> 5;
+    bool bad = false;
     int n = 0;
-    for (int w = threadIdx.x; w < nw; w += NT) n += __popc(dc_bm[w]);
+    if constexpr (FLAGS) {
+        const int nq = (span + 15) >> 4;  // 16-byte groups of flags
+        uint4 *f4 = reinterpret_cast<uint4 *>(dc_bm);
+        for (int q = threadIdx.x; q < nq; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        volatile uint8_t *fl = reinterpret_cast<uint8_t *>(dc_bm);
+        dense_expand<NT, NT>(A, B, D, D.rows[d], s, wbs, cscan, scan64, [&](const int64_t *p, const bool *ok) {
+            int32_t c[DENSE_UN];
+#pragma unroll
+            for (int u = 0; u < DENSE_UN; ++u)
+                if (ok[u]) c[u] = __ldg(B.col + p[u]);
+#pragma unroll
+            for (int u = 0; u < DENSE_UN; ++u) {
+                if (!ok[u]) continue;
+                const int x = (int)(c[u] - lo);
+                if ((unsigned)x >= (unsigned)span) {  // cannot happen: the slice boundaries select the columns
+                    bad = true;
+                    continue;
+                }
+                fl[x] = 1;
+            }
+        });
+        for (int q = threadIdx.x; q < nq; q += NT) {
+            const uint4 v = f4[q];
+            n += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        }
+    } else {
+        bad = dense_bitmap<NT>(A, B, D, D.rows[d], s, lo, span, dc_bm, wbs, cscan, scan64);
+        const int nw = (span + 31) >> 5;
+        for (int w = threadIdx.x; w < nw; w += NT) n += __popc(dc_bm[w]);
+    }
     n = block_reduce_sum<NT, int>(n, scan32);
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch((unsigned long long *)err, 5ull);
     if (threadIdx.x == 0) D.cnt[b] = n;
 }
 
-template <int NT>
+template <int NT, bool FLAGS>
 __global__ void __launch_bounds__(NT)
 k_dense_count(DevCSR A, DevCSR B, DenseArgs D, int64_t *err) {
     __shared__ int64_t s_b;
     unsigned long long *q = D.dev_n != nullptr ? D.queue : nullptr;
     const int64_t nb = dense_items(D);
     for (int64_t b = dense_next(q, 0, true, &s_b); b < nb; b = dense_next(q, b, false, &s_b))
-        dense_count_item<NT>(A, B, D, b, err);
+        dense_count_item<NT, FLAGS>(A, B, D, b, err);
 }
 
 // One thread per dense item: the slices' offsets inside the row and the row's length.
@@ -390,14 +405,12 @@ SPG_DEV bool dense_products(const DevCSR &A, const DevCSR &B, const DenseArgs &D
                             int x0, int x1, int64_t *wbs, int64_t *cscan, val_t *wa, int32_t *wlen, int32_t *lidx,
                             int64_t *scan64, Fa add, Fp add_plain) {
     constexpr int WIN = DENSE_FILL_WIN;
-    constexpr int NW = NT / 32;
     bool bad = false;
-    const int lane = lane_id(), wid = warp_id();
     const int64_t a0 = A.rp[row], a1 = A.rp[row + 1];
     const int K1 = D.K + 1;
     for (int64_t e = a0; e < a1; e += WIN) {
         const int nW = (int)min((int64_t)WIN, a1 - e);
-        // chunks of the short parts (low 40 bits) and the count of long parts (above)
+        // products of the short parts (low 40 bits) and the count of long parts (above)
         int64_t packed = 0;
         if (threadIdx.x < nW) {
             const int32_t k = A.col[e + threadIdx.x];
@@ -415,7 +428,7 @@ SPG_DEV bool dense_products(const DevCSR &A, const DevCSR &B, const DenseArgs &D
             wbs[threadIdx.x] = bs;
             wlen[threadIdx.x] = (int32_t)len;  // a B row has at most ncols < 2^31 entries
             wa[threadIdx.x] = A.val[e + threadIdx.x];
-            packed = len >= DENSE_LONG ? (int64_t(1) << 40) : (len + DENSE_CH - 1) / DENSE_CH;
+            packed = len >= DENSE_LONG ? (int64_t(1) << 40) : len;
         }
         int64_t ptot;
         const int64_t ex = block_exclusive_scan<NT, int64_t, false>(packed, scan64, ptot);
@@ -423,45 +436,38 @@ SPG_DEV bool dense_products(const DevCSR &A, const DevCSR &B, const DenseArgs &D
             cscan[threadIdx.x] = ex & ((int64_t(1) << 40) - 1);
             if (packed >> 40) lidx[ex >> 40] = threadIdx.x;
         }
-        const int64_t tc = ptot & ((int64_t(1) << 40) - 1);
+        const int64_t tshort = ptot & ((int64_t(1) << 40) - 1);
         const int nlong = (int)(ptot >> 40);
         __syncthreads();
-        // short parts: the warps' contiguous chunk ranges
-        {
-            const int64_t c0 = tc * wid / NW, c1 = tc * (wid + 1) / NW;
-            int t = 0;
-            if (c0 < c1) {
-                int lo_ = 0, hi = nW - 1;
-                while (lo_ < hi) {
-                    const int mid = (lo_ + hi + 1) >> 1;
-                    if (cscan[mid] <= c0) lo_ = mid; else hi = mid - 1;
+        // short parts: one flat sequence of their products (long parts add none to the scan),
+        // consecutive threads on consecutive products, shared atomics
+        for (int64_t q0 = 0; q0 < tshort; q0 += (int64_t)NT * DENSE_UN) {
+            int64_t pp[DENSE_UN];
+            int tt[DENSE_UN];
+#pragma unroll
+            for (int u = 0; u < DENSE_UN; ++u) {
+                const int64_t q = q0 + (int64_t)u * NT + threadIdx.x;
+                tt[u] = -1;
+                if (q < tshort) {
+                    const int t = find_segment_i64(cscan, nW, q);  // the last part starting at or before q
+                    tt[u] = t;
+                    pp[u] = wbs[t] + (q - cscan[t]);
                 }
-                t = lo_;
             }
-            for (int64_t c = c0; c < c1; ++c) {
-                // skips the entries without chunks (long parts have none)
-                while (t + 1 < nW && cscan[t + 1] <= c) ++t;
-                const int64_t off = (c - cscan[t]) * DENSE_CH;
-                const int64_t p0 = wbs[t] + off;
-                const int n = (int)min((int64_t)DENSE_CH, (int64_t)wlen[t] - off);
-                const val_t av = wa[t];
-                for (int i = lane; i < n; i += 32 * DENSE_UN) {
-                    int32_t cc[DENSE_UN];
-                    val_t v[DENSE_UN];
+            int32_t cc[DENSE_UN];
+            val_t v[DENSE_UN];
 #pragma unroll
-                    for (int u = 0; u < DENSE_UN; ++u)
-                        if (i + 32 * u < n) cc[u] = __ldg(B.col + p0 + i + 32 * u);
+            for (int u = 0; u < DENSE_UN; ++u)
+                if (tt[u] >= 0) cc[u] = __ldg(B.col + pp[u]);
 #pragma unroll
-                    for (int u = 0; u < DENSE_UN; ++u)
-                        if (i + 32 * u < n) v[u] = __ldg(B.val + p0 + i + 32 * u);
+            for (int u = 0; u < DENSE_UN; ++u)
+                if (tt[u] >= 0) v[u] = __ldg(B.val + pp[u]);
 #pragma unroll
-                    for (int u = 0; u < DENSE_UN; ++u) {
-                        if (i + 32 * u >= n) continue;
-                        const int x = (int)(cc[u] - lo);
-                        if (x < x0 || x >= x1) continue;
-                        if (!add(x, av * v[u])) bad = true;
-                    }
-                }
+            for (int u = 0; u < DENSE_UN; ++u) {
+                if (tt[u] < 0) continue;
+                const int x = (int)(cc[u] - lo);
+                if (x < x0 || x >= x1) continue;
+                if (!add(x, wa[tt[u]] * v[u])) bad = true;
             }
         }
         __syncthreads();
@@ -650,7 +656,7 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
         }
         __syncthreads();
     } else {
-        bad = dense_bitmap<NT>(A, B, D, row, s, lo, span, Bm, wbs, wlen, cscan, scan64);
+        bad = dense_bitmap<NT>(A, B, D, row, s, lo, span, Bm, wbs, cscan, scan64);
     }
     const int tot = bitmap_rank<NT>(Bm, Rd, nwords, scan32);
     if (__syncthreads_or(bad || tot != expected)) {  // the counting pass saw other columns: cannot happen
@@ -739,6 +745,7 @@ __global__ void k_dense_rowsum(DenseArgs D, int32_t *nnzc) {
 }
 
 constexpr int DENSE_COUNT_NT = 256;
+constexpr int DENSE_COUNT_FLAGS_MAX = 32768;
 constexpr int DENSE_FILL_NT = 512;
 
 // Bytes of a fill CTA's bitmap and rank directory for slices of W columns.
@@ -768,8 +775,10 @@ cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
-    const int smem = (int)(sizeof(uint32_t) * dense_nw4(D.W));  // the slice's bitmap
-    auto kern = k_dense_count<DENSE_COUNT_NT>;
+    // flag bytes for slices of up to DENSE_COUNT_FLAGS_MAX columns, else the bitmap
+    const bool flags = D.W <= DENSE_COUNT_FLAGS_MAX;
+    const int smem = flags ? D.W : (int)(sizeof(uint32_t) * dense_nw4(D.W));
+    auto kern = flags ? k_dense_count<DENSE_COUNT_NT, true> : k_dense_count<DENSE_COUNT_NT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int64_t grid = nb;

@@ -83,6 +83,10 @@ cudaError_t launch_binning(int64_t m, const int64_t *arp, const int64_t *S,
                            int64_t *ctil_rp, int32_t *hist, int64_t *cap_partial,
                            BinSummary *summary, cudaStream_t st);
 
+// C~ row offsets again from u and the bins under P (ctil_rp[0..m]; the total into *total)
+cudaError_t launch_cap_rescan(int64_t m, const int64_t *u, const uint8_t *bin, CapPolicy P, int64_t *ctil_rp,
+                              int64_t *partial, int64_t *total, cudaStream_t st);
+
 // ---- learned preallocation (predictor.cu) ----
 // Row features (warp per row).  With the stage-1 prefix S, rows with u_i <= u_min are
 // skipped, and so are the rows flagged in `skip` (when given).

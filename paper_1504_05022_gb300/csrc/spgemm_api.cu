@@ -547,20 +547,6 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
                                       p->dense_hi, p->st));
             p->count(SPGEMM_K_OTHER);
         }
-        if (o.alloc_policy == SPGEMM_ALLOC_LEARNED) {
-            // features and predicted temporary sizes of every row (used for bin 37)
-            float *X = nullptr;
-            SPG_TRY(p->alloc_n(&X, m * SPGEMM_MLP_FEATURES, LIFE_SYMBOLIC));
-            SPG_TRY(p->alloc_n(&p->pred_cap, m, LIFE_SYMBOLIC));
-            p->time_begin(SPGEMM_K_OTHER);
-            SPG_TRY(launch_row_features(p->A, p->B, X, p->st, p->S, BIN_MERGE_MIN_U, p->dense_flag));
-            SPG_TRY(launch_predict_caps(predictor_params(o.predictor), X, m, nullptr,
-                                        (float)(o.predictor_margin > 0 ? o.predictor_margin : 1.0),
-                                        o.initial_cap, p->pred_cap, p->st, p->A.rp, p->S, BIN_MERGE_MIN_U,
-                                        p->dense_flag, p->dense_K > 0 ? (int64_t)o.dense_pred_min : 0));
-            p->time_end();
-            p->count(SPGEMM_K_OTHER, 2);
-        }
         // ---- stage 2: binning ----
         nblk = bin_blocks(m);
         SPG_TRY(p->alloc_n(&p->u, m));
@@ -575,7 +561,7 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             SPG_TRY(p->alloc_n(&capp, nblk, LIFE_SYMBOLIC));
             pol.policy = o.alloc_policy;
             pol.initial_cap = o.initial_cap;
-            pol.pred_cap = p->pred_cap;
+            pol.pred_cap = nullptr;  // learned: bin-37 sizes are set after the prediction below
             pol.cap_max = p->capmax;
             pol.dense = p->dense_flag;
             p->time_begin(SPGEMM_K_BIN);
@@ -588,6 +574,24 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
         // selection have nothing to do, and their launches are skipped
         SPG_TRY(p->d2h(&p->h_summary, p->d_summary, sizeof(BinSummary)));
         if (p->h_summary.bin_count[BIN_MERGE] > 0 && (o.alloc_policy == SPGEMM_ALLOC_LEARNED || p->dense_K > 0)) {
+            if (o.alloc_policy == SPGEMM_ALLOC_LEARNED) {
+                // features and predicted temporary sizes of the bin-37 rows, then the rows of C~
+                // laid out again with those sizes (the binning above sized bin 37 as hybrid)
+                float *X = nullptr;
+                SPG_TRY(p->alloc_n(&X, m * SPGEMM_MLP_FEATURES, LIFE_SYMBOLIC));
+                SPG_TRY(p->alloc_n(&p->pred_cap, m, LIFE_SYMBOLIC));
+                p->time_begin(SPGEMM_K_OTHER);
+                SPG_TRY(launch_row_features(p->A, p->B, X, p->st, p->S, BIN_MERGE_MIN_U, p->dense_flag));
+                SPG_TRY(launch_predict_caps(predictor_params(o.predictor), X, m, nullptr,
+                                            (float)(o.predictor_margin > 0 ? o.predictor_margin : 1.0),
+                                            o.initial_cap, p->pred_cap, p->st, p->A.rp, p->S, BIN_MERGE_MIN_U,
+                                            p->dense_flag, p->dense_K > 0 ? (int64_t)o.dense_pred_min : 0));
+                pol.pred_cap = p->pred_cap;
+                SPG_TRY(launch_cap_rescan(m, p->u, p->bin, pol, p->ctil_rp, p->scan_partial, &p->d_summary->sum_cap,
+                                          p->st));
+                p->time_end();
+                p->count(SPGEMM_K_OTHER, 5);
+            }
             if (o.alloc_policy == SPGEMM_ALLOC_LEARNED) {
                 // group the bin-37 rows by the shared-memory class their predicted size needs
                 int32_t *ccap = nullptr, *scratch = nullptr;

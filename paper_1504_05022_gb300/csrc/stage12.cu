@@ -263,6 +263,22 @@ k_bin_scatter(int64_t m, const int64_t *u_in, const uint8_t *bin_in, CapPolicy P
     }
 }
 
+// The rows of C~ laid out again from the stored u_i and bins under policy P (the learned
+// sizes are known only after the binning): ctil_rp[0..m] and the total into *total.
+struct LoadCap {
+    const int64_t *u;
+    const uint8_t *bin;
+    CapPolicy P;
+    SPG_DEV int64_t operator()(int64_t i) const { return cap_of(u[i], (int)bin[i], i, P); }
+};
+
+cudaError_t launch_cap_rescan(int64_t m, const int64_t *u, const uint8_t *bin, CapPolicy P, int64_t *ctil_rp,
+                              int64_t *partial, int64_t *total, cudaStream_t st) {
+    cudaError_t e = device_exclusive_scan(m, LoadCap{u, bin, P}, StoreI64{ctil_rp}, partial, total, st);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(ctil_rp + m, total, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+}
+
 cudaError_t launch_binning(int64_t m, const int64_t *arp, const int64_t *S,
                            const int64_t *sum_u_ptr, CapPolicy P, int64_t *u, uint8_t *bin, int32_t *nnzc, int32_t *bin_rows,
                            int64_t *ctil_rp, int32_t *hist, int64_t *cap_partial,
