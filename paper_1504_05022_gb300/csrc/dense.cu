@@ -164,17 +164,20 @@ cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *
 }
 
 // ---- the product expansion shared by the count and fill kernels ----
-// Walks the A entries of `row` in windows of WIN (<= NT).  For each window, the parts of
-// the selected B rows inside slice s form one flat sequence of products (an exclusive scan
-// of the part lengths); the threads take consecutive products, DENSE_UN per thread in
-// flight, and find each product's part by a binary search of the scan.  Consecutive lanes
-// read consecutive entries of one B row (coalesced, distinct ascending columns) however
-// short the parts are: the slices of a wide B cut most rows into parts of a few entries,
-// which a part-per-warp walk would leave mostly idle.
+// Walks the A entries of `row` in windows of WIN (<= NT); wbs holds 2 WIN entries (the
+// parts' starts, then their lengths).  Where the window's parts -- the selected B rows'
+// entries inside slice s -- average DENSE_FLAT_BELOW products or more, they are cut into
+// chunks of DENSE_CH entries and warp w takes the w-th contiguous range of the chunks, its
+// lanes a chunk's entries 32 at a time.  Shorter parts (the slices of a wide B cut most
+// sparse rows into parts of a few entries, which would leave most lanes idle) form one
+// flat sequence of products: the threads take consecutive products and find each one's
+// part by a binary search of the window's scan.  Either way consecutive lanes read
+// consecutive entries of one B row (coalesced, distinct ascending columns).
 // f(p, ok) gets DENSE_UN entry positions p[] of B and which of them are valid; every lane
 // of a warp makes the same calls (so f may use warp-wide intrinsics).  Ends with a barrier.
 constexpr int DENSE_CH = 256;
 constexpr int DENSE_UN = 4;
+constexpr int DENSE_FLAT_BELOW = 32;  // windows whose parts average fewer products go flat
 
 template <int NT, int WIN, typename F>
 SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int row, int s, int64_t *wbs,
@@ -197,27 +200,62 @@ SPG_DEV void dense_expand(const DevCSR &A, const DevCSR &B, const DenseArgs &D, 
                 be = B.rp[k + 1];
             }
             wbs[threadIdx.x] = bs;
+            wbs[WIN + threadIdx.x] = be - bs;
             len = be - bs;
         }
         int64_t tot;
         const int64_t ex = block_exclusive_scan<NT, int64_t, false>(len, scan64, tot);
         if (threadIdx.x < nW) cscan[threadIdx.x] = ex;
         __syncthreads();
-        // the trip count is the same for every lane (f may be warp-collective)
-        for (int64_t q0 = 0; q0 < tot; q0 += (int64_t)NT * DENSE_UN) {
-            int64_t p[DENSE_UN];
-            bool ok[DENSE_UN];
+        if (tot >= (int64_t)DENSE_FLAT_BELOW * nW) {
+            // long parts on average: warp w takes the w-th contiguous range of the window's
+            // chunks of DENSE_CH entries, its lanes a chunk's entries 32 at a time
+            constexpr int NW = NT / 32;
+            const int lane = lane_id(), wid = warp_id();
+            const int64_t nch = threadIdx.x < nW ? (wbs[WIN + threadIdx.x] + DENSE_CH - 1) / DENSE_CH : 0;
+            int64_t tc;
+            const int64_t exc = block_exclusive_scan<NT, int64_t, false>(nch, scan64, tc);
+            if (threadIdx.x < nW) cscan[threadIdx.x] = exc;  // now the first chunk of each part
+            __syncthreads();
+            const int64_t c0 = tc * wid / NW, c1 = tc * (wid + 1) / NW;
+            int t = 0;
+            if (c0 < c1) t = find_segment_i64(cscan, nW, c0);
+            for (int64_t c = c0; c < c1; ++c) {
+                while (t + 1 < nW && cscan[t + 1] <= c) ++t;  // warp-uniform: skips parts without chunks
+                const int64_t off = (c - cscan[t]) * DENSE_CH;
+                const int64_t p0 = wbs[t] + off;
+                const int n = (int)min((int64_t)DENSE_CH, wbs[WIN + t] - off);
+                // the trip count is the same for every lane (f may be warp-collective)
+                for (int i0 = 0; i0 < n; i0 += 32 * DENSE_UN) {
+                    const int i = i0 + lane;
+                    int64_t p[DENSE_UN];
+                    bool ok[DENSE_UN];
 #pragma unroll
-            for (int u = 0; u < DENSE_UN; ++u) {
-                const int64_t q = q0 + (int64_t)u * NT + threadIdx.x;
-                ok[u] = q < tot;
-                p[u] = 0;
-                if (ok[u]) {
-                    const int t = find_segment_i64(cscan, nW, q);  // the last part starting at or before q
-                    p[u] = wbs[t] + (q - cscan[t]);
+                    for (int u = 0; u < DENSE_UN; ++u) {
+                        ok[u] = i + 32 * u < n;
+                        p[u] = p0 + i + 32 * u;
+                    }
+                    f(p, ok);
                 }
             }
-            f(p, ok);
+        } else {
+            // short parts on average: one flat sequence of products; the trip count is the
+            // same for every lane (f may be warp-collective)
+            for (int64_t q0 = 0; q0 < tot; q0 += (int64_t)NT * DENSE_UN) {
+                int64_t p[DENSE_UN];
+                bool ok[DENSE_UN];
+#pragma unroll
+                for (int u = 0; u < DENSE_UN; ++u) {
+                    const int64_t q = q0 + (int64_t)u * NT + threadIdx.x;
+                    ok[u] = q < tot;
+                    p[u] = 0;
+                    if (ok[u]) {
+                        const int t = find_segment_i64(cscan, nW, q);  // the last part starting at or before q
+                        p[u] = wbs[t] + (q - cscan[t]);
+                    }
+                }
+                f(p, ok);
+            }
         }
         __syncthreads();  // the window's tables are reused
     }
@@ -302,7 +340,7 @@ SPG_DEV int dense_span(const DevCSR &B, const DenseArgs &D, int64_t d, int s, in
 template <int NT, bool FLAGS>
 SPG_DEV void dense_count_item(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t b, int64_t *err) {
     extern __shared__ __align__(16) uint32_t dc_bm[];
-    __shared__ int64_t wbs[NT], cscan[NT], scan64[NT / 32 + 1];
+    __shared__ int64_t wbs[2 * NT], cscan[NT], scan64[NT / 32 + 1];  // part starts, then part lengths
     __shared__ int32_t scan32[NT / 32 + 1];
     const int64_t d = b / D.K;
     const int s = (int)(b - d * D.K);
@@ -439,35 +477,76 @@ SPG_DEV bool dense_products(const DevCSR &A, const DevCSR &B, const DenseArgs &D
         const int64_t tshort = ptot & ((int64_t(1) << 40) - 1);
         const int nlong = (int)(ptot >> 40);
         __syncthreads();
-        // short parts: one flat sequence of their products (long parts add none to the scan),
-        // consecutive threads on consecutive products, shared atomics
-        for (int64_t q0 = 0; q0 < tshort; q0 += (int64_t)NT * DENSE_UN) {
-            int64_t pp[DENSE_UN];
-            int tt[DENSE_UN];
+        const int nshort = nW - nlong;
+        if (tshort >= (int64_t)DENSE_FLAT_BELOW * (nshort > 0 ? nshort : 1)) {
+            // short parts averaging DENSE_FLAT_BELOW products or more: warp w takes the w-th
+            // contiguous range of their chunks of DENSE_CH entries, shared atomics
+            constexpr int NW = NT / 32;
+            const int lane = lane_id(), wid = warp_id();
+            const int64_t nch = (threadIdx.x < nW && wlen[threadIdx.x] < DENSE_LONG)
+                                    ? ((int64_t)wlen[threadIdx.x] + DENSE_CH - 1) / DENSE_CH : 0;
+            int64_t tc;
+            const int64_t exc = block_exclusive_scan<NT, int64_t, false>(nch, scan64, tc);
+            if (threadIdx.x < nW) cscan[threadIdx.x] = exc;  // now the first chunk of each part
+            __syncthreads();
+            const int64_t c0 = tc * wid / NW, c1 = tc * (wid + 1) / NW;
+            int t = 0;
+            if (c0 < c1) t = find_segment_i64(cscan, nW, c0);
+            for (int64_t c = c0; c < c1; ++c) {
+                while (t + 1 < nW && cscan[t + 1] <= c) ++t;  // warp-uniform: skips parts without chunks
+                const int64_t off = (c - cscan[t]) * DENSE_CH;
+                const int64_t p0 = wbs[t] + off;
+                const int n = (int)min((int64_t)DENSE_CH, (int64_t)wlen[t] - off);
+                const val_t av = wa[t];
+                for (int i = lane; i < n; i += 32 * DENSE_UN) {
+                    int32_t cc[DENSE_UN];
+                    val_t v[DENSE_UN];
 #pragma unroll
-            for (int u = 0; u < DENSE_UN; ++u) {
-                const int64_t q = q0 + (int64_t)u * NT + threadIdx.x;
-                tt[u] = -1;
-                if (q < tshort) {
-                    const int t = find_segment_i64(cscan, nW, q);  // the last part starting at or before q
-                    tt[u] = t;
-                    pp[u] = wbs[t] + (q - cscan[t]);
+                    for (int u = 0; u < DENSE_UN; ++u)
+                        if (i + 32 * u < n) cc[u] = __ldg(B.col + p0 + i + 32 * u);
+#pragma unroll
+                    for (int u = 0; u < DENSE_UN; ++u)
+                        if (i + 32 * u < n) v[u] = __ldg(B.val + p0 + i + 32 * u);
+#pragma unroll
+                    for (int u = 0; u < DENSE_UN; ++u) {
+                        if (i + 32 * u >= n) continue;
+                        const int x = (int)(cc[u] - lo);
+                        if (x < x0 || x >= x1) continue;
+                        if (!add(x, av * v[u])) bad = true;
+                    }
                 }
             }
-            int32_t cc[DENSE_UN];
-            val_t v[DENSE_UN];
+        } else {
+            // shorter ones: one flat sequence of their products (long parts add none to the
+            // scan), consecutive threads on consecutive products, shared atomics
+            for (int64_t q0 = 0; q0 < tshort; q0 += (int64_t)NT * DENSE_UN) {
+                int64_t pp[DENSE_UN];
+                int tt[DENSE_UN];
 #pragma unroll
-            for (int u = 0; u < DENSE_UN; ++u)
-                if (tt[u] >= 0) cc[u] = __ldg(B.col + pp[u]);
+                for (int u = 0; u < DENSE_UN; ++u) {
+                    const int64_t q = q0 + (int64_t)u * NT + threadIdx.x;
+                    tt[u] = -1;
+                    if (q < tshort) {
+                        const int t = find_segment_i64(cscan, nW, q);  // the last part starting at or before q
+                        tt[u] = t;
+                        pp[u] = wbs[t] + (q - cscan[t]);
+                    }
+                }
+                int32_t cc[DENSE_UN];
+                val_t v[DENSE_UN];
 #pragma unroll
-            for (int u = 0; u < DENSE_UN; ++u)
-                if (tt[u] >= 0) v[u] = __ldg(B.val + pp[u]);
+                for (int u = 0; u < DENSE_UN; ++u)
+                    if (tt[u] >= 0) cc[u] = __ldg(B.col + pp[u]);
 #pragma unroll
-            for (int u = 0; u < DENSE_UN; ++u) {
-                if (tt[u] < 0) continue;
-                const int x = (int)(cc[u] - lo);
-                if (x < x0 || x >= x1) continue;
-                if (!add(x, wa[tt[u]] * v[u])) bad = true;
+                for (int u = 0; u < DENSE_UN; ++u)
+                    if (tt[u] >= 0) v[u] = __ldg(B.val + pp[u]);
+#pragma unroll
+                for (int u = 0; u < DENSE_UN; ++u) {
+                    if (tt[u] < 0) continue;
+                    const int x = (int)(cc[u] - lo);
+                    if (x < x0 || x >= x1) continue;
+                    if (!add(x, wa[tt[u]] * v[u])) bad = true;
+                }
             }
         }
         __syncthreads();
@@ -553,7 +632,7 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
                              int32_t *c_col, val_t *c_val, int64_t *err, int vcap) {
     constexpr int WIN = DENSE_FILL_WIN;
     extern __shared__ __align__(16) unsigned char df_smem[];
-    __shared__ int64_t wbs[WIN], cscan[WIN], scan64[NT / 32 + 1];
+    __shared__ int64_t wbs[2 * WIN], cscan[WIN], scan64[NT / 32 + 1];  // part starts, then part lengths
     __shared__ val_t wa[WIN];
     __shared__ int32_t wlen[WIN], lidx[WIN], scan32[NT / 32 + 1];
     const int expected = D.cnt[b];
@@ -767,7 +846,7 @@ int dense_fill_max_dynamic(int per_sm) {
 }
 
 int dense_fill_static_smem() {
-    return (int)(DENSE_FILL_WIN * (2 * sizeof(int64_t) + sizeof(val_t) + 2 * sizeof(int32_t)) +
+    return (int)(DENSE_FILL_WIN * (3 * sizeof(int64_t) + sizeof(val_t) + 2 * sizeof(int32_t)) +
                  (DENSE_FILL_NT / 32 + 1) * 12 + 64);
 }
 
