@@ -160,14 +160,17 @@ typedef struct spgemm_opts {
                                 many entries before they are merged into the result (0 = 4096) */
     int32_t dense_min_u;     /* bin-37 rows with u_i >= this are computed by the dense-slice
                                 kernels instead of the merge kernel: B's columns are cut into
-                                slices that fit shared memory as fp64 sums, one CTA per (row,
-                                slice), after a pass that counts the columns of every slice.
+                                slices, one CTA per (row, slice), after a pass that counts the
+                                columns of every slice; the rows are then written straight into C.
                                 0 = a bin-37 row is dense when dense_span_div * u_i >= the width of
                                 the column range its products can reach (first to last column of
                                 the B rows it selects); negative = never.  Off with SPGEMM_MERGE_PATH,
                                 SPGEMM_LONG_ROWS_LEVEL1 and when B needs more than 64 slices */
-    int32_t dense_span;      /* widest dense slice in columns (0 = the widest that fits shared
-                                memory, at least 1,024) */
+    int32_t dense_span;      /* widest dense slice in columns (0 = 131,072, at least 1,024).  A slice
+                                narrow enough for one sum and one flag per column in shared memory
+                                (about 21,900 columns in double) is filled in one pass over its
+                                products; a wider one keeps a bitmap of its columns, its rank
+                                directory and one sum per column of the result */
     int32_t dense_span_div;  /* with dense_min_u = 0: the divisor of the rule above (0 = 8) */
     const void *predictor;   /* spgemm_predictor* for SPGEMM_ALLOC_LEARNED, else NULL; it must
                                 not be freed before spgemm_symbolic (or spgemm_galerkin) has
