@@ -629,14 +629,14 @@ SPG_DEV bool dense_products(const DevCSR &A, const DevCSR &B, const DenseArgs &D
 // twice, which pays where slices are dense (products well above their width).
 template <int NT, bool REPLAY, bool WIDE>
 SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t b, const int64_t *c_rp,
-                             int32_t *c_col, val_t *c_val, int64_t *err, int vcap) {
+                             int32_t *c_col, val_t *c_val, int64_t *err, int vcap, int cmin, int cmax) {
     constexpr int WIN = DENSE_FILL_WIN;
     extern __shared__ __align__(16) unsigned char df_smem[];
     __shared__ int64_t wbs[2 * WIN], cscan[WIN], scan64[NT / 32 + 1];  // part starts, then part lengths
     __shared__ val_t wa[WIN];
     __shared__ int32_t wlen[WIN], lidx[WIN], scan32[NT / 32 + 1];
     const int expected = D.cnt[b];
-    if (expected == 0) return;
+    if (expected <= cmin || expected > cmax) return;  // empty, or another launch's item
     const int64_t d = b / D.K;
     const int s = (int)(b - d * D.K);
     const int row = D.rows[d];
@@ -797,16 +797,16 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
     }
 }
 
+// Items whose count lies in (cmin, cmax]; with a work counter the grid is persistent.
 template <int NT, int MINB, bool REPLAY, bool WIDE>
 __global__ void __launch_bounds__(NT, MINB)
 k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_col, val_t *c_val, int64_t *err,
-             const int64_t *gate, int vcap) {
+             const int64_t *gate, int vcap, unsigned long long *counter, int cmin, int cmax) {
     __shared__ int64_t s_b;
     if (gated(gate)) return;
-    unsigned long long *q = D.dev_n != nullptr ? D.queue + 1 : nullptr;
     const int64_t nb = dense_items(D);
-    for (int64_t b = dense_next(q, 0, true, &s_b); b < nb; b = dense_next(q, b, false, &s_b))
-        dense_fill_item<NT, REPLAY, WIDE>(A, B, D, b, c_rp, c_col, c_val, err, vcap);
+    for (int64_t b = dense_next(counter, 0, true, &s_b); b < nb; b = dense_next(counter, b, false, &s_b))
+        dense_fill_item<NT, REPLAY, WIDE>(A, B, D, b, c_rp, c_col, c_val, err, vcap, cmin, cmax);
 }
 
 // One thread per dense item (precise method): the slices' offsets inside the row and the
@@ -826,6 +826,7 @@ __global__ void k_dense_rowsum(DenseArgs D, int32_t *nnzc) {
 constexpr int DENSE_COUNT_NT = 256;
 constexpr int DENSE_COUNT_FLAGS_MAX = 32768;
 constexpr int DENSE_FILL_NT = 512;
+constexpr int DENSE_FILL_TWO_MIN = 4096;  // smallest sum buffer worth a second CTA per SM
 
 // Bytes of a fill CTA's bitmap and rank directory for slices of W columns.
 static int dense_index_bytes(int W) { return (int)(2 * sizeof(int32_t) * (size_t)dense_nw4(W)); }
@@ -890,31 +891,52 @@ cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs 
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
-    // slices narrow enough for one sum per column take the single-pass form; the others hold
-    // the index, then as many sums as the rest of one CTA's shared memory holds
-    // (two CTAs per SM when two single-pass slices fit an SM's shared memory)
-    const bool wide = dense_fill_wide_bytes(D.W) <= dense_fill_max_dynamic(1);
-    const bool two = wide && dense_fill_wide_bytes(D.W) <= dense_fill_max_dynamic(2);
-    const int smem = wide ? dense_fill_wide_bytes(D.W) : dense_fill_max_dynamic(1) & ~15;
-    const int vcap = (smem - dense_index_bytes(D.W)) / (int)sizeof(val_t);
-    if (vcap < 32) return cudaErrorInvalidValue;
-    auto kern = !wide ? (replay ? k_dense_fill<DENSE_FILL_NT, 1, true, false> : k_dense_fill<DENSE_FILL_NT, 1, false, false>)
-                : two ? (replay ? k_dense_fill<DENSE_FILL_NT, 2, true, true> : k_dense_fill<DENSE_FILL_NT, 2, false, true>)
-                      : (replay ? k_dense_fill<DENSE_FILL_NT, 1, true, true> : k_dense_fill<DENSE_FILL_NT, 1, false, true>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    int64_t grid = nb;
-    if (D.dev_n != nullptr) {  // persistent grid over the items counted on the device
-        if (D.queue == nullptr) return cudaErrorInvalidValue;
-        e = cudaMemsetAsync(D.queue + 1, 0, sizeof(unsigned long long), st);
+    // one launch: a grid over the items, or a persistent grid taking them from counter q
+    auto go = [&](auto kern, int smem, int vcap, unsigned long long *q, int cmin, int cmax) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        grid = persistent_blocks((const void *)kern, DENSE_FILL_NT, smem, nb);
-        if (grid <= 0) return cudaErrorInvalidValue;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        int64_t grid = nb;
+        if (q != nullptr) {
+            e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
+            if (e != cudaSuccess) return e;
+            grid = persistent_blocks((const void *)kern, DENSE_FILL_NT, smem, nb);
+            if (grid <= 0) return cudaErrorInvalidValue;
+        }
+        kern<<<(unsigned)grid, DENSE_FILL_NT, smem, st>>>(A, B, D, c_rp, c_col, c_val, err, gate, vcap, q, cmin,
+                                                           cmax);
+        return cudaGetLastError();
+    };
+    if (D.dev_n != nullptr && D.queue == nullptr) return cudaErrorInvalidValue;
+    const int index = dense_index_bytes(D.W);
+    if (dense_fill_wide_bytes(D.W) <= dense_fill_max_dynamic(1)) {
+        // single-pass form (two CTAs per SM when two slices fit an SM's shared memory)
+        const int smem = dense_fill_wide_bytes(D.W);
+        const int vcap = (smem - index) / (int)sizeof(val_t);
+        unsigned long long *q = D.dev_n != nullptr ? D.queue + 1 : nullptr;
+        if (smem <= dense_fill_max_dynamic(2))
+            return replay ? go(k_dense_fill<DENSE_FILL_NT, 2, true, true>, smem, vcap, q, 0, INT32_MAX)
+                          : go(k_dense_fill<DENSE_FILL_NT, 2, false, true>, smem, vcap, q, 0, INT32_MAX);
+        return replay ? go(k_dense_fill<DENSE_FILL_NT, 1, true, true>, smem, vcap, q, 0, INT32_MAX)
+                      : go(k_dense_fill<DENSE_FILL_NT, 1, false, true>, smem, vcap, q, 0, INT32_MAX);
     }
-    kern<<<(unsigned)grid, DENSE_FILL_NT, smem, st>>>(A, B, D, c_rp, c_col, c_val, err, gate, vcap);
-    return cudaGetLastError();
+    // compact form: the index, then as many sums as the rest of the CTA's shared memory holds.
+    // With work counters, the items whose slices have at most vcap2 entries run at two CTAs per
+    // SM (half the shared memory each), the others at one
+    const int smem1 = dense_fill_max_dynamic(1) & ~15, smem2 = dense_fill_max_dynamic(2) & ~15;
+    const int vcap1 = (smem1 - index) / (int)sizeof(val_t), vcap2 = (smem2 - index) / (int)sizeof(val_t);
+    if (vcap1 < 32) return cudaErrorInvalidValue;
+    if (D.queue != nullptr && vcap2 >= DENSE_FILL_TWO_MIN) {
+        cudaError_t e = replay ? go(k_dense_fill<DENSE_FILL_NT, 2, true, false>, smem2, vcap2, D.queue + 1, 0, vcap2)
+                               : go(k_dense_fill<DENSE_FILL_NT, 2, false, false>, smem2, vcap2, D.queue + 1, 0, vcap2);
+        if (e != cudaSuccess) return e;
+        return replay ? go(k_dense_fill<DENSE_FILL_NT, 1, true, false>, smem1, vcap1, D.queue + 2, vcap2, INT32_MAX)
+                      : go(k_dense_fill<DENSE_FILL_NT, 1, false, false>, smem1, vcap1, D.queue + 2, vcap2, INT32_MAX);
+    }
+    unsigned long long *q = D.dev_n != nullptr ? D.queue + 1 : nullptr;
+    return replay ? go(k_dense_fill<DENSE_FILL_NT, 1, true, false>, smem1, vcap1, q, 0, INT32_MAX)
+                  : go(k_dense_fill<DENSE_FILL_NT, 1, false, false>, smem1, vcap1, q, 0, INT32_MAX);
 }
 
 }  // namespace spg

@@ -212,7 +212,8 @@ struct DenseArgs {
     int32_t *soff;         // n K offsets of the slices inside their row of C
     const int64_t *dev_n = nullptr;  // when set: the number of dense items is *dev_n (<= n), read on
                                      // the device; the kernels run persistent grids over (item, slice)
-    unsigned long long *queue = nullptr;  // with dev_n: two work counters (count, fill), zeroed by the launchers
+    unsigned long long *queue = nullptr;  // three work counters (count, fill, fill of the heavy items),
+                                          // zeroed by the launchers; needed with dev_n
 };
 cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cudaStream_t st);
 // per row: flag (1 = dense-slice row: bin 37, and u_i >= dmin if dmin > 0, else div u_i >= the

@@ -174,8 +174,10 @@ struct spgemm_plan {
     int32_t *dense_cnt = nullptr, *dense_soff = nullptr;
     cudaEvent_t dense_count_done = nullptr;  // the counts' stream reached the end of the counting pass
     DenseArgs dense_args() const {
-        return DenseArgs{dense_order, dense_rows, dense_clo, dense_chi, dense_n, dense_K, dense_W, dense_bnd,
-                         dense_cnt, dense_soff};
+        DenseArgs D{dense_order, dense_rows, dense_clo, dense_chi, dense_n, dense_K, dense_W, dense_bnd,
+                    dense_cnt, dense_soff};
+        D.queue = d_queue;
+        return D;
     }
     // batched plans: the pairs and the concatenation offsets
     int64_t npairs = 0;
@@ -634,6 +636,7 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
             }
             SPG_TRY(p->alloc_n(&p->dense_cnt, p->dense_n * p->dense_K));
             SPG_TRY(p->alloc_n(&p->dense_soff, p->dense_n * p->dense_K));
+            SPG_TRY(p->alloc_n(&p->d_queue, 3));  // work counters of the fill launches
         }
         // C~ (hybrid: u_i for bins 0..36, 256 for bin 37)
         SPG_TRY(p->alloc_n(&p->ctil_col, p->h_summary.sum_cap, LIFE_NUMERIC));
@@ -1859,7 +1862,7 @@ static spgemm_status dplan_buffers(spgemm_dplan *d) {
         SPG_TRY(p->alloc_n(&p->d_summary, 1));
         SPG_TRY(p->alloc_n(&p->d_err, 1));
         SPG_TRY(p->alloc_n(&d->gate, 1));
-        SPG_TRY(p->alloc_n(&p->d_queue, 2));
+        SPG_TRY(p->alloc_n(&p->d_queue, 3));
         SPG_TRY(p->alloc_n(&p->S, nnzA + 1));
         SPG_TRY(p->alloc_n(&p->scan_partial, std::max(bound_partial_size(nnzA), bin_blocks(m) + 1) + 1));
         SPG_TRY(p->alloc_n(&p->u, m));
