@@ -70,24 +70,42 @@ void *get_pinned() {
     return p;
 }
 
-// Auxiliary streams per device (created once, kept for the process): the learned
-// launch classes of bin 37 run on them concurrently, so one class's tail of long
-// CTAs overlaps the next class instead of idling the SMs.
+// Auxiliary streams (created once, kept for the process): the learned launch classes of
+// bin 37 run on them concurrently, so one class's tail of long CTAs overlaps the next class
+// instead of idling the SMs, and the dense-slice kernels run beside the merge kernels.  Each
+// stream a plan runs on gets aux streams of its own (up to MAX_AUX_OWNERS streams per device,
+// beyond which the last set is shared), so plans on different streams stay independent.
 constexpr int NUM_AUX_STREAMS = 5;
 constexpr int DENSE_AUX = NUM_AUX_STREAMS - 1;  // the dense-slice kernels; the others take the launch classes
+constexpr size_t MAX_AUX_OWNERS = 16;
+struct AuxSet {
+    int device;
+    cudaStream_t owner;
+    std::vector<cudaStream_t> s;
+};
 std::mutex g_aux_mu;
-std::vector<std::vector<cudaStream_t>> g_aux;
+std::vector<AuxSet> g_aux;
 
-cudaStream_t aux_stream(int device, int i) {
+cudaStream_t aux_stream(int device, cudaStream_t owner, int i) {
     std::lock_guard<std::mutex> lk(g_aux_mu);
-    if ((int)g_aux.size() <= device) g_aux.resize(device + 1);
-    auto &v = g_aux[device];
-    while ((int)v.size() < NUM_AUX_STREAMS) {
-        cudaStream_t s = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-        v.push_back(s);
+    AuxSet *set = nullptr;
+    size_t on_device = 0;
+    for (auto &a : g_aux) {
+        if (a.device != device) continue;
+        ++on_device;
+        set = &a;  // the device's last set, unless the owner has one
+        if (a.owner == owner) break;
     }
-    return v[i % NUM_AUX_STREAMS];
+    if (set == nullptr || (set->owner != owner && on_device < MAX_AUX_OWNERS)) {
+        g_aux.push_back(AuxSet{device, owner, {}});
+        set = &g_aux.back();
+    }
+    while ((int)set->s.size() < NUM_AUX_STREAMS) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        set->s.push_back(st);
+    }
+    return set->s[i % NUM_AUX_STREAMS];
 }
 
 void put_pinned(void *p) {
@@ -900,7 +918,7 @@ static spgemm_status launch_dense_counts(spgemm_plan *p) {
     {
         cudaStream_t ds = p->st;
         if (!p->opts.record_timing) {
-            ds = aux_stream(p->device, DENSE_AUX);
+            ds = aux_stream(p->device, p->st, DENSE_AUX);
             if (ds == nullptr) return SPGEMM_ERR_CUDA;
             cudaEvent_t go = nullptr;
             SPG_TRY(cudaEventCreateWithFlags(&go, cudaEventDisableTiming));
@@ -993,7 +1011,7 @@ spgemm_status run_bin37(spgemm_plan *p) {
                 if (cnt == 0) continue;
                 cudaStream_t cs = p->st;
                 if (concurrent) {
-                    cs = aux_stream(p->device, nlaunched % DENSE_AUX);
+                    cs = aux_stream(p->device, p->st, nlaunched % DENSE_AUX);
                     if (cs == nullptr) {
                         status = SPGEMM_ERR_CUDA;
                         goto fail;
@@ -1142,7 +1160,7 @@ extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
             // the other rows (their own stream unless every kernel is timed)
             cudaStream_t ds = p->st;
             if (!p->opts.record_timing) {
-                ds = aux_stream(p->device, DENSE_AUX);
+                ds = aux_stream(p->device, p->st, DENSE_AUX);
                 if (ds == nullptr) {
                     status = SPGEMM_ERR_CUDA;
                     goto fail;
