@@ -800,14 +800,11 @@ def run_e2e(args, spg, pairs, dev, stream, opts, world=1):
     """Same metric through the public API with host buffers: every step copies A from pinned
     host memory to the device, computes C = A*A and reads every byte of C (row pointers,
     columns, values) back to the host.  A result of at most STAGE_BYTES lands in pinned host
-    arrays; a larger one streams through a pinned staging buffer of STAGE_BYTES in chunks,
+    arrays; a larger one streams through one pinned staging buffer of STAGE_BYTES in chunks,
     each chunk overwriting the previous one (the host keeps no copy), so a run pins a bounded
-    amount of host memory whatever the size of C.
-
-    Two steps are in flight, on two streams: one step's copy of C to the host overlaps the
-    next step's product (each stream has its own staging buffer and keeps its step's C alive
-    until its copy is done).  The value is the products of `reps` steps over the wall time of
-    those steps, after two untimed ones.  serial_ms_per_step times one step alone (median)."""
+    amount of host memory whatever the size of C.  One step at a time, each bracketed by a
+    device synchronisation; the value is the median step.  (Keeping two steps in flight on
+    two streams, so that one step's copy of C overlaps the next product, measured slower.)"""
     import torch
     if len(pairs) != 1 or pairs[0][1] is not pairs[0][0]:
         return None
@@ -816,69 +813,50 @@ def run_e2e(args, spg, pairs, dev, stream, opts, world=1):
           for x in (A.row_ptr.astype(np.int32), A.col, A.val)]
     h2d = sum(t.numel() * t.element_size() for t in hp)
     reps = max(3, min(args.steps, 10))
-    streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    out_host = [None, None]
-    staging = [None, None]
-    keep = [None, None]
+    times, d2h = [], 0
+    out_host = None
+    staging = None
 
-    def read_back(C, slot):
+    def read_back(C):
+        nonlocal out_host, staging
         srcs = (C.row_ptr, C.col, C.val)
         total = sum(t.numel() * t.element_size() for t in srcs)
         if total <= STAGE_BYTES:
-            if out_host[slot] is None or out_host[slot][1].numel() != C.nnz:
-                out_host[slot] = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in srcs]
-            for h, d in zip(out_host[slot], srcs):
+            if out_host is None or out_host[1].numel() != C.nnz:
+                out_host = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in srcs]
+            for h, d in zip(out_host, srcs):
                 h.copy_(d, non_blocking=True)
             return total, "pinned host arrays"
-        if staging[slot] is None:
-            staging[slot] = torch.empty(STAGE_BYTES, dtype=torch.uint8).pin_memory()
+        if staging is None:
+            staging = torch.empty(STAGE_BYTES, dtype=torch.uint8).pin_memory()
         for d in srcs:
             b = d.view(torch.uint8)
             for off in range(0, b.numel(), STAGE_BYTES):
                 n = min(STAGE_BYTES, b.numel() - off)
-                staging[slot][:n].copy_(b[off:off + n], non_blocking=True)
-        return total, f"streamed through a {STAGE_BYTES >> 20} MiB pinned staging buffer per stream"
+                staging[:n].copy_(b[off:off + n], non_blocking=True)
+        return total, f"streamed through one {STAGE_BYTES >> 20} MiB pinned staging buffer"
 
-    def one_step(k):
-        slot = k % 2
-        s = streams[slot]
-        keep[slot] = None  # the step two before: its copy is ordered on this stream before any new work
-        with torch.cuda.stream(s):
-            rp, col, val = (t.to(dev, non_blocking=True) for t in hp)
-            Ad = spg.CSR(rp, col, val, (A.nrows, A.ncols))
-            plan = spg.Plan(Ad, Ad, stream=s, **opts)
-            C = plan.numeric()
-            nbytes, how = read_back(C, slot)
-        keep[slot] = (plan, C, Ad)  # alive until its copy to the host is done
-        return nbytes, how
-
-    # one step alone, synchronously (median of three)
-    serial = []
-    for k in range(3):
+    how = None
+    for k in range(reps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        d2h, how = one_step(0)
+        with torch.cuda.stream(stream):
+            rp, col, val = (t.to(dev, non_blocking=True) for t in hp)
+            Ad = spg.CSR(rp, col, val, (A.nrows, A.ncols))
+            C = spg.Plan(Ad, Ad, stream=stream, **opts).numeric()
+            d2h, how = read_back(C)
         torch.cuda.synchronize()
-        serial.append(time.perf_counter() - t0)
-    # two steps in flight
-    for k in range(2):
-        one_step(k)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(reps):
-        d2h, how = one_step(k)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    keep[0] = keep[1] = None
+        dt = time.perf_counter() - t0
+        del C, Ad
+        if k > 0:
+            times.append(dt)
     del staging, out_host
-    torch.cuda.synchronize()
     u_sum = int(_products(A))
-    value, ms = job_gflops(u_sum, wall / reps * 1e3, world, dev)
+    value, ms = job_gflops(u_sum, float(np.median(times)) * 1e3, world, dev)
     return {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": ms, "steps": reps,
-            "serial_ms_per_step": float(np.median(serial)) * 1e3,
-            "note": f"{reps} steps after 2 untimed, two in flight on two streams (one step's copy of C overlaps "
-                    f"the next step's product); A copied from pinned host memory, C {how}"}
+            "note": f"median of {reps} steps after 1 untimed, one at a time; A copied from pinned host memory, "
+                    f"C {how}"}
 
 
 def _products(A):
