@@ -179,6 +179,16 @@ typedef struct spgemm_opts {
     int32_t dense_pred_min;  /* learned policy: a bin-37 row whose predicted nnz(c_i) is at least this
                                 is computed by the dense-slice kernels (the network's choice of
                                 kernel as well as of size); 0 = off */
+    int32_t dense_keep;      /* slices wider than 32,768 columns (counted with a bitmap, filled in the
+                                compact form): the counting pass leaves every (row, slice)'s column
+                                bitmap in device memory (ceil(W / 32) + 1 words, rounded up to 4, per
+                                (row, slice), released when spgemm_numeric returns) and the fill reads
+                                it back instead of marking the columns again from the products.
+                                0 = kept by the hybrid, upper-bound and learned policies when the
+                                bitmaps take at most a quarter of the free device memory, never by the
+                                precise policy (whose peak stays C plus O(rows) tables); positive = the
+                                same test under every policy; negative = never.  Products sized on the
+                                device never keep them (their tables are sized for every row) */
 } spgemm_opts;
 
 /* Fills *opts with the defaults (hybrid policy, initial_cap 256, no checks). */

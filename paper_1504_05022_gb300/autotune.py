@@ -21,7 +21,9 @@ measured device time, over the parameters the library exposes for that choice:
 * dense_span   - the slices' width (and with it their form: one sum per column of a
                  narrow slice, or a bitmap with compact sums for a wide one);
 * dense_pred_min - the learned policy's choice of kernel: rows predicted at least this
-                 long go to the dense column slices.
+                 long go to the dense column slices;
+* dense_keep   - whether the slices' counting pass leaves its column bitmaps for the
+                 fill (device memory for a pass over the products).
 
 A configuration is kept only if it is faster and its peak device memory stays
 within 5% of the default configuration's, so tuning never buys time with memory.
@@ -65,14 +67,15 @@ SPACE = {
                                              # enough for a sum per column: the single-pass form
     "dense_span_div": [0, 16, 4, 64],     # 0 = 8: dense when 8 u_i >= the row's column range
     "dense_pred_min": [0, 12288, 6144, 3072],  # learned: predicted nnz(c_i) that sends a row to the slices
+    "dense_keep": [0, -1],                # 0 = the count leaves its bitmaps for the compact fill, -1 = never
 }
 POLICY_PARAMS = {
     "hybrid": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "merge_miss",
-               "initial_cap", "dense_min_u", "dense_span", "dense_span_div"],
+               "initial_cap", "dense_min_u", "dense_span", "dense_span_div", "dense_keep"],
     "learned": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "merge_miss",
-                "predictor_margin", "dense_min_u", "dense_span", "dense_span_div", "dense_pred_min"],
+                "predictor_margin", "dense_min_u", "dense_span", "dense_span_div", "dense_pred_min", "dense_keep"],
     "upper_bound": ["heap_max_u", "heap_block", "merge_batch", "smem_cap_max", "merge_wide_above", "dense_min_u",
-                    "dense_span", "dense_span_div"],
+                    "dense_span", "dense_span_div", "dense_keep"],
 }
 MEMORY_SLACK = 1.05
 

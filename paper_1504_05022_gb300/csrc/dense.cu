@@ -5,7 +5,8 @@
 // B's columns are cut into K slices of W columns (W a multiple of 32, at most
 // DENSE_W_MAX, K W >= ncols).  A slice of a row is one CTA.  The counting pass marks
 // the columns of the row's products in the slice in a shared bitmap and counts its
-// bits.  The fill pass marks them again, ranks the bitmap (set bits before each word),
+// bits, and may leave the bitmap in device memory.  The fill pass reads it back (or marks
+// the columns again when it was not kept), ranks the bitmap (set bits before each word),
 // and adds every product into a compact buffer of sums, one per column of the result,
 // at its column's rank: clearing and writing out cost the slice's entries, not its
 // width, and the sums come out in column order.  There are no misses, no merges and no
@@ -14,9 +15,10 @@
 // boundaries, built once per call, and is cut into chunks of consecutive entries that
 // the warps share out.
 //
-// Because the rows are counted first, they need no temporary space at all: their sizes
+// Because the rows are counted first, they need no temporary result rows: their sizes
 // go into the row counts of C with the other rows', and the values are written
-// straight into C once its row pointers exist.  The same launch recomputes the values
+// straight into C once its row pointers exist (the kept bitmaps, W / 8 bytes per
+// (row, slice), are the only temporary, and an optional one).  The same launch recomputes the values
 // for a values-only replay.
 #include "internal.h"
 #include "common.cuh"
@@ -382,6 +384,12 @@ SPG_DEV void dense_count_item(const DevCSR &A, const DevCSR &B, const DenseArgs 
         bad = dense_bitmap<NT>(A, B, D, D.rows[d], s, lo, span, dc_bm, wbs, cscan, scan64);
         const int nw = (span + 31) >> 5;
         for (int w = threadIdx.x; w < nw; w += NT) n += __popc(dc_bm[w]);
+        if (D.keep != nullptr) {
+            // the bitmap, in whole 16-byte groups (the words past the span were cleared), for the fill
+            const uint4 *b4 = reinterpret_cast<const uint4 *>(dc_bm);
+            uint4 *k4 = reinterpret_cast<uint4 *>(D.keep + b * (int64_t)D.keep_words);
+            for (int q = threadIdx.x; q < (nw + 3) >> 2; q += NT) k4[q] = b4[q];
+        }
     }
     n = block_reduce_sum<NT, int>(n, scan32);
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch((unsigned long long *)err, 5ull);
@@ -734,6 +742,12 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
             bitmap_set_warp(Bm, x, in);
         }
         __syncthreads();
+    } else if (D.keep != nullptr) {
+        // the bitmap the counting pass left for this (row, slice)
+        const uint4 *k4 = reinterpret_cast<const uint4 *>(D.keep + b * (int64_t)D.keep_words);
+        uint4 *b4 = reinterpret_cast<uint4 *>(Bm);
+        for (int q = threadIdx.x; q < (nwords + 3) >> 2; q += NT) b4[q] = __ldg(k4 + q);
+        __syncthreads();
     } else {
         bad = dense_bitmap<NT>(A, B, D, row, s, lo, span, Bm, wbs, cscan, scan64);
     }
@@ -851,12 +865,19 @@ int dense_fill_static_smem() {
                  (DENSE_FILL_NT / 32 + 1) * 12 + 64);
 }
 
+int dense_keep_words(int W) {
+    if (W <= DENSE_COUNT_FLAGS_MAX || dense_fill_wide_bytes(W) <= dense_fill_max_dynamic(1)) return 0;
+    return dense_nw4(W);  // a multiple of 4: every item's bitmap starts on a 16-byte boundary
+}
+
 cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t *err, cudaStream_t st) {
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
     // flag bytes for slices of up to DENSE_COUNT_FLAGS_MAX columns, else the bitmap
     const bool flags = D.W <= DENSE_COUNT_FLAGS_MAX;
+    if (D.keep != nullptr && (flags || D.keep_words < dense_nw4(D.W) || D.keep_words % 4 != 0))
+        return cudaErrorInvalidValue;
     const int smem = flags ? D.W : (int)(sizeof(uint32_t) * dense_nw4(D.W));
     auto kern = flags ? k_dense_count<DENSE_COUNT_NT, true> : k_dense_count<DENSE_COUNT_NT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -891,6 +912,7 @@ cudaError_t launch_dense_fill(const DevCSR &A, const DevCSR &B, const DenseArgs 
     if (D.n <= 0) return cudaSuccess;
     const int64_t nb = D.n * D.K;
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
+    if (D.keep != nullptr && (D.keep_words < dense_nw4(D.W) || D.keep_words % 4 != 0)) return cudaErrorInvalidValue;
     // one launch: a grid over the items, or a persistent grid taking them from counter q
     auto go = [&](auto kern, int smem, int vcap, unsigned long long *q, int cmin, int cmax) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

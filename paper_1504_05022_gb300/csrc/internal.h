@@ -214,6 +214,9 @@ struct DenseArgs {
                                      // the device; the kernels run persistent grids over (item, slice)
     unsigned long long *queue = nullptr;  // three work counters (count, fill, fill of the heavy items),
                                           // zeroed by the launchers; needed with dev_n
+    uint32_t *keep = nullptr;  // when set (bitmap counts, compact fills only): keep_words words per
+    int keep_words = 0;        // (row, slice), where the count leaves the slice's column bitmap and
+                               // the fill reads it back instead of marking the columns again
 };
 cudaError_t launch_dense_bounds(const DevCSR &B, int K, int W, int32_t *bnd, cudaStream_t st);
 // per row: flag (1 = dense-slice row: bin 37, and u_i >= dmin if dmin > 0, else div u_i >= the
@@ -229,6 +232,9 @@ cudaError_t launch_dense_select(const int32_t *bin_rows, int64_t m, BinSummary *
 // counts the columns of every (row, slice) into D.cnt (reads no work-item table, so it
 // may run beside the merge launches)
 cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs &D, int64_t *err, cudaStream_t st);
+// Words per (row, slice) of a kept column bitmap for slices of W columns, or 0 when the count
+// does not build bitmaps for such slices or the fill does not read them (the single-pass form).
+int dense_keep_words(int W);
 // slice offsets inside the rows, and the dense items' lengths in the work-item table
 cudaError_t launch_dense_rows(const MergeItems &it, const DenseArgs &D, cudaStream_t st);
 // precise method: slice offsets inside the rows, and nnz(c_i) of every dense row into nnzc

@@ -190,11 +190,15 @@ struct spgemm_plan {
     int32_t *dense_clo = nullptr, *dense_chi = nullptr;  // and their column ranges
     int32_t *dense_bnd = nullptr;         // per B row, K + 1 slice boundaries (K > 1)
     int32_t *dense_cnt = nullptr, *dense_soff = nullptr;
+    uint32_t *dense_keep = nullptr;  // the counting pass's column bitmaps, kept for the fill (numeric only)
+    int dense_keep_words = 0;        // words per (row, slice) of dense_keep
     cudaEvent_t dense_count_done = nullptr;  // the counts' stream reached the end of the counting pass
     DenseArgs dense_args() const {
         DenseArgs D{dense_order, dense_rows, dense_clo, dense_chi, dense_n, dense_K, dense_W, dense_bnd,
                     dense_cnt, dense_soff};
         D.queue = d_queue;
+        D.keep = dense_keep;
+        D.keep_words = dense_keep_words;
         return D;
     }
     // batched plans: the pairs and the concatenation offsets
@@ -909,6 +913,31 @@ fail:
     return status;
 }
 
+// The column bitmaps that the slices' counting pass leaves for the fill (opts.dense_keep):
+// only where the count builds bitmaps and the fill is the compact form, never by default in
+// the precise method, and only while they take at most a quarter of the free device memory.
+// Released with the other numeric temporaries; without them the fill marks the columns again.
+static void alloc_dense_keep(spgemm_plan *p) {
+    p->dense_keep = nullptr;
+    p->dense_keep_words = 0;
+    const int want = p->opts.dense_keep;
+    const int kw = p->dense_K > 0 ? dense_keep_words(p->dense_W) : 0;
+    if (p->dense_n == 0 || kw == 0 || want < 0 || (want == 0 && p->opts.alloc_policy == SPGEMM_ALLOC_PRECISE))
+        return;
+    const int64_t words = p->dense_n * p->dense_K * (int64_t)kw;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if ((uint64_t)words * sizeof(uint32_t) > free_b / 4) return;
+    if (p->alloc_n(&p->dense_keep, words, LIFE_NUMERIC) != cudaSuccess) {
+        p->dense_keep = nullptr;
+        return;
+    }
+    p->dense_keep_words = kw;
+}
+
 // Dense-slice rows: their column counts, launched first in stage 3 on their own
 // stream (unless every kernel is timed), beside the heap, ESC and merge kernels; the
 // event joins them before the row sizes are finalised.
@@ -1129,6 +1158,7 @@ extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
     StageArgs a = stage_args(p);
     {
         // ---- stage 3: the dense-slice rows' counts, then bin groups 3 (heap) and 4 (bitonic ESC) ----
+        if (p->h_summary.bin_count[BIN_MERGE] > 0) alloc_dense_keep(p);
         status = launch_dense_counts(p);
         if (status != SPGEMM_OK) goto fail;
         SPG_TRY(launch_short_bins(p, a, true));
@@ -1207,6 +1237,8 @@ extern "C" spgemm_status spgemm_numeric(spgemm_plan *p, spgemm_csr_out *C_out) {
         p->stats.bytes_ctilde = p->bytes_ctilde;
         p->numeric_done = true;
         p->release_temps(LIFE_NUMERIC);
+        p->dense_keep = nullptr;  // released above: a values-only replay marks the columns from C
+        p->dense_keep_words = 0;
         *C_out = p->C;
     }
     return SPGEMM_OK;
@@ -1752,6 +1784,8 @@ static DenseArgs dense_args_of(const spgemm_plan *p, bool dev) {
         D.n = p->A.nrows;  // every row may be in bin 37: the arrays hold n K entries
         D.dev_n = &p->d_summary->dense_count;
         D.queue = p->d_queue;
+        D.keep = nullptr;  // tables sized for every row: no room kept for bitmaps
+        D.keep_words = 0;
     }
     return D;
 }
@@ -1823,6 +1857,7 @@ static spgemm_status run_precise(spgemm_plan *p, spgemm_csr_out *C_out) {
     spgemm_status status = SPGEMM_OK;
     const int64_t m = p->A.nrows;
     {
+        alloc_dense_keep(p);
         SPG_TRY(precise_count(p, false));
         SPG_TRY(p->alloc_n(&p->C.row_ptr, m + 1));
         p->time_begin(SPGEMM_K_SCAN);
@@ -1846,6 +1881,8 @@ static spgemm_status run_precise(spgemm_plan *p, spgemm_csr_out *C_out) {
         p->stats.bytes_ctilde = p->bytes_ctilde;
         p->numeric_done = true;
         p->release_temps(LIFE_NUMERIC);
+        p->dense_keep = nullptr;  // released above: a values-only replay marks the columns from C
+        p->dense_keep_words = 0;
         *C_out = p->C;
     }
     return SPGEMM_OK;

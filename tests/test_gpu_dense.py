@@ -242,3 +242,50 @@ def test_learned_kernel_choice_sends_long_rows_to_the_slices(spg, oracle_mod):
     assert st["rows_dense"] > st0["rows_dense"]
     assert st["item_rounds"] < st0["item_rounds"]
     plan.check()
+
+
+def _kept_bytes(st, W):
+    """Bytes of the kept bitmaps: ceil(W / 32) + 1 words rounded up to 4, per (row, slice)."""
+    return st["rows_dense"] * st["dense_slices"] * 4 * (((W + 31) // 32 + 4) & ~3)
+
+
+@pytest.mark.parametrize("case", ["square", "rect"])
+@pytest.mark.parametrize("policy", ["hybrid", "learned", "precise"])
+def test_dense_kept_bitmaps(spg, oracle_mod, case, policy):
+    """Slices wider than 32,768 columns are counted with a bitmap, which the counting pass may
+    leave in device memory for the compact fill instead of the fill marking the columns again
+    (dense_keep).  C is the oracle's with the bitmaps kept and without; the precise policy keeps
+    them only when asked, and its peak then grows by exactly their size; a values-only replay
+    afterwards (the bitmaps are gone) is exact too."""
+    if case == "square":
+        A = B = gen.rmat(16, 8, seed=71)  # one slice of 65,536 columns
+        kw = {}
+        W = 65536
+    else:
+        A = gen.rmat(13, 24, seed=72)
+        B = gen.erdos_renyi(8192, 40, seed=73, ncols=100001)
+        kw = {"dense_span": 65536, "dense_min_u": 600}  # two slices of 50,016 columns
+        W = 50016
+    opts, _keep = _policy_opts(policy)
+    peaks = {}
+    for keep in (-1, 0, 1):
+        plan, C, Ad = _run(spg, A, B, dense_keep=keep, **kw, **opts)
+        _check(oracle_mod, A, B, C, label=f"kept bitmaps {case}/{policy}/{keep}")
+        st = plan.stats()
+        assert st["rows_dense"] > 0 and st["dense_slices"] == (1 if case == "square" else 2)
+        peaks[keep] = st["peak_bytes"]
+        if keep == 1 and case == "square":
+            rng = np.random.default_rng(74)
+            A2 = gen.HostCSR(A.nrows, A.ncols, A.row_ptr, A.col, rng.uniform(-1, 1, A.nnz))
+            Ad.val.copy_(torch.from_numpy(A2.val))
+            plan.replay()
+            torch.cuda.synchronize()
+            plan.check()
+            _check(oracle_mod, A2, A2, C, label=f"kept bitmaps replay {policy}")
+    kb = _kept_bytes(st, W)
+    if policy == "precise":
+        assert peaks[0] == peaks[-1]
+        assert peaks[1] - peaks[-1] == kb
+    else:
+        assert peaks[0] == peaks[1]
+        assert peaks[-1] <= peaks[0] <= peaks[-1] + kb
