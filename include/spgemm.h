@@ -179,9 +179,9 @@ typedef struct spgemm_opts {
     int32_t dense_pred_min;  /* learned policy: a bin-37 row whose predicted nnz(c_i) is at least this
                                 is computed by the dense-slice kernels (the network's choice of
                                 kernel as well as of size); 0 = off */
-    int32_t dense_keep;      /* slices wider than 32,768 columns (counted with a bitmap, filled in the
-                                compact form): the counting pass leaves every (row, slice)'s column
-                                bitmap in device memory (ceil(W / 32) + 1 words, rounded up to 4, per
+    int32_t dense_keep;      /* slices too wide for the single-pass fill (about 21,900 columns in
+                                double, 40,000 in float), which the compact form fills: the counting
+                                pass leaves every (row, slice)'s column bitmap in device memory (ceil(W / 32) + 1 words, rounded up to 4, per
                                 (row, slice), released when spgemm_numeric returns) and the fill reads
                                 it back instead of marking the columns again from the products.
                                 0 = kept by the hybrid, upper-bound and learned policies when the

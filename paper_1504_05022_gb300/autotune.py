@@ -63,8 +63,9 @@ SPACE = {
     "initial_cap": [256, 512, 1024],
     "predictor_margin": [None, 1.15, 1.5, 2.0],  # None = the margin stored with the weights
     "dense_min_u": [0, 16384, 4096, -1],  # 0 = the rule of dense_span_div, -1 = no dense-slice rows
-    "dense_span": [0, 21856, 16384, 10912],  # 0 = 131,072-column slices (bitmap, compact sums); narrow
-                                             # enough for a sum per column: the single-pass form
+    "dense_span": [0, 65536, 32768, 21856, 16384, 10912],  # 0 = 131,072-column slices (bitmap, compact
+                                                           # sums); narrow enough for a sum per column
+                                                           # (21,856 and below in double): single-pass
     "dense_span_div": [0, 16, 4, 64],     # 0 = 8: dense when 8 u_i >= the row's column range
     "dense_pred_min": [0, 12288, 6144, 3072],  # learned: predicted nnz(c_i) that sends a row to the slices
     "dense_keep": [0, -1],                # 0 = the count leaves its bitmaps for the compact fill, -1 = never

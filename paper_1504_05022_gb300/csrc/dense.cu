@@ -355,7 +355,7 @@ SPG_DEV void dense_count_item(const DevCSR &A, const DevCSR &B, const DenseArgs 
     bool bad = false;
     int n = 0;
     if constexpr (FLAGS) {
-        const int nq = (span + 15) >> 4;  // 16-byte groups of flags
+        const int nq = ((span + 31) >> 5) << 1;  // 16-byte groups of flags, whole 32-column words
         uint4 *f4 = reinterpret_cast<uint4 *>(dc_bm);
         for (int q = threadIdx.x; q < nq; q += NT) f4[q] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
@@ -379,6 +379,25 @@ SPG_DEV void dense_count_item(const DevCSR &A, const DevCSR &B, const DenseArgs 
         for (int q = threadIdx.x; q < nq; q += NT) {
             const uint4 v = f4[q];
             n += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        }
+        if (D.keep != nullptr) {
+            // the flags as a bitmap (32 columns per word, whole 16-byte groups), for the fill
+            uint32_t *kb = D.keep + b * (int64_t)D.keep_words;
+            const int nw = (span + 31) >> 5;
+            for (int w = threadIdx.x; w < ((nw + 3) & ~3); w += NT) {
+                uint32_t m = 0;
+                if (w < nw) {
+                    const uint4 lo4 = f4[2 * w], hi4 = f4[2 * w + 1];
+                    const uint32_t q[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        // byte j of q[k] (0 or 1) is column 4k + j
+                        const uint32_t y = q[k];
+                        m |= ((y & 1u) | ((y >> 7) & 2u) | ((y >> 14) & 4u) | ((y >> 21) & 8u)) << (4 * k);
+                    }
+                }
+                kb[w] = m;
+            }
         }
     } else {
         bad = dense_bitmap<NT>(A, B, D, D.rows[d], s, lo, span, dc_bm, wbs, cscan, scan64);
@@ -866,7 +885,7 @@ int dense_fill_static_smem() {
 }
 
 int dense_keep_words(int W) {
-    if (W <= DENSE_COUNT_FLAGS_MAX || dense_fill_wide_bytes(W) <= dense_fill_max_dynamic(1)) return 0;
+    if (dense_fill_wide_bytes(W) <= dense_fill_max_dynamic(1)) return 0;
     return dense_nw4(W);  // a multiple of 4: every item's bitmap starts on a 16-byte boundary
 }
 
@@ -876,7 +895,7 @@ cudaError_t launch_dense_count(const DevCSR &A, const DevCSR &B, const DenseArgs
     if (nb > INT32_MAX || D.W % 32 != 0 || (int64_t)D.K * D.W < B.ncols) return cudaErrorInvalidValue;
     // flag bytes for slices of up to DENSE_COUNT_FLAGS_MAX columns, else the bitmap
     const bool flags = D.W <= DENSE_COUNT_FLAGS_MAX;
-    if (D.keep != nullptr && (flags || D.keep_words < dense_nw4(D.W) || D.keep_words % 4 != 0))
+    if (D.keep != nullptr && (D.keep_words < dense_nw4(D.W) || D.keep_words % 4 != 0))
         return cudaErrorInvalidValue;
     const int smem = flags ? D.W : (int)(sizeof(uint32_t) * dense_nw4(D.W));
     auto kern = flags ? k_dense_count<DENSE_COUNT_NT, true> : k_dense_count<DENSE_COUNT_NT, false>;

@@ -249,18 +249,23 @@ def _kept_bytes(st, W):
     return st["rows_dense"] * st["dense_slices"] * 4 * (((W + 31) // 32 + 4) & ~3)
 
 
-@pytest.mark.parametrize("case", ["square", "rect"])
+@pytest.mark.parametrize("case", ["square", "rect", "flags"])
 @pytest.mark.parametrize("policy", ["hybrid", "learned", "precise"])
 def test_dense_kept_bitmaps(spg, oracle_mod, case, policy):
-    """Slices wider than 32,768 columns are counted with a bitmap, which the counting pass may
-    leave in device memory for the compact fill instead of the fill marking the columns again
-    (dense_keep).  C is the oracle's with the bitmaps kept and without; the precise policy keeps
+    """Slices too wide for the single-pass fill are filled in the compact form; the counting pass
+    may leave each (row, slice)'s column bitmap in device memory for it, instead of the fill
+    marking the columns again (dense_keep): counted with a bitmap (slices wider than 32,768
+    columns), or with flag bytes turned into a bitmap (the "flags" case, 32,768 columns).  C is the oracle's with the bitmaps kept and without; the precise policy keeps
     them only when asked, and its peak then grows by exactly their size; a values-only replay
     afterwards (the bitmaps are gone) is exact too."""
     if case == "square":
         A = B = gen.rmat(16, 8, seed=71)  # one slice of 65,536 columns
         kw = {}
         W = 65536
+    elif case == "flags":
+        A = B = gen.rmat(15, 16, seed=75)  # one slice of 32,768 columns
+        kw = {}
+        W = 32768
     else:
         A = gen.rmat(13, 24, seed=72)
         B = gen.erdos_renyi(8192, 40, seed=73, ncols=100001)
@@ -272,7 +277,7 @@ def test_dense_kept_bitmaps(spg, oracle_mod, case, policy):
         plan, C, Ad = _run(spg, A, B, dense_keep=keep, **kw, **opts)
         _check(oracle_mod, A, B, C, label=f"kept bitmaps {case}/{policy}/{keep}")
         st = plan.stats()
-        assert st["rows_dense"] > 0 and st["dense_slices"] == (1 if case == "square" else 2)
+        assert st["rows_dense"] > 0 and st["dense_slices"] == (2 if case == "rect" else 1)
         peaks[keep] = st["peak_bytes"]
         if keep == 1 and case == "square":
             rng = np.random.default_rng(74)
