@@ -121,6 +121,8 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    INTERVAL_MS = 200
+
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
@@ -133,7 +135,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -284,8 +286,8 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
         plans, C = step()
         ev[k][1].record(stream)
         torch.cuda.synchronize()
-        for p in plans:
-            launches += sum(p.stats()["launches"].values())
+        # (no loop variable: a name left bound to a plan would keep its result alive into the next step)
+        launches += sum(sum(q.stats()["launches"].values()) for q in plans)
         if k < args.steps - 1:
             del plans, C
     torch.cuda.synchronize()
@@ -305,7 +307,7 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
     arrays = [p.arrays() for p in plans]
     sum_u = sum(p.upper_bound_nnz for p in plans)
     value, ms_step = job_gflops(sum_u, float(np.median(times)), world, dev)
-    res = {"policy": policy, "ms_per_step": ms_step, "value": value,
+    res = {"policy": policy, "ms_per_step": ms_step, "value": value, "ms_steps": [round(t, 3) for t in times],
            "kms": kms, "launches": launches, "wall_s": t_wall,
            "st_all": st_all, "arrays": arrays, "sum_u": sum_u, "nnz_C": int(st_all[-1]["nnz_c"]),
            "heap_max_u": opts.get("heap_max_u"),
@@ -754,6 +756,7 @@ def run_ours(args, rank, world, device):
         "e2e": e2e,
         "gpu_launches": int(main_m["launches"]),
         "wall_s_timed": main_m["wall_s"],
+        "ms_steps": main_m["ms_steps"],
         "kernel_ms_per_step": main_m["kms"],
         "memory": {"peak_bytes": main_m["peak_bytes"],
                    "c_bytes": int(main_m["nnz_C"]) * 12 + 8 * (int(main_m["arrays"][-1]["u"].shape[0]) + 1),

@@ -261,6 +261,9 @@ typedef struct spgemm_stats {
     int64_t item_rounds;        /* bin-37 work items summed over every launch of the bin-37 merge
                                    kernel: a row counts once per progressive round it runs in, and
                                    each half of a split row counts on its own */
+    double alloc_host_ms;       /* host milliseconds spent in the plan's device allocations (from a
+                                   stream-ordered pool: long when the pool must map new memory) */
+    int64_t allocs;             /* device allocations made by the plan */
 } spgemm_stats;
 
 /* Copies the plan's counters into *out.  Timings are read after synchronising

@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
                 ("merge_rounds", c_i64), ("rows_relaunched", c_i64), ("rows_level1", c_i64), ("rows_split", c_i64),
                 ("rows_fallback", c_i64), ("bytes_ctilde", c_i64), ("peak_bytes", c_i64),
                 ("launches", c_i32 * 8), ("kernel_ms", c_f32 * 8), ("held_bytes", c_i64), ("rows_dense", c_i64),
-                ("dense_slices", c_i64), ("item_rounds", c_i64)]
+                ("dense_slices", c_i64), ("item_rounds", c_i64), ("alloc_host_ms", c_f64), ("allocs", c_i64)]
 
 
 class PlanArrays(ctypes.Structure):

@@ -10,6 +10,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -234,7 +235,10 @@ struct spgemm_plan {
 
     cudaError_t alloc(void **p, size_t bytes, int life = LIFE_PLAN) {
         if (bytes == 0) bytes = 16;
+        const auto t0 = std::chrono::steady_clock::now();
         cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+        stats.alloc_host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        stats.allocs += 1;
         if (e != cudaSuccess) {
             *p = nullptr;
             cudaGetLastError();
@@ -1304,6 +1308,8 @@ extern "C" spgemm_status spgemm_plan_stats(spgemm_plan *p, spgemm_stats *out) {
         out->held_bytes += ws.held_bytes;
         out->rows_dense += ws.rows_dense;
         out->dense_slices = std::max(out->dense_slices, ws.dense_slices);
+        out->alloc_host_ms += ws.alloc_host_ms;
+        out->allocs += ws.allocs;
         for (int k = 0; k < SPGEMM_K_COUNT; ++k) {
             out->launches[k] += ws.launches[k];
             out->kernel_ms[k] += ws.kernel_ms[k];

@@ -214,6 +214,7 @@ class Plan:
             "rows_split": s.rows_split,
             "rows_fallback": s.rows_fallback, "bytes_ctilde": s.bytes_ctilde, "peak_bytes": s.peak_bytes, "held_bytes": s.held_bytes,
             "rows_dense": s.rows_dense, "dense_slices": s.dense_slices, "item_rounds": s.item_rounds,
+            "alloc_host_ms": s.alloc_host_ms, "allocs": s.allocs,
             "launches": dict(zip(_lib.KERNELS, list(s.launches))),
             "kernel_ms": dict(zip(_lib.KERNELS, [float(x) for x in s.kernel_ms])),
         }
