@@ -184,35 +184,38 @@ SPG_DEV void lower_bound_multi(const int32_t *a, int n, const int32_t (&key)[IPT
 }
 
 // Rank directory of a bitmap: Rd[w] = number of set bits in Bm[0..w) for w <
-// nwords; returns the total.  Each thread takes a run of consecutive words, read
-// and written as 16-byte vectors when the run is 4 words (Bm and Rd 16-byte
-// aligned).  scan32 needs NT/32 + 1 ints and must not be reused before the next
-// barrier after this call.  All threads call; ends with a barrier.
+// nwords; returns the total.  Each thread takes a run of consecutive words, a whole
+// number of 16-byte groups (Bm and Rd 16-byte aligned), read and written as vectors
+// (the last, partial group of the bitmap word by word).  scan32 needs NT/32 + 1 ints
+// and must not be reused before the next barrier after this call.  All threads
+// call; ends with a barrier.
 template <int NT>
 SPG_DEV int bitmap_rank(const uint32_t *Bm, int32_t *Rd, int nwords, int32_t *scan32) {
     const int per = ((nwords + NT - 1) / NT + 3) & ~3;
     const int w0 = threadIdx.x * per;
-    const bool vec = per == 4 && w0 + 4 <= nwords;
-    int c[4] = {0, 0, 0, 0};
+    const int w1 = min(nwords, w0 + per);
     int sum = 0;
-    if (vec) {
-        const uint4 b = *reinterpret_cast<const uint4 *>(Bm + w0);
-        c[0] = __popc(b.x);
-        c[1] = __popc(b.y);
-        c[2] = __popc(b.z);
-        c[3] = __popc(b.w);
-        sum = c[0] + c[1] + c[2] + c[3];
-    } else {
-        for (int w = w0; w < min(nwords, w0 + per); ++w) sum += __popc(Bm[w]);
+    for (int w = w0; w < w1; w += 4) {
+        if (w + 4 <= w1) {
+            const uint4 b = *reinterpret_cast<const uint4 *>(Bm + w);
+            sum += __popc(b.x) + __popc(b.y) + __popc(b.z) + __popc(b.w);
+        } else {
+            for (int k = w; k < w1; ++k) sum += __popc(Bm[k]);
+        }
     }
     int tot;
     int ex = block_exclusive_scan<NT, int, false>(sum, scan32, tot);
-    if (vec) {
-        *reinterpret_cast<int4 *>(Rd + w0) = make_int4(ex, ex + c[0], ex + c[0] + c[1], ex + c[0] + c[1] + c[2]);
-    } else {
-        for (int w = w0; w < min(nwords, w0 + per); ++w) {
-            Rd[w] = ex;
-            ex += __popc(Bm[w]);
+    for (int w = w0; w < w1; w += 4) {
+        if (w + 4 <= w1) {
+            const uint4 b = *reinterpret_cast<const uint4 *>(Bm + w);
+            const int c0 = __popc(b.x), c1 = __popc(b.y), c2 = __popc(b.z);
+            *reinterpret_cast<int4 *>(Rd + w) = make_int4(ex, ex + c0, ex + c0 + c1, ex + c0 + c1 + c2);
+            ex += c0 + c1 + c2 + __popc(b.w);
+        } else {
+            for (int k = w; k < w1; ++k) {
+                Rd[k] = ex;
+                ex += __popc(Bm[k]);
+            }
         }
     }
     __syncthreads();

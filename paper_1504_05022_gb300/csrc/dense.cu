@@ -329,6 +329,12 @@ SPG_DEV int64_t dense_next(unsigned long long *counter, int64_t cur, bool first,
     return *s_b;
 }
 
+// Starts moving `bytes` (a multiple of 16) at p (16-byte aligned) from memory into L2; the
+// copy completes on its own, nothing waits for it.
+SPG_DEV void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 SPG_DEV int64_t dense_items(const DenseArgs &D) { return (D.dev_n != nullptr ? *D.dev_n : D.n) * (int64_t)D.K; }
 
 // The columns of slice s that row d of the dense items can reach: [lo, lo + span).
@@ -780,12 +786,15 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
     for (int w0 = 0; w0 < nwords;) {
         // the last word end w1 with rank_at(w1) - Rd[w0] <= vcap (a word holds <= 32 <= vcap entries)
         const int e0 = Rd[w0];
-        int lo_ = w0 + 1, hi = nwords;
-        while (lo_ < hi) {
-            const int mid = (lo_ + hi + 1) >> 1;
-            if (rank_at(mid) - e0 <= vcap) lo_ = mid; else hi = mid - 1;
+        int w1 = nwords;  // the rest of the slice, when it fits
+        if (tot - e0 > vcap) {
+            int lo_ = w0 + 1, hi = nwords;
+            while (lo_ < hi) {
+                const int mid = (lo_ + hi + 1) >> 1;
+                if (rank_at(mid) - e0 <= vcap) lo_ = mid; else hi = mid - 1;
+            }
+            w1 = lo_;
         }
-        const int w1 = lo_;
         const int n = rank_at(w1) - e0;
         const int x0 = w0 << 5, x1 = min(span, w1 << 5);
         for (int k = threadIdx.x; k < n; k += NT) V[k] = val_t(0);
@@ -813,16 +822,30 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
             return;
         }
         // write-out: the sums in column order (contiguous), and the columns word by word
+        // (a thread takes a 16-byte group of words when the piece starts on one)
         for (int k = threadIdx.x; k < n; k += NT) c_val[o + e0 + k] = V[k];
         if (!REPLAY) {
-            for (int w = w0 + (int)threadIdx.x; w < w1; w += NT) {
-                uint32_t bits = Bm[w];
-                int64_t q = o + Rd[w];
+            auto put = [&](int w, uint32_t bits, int r) {
+                int64_t q = o + r;
                 while (bits) {
                     const int t = __ffs(bits) - 1;
                     bits &= bits - 1u;
                     c_col[q++] = (int32_t)(lo + ((int64_t)w << 5) + t);
                 }
+            };
+            if ((w0 & 3) == 0) {
+                for (int g = (w0 >> 2) + (int)threadIdx.x; g < (w1 + 3) >> 2; g += NT) {
+                    const int w = g << 2;
+                    const uint4 bv = *reinterpret_cast<const uint4 *>(Bm + w);
+                    if ((bv.x | bv.y | bv.z | bv.w) == 0u) continue;
+                    const int4 rv = *reinterpret_cast<const int4 *>(Rd + w);  // entries past w1 are not used
+                    put(w, bv.x, rv.x);
+                    if (w + 1 < w1) put(w + 1, bv.y, rv.y);
+                    if (w + 2 < w1) put(w + 2, bv.z, rv.z);
+                    if (w + 3 < w1) put(w + 3, bv.w, rv.w);
+                }
+            } else {
+                for (int w = w0 + (int)threadIdx.x; w < w1; w += NT) put(w, Bm[w], Rd[w]);
             }
         }
         __syncthreads();  // V is reused by the next piece
@@ -835,11 +858,26 @@ template <int NT, int MINB, bool REPLAY, bool WIDE>
 __global__ void __launch_bounds__(NT, MINB)
 k_dense_fill(DevCSR A, DevCSR B, DenseArgs D, const int64_t *c_rp, int32_t *c_col, val_t *c_val, int64_t *err,
              const int64_t *gate, int vcap, unsigned long long *counter, int cmin, int cmax) {
-    __shared__ int64_t s_b;
+    __shared__ int64_t s_b, s_nx;
     if (gated(gate)) return;
     const int64_t nb = dense_items(D);
-    for (int64_t b = dense_next(counter, 0, true, &s_b); b < nb; b = dense_next(counter, b, false, &s_b))
+    int64_t b = dense_next(counter, 0, true, &s_b);
+    while (b < nb) {
+        // the CTA's next item is taken one item ahead, so that its kept bitmap (written by the
+        // counting pass, long out of L2) is on its way into L2 while this item is filled
+        if (threadIdx.x == 0) {
+            const int64_t nx = counter != nullptr ? (int64_t)atomicAdd(counter, 1ull) : b + gridDim.x;
+            s_nx = nx;
+            if (!REPLAY && D.keep != nullptr && nx < nb) {
+                const int c = D.cnt[nx];
+                if (c > cmin && c <= cmax) prefetch_l2(D.keep + nx * (int64_t)D.keep_words, 4u * (uint32_t)D.keep_words);
+            }
+        }
         dense_fill_item<NT, REPLAY, WIDE>(A, B, D, b, c_rp, c_col, c_val, err, vcap, cmin, cmax);
+        __syncthreads();  // s_nx is visible and the item's shared memory is free
+        b = s_nx;
+        __syncthreads();  // every thread has read s_nx before thread 0 overwrites it
+    }
 }
 
 // One thread per dense item (precise method): the slices' offsets inside the row and the
