@@ -241,6 +241,7 @@ def measure(args, spg, pairs, dev, stream, policy, flush, world, sample_clocks=F
         if value_type == "f32" and autotune.load(tw + ":f32", policy):
             tw = tw + ":f32"
     opts, keep = policy_opts(policy, tw, value_type)
+    spg.pool_trim(dev.index)  # every policy starts from a pool holding no memory of the previous one
     timing_opts = dict(opts, record_timing=True)  # per-kernel split, taken in one extra untimed step
     vdt = torch.float32 if value_type == "f32" else torch.float64
     Ad = [spg.CSR.from_host(A, device=dev, rowptr_dtype=torch.int32, dtype=vdt) for A, _ in pairs]
@@ -442,6 +443,7 @@ class BatchRig:
 
     def batched(self, policy, clocks=False, wave_mproducts=0, tuned=False):
         """One BatchPlan per step.  Returns (figures, the last step's plan, objects to keep alive)."""
+        self.spg.pool_trim(self.dev.index)
         import torch
         args, spg = self.args, self.spg
         opts, keep = policy_opts(policy, "batch512" if tuned and args.tuned else None)
@@ -476,6 +478,7 @@ class BatchRig:
 
     def sequential(self, policy):
         """The 512 pairs as 512 plain calls, one after another, on one stream."""
+        self.spg.pool_trim(self.dev.index)
         args, spg = self.args, self.spg
         opts, keep = policy_opts(policy)
 
@@ -500,6 +503,7 @@ class BatchRig:
 
     def replay_graph(self, policy):
         """Values-only replay (structure reused) of the batched plan, captured in one CUDA graph."""
+        self.spg.pool_trim(self.dev.index)
         import torch
         args, spg = self.args, self.spg
         opts, keep_g = policy_opts(policy, "batch512" if args.tuned else None)
@@ -519,6 +523,7 @@ class BatchRig:
     def device_graph(self, capacity):
         """The whole batch -- concatenation and stages 1-4, every size on the device (precise
         method, persistent per-bin kernels) -- captured in one CUDA graph."""
+        self.spg.pool_trim(self.dev.index)
         import torch
         args, spg = self.args, self.spg
         gstream = torch.cuda.Stream(self.dev)

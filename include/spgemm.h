@@ -221,6 +221,15 @@ spgemm_status spgemm_numeric(spgemm_plan *plan, spgemm_csr_out *C_out);
    the plan itself.  NULL is accepted. */
 spgemm_status spgemm_free(spgemm_plan *plan);
 
+/* Every plan allocates from one stream-ordered memory pool per device, which keeps the
+   blocks freed by earlier plans for reuse (no release threshold), so a process that ran a
+   large product keeps holding that device memory.  This returns the pool's unused memory
+   on `device` to the system, keeping at most keep_bytes (cudaMemPoolTrimTo).  Synchronise
+   the streams of the plans freed on that device first: blocks whose stream-ordered free has
+   not run yet are still in use.  SPGEMM_ERR_INVALID_ARG for a negative device or
+   keep_bytes; no-op for a device the library has not allocated on. */
+spgemm_status spgemm_pool_trim(int32_t device, int64_t keep_bytes);
+
 /* Static English text for a status code. */
 const char *spgemm_status_string(spgemm_status status);
 

@@ -62,6 +62,7 @@ SIGNATURES = {
                          ctypes.POINTER(c_ptr), ctypes.POINTER(c_i64)], c_i32),
     "spgemm_numeric": ([c_ptr, ctypes.POINTER(CsrOut)], c_i32),
     "spgemm_free": ([c_ptr], c_i32),
+    "spgemm_pool_trim": ([c_i32, c_i64], c_i32),
     "spgemm_status_string": ([c_i32], ctypes.c_char_p),
     "spgemm_plan_stats": ([c_ptr, ctypes.POINTER(Stats)], c_i32),
     "spgemm_plan_arrays_get": ([c_ptr, ctypes.POINTER(PlanArrays)], c_i32),

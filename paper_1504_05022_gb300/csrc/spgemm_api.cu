@@ -1270,6 +1270,18 @@ extern "C" spgemm_status spgemm_merge_micro(int32_t method, int32_t threads, int
     return from_cuda(e);
 }
 
+extern "C" spgemm_status spgemm_pool_trim(int32_t device, int64_t keep_bytes) {
+    if (device < 0 || keep_bytes < 0) return SPGEMM_ERR_INVALID_ARG;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        for (auto &q : g_pools)
+            if (q.device == device) pool = q.pool;
+    }
+    if (pool == nullptr) return SPGEMM_OK;
+    return from_cuda(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
+}
+
 extern "C" spgemm_status spgemm_free(spgemm_plan *p) {
     if (!p) return SPGEMM_OK;
     p->release();

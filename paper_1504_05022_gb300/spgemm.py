@@ -341,6 +341,15 @@ class BatchPlan(Plan):
         return {k: np.concatenate([p[k] for p in parts]) for k in ("u", "bin", "row_nnz")}
 
 
+def pool_trim(device: int = 0, keep_bytes: int = 0) -> None:
+    """Returns the device memory that the libraries' pools (double and single precision) keep
+    for reuse on `device` to the system, down to keep_bytes each (synchronises the device
+    first)."""
+    torch.cuda.synchronize(device)
+    for dt in ("f64", "f32"):
+        _lib.check(_lib.load(dtype=dt).spgemm_pool_trim(int(device), int(keep_bytes)), "spgemm_pool_trim")
+
+
 def spgemm_batched(As, Bs, stream=None, **opts):
     """[A_i * B_i] for all pairs, computed as one block-diagonal product."""
     return BatchPlan(As, Bs, stream=stream, **opts).numeric()

@@ -83,6 +83,8 @@ def test_argument_errors_without_gpu(lib):
     assert lib.spgemm_symbolic(ctypes.byref(A), ctypes.byref(B), None, None, None, None) == 1
     assert lib.spgemm_numeric(None, None) == 1
     assert lib.spgemm_free(None) == 0
+    assert lib.spgemm_pool_trim(-1, 0) == 1 and lib.spgemm_pool_trim(0, -1) == 1
+    assert lib.spgemm_pool_trim(0, 0) == 0  # no pool yet: nothing to return
 
 
 def test_every_field_offset_matches_the_c_compiler(tmp_path):

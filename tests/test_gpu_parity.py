@@ -381,3 +381,20 @@ def test_bitmap_kernel_two_level_rmat(spg, oracle_mod):
     plan, C = run(spg, A, A, merge_kernel="bitmap", dense_min_u=-1)
     check(oracle_mod, A, A, C, label="two-level R-MAT 2^18")
     assert plan.stats()["bin_count"][37] > 0
+
+
+def test_pool_trim_returns_memory_and_products_stay_exact(spg, oracle_mod):
+    """The library's pool keeps freed blocks; pool_trim hands them back to the system, and the
+    next product (which maps fresh memory) is still the oracle's."""
+    A = gen.rmat(13, 16, seed=81)
+    Ad = spg.CSR.from_host(A)
+    C = spg.spgemm(Ad, Ad)
+    check(oracle_mod, A, A, C, label="before trim")
+    del C
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    spg.pool_trim()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0
+    C = spg.spgemm(Ad, Ad)
+    check(oracle_mod, A, A, C, label="after trim")
