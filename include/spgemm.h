@@ -189,6 +189,12 @@ typedef struct spgemm_opts {
                                 precise policy (whose peak stays C plus O(rows) tables); positive = the
                                 same test under every policy; negative = never.  Products sized on the
                                 device never keep them (their tables are sized for every row) */
+    int64_t max_bytes;       /* device bytes the plan may hold at once (0 = no limit): an allocation
+                                that would exceed it fails as if the device were full and the call
+                                returns SPGEMM_ERR_OOM (the kept bitmaps of dense_keep are skipped
+                                instead).  A failed spgemm_symbolic leaves nothing allocated; a
+                                failed spgemm_numeric leaves its temporaries with the plan until
+                                spgemm_free releases them */
 } spgemm_opts;
 
 /* Fills *opts with the defaults (hybrid policy, initial_cap 256, no checks). */

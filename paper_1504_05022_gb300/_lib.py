@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("merge_wide_above", c_i32), ("merge_kernel", c_i32), ("merge_miss", c_i32),
                 ("dense_min_u", c_i32), ("dense_span", c_i32), ("dense_span_div", c_i32),
                 ("predictor", c_ptr),
-                ("predictor_margin", c_f64), ("dense_pred_min", c_i32), ("dense_keep", c_i32)]
+                ("predictor_margin", c_f64), ("dense_pred_min", c_i32), ("dense_keep", c_i32),
+                ("max_bytes", c_i64)]
 
 
 class Stats(ctypes.Structure):

@@ -235,6 +235,10 @@ struct spgemm_plan {
 
     cudaError_t alloc(void **p, size_t bytes, int life = LIFE_PLAN) {
         if (bytes == 0) bytes = 16;
+        if (opts.max_bytes > 0 && bytes_held + (int64_t)bytes > opts.max_bytes) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
         const auto t0 = std::chrono::steady_clock::now();
         cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, st);
         stats.alloc_host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

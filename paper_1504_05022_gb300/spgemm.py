@@ -127,7 +127,7 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
               predictor_margin: float = 1.0, wave_mproducts: int = 0, heap_max_u: int = 0,
               merge_wide_above: int = 0, merge_kernel: str = "auto", merge_miss: int = 0,
               dense_min_u: int = 0, dense_span: int = 0, dense_span_div: int = 0,
-              dense_pred_min: int = 0, dense_keep: int = 0) -> _lib.Opts:
+              dense_pred_min: int = 0, dense_keep: int = 0, max_bytes: int = 0) -> _lib.Opts:
     L = _lib.load()
     o = _lib.Opts()
     _lib.check(L.spgemm_opts_init(ctypes.byref(o)), "spgemm_opts_init")
@@ -149,6 +149,7 @@ def make_opts(alloc_policy: str = "hybrid", initial_cap: int = 256, check_inputs
     o.dense_span_div = int(dense_span_div)
     o.dense_pred_min = int(dense_pred_min)
     o.dense_keep = int(dense_keep)
+    o.max_bytes = int(max_bytes)
     # a Predictor object (whose device weights the caller keeps alive) or a raw handle
     o.predictor = getattr(predictor, "handle", predictor)
     o.predictor_margin = float(predictor_margin)

@@ -64,8 +64,9 @@ def test_struct_layout_matches_header():
     from paper_1504_05022_gb300 import _lib
     assert ctypes.sizeof(_lib.CsrIn) == 56
     assert ctypes.sizeof(_lib.CsrOut) == 48
-    assert _lib.Opts.predictor.offset == 64 and ctypes.sizeof(_lib.Opts) == 88
+    assert _lib.Opts.predictor.offset == 64 and ctypes.sizeof(_lib.Opts) == 96
     assert _lib.Opts.dense_pred_min.offset == 80 and _lib.Opts.dense_keep.offset == 84
+    assert _lib.Opts.max_bytes.offset == 88
     assert _lib.Stats.launches.offset == 38 * 8 + 10 * 8
     assert _lib.Opts.long_rows.offset == 7 * 4
 

@@ -54,14 +54,14 @@ def test_make_opts_sets_every_field():
                   merge_batch=1024, smem_cap_max=4096, heap_block=64, long_rows="level1", predictor=12345,
                   predictor_margin=1.5, wave_mproducts=7, heap_max_u=16, merge_wide_above=2048,
                   merge_kernel="bitmap", merge_miss=8192, dense_min_u=-1, dense_span=10912, dense_span_div=16,
-                  dense_pred_min=4096, dense_keep=-1)
+                  dense_pred_min=4096, dense_keep=-1, max_bytes=1 << 40)
     got = {name: getattr(o, name) for name, _ in _lib.Opts._fields_}
     assert got == {"alloc_policy": 1, "initial_cap": 512, "check_inputs": 1, "record_timing": 1,
                    "merge_batch": 1024, "smem_cap_max": 4096, "heap_block": 64, "long_rows": 1,
                    "wave_mproducts": 7, "heap_max_u": 16, "merge_wide_above": 2048, "merge_kernel": 2,
                    "merge_miss": 8192, "dense_min_u": -1, "dense_span": 10912, "dense_span_div": 16,
                    "predictor": 12345, "predictor_margin": 1.5, "dense_pred_min": 4096,
-                   "dense_keep": -1}
+                   "dense_keep": -1, "max_bytes": 1 << 40}
 
     class _Pred:
         handle = 777
