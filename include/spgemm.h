@@ -236,6 +236,15 @@ spgemm_status spgemm_free(spgemm_plan *plan);
    keep_bytes; no-op for a device the library has not allocated on. */
 spgemm_status spgemm_pool_trim(int32_t device, int64_t keep_bytes);
 
+/* The bounds-checked build (libspgemm_check.so: the same sources with SPGEMM_CHECK defined).
+   Its kernels check the indices of their result writes and shared-memory scatters; an index
+   outside its array records a site code (the first one recorded stays) and the access is
+   skipped, without a trap, so the context stays usable.  *code_out = 0 when no check failed
+   since the last reset, the first code recorded otherwise, and -1 in a build without the
+   checks.  reset != 0 clears the record.  Synchronise the device first; SPGEMM_ERR_INVALID_ARG
+   for a NULL code_out. */
+spgemm_status spgemm_check_status(int64_t *code_out, int32_t reset);
+
 /* Static English text for a status code. */
 const char *spgemm_status_string(spgemm_status status);
 

@@ -20,8 +20,11 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libspgemm.so")
 LIB_F32 = os.path.join(BUILD, "libspgemm_f32.so")
-# value type -> (library, object directory, extra nvcc flags)
-VARIANTS = {"f64": (LIB, BUILD, []), "f32": (LIB_F32, os.path.join(BUILD, "f32"), ["-DSPGEMM_FLOAT"])}
+LIB_CHECK = os.path.join(BUILD, "check", "libspgemm_check.so")
+# variant -> (library, object directory, extra nvcc flags); "check" is the bounds-checked
+# double-precision build (SPGEMM_CHECK), made only on request
+VARIANTS = {"f64": (LIB, BUILD, []), "f32": (LIB_F32, os.path.join(BUILD, "f32"), ["-DSPGEMM_FLOAT"]),
+            "check": (LIB_CHECK, os.path.join(BUILD, "check"), ["-DSPGEMM_CHECK"])}
 
 SOURCES = ["stage12.cu", "heap.cu", "esc.cu", "merge.cu", "merge_bm.cu", "dense.cu", "merge_micro.cu", "arrange.cu", "predictor.cu", "replay.cu", "batched.cu",
            "spgemm_api.cu", "noalloc.cu"]
@@ -51,13 +54,15 @@ def _digest() -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link both libraries where a source changed; returns libspgemm.so's path."""
+def build(force: bool = False, verbose: bool = False, extra_flags=(), variants=("f64", "f32")) -> str:
+    """Compile and link the libraries of `variants` (both precisions by default) where a
+    source changed; returns the first variant's library path."""
     nvcc = _nvcc()
     todo = []
-    for name, (lib, odir, vflags) in VARIANTS.items():
+    for name in variants:
+        lib, odir, vflags = VARIANTS[name]
         os.makedirs(odir, exist_ok=True)
-        stamp = os.path.join(odir, "stamp.txt" if name == "f64" else "stamp_f32.txt")
+        stamp = os.path.join(odir, "stamp.txt" if name != "f32" else "stamp_f32.txt")
         dig = _digest() + repr(tuple(extra_flags) + tuple(vflags))
         if not force and os.path.exists(lib) and os.path.exists(stamp):
             with open(stamp) as f:
@@ -65,7 +70,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                     continue
         todo.append((lib, odir, _flags(list(extra_flags) + vflags), stamp, dig))
     if not todo:
-        return LIB
+        return VARIANTS[variants[0]][0]
 
     def compile_one(job):
         src, odir, flags = job
@@ -91,7 +96,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         os.replace(tmp, lib)
         with open(stamp, "w") as f:
             f.write(dig)
-    return LIB
+    return VARIANTS[variants[0]][0]
+
+
+def build_check(force: bool = False) -> str:
+    """The bounds-checked double-precision library (SPGEMM_CHECK); returns its path."""
+    return build(force=force, variants=("check",))
 
 
 if __name__ == "__main__":

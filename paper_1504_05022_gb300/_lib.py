@@ -64,6 +64,7 @@ SIGNATURES = {
     "spgemm_numeric": ([c_ptr, ctypes.POINTER(CsrOut)], c_i32),
     "spgemm_free": ([c_ptr], c_i32),
     "spgemm_pool_trim": ([c_i32, c_i64], c_i32),
+    "spgemm_check_status": ([ctypes.POINTER(c_i64), c_i32], c_i32),
     "spgemm_status_string": ([c_i32], ctypes.c_char_p),
     "spgemm_plan_stats": ([c_ptr, ctypes.POINTER(Stats)], c_i32),
     "spgemm_plan_arrays_get": ([c_ptr, ctypes.POINTER(PlanArrays)], c_i32),
@@ -108,8 +109,15 @@ _libs = {}           # value type ("f64", "f32") -> loaded library
 VALUE_TYPES = ("f64", "f32")
 
 
+def checked() -> bool:
+    """SPGEMM_CHECKED=1 selects the bounds-checked build for double precision."""
+    return os.environ.get("SPGEMM_CHECKED") == "1"
+
+
 def lib_path(dtype: str = "f64") -> str:
-    return _build.LIB_F32 if dtype == "f32" else _build.LIB
+    if dtype == "f32":
+        return _build.LIB_F32
+    return _build.LIB_CHECK if checked() else _build.LIB
 
 
 def load(build_if_missing: bool = True, dtype: str = "f64"):
@@ -126,7 +134,10 @@ def load(build_if_missing: bool = True, dtype: str = "f64"):
     if not os.path.exists(path):
         if not build_if_missing:
             raise ImportError(f"{os.path.basename(path)} not built ({path}); run __graft_entry__.build()")
-        _build.build()
+        if dtype == "f64" and checked():
+            _build.build_check()
+        else:
+            _build.build()
     lib = ctypes.CDLL(path)
     for name, (args, res) in SIGNATURES.items():
         fn = getattr(lib, name)

@@ -52,7 +52,7 @@ k_arrange_short(StageArgs a, RowSet R, const uint8_t *__restrict__ bin,
                 }
                 const unsigned m = __ballot_sync(SPG_FULL, hit);
                 if (m) {
-                    if (lane == __ffs(m) - 1) {
+                    if (lane == __ffs(m) - 1 && SPG_IN(o < c_rp[row + 1], 103)) {
                         c_col[o] = a.B.col[b0];
                         c_val[o] = a.A.val[p] * a.B.val[b0];
                     }
@@ -63,6 +63,7 @@ k_arrange_short(StageArgs a, RowSet R, const uint8_t *__restrict__ bin,
         }
         const int64_t n = c_rp[row + 1] - o;
         const int64_t src = a.ctil_rp[row];
+        if (!SPG_IN(src + n <= a.ctil_rp[row + 1], 104)) continue;  // C~ holds the row
         for (int64_t t = lane; t < n; t += 32) {
             c_col[o + t] = a.ctil_col[src + t];
             c_val[o + t] = a.ctil_val[src + t];
@@ -138,6 +139,7 @@ k_arrange_long(MergeItems it, const int64_t *__restrict__ c_rp, int32_t *__restr
             const int64_t n = it.len[x];
             const int32_t *sc = it.home_col[x];
             const val_t *sv = it.home_val[x];
+            if (!SPG_IN(o + n <= c_rp[it.row[j] + 1], 105)) break;  // the leaves fill the row of C exactly
             for (int64_t t = threadIdx.x; t < n; t += ARR_NT) {
                 c_col[o + t] = sc[t];
                 c_val[o + t] = sv[t];

@@ -18,6 +18,31 @@ constexpr int32_t KEY_PAD = INT_MAX;
 
 SPG_DEV int lane_id() { return threadIdx.x & 31; }
 
+// ---- the bounds-checked build ----
+// Built with SPGEMM_CHECK, SPG_IN(cond, code) records `code` in this translation unit's
+// status word when cond is false (the first code recorded stays) and yields false, so that
+// the caller skips the access; the kernel carries on (no trap) and the host reads the words
+// with spgemm_check_status.  Without SPGEMM_CHECK it is `true` and costs nothing.
+#ifdef SPGEMM_CHECK
+static __device__ unsigned long long spg_check_word;
+SPG_DEV bool spg_in(bool ok, int code) {
+    if (!ok) atomicCAS(&spg_check_word, 0ull, (unsigned long long)code);
+    return ok;
+}
+#define SPG_IN(cond, code) (::spg::spg_in((cond), (code)))
+static cudaError_t spg_read_check_word(unsigned long long *out, bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, spg_check_word, sizeof(*out));
+    if (e == cudaSuccess && reset) {
+        const unsigned long long zero = 0;
+        e = cudaMemcpyToSymbol(spg_check_word, &zero, sizeof(zero));
+    }
+    return e;
+}
+static const int spg_check_registered = register_check_reader(spg_read_check_word);
+#else
+#define SPG_IN(cond, code) (true)
+#endif
+
 // The rows of a RowSet: host-known, or a range of `rows` whose ends are read here.
 SPG_DEV void rowset_range(const RowSet &R, const int32_t *&rows, int64_t &n) {
     if (R.dev_lo != nullptr) {

@@ -745,6 +745,7 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
             if (wd == 0u) continue;
             if ((wd >> (x & 31)) & 1u) {
                 const int64_t pos = o + Rd[x >> 5] + __popc(wd & ((1u << (x & 31)) - 1u));
+                if (!SPG_IN(pos < o + expected, 112)) continue;  // the slice's entries of C
                 c_col[pos] = (int32_t)(lo + x);
                 c_val[pos] = V[x];
             }
@@ -808,13 +809,13 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
             [&](int x, val_t v) {
                 const int q = pos_of(x);
                 if (q < 0) return false;  // a column the bitmap does not hold: cannot happen
-                atomicAdd(&V[q], v);
+                if (SPG_IN(q < n, 109)) atomicAdd(&V[q], v);
                 return true;
             },
             [&](int x, val_t v) {
                 const int q = pos_of(x);
                 if (q < 0) return false;
-                V[q] += v;
+                if (SPG_IN(q < n, 109)) V[q] += v;
                 return true;
             });
         if (__syncthreads_or(bad)) {
@@ -823,9 +824,11 @@ SPG_DEV void dense_fill_item(const DevCSR &A, const DevCSR &B, const DenseArgs &
         }
         // write-out: the sums in column order (contiguous), and the columns word by word
         // (a thread takes a 16-byte group of words when the piece starts on one)
-        for (int k = threadIdx.x; k < n; k += NT) c_val[o + e0 + k] = V[k];
+        if (SPG_IN(e0 + n <= expected, 111))
+            for (int k = threadIdx.x; k < n; k += NT) c_val[o + e0 + k] = V[k];
         if (!REPLAY) {
             auto put = [&](int w, uint32_t bits, int r) {
+                if (!SPG_IN(r + __popc(bits) <= expected, 110)) return;  // the slice's entries of C
                 int64_t q = o + r;
                 while (bits) {
                     const int t = __ffs(bits) - 1;

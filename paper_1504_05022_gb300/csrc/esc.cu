@@ -184,6 +184,7 @@ k_esc(StageArgs a, RowSet R) {
             const int total = __shfl_sync(SPG_FULL, inc, 31);
             int o = inc - cnt;
             const int64_t base = a.ctil_rp[row];
+            if (!SPG_IN(base + total <= a.ctil_rp[row + 1], 102)) tails = 0;  // the row's space in C~ (or C)
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 if (tails & (1u << e)) {

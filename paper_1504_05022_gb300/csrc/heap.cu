@@ -92,6 +92,7 @@ k_heap(StageArgs a, RowSet R, int slots) {
         }
         const int cnt = n - rs;
         const int64_t o = a.ctil_rp[row];
+        if (!SPG_IN(o + cnt <= a.ctil_rp[row + 1], 101)) continue;  // the row's space in C~ (or C)
         for (int r = 0; r < cnt; ++r) {
             a.ctil_col[o + r] = HK(rs + r);
             a.ctil_val[o + r] = HV(rs + r);

@@ -108,6 +108,11 @@ cudaError_t launch_class_partition_tail(const int32_t *bin_rows, int64_t m, BinS
 const float *predictor_params(const void *pred);
 
 // ---- stage 3 ----
+// The status words of the bounds-checked build: every translation unit built with
+// SPGEMM_CHECK registers the reader of its word (spgemm_check_status reads them all).
+using CheckReader = cudaError_t (*)(unsigned long long *word, bool reset);
+int register_check_reader(CheckReader read);
+
 struct StageArgs {
     DevCSR A, B;
     const int64_t *ctil_rp;

@@ -265,7 +265,7 @@ SPG_DEV int bm_merge_misses(const BmSmem &s, Index &ix, int rlen, int nm, int32_
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if (np[q] >= 0) {
+            if (np[q] >= 0 && SPG_IN(np[q] < fnew, 108)) {
                 s.Rk[np[q]] = kk[q];
                 s.Rv[np[q]] = vv[q];
             }
@@ -276,11 +276,15 @@ SPG_DEV int bm_merge_misses(const BmSmem &s, Index &ix, int rlen, int nm, int32_
     for (int m = threadIdx.x; m < nm; m += NT) {
         const int32_t c = s.Mk[m];
         const int t = ix.lookup(c - lo);
+        if (!SPG_IN(t >= 0 && t < fnew, 108)) continue;
         s.Rk[t] = c;
         s.Rv[t] = 0.0;
     }
     __syncthreads();
-    for (int m = threadIdx.x; m < nm; m += NT) atomicAdd(&s.Rv[ix.lookup(s.Mk[m] - lo)], s.Mv[m]);
+    for (int m = threadIdx.x; m < nm; m += NT) {
+        const int t = ix.lookup(s.Mk[m] - lo);
+        if (SPG_IN(t >= 0 && t < fnew, 108)) atomicAdd(&s.Rv[t], s.Mv[m]);
+    }
     __syncthreads();
     return fnew;
 }
@@ -489,7 +493,7 @@ k_merge_bm(StageArgs a, MergeItems it, MergeLaunch L) {
             // fuse the hits
 #pragma unroll
             for (int k = 0; k < BM_IPT; ++k)
-                if (rpos[k] >= 0) atomicAdd(&s.Rv[rpos[k]], val[k]);
+                if (rpos[k] >= 0 && SPG_IN(rpos[k] < rlen, 107)) atomicAdd(&s.Rv[rpos[k]], val[k]);
             // (2)-(3) append the misses to the buffer: one shared atomic per warp
             {
                 const int nm = __popc(miss);
@@ -501,8 +505,10 @@ k_merge_bm(StageArgs a, MergeItems it, MergeLaunch L) {
 #pragma unroll
                 for (int k = 0; k < BM_IPT; ++k) {
                     if ((miss >> k) & 1u) {
-                        s.Mk[slot] = key[k];
-                        s.Mv[slot] = val[k];
+                        if (SPG_IN(slot < mcap, 106)) {
+                            s.Mk[slot] = key[k];
+                            s.Mv[slot] = val[k];
+                        }
                         ++slot;
                     }
                 }

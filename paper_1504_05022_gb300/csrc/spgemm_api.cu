@@ -1274,6 +1274,35 @@ extern "C" spgemm_status spgemm_merge_micro(int32_t method, int32_t threads, int
     return from_cuda(e);
 }
 
+namespace spg {
+static std::vector<CheckReader> &check_readers() {
+    static std::vector<CheckReader> readers;
+    return readers;
+}
+int register_check_reader(CheckReader read) {
+    check_readers().push_back(read);
+    return 0;
+}
+}  // namespace spg
+
+extern "C" spgemm_status spgemm_check_status(int64_t *code_out, int32_t reset) {
+    if (!code_out) return SPGEMM_ERR_INVALID_ARG;
+#ifdef SPGEMM_CHECK
+    int64_t first = 0;
+    for (spg::CheckReader read : spg::check_readers()) {
+        unsigned long long w = 0;
+        cudaError_t e = read(&w, reset != 0);
+        if (e != cudaSuccess) return from_cuda(e);
+        if (first == 0 && w != 0) first = (int64_t)w;
+    }
+    *code_out = first;
+#else
+    (void)reset;
+    *code_out = -1;
+#endif
+    return SPGEMM_OK;
+}
+
 extern "C" spgemm_status spgemm_pool_trim(int32_t device, int64_t keep_bytes) {
     if (device < 0 || keep_bytes < 0) return SPGEMM_ERR_INVALID_ARG;
     cudaMemPool_t pool = nullptr;

@@ -86,6 +86,9 @@ def test_argument_errors_without_gpu(lib):
     assert lib.spgemm_free(None) == 0
     assert lib.spgemm_pool_trim(-1, 0) == 1 and lib.spgemm_pool_trim(0, -1) == 1
     assert lib.spgemm_pool_trim(0, 0) == 0  # no pool yet: nothing to return
+    code = ctypes.c_int64(0)
+    assert lib.spgemm_check_status(None, 0) == 1
+    assert lib.spgemm_check_status(ctypes.byref(code), 0) == 0 and code.value == -1  # not the checked build
 
 
 def test_every_field_offset_matches_the_c_compiler(tmp_path):
