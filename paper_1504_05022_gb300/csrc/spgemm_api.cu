@@ -52,7 +52,10 @@ cudaError_t get_pool(int device, cudaMemPool_t *out) {
     return cudaSuccess;
 }
 
-// Small pinned host blocks for the few device->host size reads of a call.
+// Small pinned host blocks for the few device->host size reads of a call, mapped into the
+// device's address space: a kernel stores the sizes there, so the reads do not go through a
+// copy engine and never queue behind large copies that other streams have in flight (a
+// caller copying one result to the host while the next product runs).
 std::mutex g_pin_mu;
 std::vector<void *> g_pinned_free;
 constexpr size_t PIN_BYTES = 4096;
@@ -67,8 +70,21 @@ void *get_pinned() {
         }
     }
     void *p = nullptr;
-    if (cudaMallocHost(&p, PIN_BYTES) != cudaSuccess) return nullptr;
+    if (cudaHostAlloc(&p, PIN_BYTES, cudaHostAllocMapped) != cudaSuccess) return nullptr;
     return p;
+}
+
+static_assert(sizeof(BinSummary) <= PIN_BYTES, "the stage-2 summary is read through one pinned block");
+
+__global__ void k_read_bytes(const unsigned char *__restrict__ src, unsigned char *dst, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+__global__ void k_read_words2(const int64_t *a, const int64_t *b, int64_t *dst) {
+    if (threadIdx.x == 0) {
+        dst[0] = *a;
+        dst[1] = *b;
+    }
 }
 
 // Auxiliary streams (created once, kept for the process): the learned launch classes of
@@ -287,8 +303,13 @@ struct spgemm_plan {
     // two 8-byte device words with one synchronisation
     cudaError_t d2h2(int64_t *dst, const int64_t *src0, const int64_t *src1) {
         int64_t *pin = static_cast<int64_t *>(pinned);
-        cudaError_t e = cudaMemcpyAsync(pin, src0, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(pin + 1, src1, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        void *dev = nullptr;
+        cudaError_t e = cudaHostGetDevicePointer(&dev, pinned, 0);
+        if (e == cudaSuccess) {
+            k_read_words2<<<1, 32, 0, st>>>(src0, src1, static_cast<int64_t *>(dev));
+            e = cudaGetLastError();
+            count(SPGEMM_K_OTHER);
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
         dst[0] = pin[0];
@@ -296,7 +317,16 @@ struct spgemm_plan {
         return cudaSuccess;
     }
     cudaError_t d2h(void *dst, const void *src, size_t bytes) {
-        cudaError_t e = cudaMemcpyAsync(pinned, src, bytes, cudaMemcpyDeviceToHost, st);
+        cudaError_t e;
+        void *dev = nullptr;
+        if (bytes <= PIN_BYTES && (e = cudaHostGetDevicePointer(&dev, pinned, 0)) == cudaSuccess) {
+            k_read_bytes<<<1, 256, 0, st>>>(static_cast<const unsigned char *>(src), static_cast<unsigned char *>(dev),
+                                            (int)bytes);
+            e = cudaGetLastError();
+            count(SPGEMM_K_OTHER);
+        } else {
+            e = bytes <= PIN_BYTES ? e : cudaErrorInvalidValue;  // the pinned block holds PIN_BYTES
+        }
         if (e != cudaSuccess) return e;
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
