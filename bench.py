@@ -739,7 +739,7 @@ def run_ours(args, rank, world, device):
         # the same product in single precision (the paper's SpSGEMM), same policy and parameters
         cmp[head + "_f32"] = measure(args, spg, pairs, dev, stream, head, flush, world, tuned=True, value_type="f32")
     e2e_opts, e2e_keep = policy_opts(head, TUNED_AS.get(args.workload, args.workload) if args.tuned else None)  # keeps the predictor alive
-    e2e = run_e2e(args, spg, pairs, dev, stream, e2e_opts, world)
+    e2e = None if args.no_e2e else run_e2e(args, spg, pairs, dev, stream, e2e_opts, world)
     chain = galerkin_graph(args, spg, dev, stream, flush, e2e_opts, world) if args.workload == "galerkin64" else None
     del e2e_keep
 
@@ -1092,6 +1092,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch-compare", action="store_true",
                     help="R-MAT 2^20 line: do not also time the 512-pair batch (batched against sequential calls)")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end figure (profiling runs: every product of the run is then a whole one)")
     ap.add_argument("--no-tuned", dest="tuned", action="store_false",
                     help="do not apply the autotuner's parameters to the reported policy")
     ap.add_argument("--merge-kernel", default="auto", choices=["auto", "merge_path", "bitmap"],
