@@ -710,6 +710,7 @@ def roofline(args, pairs, m):
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "compulsory_bytes_per_step": comp, "compulsory_gbs": comp_gbs, "compulsory_frac": comp_gbs / hbm_peak,
             "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic, "peak_source": peak_src,
+            "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
             "algorithmic_bytes_per_step": bytes_dom, "kernel_ms_per_step": dom_ms,
             "launches_per_step": dom_launches, "fp64": fp64,
             "note": "achieved = algorithmic bytes of the kernel class per step / its summed CUDA-event time per step; "
@@ -801,6 +802,7 @@ def memory_comparison(pairs, c_bytes, head, main_m, cmp):
     return mem
 
 
+NOMINAL_HBM_GBS = 8000.0  # the round nominal HBM3e figure the roofline is also quoted against
 STAGE_BYTES = 1 << 30  # pinned staging buffer for results larger than this
 PIECE_BYTES = 64 << 20  # size of the copies that run beside a product
 
