@@ -62,7 +62,7 @@ SPACE = {
     "merge_miss": [4096, 2048, 8192],
     "initial_cap": [256, 512, 1024],
     "predictor_margin": [None, 1.15, 1.5, 2.0],  # None = the margin stored with the weights
-    "dense_min_u": [0, 16384, 4096, -1],  # 0 = the rule of dense_span_div, -1 = no dense-slice rows
+    "dense_min_u": [0, 16384, 8192, 4096, 2048, 1024, -1],  # 0 = the rule of dense_span_div, -1 = no slice rows
     "dense_span": [0, 65536, 32768, 21856, 16384, 10912],  # 0 = 131,072-column slices (bitmap, compact
                                                            # sums); narrow enough for a sum per column
                                                            # (21,856 and below in double): single-pass
