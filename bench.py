@@ -807,6 +807,21 @@ STAGE_BYTES = 1 << 30  # pinned staging buffer for results larger than this
 PIECE_BYTES = 64 << 20  # size of the copies that run beside a product
 
 
+def row_blocks(A, B, max_blocks=8, block_bytes=4 << 30):
+    """Row ranges [r0, r1) of A, consecutive and covering every row, that split the products of
+    A*B into about equal parts: one block per block_bytes of products at 12 bytes each, at most
+    max_blocks, none empty."""
+    blen = np.diff(B.row_ptr)
+    cs = np.concatenate([[0], np.cumsum(blen[A.col], dtype=np.int64)])
+    u = cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]  # products per row
+    u_sum = int(u.sum())
+    nb = int(min(max_blocks, max(1, -(-u_sum * 12 // block_bytes))))
+    cu = np.concatenate([[0], np.cumsum(u)])
+    cuts = [0] + [int(np.searchsorted(cu, u_sum * b / nb)) for b in range(1, nb)] + [A.nrows]
+    cuts = sorted(set(min(max(c, 0), A.nrows) for c in cuts))
+    return [(r0, r1) for r0, r1 in zip(cuts[:-1], cuts[1:]) if r1 > r0]
+
+
 def run_e2e(args, spg, pairs, dev, stream, opts, world=1):
     """Same metric through the public API with host buffers: every step copies A from pinned
     host memory to the device, computes C = A*A and reads every byte of C (row pointers,
@@ -826,19 +841,11 @@ def run_e2e(args, spg, pairs, dev, stream, opts, world=1):
     A = pairs[0][0]
     hp = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
           for x in (A.row_ptr.astype(np.int32), A.col, A.val)]
-    blen = np.diff(A.row_ptr)
-    cs = np.concatenate([[0], np.cumsum(blen[A.col], dtype=np.int64)])
-    u = cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]  # products per row
-    u_sum = int(u.sum())
-    nb = int(min(8, max(1, -(-u_sum * 12 // (4 << 30)))))  # about 4 GiB of products' bytes per block
-    cu = np.concatenate([[0], np.cumsum(u)])
-    cuts = [0] + [int(np.searchsorted(cu, u_sum * b / nb)) for b in range(1, nb)] + [A.nrows]
-    cuts = sorted(set(min(max(c, 0), A.nrows) for c in cuts))
+    u_sum = int(_products(A))
     blocks = []  # (r0, r1, first entry, pinned rebased row pointers)
-    for r0, r1 in zip(cuts[:-1], cuts[1:]):
-        if r1 > r0:
-            rp = A.row_ptr[r0:r1 + 1]
-            blocks.append((r0, r1, int(rp[0]), torch.from_numpy((rp - rp[0]).astype(np.int32)).pin_memory()))
+    for r0, r1 in row_blocks(A, A):
+        rp = A.row_ptr[r0:r1 + 1]
+        blocks.append((r0, r1, int(rp[0]), torch.from_numpy((rp - rp[0]).astype(np.int32)).pin_memory()))
     h2d = sum(t.numel() * t.element_size() for t in hp)
     if len(blocks) > 1:
         h2d += sum(b[3].numel() * 4 for b in blocks)

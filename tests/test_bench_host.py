@@ -210,3 +210,22 @@ def test_reference_arm_times_exactly_k_steps_after_w(oracle_mod, monkeypatch):
     r = bench.run_reference(_RefArgs("lap2d64", 3, 2))
     assert len(calls) == 5 and "3 timed steps after 2 untimed" in r["sample"]
     assert r["value"] > 0 and r["ms_per_step"] > 0 and r["kind"] == "oracle" and r["cores"] >= 1
+
+
+def test_row_blocks_cover_every_row_and_balance_the_products():
+    """The end-to-end figure's row blocks: consecutive, covering all rows, none empty, at most
+    the block limit, and about equal in products."""
+    import gen
+    A = gen.rmat(12, 16, seed=3)
+    blen = np.diff(A.row_ptr)
+    u = np.array([blen[A.col[A.row_ptr[i]:A.row_ptr[i + 1]]].sum() for i in range(A.nrows)])
+    for max_blocks, block_bytes in ((8, 1 << 20), (3, 1 << 20), (8, 1 << 40)):
+        bl = bench.row_blocks(A, A, max_blocks=max_blocks, block_bytes=block_bytes)
+        assert bl[0][0] == 0 and bl[-1][1] == A.nrows
+        assert all(r1 > r0 for r0, r1 in bl) and all(bl[k][1] == bl[k + 1][0] for k in range(len(bl) - 1))
+        assert 1 <= len(bl) <= max_blocks
+        if block_bytes == 1 << 40:
+            assert len(bl) == 1
+        else:
+            parts = [int(u[r0:r1].sum()) for r0, r1 in bl]
+            assert max(parts) <= u.sum() / len(bl) + u.max()  # a cut falls within one row of the target
