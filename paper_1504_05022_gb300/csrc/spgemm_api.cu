@@ -571,7 +571,7 @@ static spgemm_status plan_symbolic_core(spgemm_plan *p) {
         SPG_TRY(cudaMemsetAsync(p->d_summary, 0, sizeof(BinSummary), p->st));
         SPG_TRY(cudaMemsetAsync(p->d_err, 0, sizeof(int64_t), p->st));
         if (o.check_inputs) {
-            // the verdict is read before any kernel indexes B through A's columns
+            // the check's result is read before any kernel indexes B through A's columns
             p->time_begin(SPGEMM_K_OTHER);
             SPG_TRY(launch_validate(p->A, &p->d_summary->status, p->st));
             SPG_TRY(launch_validate(p->B, &p->d_summary->status, p->st));

@@ -1,6 +1,6 @@
 """Host side of the learned preallocation, on the CPU: the training recipe, the parameter
 layout shared with the device kernels, the rounding of a predicted row size, and the stored
-weights judged by the oracle on matrices the training held out (every seed s with s % 5 == 2).
+weights checked with the oracle on matrices the training held out (every seed s with s % 5 == 2).
 The network's forward pass here is the oracle's (FP64); its row sizes are the oracle's exact
 counts, so what is measured is the stored network itself."""
 import json
